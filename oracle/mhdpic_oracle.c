@@ -1,0 +1,533 @@
+/*
+ * FP64 CPU oracle of the MHD-PIC cosmic-ray particle update
+ * (Bai, Caprioli, Sironi & Spitkovsky, arXiv:1412.1087).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * reference the CUDA path is checked against.  It shares no code, header,
+ * table or constant with the CUDA library.  Only the test-suite, the smoke
+ * check and the benchmark's CPU-baseline leg may load it; the product path
+ * never does.
+ *
+ * Everything is double precision, one particle at a time, in the order the
+ * paper states the method:
+ *   Section 2.1  eq:emf0, eq:lorentz2, eq:emfcr2   cell-centred electric field
+ *   Section 2.2  eq:4vel, eq:parEk                  four-velocity, gamma, E_k
+ *   Section 3    TSC (quadratic spline) interpolation and deposit
+ *   App. A.1     eq:nJCR, eq:ng                     particle charge / current
+ *   App. A.2     drift-kick-rotate-kick-drift Boris step, E-parallel cleaning
+ *   App. A.3     corrector deposit of -dM, -dE_k at x^(n+1/2)
+ *
+ * Readings where the paper is garbled or silent (each also listed in the
+ * design notes):
+ *   - Boris rotation vector b = (h/2) B / gamma (the standard half angle; the
+ *     printed "b = h B / gamma" would double the rotation angle).
+ *   - E-parallel cleaning E <- E - (E.B) B / |B|^2, skipped when |B| = 0.
+ *   - TSC nodes are cell centres; s = (x - x0)/dx, i = floor(s),
+ *     delta = s - i - 1/2, weights 1/2(1/2-delta)^2, 3/4-delta^2,
+ *     1/2(1/2+delta)^2 on cells i-1, i, i+1.
+ *   - Reflecting boundary: specular (x -> mirror, v_d -> -v_d); a stencil
+ *     cell outside the wall is folded onto its mirror cell.  A particle that
+ *     lands exactly on the upper wall is placed just inside it.
+ *   - m_CR is a per-particle mass; charge and current deposits are divided
+ *     by the cell volume dV, the corrector deposit is a momentum / energy
+ *     and is divided by dV when it is applied to the gas.
+ *   - The kinetic-energy difference E_k(v') - E_k(v), E_k = v^2/(gamma+1),
+ *     is evaluated as (v'-v).(v'+v)/(gamma'+gamma), an exact rewriting that
+ *     avoids cancellation.
+ *   - Without an MHD solver only the corrector deposit is applied to the gas;
+ *     the moments n_CR, J_CR deposited at the end of a step feed R, F_CR and
+ *     the CR-Hall electric field of the next step.
+ *
+ * Array layouts: positions x[d*np + j] (d < ndim), four-velocities
+ * v[d*np + j] (d < 3), cell arrays plane-major a[q*ncell + c] with
+ * c = (k*ny + j)*nx + i.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int32_t ndim;   /* 2 or 3 */
+    int32_t n[3];   /* cells per dimension, n[2] = 1 in 2-D */
+    double dx[3];   /* cell widths, dx[2] is the cell depth in 2-D */
+    double x0[3];   /* lower corner */
+    int32_t bc[3];  /* 0 periodic, 1 reflecting walls on both faces */
+} orc_grid;
+
+typedef struct {
+    double qm_cr;   /* (q/mc) of the CR particles */
+    double qm_gas;  /* (q/mc)_g of the gas ions */
+    double C;       /* artificial speed of light */
+    double m_cr;    /* particle "mass" m_CR */
+    int32_t hall;   /* 1: include the CR-Hall term in the electric field */
+} orc_params;
+
+/* ------------------------------------------------------------------ */
+/* small vector helpers                                                */
+/* ------------------------------------------------------------------ */
+
+static double dot3(const double a[3], const double b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+static void cross3(const double a[3], const double b[3], double out[3])
+{
+    double r0 = a[1] * b[2] - a[2] * b[1];
+    double r1 = a[2] * b[0] - a[0] * b[2];
+    double r2 = a[0] * b[1] - a[1] * b[0];
+    out[0] = r0;
+    out[1] = r1;
+    out[2] = r2;
+}
+
+static int64_t ncell_of(const orc_grid *g)
+{
+    return (int64_t)g->n[0] * g->n[1] * g->n[2];
+}
+
+static double cell_volume(const orc_grid *g)
+{
+    return g->dx[0] * g->dx[1] * g->dx[2];
+}
+
+/* Lorentz factor of a four-velocity v: gamma = sqrt(C^2 + v^2) / C (Section 2.2). */
+double orc_gamma(const double v[3], double C)
+{
+    return sqrt(C * C + dot3(v, v)) / C;
+}
+
+/* Kinetic energy per unit mass E_k = (gamma - 1) C^2 = v^2 / (gamma + 1) (eq:parEk). */
+double orc_kinetic_energy(const double v[3], double C)
+{
+    return dot3(v, v) / (orc_gamma(v, C) + 1.0);
+}
+
+/* ------------------------------------------------------------------ */
+/* TSC shape (Section 3: second-order quadratic spline)                 */
+/* ------------------------------------------------------------------ */
+
+/* Weights of the three cell centres nearest to position s (cell units). */
+void orc_tsc_weights(double s, int64_t *i, double w[3])
+{
+    double fi = floor(s);
+    double delta = s - fi - 0.5;
+    *i = (int64_t)fi;
+    w[0] = 0.5 * (0.5 - delta) * (0.5 - delta);
+    w[1] = 0.75 - delta * delta;
+    w[2] = 0.5 * (0.5 + delta) * (0.5 + delta);
+}
+
+/* Map a stencil cell index onto the grid: periodic wrap or mirror fold. */
+static int64_t map_index(const orc_grid *g, int d, int64_t i)
+{
+    int64_t n = g->n[d];
+    if (g->bc[d] == 0) {
+        int64_t r = i % n;
+        return r < 0 ? r + n : r;
+    }
+    /* reflecting: cell -1-k mirrors cell k, cell n+k mirrors cell n-1-k */
+    for (;;) {
+        if (i < 0)
+            i = -1 - i;
+        else if (i >= n)
+            i = 2 * n - 1 - i;
+        else
+            return i;
+    }
+}
+
+/* Stencil of one particle: up to 27 (cell, weight) pairs. Returns the count. */
+static int stencil(const orc_grid *g, const double *xp, int64_t cells[27], double wts[27])
+{
+    int64_t base[3] = {0, 0, 0};
+    double w[3][3] = {{0, 1, 0}, {0, 1, 0}, {0, 1, 0}};
+    for (int d = 0; d < g->ndim; ++d) {
+        double s = (xp[d] - g->x0[d]) / g->dx[d];
+        orc_tsc_weights(s, &base[d], w[d]);
+    }
+    int m = 0;
+    int kz = g->ndim == 3 ? 3 : 1;
+    for (int c = 0; c < kz; ++c) {
+        for (int b = 0; b < 3; ++b) {
+            for (int a = 0; a < 3; ++a) {
+                int64_t ii = map_index(g, 0, base[0] + a - 1);
+                int64_t jj = map_index(g, 1, base[1] + b - 1);
+                int64_t kk = 0;
+                double wz = 1.0;
+                if (g->ndim == 3) {
+                    kk = map_index(g, 2, base[2] + c - 1);
+                    wz = w[2][c];
+                }
+                cells[m] = (kk * g->n[1] + jj) * g->n[0] + ii;
+                wts[m] = w[0][a] * w[1][b] * wz;
+                ++m;
+            }
+        }
+    }
+    return m;
+}
+
+/* Interpolate nq cell-centred planes (plane-major) to one particle position. */
+void orc_gather(const orc_grid *g, const double *xp, const double *planes, int nq, double *out)
+{
+    int64_t cells[27];
+    double wts[27];
+    int m = stencil(g, xp, cells, wts);
+    int64_t nc = ncell_of(g);
+    for (int q = 0; q < nq; ++q) {
+        double acc = 0.0;
+        for (int k = 0; k < m; ++k)
+            acc += wts[k] * planes[q * nc + cells[k]];
+        out[q] = acc;
+    }
+}
+
+/* Deposit nq particle quantities onto nq cell planes with the same weights. */
+void orc_deposit(const orc_grid *g, const double *xp, const double *q, int nq, double *planes)
+{
+    int64_t cells[27];
+    double wts[27];
+    int m = stencil(g, xp, cells, wts);
+    int64_t nc = ncell_of(g);
+    for (int k = 0; k < m; ++k)
+        for (int a = 0; a < nq; ++a)
+            planes[a * nc + cells[k]] += q[a] * wts[k];
+}
+
+/* ------------------------------------------------------------------ */
+/* particle boundary                                                    */
+/* ------------------------------------------------------------------ */
+
+void orc_boundary(const orc_grid *g, double *xp, double *v)
+{
+    for (int d = 0; d < g->ndim; ++d) {
+        double lo = g->x0[d];
+        double L = g->n[d] * g->dx[d];
+        double hi = lo + L;
+        if (g->bc[d] == 0) {
+            double r = xp[d] - lo;
+            r -= L * floor(r / L);
+            if (r >= L)
+                r -= L;
+            xp[d] = lo + r;
+        } else {
+            if (xp[d] < lo) {
+                xp[d] = 2.0 * lo - xp[d];
+                v[d] = -v[d];
+            } else if (xp[d] >= hi) {
+                xp[d] = 2.0 * hi - xp[d];
+                v[d] = -v[d];
+            }
+            if (xp[d] >= hi)
+                xp[d] = nextafter(hi, lo);
+            if (xp[d] < lo)
+                xp[d] = lo;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* cell-centred electric field (Section 2.1, used as in Section 2.2)    */
+/* ------------------------------------------------------------------ */
+
+/*
+ * E0 = -v_g x B (eq:emf0).  With the CR-Hall term:
+ *   n_g = (q/mc)_g rho (eq:ng), R = n_CR / (n_g + n_CR) (eq:defR),
+ *   F_CR = (1 - R)(n_CR E0 + J_CR x B) (eq:lorentz2),
+ *   E = E0 - F_CR / n_g (eq:emfcr2).
+ * mom_dep holds the charge and current densities (n, Jx, Jy, Jz) deposited at
+ * the current particle positions.
+ */
+void orc_field_prep(const orc_grid *g, const orc_params *p, const double *rho, const double *mom,
+                    const double *B, const double *mom_dep, double *E)
+{
+    int64_t nc = ncell_of(g);
+    for (int64_t c = 0; c < nc; ++c) {
+        double vg[3], Bc[3], E0[3];
+        for (int d = 0; d < 3; ++d) {
+            vg[d] = mom[d * nc + c] / rho[c];
+            Bc[d] = B[d * nc + c];
+        }
+        double vxb[3];
+        cross3(vg, Bc, vxb);
+        for (int d = 0; d < 3; ++d)
+            E0[d] = -vxb[d];
+        if (p->hall) {
+            double ng = p->qm_gas * rho[c];
+            double n = mom_dep[c];
+            double J[3] = {mom_dep[nc + c], mom_dep[2 * nc + c], mom_dep[3 * nc + c]};
+            double R = n / (ng + n);
+            double JxB[3];
+            cross3(J, Bc, JxB);
+            for (int d = 0; d < 3; ++d) {
+                double F = (1.0 - R) * (n * E0[d] + JxB[d]);
+                E[d * nc + c] = E0[d] - F / ng;
+            }
+        } else {
+            for (int d = 0; d < 3; ++d)
+                E[d * nc + c] = E0[d];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* moments deposit (Appendix A.1, eq:nJCR)                              */
+/* ------------------------------------------------------------------ */
+
+/* n_CR += (q/mc) m_CR W / dV,  J_CR += (q/mc) m_CR u W / dV at each position. */
+void orc_deposit_moments(const orc_grid *g, const orc_params *p, int64_t np, const double *x,
+                         const double *v, double *mom_dep)
+{
+    double dV = cell_volume(g);
+    for (int64_t j = 0; j < np; ++j) {
+        double xp[3] = {0, 0, 0}, vj[3];
+        for (int d = 0; d < g->ndim; ++d)
+            xp[d] = x[d * np + j];
+        for (int d = 0; d < 3; ++d)
+            vj[d] = v[d * np + j];
+        double gam = orc_gamma(vj, p->C);
+        double q[4];
+        q[0] = p->qm_cr * p->m_cr / dV;
+        for (int d = 0; d < 3; ++d)
+            q[1 + d] = p->qm_cr * p->m_cr * (vj[d] / gam) / dV;
+        orc_deposit(g, xp, q, 4, mom_dep);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* particle step (Appendix A.2 and the corrector of Appendix A.3)       */
+/* ------------------------------------------------------------------ */
+
+/*
+ * One drift-kick-rotate-kick-drift step of every particle with h = (q/mc) dt:
+ *   x^(n+1/2) = x^(n) + u^(n) dt/2
+ *   E, B interpolated at x^(n+1/2); E <- E - (E.B)B/|B|^2
+ *   v^0 = v^(n) + (h/2) E
+ *   gamma = gamma(v^0),  b = (h/2) B / gamma
+ *   v^1 = v^0 + 2 (v^0 + v^0 x b) x b / (1 + b^2)
+ *   v^(n+1) = v^1 + (h/2) E
+ *   x^(n+1) = x^(n+1/2) + u^(n+1) dt/2
+ * Corrector deposit at x^(n+1/2): corr += (-m dv, -m dE_k) (momentum, energy).
+ * Moments deposit at x^(n+1): mom_dep += (n, J) of eq:nJCR.
+ * corr holds 4 planes (Mx, My, Mz, E_k); mom_dep holds 4 planes (n, Jx, Jy, Jz).
+ * Either deposit pointer may be NULL to skip it.
+ */
+void orc_push(const orc_grid *g, const orc_params *p, double dt, int64_t np, double *x, double *v,
+              const double *E, const double *B, double *corr, double *mom_dep)
+{
+    const double h = p->qm_cr * dt;
+    const double C = p->C;
+    const double m = p->m_cr;
+    const double dV = cell_volume(g);
+    int64_t nc = ncell_of(g);
+    /* interleave E and B planes for one gather call */
+    double *EB = (double *)malloc(sizeof(double) * 6 * (size_t)nc);
+    memcpy(EB, E, sizeof(double) * 3 * (size_t)nc);
+    memcpy(EB + 3 * nc, B, sizeof(double) * 3 * (size_t)nc);
+
+    for (int64_t j = 0; j < np; ++j) {
+        double xp[3] = {0, 0, 0}, vn[3];
+        for (int d = 0; d < g->ndim; ++d)
+            xp[d] = x[d * np + j];
+        for (int d = 0; d < 3; ++d)
+            vn[d] = v[d * np + j];
+
+        /* drift to the half step */
+        double g0 = orc_gamma(vn, C);
+        for (int d = 0; d < g->ndim; ++d)
+            xp[d] = xp[d] + 0.5 * dt * (vn[d] / g0);
+        orc_boundary(g, xp, vn);
+
+        /* fields at x^(n+1/2) */
+        double f[6];
+        orc_gather(g, xp, EB, 6, f);
+        double Ep[3] = {f[0], f[1], f[2]};
+        double Bp[3] = {f[3], f[4], f[5]};
+        double B2 = dot3(Bp, Bp);
+        if (B2 > 0.0) {
+            double eb = dot3(Ep, Bp) / B2;
+            for (int d = 0; d < 3; ++d)
+                Ep[d] -= eb * Bp[d];
+        }
+
+        /* kick - rotate - kick */
+        double v0[3], v1[3], vnew[3], b[3], t[3], txb[3];
+        for (int d = 0; d < 3; ++d)
+            v0[d] = vn[d] + 0.5 * h * Ep[d];
+        double gam = orc_gamma(v0, C);
+        for (int d = 0; d < 3; ++d)
+            b[d] = 0.5 * h * Bp[d] / gam;
+        cross3(v0, b, t);
+        for (int d = 0; d < 3; ++d)
+            t[d] += v0[d];
+        cross3(t, b, txb);
+        double b2 = dot3(b, b);
+        for (int d = 0; d < 3; ++d)
+            v1[d] = v0[d] + 2.0 * txb[d] / (1.0 + b2);
+        for (int d = 0; d < 3; ++d)
+            vnew[d] = v1[d] + 0.5 * h * Ep[d];
+
+        /* corrector deposit: -m (v^(n+1) - v^(n)), -m (E_k^(n+1) - E_k^(n)) */
+        double g1 = orc_gamma(vnew, C);
+        if (corr) {
+            double dv[3], sv[3];
+            for (int d = 0; d < 3; ++d) {
+                dv[d] = vnew[d] - vn[d];
+                sv[d] = vnew[d] + vn[d];
+            }
+            double dEk = dot3(dv, sv) / (g1 + g0);
+            double q[4] = {-m * dv[0], -m * dv[1], -m * dv[2], -m * dEk};
+            orc_deposit(g, xp, q, 4, corr);
+        }
+
+        /* drift to the full step */
+        for (int d = 0; d < g->ndim; ++d)
+            xp[d] = xp[d] + 0.5 * dt * (vnew[d] / g1);
+        orc_boundary(g, xp, vnew);
+
+        if (mom_dep) {
+            double q[4];
+            q[0] = p->qm_cr * m / dV;
+            for (int d = 0; d < 3; ++d)
+                q[1 + d] = p->qm_cr * m * (vnew[d] / g1) / dV;
+            orc_deposit(g, xp, q, 4, mom_dep);
+        }
+
+        for (int d = 0; d < g->ndim; ++d)
+            x[d * np + j] = xp[d];
+        for (int d = 0; d < 3; ++d)
+            v[d * np + j] = vnew[d];
+    }
+    free(EB);
+}
+
+/* ------------------------------------------------------------------ */
+/* feedback to the gas (Section 2.1 Newton's third law, App. A.3)       */
+/* ------------------------------------------------------------------ */
+
+/* rho v += corr_M / dV,  E_gas += corr_E / dV; the corrector planes are zeroed. */
+void orc_apply_feedback(const orc_grid *g, double *mom, double *egas, double *corr)
+{
+    int64_t nc = ncell_of(g);
+    double dV = cell_volume(g);
+    for (int64_t c = 0; c < nc; ++c) {
+        for (int d = 0; d < 3; ++d)
+            mom[d * nc + c] += corr[d * nc + c] / dV;
+        egas[c] += corr[3 * nc + c] / dV;
+    }
+    memset(corr, 0, sizeof(double) * 4 * (size_t)nc);
+}
+
+/* Totals of gas + CR momentum and energy: out = {Pgas x,y,z, Egas, Pcr x,y,z, Ecr}. */
+void orc_totals(const orc_grid *g, const orc_params *p, int64_t np, const double *v,
+                const double *mom, const double *egas, double out[8])
+{
+    int64_t nc = ncell_of(g);
+    double dV = cell_volume(g);
+    for (int k = 0; k < 8; ++k)
+        out[k] = 0.0;
+    for (int64_t c = 0; c < nc; ++c) {
+        for (int d = 0; d < 3; ++d)
+            out[d] += mom[d * nc + c] * dV;
+        out[3] += egas[c] * dV;
+    }
+    for (int64_t j = 0; j < np; ++j) {
+        double vj[3] = {v[j], v[np + j], v[2 * np + j]};
+        for (int d = 0; d < 3; ++d)
+            out[4 + d] += p->m_cr * vj[d];
+        out[7] += p->m_cr * orc_kinetic_energy(vj, p->C);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* full step: fields, push with both deposits, feedback                 */
+/* ------------------------------------------------------------------ */
+
+/*
+ * mom_dep holds the moments of the current positions on entry and of the new
+ * positions on return.  corr must be zero on entry and is zero on return.
+ * E is caller-provided scratch of 3 planes.
+ */
+void orc_step(const orc_grid *g, const orc_params *p, double dt, int64_t np, double *x, double *v,
+              const double *rho, double *mom, double *egas, const double *B, double *mom_dep,
+              double *corr, double *E)
+{
+    int64_t nc = ncell_of(g);
+    orc_field_prep(g, p, rho, mom, B, mom_dep, E);
+    memset(mom_dep, 0, sizeof(double) * 4 * (size_t)nc);
+    orc_push(g, p, dt, np, x, v, E, B, corr, mom_dep);
+    orc_apply_feedback(g, mom, egas, corr);
+}
+
+/* ------------------------------------------------------------------ */
+/* cell sort (the layout of the GPU build; the paper has no sort)        */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Sort key of a cell with coordinates (i, j, k) for bricks of bx*by*bz cells:
+ * the brick number (bricks numbered x fastest) times the brick volume plus the
+ * cell's x-fastest number inside its brick.  With a brick equal to the whole
+ * grid the key is the linear cell index.
+ */
+int64_t orc_sort_nkeys(const orc_grid *g, const int32_t brick[3])
+{
+    int64_t nb = 1, vol = 1;
+    for (int d = 0; d < 3; ++d) {
+        nb *= (g->n[d] + brick[d] - 1) / brick[d];
+        vol *= brick[d];
+    }
+    return nb * vol;
+}
+
+int64_t orc_sort_key(const orc_grid *g, const int32_t brick[3], int64_t cell)
+{
+    int64_t nx = g->n[0], ny = g->n[1];
+    int64_t i = cell % nx;
+    int64_t j = (cell / nx) % ny;
+    int64_t k = cell / (nx * ny);
+    int64_t nbx = (nx + brick[0] - 1) / brick[0];
+    int64_t nby = (ny + brick[1] - 1) / brick[1];
+    int64_t bid = ((k / brick[2]) * nby + j / brick[1]) * nbx + i / brick[0];
+    int64_t in = ((k % brick[2]) * brick[1] + j % brick[1]) * brick[0] + i % brick[0];
+    return bid * (int64_t)brick[0] * brick[1] * brick[2] + in;
+}
+
+/* Linear cell of each FP64 position: i_d = floor((x_d - x0_d) / dx_d). */
+void orc_cells_of(const orc_grid *g, int64_t np, const double *x, int32_t *cell)
+{
+    for (int64_t j = 0; j < np; ++j) {
+        int64_t idx[3] = {0, 0, 0};
+        for (int d = 0; d < g->ndim; ++d) {
+            int64_t i = (int64_t)floor((x[d * np + j] - g->x0[d]) / g->dx[d]);
+            if (i < 0)
+                i = 0;
+            if (i >= g->n[d])
+                i = g->n[d] - 1;
+            idx[d] = i;
+        }
+        cell[j] = (int32_t)((idx[2] * g->n[1] + idx[1]) * g->n[0] + idx[0]);
+    }
+}
+
+/*
+ * Stable counting sort of particles by key.  perm[r] = index of the particle
+ * that goes to rank r; counts[key] = particles with that key (nkeys entries).
+ */
+void orc_sort_cells(const orc_grid *g, const int32_t brick[3], int64_t np, const int32_t *cell,
+                    int64_t *perm, int64_t *counts)
+{
+    int64_t nk = orc_sort_nkeys(g, brick);
+    int64_t *start = (int64_t *)calloc((size_t)nk + 1, sizeof(int64_t));
+    memset(counts, 0, sizeof(int64_t) * (size_t)nk);
+    for (int64_t j = 0; j < np; ++j)
+        counts[orc_sort_key(g, brick, cell[j])] += 1;
+    for (int64_t k = 0; k < nk; ++k)
+        start[k + 1] = start[k] + counts[k];
+    for (int64_t j = 0; j < np; ++j) {
+        int64_t k = orc_sort_key(g, brick, cell[j]);
+        perm[start[k]++] = j;
+    }
+    free(start);
+}
