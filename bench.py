@@ -1,0 +1,358 @@
+"""Benchmark of the cosmic-ray particle update (particle-steps per second).
+
+Default workload: 3-D periodic 128^3 box, 32 CRs per cell (67,108,864 CRs),
+uniform gas with a random-phase Alfvenic perturbation dB/B0 = 0.1 (64 modes),
+CR beam |p| = 100 boosted to 10 v_A along B, C = 300.  One step is the whole
+hot path: staged-field push with both deposits (interp_push), feedback to the
+gas with field restaging (apply_feedback), and the cell sort every
+``--sort-every`` steps.
+
+Prints ONE JSON line.  Under torchrun each rank advances its own independent
+box (seed = rank), the time is the maximum over ranks and the value is the
+particle-steps of all ranks per second (weak scaling, no collective on the
+data path).
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CR particle-steps/s (push+deposit), % HBM roofline; mixed vs FP64 at stated err"
+UNIT = "particle-steps/s"
+
+# bytes the method must move per particle-step in the push kernel (3-D mixed):
+# particle state read + write (int32 cell, 3 f32 offsets, 3 f32 four-velocity)
+PARTICLE_BYTES = {(3, "mixed"): 28, (2, "mixed"): 24, (3, "fp64"): 48, (2, "fp64"): 40}
+# per cell and launch: staged E, B read once (6 words) + 8 deposit channels
+# read-modify-written once (8 B each, twice)
+CELL_FIELD_BYTES = {"mixed": 24, "fp64": 48}
+CELL_DEPOSIT_BYTES = 8 * 8 * 2
+
+
+def _rank_env():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, w, lr
+
+
+def _workload(args, seed):
+    from paper_1412_1087_gb300 import workloads as wl
+    return wl.alfvenic_beam_3d(seed=seed, n=args.n, ppc=args.ppc)
+
+
+def _workload_desc(args):
+    return ("alfvenic_beam_3d: 3-D periodic %d^3 grid, %d CR/cell (%d CRs), uniform gas + random-phase "
+            "Alfvenic dB/B0=0.1 (64 modes), beam |p|=100 boosted 10 v_A along B, C=300, TSC"
+            % (args.n, args.ppc, args.n ** 3 * args.ppc))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _time_engine(eng, box, steps, warmup, sort_every, torch, per_push=True):
+    """Run warmup + timed steps; returns (total_ms, push_ms_sum, launches)."""
+    st = eng.stream
+    for k in range(warmup):
+        eng.interp_push(box.dt, 1)
+        eng.apply_feedback(False)
+        if sort_every and (k + 1) % sort_every == 0:
+            eng.sort()
+    torch.cuda.synchronize()
+    l0 = eng.launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(st)
+    for k in range(steps):
+        if per_push:
+            ev[k][0].record(st)
+        eng.interp_push(box.dt, 1)
+        if per_push:
+            ev[k][1].record(st)
+        eng.apply_feedback(False)
+        if sort_every and (k + 1) % sort_every == 0:
+            eng.sort()
+    end.record(st)
+    torch.cuda.synchronize()
+    total = start.elapsed_time(end)
+    push = sum(a.elapsed_time(b) for a, b in ev) if per_push else float("nan")
+    return total, push, eng.launches() - l0
+
+
+def _cpu_baseline(args, seed, nsteps):
+    import oracle as orc
+    from paper_1412_1087_gb300 import workloads as wl
+    box = wl.alfvenic_beam_3d(seed=seed, n=args.sample_n, ppc=args.ppc)
+    x = wl.absolute_positions(box)
+    v = box.p.astype(np.float64)
+    st = orc.State(box, x, v)
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        st.step(box.dt)
+    dt = time.perf_counter() - t0
+    ps = box.np * nsteps
+    return {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "alfvenic_beam_3d recipe at %d^3 x %d CR/cell (%d CRs), %d full steps, single thread"
+                      % (args.sample_n, args.ppc, box.np, nsteps), "seconds": dt}
+
+
+def _error_vs_oracle(args, seed, torch):
+    """One step of the mixed and FP64 GPU paths against the oracle on the sample box."""
+    import oracle as orc
+    from paper_1412_1087_gb300 import mhdpic as m
+    from paper_1412_1087_gb300 import workloads as wl
+    box = wl.alfvenic_beam_3d(seed=seed, n=args.err_n, ppc=args.ppc)
+    g = orc.grid_of(box)
+    perm, _ = orc.sort_cells(g, (4, 4, 4), box.cell)
+    x = np.ascontiguousarray(wl.absolute_positions(box)[:, perm])
+    v = np.ascontiguousarray(box.p.astype(np.float64)[:, perm])
+    st = orc.State(box, x, v)
+    corr, md = st.push_only(box.dt)
+    out = {}
+    for name, prec in (("mixed", m.MHDPIC_PREC_MIXED), ("fp64", m.MHDPIC_PREC_FP64)):
+        eng = m.Engine([box], precision=prec)
+        eng.interp_push(box.dt, 1)
+        gc = eng.deposits(0).cpu().numpy()
+        gm = eng.deposits(1).cpu().numpy()
+        eng.close()
+        rl = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+        out[name] = {"corrector_rel_l2_max": max(rl(gc[q], corr[q]) for q in range(4)),
+                     "moments_rel_l2_max": max(rl(gm[q], md[q]) for q in range(4))}
+    out["sample"] = "one step at %d^3 x %d CR/cell" % (args.err_n, args.ppc)
+    return out
+
+
+def run_native(args):
+    import torch
+    from paper_1412_1087_gb300 import build as libbuild
+    from paper_1412_1087_gb300 import mhdpic as m
+
+    rank, world, lrank = _rank_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(lrank)
+    if rank == 0:
+        libbuild.build()
+    if world > 1:
+        dist.barrier()
+    m.load()
+    box = _workload(args, seed=rank)
+    eng = m.Engine([box], precision=m.MHDPIC_PREC_MIXED, device="cuda:%d" % lrank)
+    npart = box.np
+
+    # timed region (device time, max over ranks)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(lrank) as clk:
+        total_ms, push_ms, launches = _time_engine(eng, box, args.steps, args.warmup, args.sort_every, torch)
+    clocks = clk.summary()
+    flags = eng.status()
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda:%d" % lrank)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = npart * world * args.steps / (total_ms / 1e3)
+
+    # roofline of the push kernel (the dominant kernel)
+    peak, peak_kind = _peaks()
+    nc = box.ncell
+    bytes_push = npart * 2 * PARTICLE_BYTES[(3, "mixed")] + nc * (CELL_FIELD_BYTES["mixed"] + CELL_DEPOSIT_BYTES)
+    push_avg_s = push_ms / args.steps / 1e3
+    achieved = bytes_push / push_avg_s / 1e9
+    eng_stats = {"push_ms_per_step": push_ms / args.steps}
+
+    # plain FP64 GPU path on the same workload
+    fp64 = None
+    if args.fp64_steps > 0:
+        eng.close()
+        del eng
+        torch.cuda.empty_cache()
+        e64 = m.Engine([box], precision=m.MHDPIC_PREC_FP64, device="cuda:%d" % lrank)
+        t64, p64, _ = _time_engine(e64, box, args.fp64_steps, 1, args.sort_every, torch)
+        v64 = npart * args.fp64_steps / (t64 / 1e3)
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": t64 / args.fp64_steps,
+                "steps": args.fp64_steps, "speedup_mixed_over_fp64": value / world / v64}
+        e64.close()
+        del e64
+        torch.cuda.empty_cache()
+    else:
+        eng.close()
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if args.e2e_steps > 0:
+        eh = m.Engine([box], precision=m.MHDPIC_PREC_MIXED, memory=m.MHDPIC_MEM_HOST, device="cuda:%d" % lrank)
+        te, _, _ = _time_engine(eh, box, args.e2e_steps, 1, args.sort_every, torch, per_push=False)
+        eh.close()
+        pbytes = npart * PARTICLE_BYTES[(3, "mixed")]
+        h2d = pbytes + nc * 8 * 8            # push: particles; feedback: rho, mom(3), egas, B(3)
+        d2h = pbytes + nc * 4 * 8            # push: particles; feedback: mom(3), egas
+        sort_extra = (2 * pbytes) / args.sort_every if args.sort_every else 0
+        e2e = {"value": npart * world * args.e2e_steps / (te / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d + sort_extra / 2), "d2h_bytes_per_step": int(d2h + sort_extra / 2),
+               "steps": args.e2e_steps, "ms_per_step": te / args.e2e_steps}
+
+    out = None
+    if rank == 0:
+        cpu = _cpu_baseline(args, seed=0, nsteps=args.cpu_steps) if args.cpu_steps > 0 else None
+        err = _error_vs_oracle(args, 0, torch) if args.err_n > 0 else None
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 push + i64 fixed-point deposits",
+            "data": "synthetic",
+            "config": {"workload": _workload_desc(args), "precision": "mixed", "sort_every": args.sort_every,
+                       "l2": "inputs larger than L2 (%.2f GB particle state)" % (npart * 28 / 1e9),
+                       "parallelism": "independent box per GPU" if world > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_push<3,mixed,full>",
+                         "peak_kind": peak_kind, "bytes_per_launch": bytes_push,
+                         "avg_launch_ms": push_avg_s * 1e3},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "fp64_gpu": fp64,
+            "error_vs_oracle": err,
+            "status_flags": m.status_names(flags),
+            "detail": eng_stats,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def run_reference(args):
+    rank, world, _ = _rank_env()
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    from paper_1412_1087_gb300 import workloads as wl
+    import oracle as orc
+    box = wl.alfvenic_beam_3d(seed=0, n=args.sample_n, ppc=args.ppc)
+    st = orc.State(box, wl.absolute_positions(box), box.p.astype(np.float64))
+    for _ in range(args.warmup):
+        st.step(box.dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st.step(box.dt)
+    dt = time.perf_counter() - t0
+    value = box.np * args.steps / dt
+    sample = ("FP64 CPU oracle, alfvenic_beam_3d recipe at %d^3 x %d CR/cell (%d CRs) per step, single thread"
+              % (args.sample_n, args.ppc, box.np))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": _workload_desc(args), "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--n", type=int, default=128, help="cells per side of the 3-D box")
+    ap.add_argument("--ppc", type=int, default=32)
+    ap.add_argument("--sort-every", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--sample-n", type=int, default=40, help="side of the oracle's sample box")
+    ap.add_argument("--err-n", type=int, default=24, help="side of the error-check box (0: skip)")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "native":
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

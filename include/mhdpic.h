@@ -1,0 +1,221 @@
+/*
+ * mhdpic.h - C ABI of the GB300 (sm_103a) cosmic-ray particle update of the
+ * MHD-PIC method (Bai, Caprioli, Sironi & Spitkovsky, arXiv:1412.1087).
+ *
+ * One particle step, as the paper defines it:
+ *   - the cell-centred electric field E = E0 - F_CR/n_g with E0 = -v_g x B
+ *     (Section 2.1, eq:emf0, eq:lorentz2, eq:emfcr2; used by the particles as
+ *     stated in Section 2.2);
+ *   - drift half a step, TSC interpolation of E and B (Section 3), removal of
+ *     the E component along B, relativistic Boris kick-rotate-kick with an
+ *     artificial light speed C, drift half a step (Appendix A.2);
+ *   - TSC deposit of -m dv and -m dE_k at the half-step position (the
+ *     corrector of Appendix A.3) and of the charge and current densities
+ *     n_CR, J_CR at the new position (Appendix A.1, eq:nJCR);
+ *   - applying the corrector deposit to the gas momentum and energy
+ *     (Section 2.1: Newton's third law and eq:eng; Appendix A.3).
+ * Units are the paper's code units: the factor c is absorbed into E and J.
+ *
+ * All calls are asynchronous on the stream given at init unless stated; none
+ * aborts.  Every call returns MHDPIC_OK (0) or a negative MHDPIC_E* code;
+ * mhdpic_strerror() gives a message and mhdpic_last_error() the detail of the
+ * last failure on the calling thread.
+ *
+ * Ownership: the caller owns every particle and gas buffer (plain pointers,
+ * device memory unless options.memory == MHDPIC_MEM_HOST).  The library owns
+ * only its scratch (sort keys, permutation, staged fields, fixed-point deposit
+ * grids, work list, status word), allocated by mhdpic_init and freed by
+ * mhdpic_destroy.  Buffers must stay valid and unmoved between init and
+ * destroy.
+ *
+ * Layouts (np = total particles of all boxes, nc = total cells of all boxes):
+ *   particles, box-major: box b owns particles [box_start[b], box_start[b+1]);
+ *   MIXED:  cell[np] int32   linear cell of the particle inside its box,
+ *                            c = (k*ny + j)*nx + i;
+ *           off[ndim*np]     float, plane d holds the offset in [0,1) of the
+ *                            particle inside its cell along dimension d;
+ *           p[3*np]          float, four-velocity v = gamma*u (eq:4vel);
+ *   FP64:   x[ndim*np]       double, absolute position, plane-major;
+ *           p64[3*np]        double, four-velocity;
+ *   gas (cells box-major, box b's cells start at the sum of earlier boxes'
+ *   cell counts, c as above inside a box):
+ *           rho[nc], mom[3*nc] (momentum density rho*v_g, plane-major),
+ *           egas[nc] (total energy density), B[3*nc] (cell-centred field).
+ */
+#ifndef MHDPIC_H
+#define MHDPIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define MHDPIC_OK 0
+#define MHDPIC_E_ARG (-1)      /* invalid argument (message in mhdpic_last_error) */
+#define MHDPIC_E_CUDA (-2)     /* a CUDA runtime call failed */
+#define MHDPIC_E_NOMEM (-3)    /* device allocation failed */
+#define MHDPIC_E_STATUS (-4)   /* a device status flag is set (mhdpic_get_status) */
+#define MHDPIC_E_CAPACITY (-5) /* a size limit of the library was exceeded */
+#define MHDPIC_E_STATE (-6)    /* call made in the wrong state (e.g. destroyed ctx) */
+
+/* ---- enumerations ---- */
+#define MHDPIC_BC_PERIODIC 0
+#define MHDPIC_BC_REFLECT 1 /* conducting wall: specular particle reflection, mirror-folded stencil */
+#define MHDPIC_SHAPE_TSC 2  /* triangular-shaped cloud (quadratic spline), Section 3 */
+#define MHDPIC_PREC_FP64 0  /* all particle arithmetic in double */
+#define MHDPIC_PREC_MIXED 1 /* int32 cell + f32 offset, f32 push, int64 fixed-point deposits */
+#define MHDPIC_MEM_DEVICE 0 /* caller buffers are device pointers */
+#define MHDPIC_MEM_HOST 1   /* caller buffers are (pinned) host pointers; each call copies */
+
+/* ---- device status flags (sticky until mhdpic_clear_status) ---- */
+#define MHDPIC_ST_FAST_MOVER 1u /* a particle moved more than 2 cells in one half step (App. A.4) */
+#define MHDPIC_ST_NONFINITE 2u  /* a non-finite position or four-velocity was produced */
+#define MHDPIC_ST_OVERFLOW 4u   /* a fixed-point deposit exceeded its headroom */
+#define MHDPIC_ST_SORT_CAP 8u   /* a cell held more particles than the sort's segment limit */
+#define MHDPIC_ST_CELL_RANGE 16u/* a particle's cell index was outside its box */
+
+typedef struct mhdpic_ctx mhdpic_ctx;
+
+/* Grid of one box.  2-D boxes have ndim = 2, n[2] = 1; dx[2] is then the cell
+ * depth that enters the cell volume dV = dx[0]*dx[1]*dx[2]. */
+typedef struct {
+    int32_t ndim;  /* 2 or 3 */
+    int32_t n[3];  /* cells per dimension */
+    double dx[3];  /* cell widths (> 0) */
+    double x0[3];  /* lower corner of the box */
+    int32_t bc[3]; /* MHDPIC_BC_PERIODIC or MHDPIC_BC_REFLECT, per dimension */
+} mhdpic_grid;
+
+/* Physical parameters of one box (Sections 2.2, App. A.1). */
+typedef struct {
+    double qm_cr;  /* (q/mc) of the CR species */
+    double qm_gas; /* (q/mc)_g of the gas ions: n_g = qm_gas * rho (eq:ng) */
+    double C;      /* artificial speed of light (Section 2.2) */
+    double m_cr;   /* particle "mass" m_CR (App. A.1) */
+    int32_t hall;  /* 1: E = E0 - F_CR/n_g (eq:emfcr2); 0: E = E0 */
+    int32_t shape; /* MHDPIC_SHAPE_TSC (the only shape the paper uses) */
+} mhdpic_params;
+
+/* Library options, shared by all boxes of a context. */
+typedef struct {
+    int32_t precision; /* MHDPIC_PREC_MIXED or MHDPIC_PREC_FP64 */
+    int32_t memory;    /* MHDPIC_MEM_DEVICE or MHDPIC_MEM_HOST */
+    int32_t brick[3];  /* cells per sort brick and per push tile (0: 4x4x4 in 3-D, 8x8 in 2-D) */
+    int32_t reserved[8];
+} mhdpic_options;
+
+/* Caller-owned particle buffers (see the layout above). */
+typedef struct {
+    int64_t np;               /* total particles (may be 0) */
+    const int64_t *box_start; /* HOST array [nbox+1], box_start[0] = 0, box_start[nbox] = np */
+    int32_t *cell;            /* MIXED */
+    float *off;               /* MIXED */
+    float *p;                 /* MIXED */
+    double *x;                /* FP64 */
+    double *p64;              /* FP64 */
+} mhdpic_particles;
+
+/* Caller-owned gas buffers (see the layout above). rho and B are read only. */
+typedef struct {
+    double *rho;
+    double *mom;
+    double *egas;
+    double *B;
+} mhdpic_gas;
+
+/*
+ * mhdpic_init - validate a batch of nbox independent boxes, allocate scratch,
+ * choose the fixed-point scales, sort the particles (as mhdpic_sort), deposit
+ * their charge and current (as mhdpic_deposit) and stage the fields.
+ *   ctx     out: new context (NULL on failure)
+ *   grids, params: host arrays [nbox]
+ *   stream: cudaStream_t (NULL = legacy default stream) used by every call
+ * Positions must lie inside their box; particle data are permuted in place.
+ * Synchronises the stream once (it reads per-cell counts back).
+ */
+int mhdpic_init(mhdpic_ctx **ctx, int32_t nbox, const mhdpic_grid *grids,
+                const mhdpic_params *params, const mhdpic_options *options,
+                const mhdpic_particles *particles, const mhdpic_gas *gas, void *stream);
+
+/*
+ * mhdpic_sort - stable counting sort of each box's particles by cell key: the
+ * brick number (bricks of options.brick cells, numbered x fastest) times the
+ * brick volume plus the cell's x-fastest number inside its brick.  The paper
+ * has no sort (cell ordering is this library's layout); positions and
+ * four-velocities are permuted in place and the push work list is rebuilt.
+ *   perm_out   device int64[np] or NULL: perm_out[r] = old index of the
+ *              particle now at rank r (global indices)
+ *   counts_out device int32[nkeys] or NULL: particles per key, keys of box b
+ *              after those of earlier boxes (nkeys from mhdpic_num_keys)
+ */
+int mhdpic_sort(mhdpic_ctx *ctx, int64_t *perm_out, int32_t *counts_out);
+
+/*
+ * mhdpic_interp_push - nsub particle sub-steps of length dt with the staged
+ * fields held fixed (App. A.2; sub-cycling as in App. A.4).  Each sub-step
+ * drifts, interpolates E and B by TSC at x^(n+1/2), removes E along B, applies
+ * the relativistic Boris kick-rotate-kick and drifts again; it adds
+ * (-m dv, -m dE_k) at x^(n+1/2) to the corrector accumulators (App. A.3).  The
+ * last sub-step also deposits n_CR and J_CR at the new positions (eq:nJCR),
+ * which the next field staging uses.  dt must be > 0, nsub >= 1.
+ */
+int mhdpic_interp_push(mhdpic_ctx *ctx, double dt, int32_t nsub);
+
+/*
+ * mhdpic_deposit - TSC deposit of n_CR = (q/mc) m_CR W/dV and
+ * J_CR = (q/mc) m_CR u W/dV (App. A.1, eq:nJCR) at the current positions,
+ * replacing the current moments, then restage the fields from the gas and
+ * these moments.  The corrector accumulators are left untouched.
+ */
+int mhdpic_deposit(mhdpic_ctx *ctx);
+
+/*
+ * mhdpic_apply_feedback - add the accumulated corrector deposit to the gas:
+ * rho*v += dM/dV, egas += dE/dV (Section 2.1, App. A.3), zero the
+ * accumulators, and restage E, B for the next push from the updated gas and
+ * the latest moments (eq:emf0, eq:lorentz2, eq:emfcr2).
+ *   totals_out HOST double[8*nbox] or NULL.  When given, the call also forms
+ *   per box the FP64 totals {P_gas x,y,z, E_gas, P_CR x,y,z, E_CR} with
+ *   P_gas = sum rho*v dV, E_gas = sum egas dV, P_CR = sum m v,
+ *   E_CR = sum m E_k (eq:parEk) in a fixed-order reduction, and synchronises
+ *   the stream to return them.
+ */
+int mhdpic_apply_feedback(mhdpic_ctx *ctx, double *totals_out);
+
+/*
+ * mhdpic_get_deposits - convert fixed-point accumulators to double.
+ *   which 0: corrector (dMx, dMy, dMz, dE) as accumulated since the last
+ *            apply (momentum and energy, not densities; the sign is the gas's)
+ *   which 1: current moments (n, Jx, Jy, Jz) as densities
+ *   out   device double[4*nc], plane-major.
+ */
+int mhdpic_get_deposits(mhdpic_ctx *ctx, int32_t which, double *out);
+
+/* Staged cell-centred fields as double: out device double[6*nc] = Ex,Ey,Ez,Bx,By,Bz. */
+int mhdpic_get_fields(mhdpic_ctx *ctx, double *out);
+
+/* Number of sort keys of all boxes (length of counts_out). */
+int64_t mhdpic_num_keys(const mhdpic_ctx *ctx);
+
+/* Device status flags (MHDPIC_ST_*), OR-ed over all calls since the last
+ * clear.  Synchronises the stream. */
+int mhdpic_get_status(mhdpic_ctx *ctx, uint32_t *flags);
+int mhdpic_clear_status(mhdpic_ctx *ctx);
+
+/* Count of this library's kernel launches since init (for benchmarks). */
+int64_t mhdpic_launch_count(const mhdpic_ctx *ctx);
+
+/* Free the context and its scratch (synchronises the stream). NULL is a no-op. */
+int mhdpic_destroy(mhdpic_ctx *ctx);
+
+/* Static message for a return code, and the detailed message of the last
+ * failure on this thread. */
+const char *mhdpic_strerror(int code);
+const char *mhdpic_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHDPIC_H */

@@ -1,0 +1,91 @@
+// Device helpers shared by the library's kernels.
+#pragma once
+
+#include "mhdpic_internal.cuh"
+
+namespace mhdpic {
+
+// Box that owns global index i, given CSR starts [nbox+1] (empty boxes skipped).
+__device__ __forceinline__ int find_box(const int64_t *__restrict__ starts, int nbox, int64_t i)
+{
+    int lo = 0, hi = nbox - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(starts + mid) <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Map an unwrapped cell coordinate g along dimension d onto the box: periodic
+// wrap, or mirror fold at a reflecting wall (cell -1-k mirrors cell k).
+__device__ __forceinline__ int map_coord(int g, int n, int bc)
+{
+    if (bc == MHDPIC_BC_PERIODIC) {
+        if (g >= 0 && g < n)
+            return g;
+        int r = g % n;
+        return r < 0 ? r + n : r;
+    }
+    for (int it = 0; it < 64; ++it) {
+        if (g < 0)
+            g = -1 - g;
+        else if (g >= n)
+            g = 2 * n - 1 - g;
+        else
+            return g;
+    }
+    return 0;
+}
+
+__device__ __forceinline__ void set_status(uint32_t *status, uint32_t flag)
+{
+    atomicOr(status, flag);
+}
+
+// Signed 64-bit fixed-point value added to an unsigned accumulator: two's
+// complement addition is the same operation, so the grid sum is exact and
+// independent of the order of the additions.
+__device__ __forceinline__ void red_add(unsigned long long *addr, long long v)
+{
+    atomicAdd(addr, (unsigned long long)v);
+}
+
+__device__ __forceinline__ long long to_fixed(float v)
+{
+    return __float2ll_rn(v);
+}
+
+__device__ __forceinline__ long long to_fixed(double v)
+{
+    return __double2ll_rn(v);
+}
+
+// TSC (quadratic spline) weights from the offset o in [0,1) inside the cell:
+// with delta = o - 1/2 the weights of cells i-1, i, i+1 are
+// (1/2)(1/2 - delta)^2 = (1/2)(1-o)^2, 3/4 - delta^2, (1/2)(1/2 + delta)^2 = (1/2)o^2.
+template <typename R>
+__device__ __forceinline__ void tsc_from_offset(R o, R w[3])
+{
+    R a = R(1) - o;
+    R dl = o - R(0.5);
+    w[0] = R(0.5) * a * a;
+    w[1] = R(0.75) - dl * dl;
+    w[2] = R(0.5) * o * o;
+}
+
+// Box-local linear cell -> integer coordinates.
+__device__ __forceinline__ void decode_cell(const BoxDev &b, int32_t c, int ci[3])
+{
+    uint32_t uc = (uint32_t)c;
+    uint32_t k = fdiv(uc, b.div_nxy);
+    uint32_t r = uc - k * (uint32_t)b.div_nxy.d;
+    uint32_t j = fdiv(r, b.div_nx);
+    ci[0] = (int)(r - j * (uint32_t)b.div_nx.d);
+    ci[1] = (int)j;
+    ci[2] = (int)k;
+}
+
+}  // namespace mhdpic

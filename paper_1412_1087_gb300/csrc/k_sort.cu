@@ -1,0 +1,472 @@
+// Cell sort of the particles (the library's layout; the paper has no sort).
+//
+// Stable counting sort by key = brick number * brick volume + cell number in
+// the brick (x fastest at both levels), per box, keys of later boxes after
+// earlier ones.  Steps:
+//   1. key of each particle, rank among equal keys by warp-aggregated atomics
+//      (this rank is not yet the stable one);
+//   2. exclusive scan of the per-key counts;
+//   3. scatter of the particle indices to their key segment;
+//   4. sort of each key segment by particle index, which makes the result the
+//      stable order: the permutation equals a stable sort by key;
+//   5. gather of the particle arrays through the permutation;
+//   6. the push work list: every brick's particle range cut into items of at
+//      most ITEM_MAX_PARTICLES.
+#include <climits>
+
+#include "device_common.cuh"
+
+namespace mhdpic {
+
+namespace {
+
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_PER_THREAD = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_PER_THREAD;
+constexpr int WARP_SORT_MAX = 1024;     // per-warp shared-memory bitonic sort
+constexpr int BLOCK_SORT_MAX = 8192;    // per-block shared-memory bitonic sort
+constexpr int RANK_SORT_MAX = 1 << 20;  // quadratic ranking beyond that is refused
+
+__device__ __forceinline__ int64_t brick_key(const BoxDev &b, const int32_t brick[3], int ci, int cj,
+                                             int ck)
+{
+    int64_t bid = ((int64_t)(ck / brick[2]) * b.nb[1] + cj / brick[1]) * b.nb[0] + ci / brick[0];
+    int64_t in = ((int64_t)(ck % brick[2]) * brick[1] + cj % brick[1]) * brick[0] + ci % brick[0];
+    return b.key0 + bid * ((int64_t)brick[0] * brick[1] * brick[2]) + in;
+}
+
+template <int PREC>
+__global__ void k_sort_keys(Ctx c, int32_t *__restrict__ count, int32_t *__restrict__ pkey,
+                            int32_t *__restrict__ pslot)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.np;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int bx = find_box(c.box_part_start, c.nbox, i);
+        const BoxDev &b = c.boxes[bx];
+        int ci[3] = {0, 0, 0};
+        if (PREC == MHDPIC_PREC_MIXED) {
+            int32_t cl = c.cell[i];
+            if (cl < 0 || cl >= b.ncell) {
+                set_status(c.status, MHDPIC_ST_CELL_RANGE);
+                cl = cl < 0 ? 0 : (int32_t)(b.ncell - 1);
+            }
+            decode_cell(b, cl, ci);
+        } else {
+            for (int d = 0; d < c.ndim; ++d) {
+                double s = (c.x[(int64_t)d * c.np + i] - b.x0[d]) / b.dx[d];
+                double f = floor(s);
+                int v = f < 0.0 ? 0 : (f >= (double)b.n[d] ? b.n[d] - 1 : (int)f);
+                if (!(f >= 0.0 && f < (double)b.n[d]))
+                    set_status(c.status, MHDPIC_ST_CELL_RANGE);
+                ci[d] = v;
+            }
+        }
+        int32_t key = (int32_t)brick_key(b, c.brick, ci[0], ci[1], ci[2]);
+        unsigned active = __activemask();
+        unsigned peers = __match_any_sync(active, key);
+        int leader = __ffs(peers) - 1;
+        int rank = __popc(peers & ((1u << lane) - 1u));
+        int base = 0;
+        if (lane == leader)
+            base = atomicAdd(count + key, __popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        pkey[i] = key;
+        pslot[i] = base + rank;
+    }
+}
+
+// --- exclusive scan of int32 (values and totals < 2^31) ---
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_sums, int *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o)
+            x += y;
+    }
+    if (lane == 31)
+        warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        int s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o)
+                s += y;
+        }
+        if (lane < nw)
+            warp_sums[lane] = s;
+    }
+    __syncthreads();
+    int pre = (wid > 0 ? warp_sums[wid - 1] : 0) + x - v;
+    if (total)
+        *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return pre;
+}
+
+__global__ void k_scan_tiles(const int32_t *__restrict__ in, int64_t n, int32_t *__restrict__ sums)
+{
+    __shared__ int ws[32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_PER_THREAD;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER_THREAD; ++k)
+        if (base + k < n)
+            s += in[base + k];
+    int tot;
+    block_exclusive_scan(s, ws, &tot);
+    if (threadIdx.x == 0)
+        sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(int32_t *sums, int nt)
+{
+    __shared__ int ws[32];
+    int carry = 0;
+    for (int start = 0; start < nt; start += blockDim.x) {
+        int i = start + threadIdx.x;
+        int v = i < nt ? sums[i] : 0;
+        int tot;
+        int pre = block_exclusive_scan(v, ws, &tot);
+        if (i < nt)
+            sums[i] = pre + carry;
+        carry += tot;
+    }
+}
+
+__global__ void k_scan_apply(const int32_t *__restrict__ in, int64_t n,
+                             const int32_t *__restrict__ sums, int32_t *__restrict__ out)
+{
+    __shared__ int ws[32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_PER_THREAD;
+    int vals[SCAN_PER_THREAD];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+        vals[k] = base + k < n ? in[base + k] : 0;
+        s += vals[k];
+    }
+    int pre = block_exclusive_scan(s, ws, nullptr) + sums[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+        if (base + k < n)
+            out[base + k] = pre;
+        pre += vals[k];
+    }
+    // the thread holding the last element closes the array with the total
+    if (base <= n - 1 && n - 1 < base + SCAN_PER_THREAD)
+        out[n] = pre;
+}
+
+// out[0..n] = exclusive scan of in[0..n), out[n] = total.
+int scan(const int32_t *in, int64_t n, int32_t *out, int32_t *tmp, cudaStream_t st)
+{
+    if (n <= 0) {
+        cudaMemsetAsync(out, 0, sizeof(int32_t), st);
+        return 0;
+    }
+    int nt = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
+    k_scan_tiles<<<nt, SCAN_THREADS, 0, st>>>(in, n, tmp);
+    k_scan_sums<<<1, SCAN_THREADS, 0, st>>>(tmp, nt);
+    k_scan_apply<<<nt, SCAN_THREADS, 0, st>>>(in, n, tmp, out);
+    return 3;
+}
+
+__global__ void k_sort_scatter(int64_t np, const int32_t *__restrict__ pkey,
+                               const int32_t *__restrict__ pslot, const int32_t *__restrict__ offset,
+                               int32_t *__restrict__ perm)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+         i += (int64_t)gridDim.x * blockDim.x)
+        perm[offset[pkey[i]] + pslot[i]] = (int32_t)i;
+}
+
+// Segments of up to 32 are sorted in registers, up to WARP_SORT_MAX in the
+// warp's shared memory; longer ones are listed for k_sort_big.
+__global__ void __launch_bounds__(256) k_sort_segments(int64_t nkeys, const int32_t *__restrict__ offset,
+                                                       int32_t *__restrict__ perm,
+                                                       int32_t *__restrict__ big_list,
+                                                       int32_t *__restrict__ big_count)
+{
+    __shared__ int32_t buf[8][WARP_SORT_MAX];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t *a = buf[wid];
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; k < nkeys; k += nwarps) {
+        int s = offset[k], e = offset[k + 1];
+        int n = e - s;
+        if (n <= 1)
+            continue;
+        if (n <= 32) {
+            int v = lane < n ? perm[s + lane] : INT_MAX;
+#pragma unroll
+            for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+                for (int j = kk >> 1; j > 0; j >>= 1) {
+                    int o = __shfl_xor_sync(0xffffffffu, v, j);
+                    bool up = (lane & kk) == 0;
+                    bool lower = (lane & j) == 0;
+                    int mn = min(v, o), mx = max(v, o);
+                    v = (lower == up) ? mn : mx;
+                }
+            }
+            if (lane < n)
+                perm[s + lane] = v;
+        } else if (n <= WARP_SORT_MAX) {
+            int P = 64;
+            while (P < n)
+                P <<= 1;
+            for (int i = lane; i < P; i += 32)
+                a[i] = i < n ? perm[s + i] : INT_MAX;
+            __syncwarp();
+            for (int kk = 2; kk <= P; kk <<= 1) {
+                for (int j = kk >> 1; j > 0; j >>= 1) {
+                    for (int i = lane; i < P; i += 32) {
+                        int ixj = i ^ j;
+                        if (ixj > i) {
+                            int x = a[i], y = a[ixj];
+                            bool asc = (i & kk) == 0;
+                            if ((x > y) == asc) {
+                                a[i] = y;
+                                a[ixj] = x;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            for (int i = lane; i < n; i += 32)
+                perm[s + i] = a[i];
+            __syncwarp();
+        } else if (lane == 0) {
+            int slot = atomicAdd(big_count, 1);
+            big_list[slot] = (int32_t)k;
+        }
+    }
+}
+
+// Long segments: block bitonic sort in shared memory, or a quadratic ranking
+// (elements are distinct particle indices) through `scratch` beyond that.
+__global__ void __launch_bounds__(1024) k_sort_big(const int32_t *__restrict__ offset,
+                                                   int32_t *__restrict__ perm,
+                                                   const int32_t *__restrict__ big_list,
+                                                   const int32_t *__restrict__ big_count,
+                                                   int32_t *__restrict__ scratch, uint32_t *status)
+{
+    __shared__ int32_t a[BLOCK_SORT_MAX];
+    const int nb = *big_count;
+    for (int q = blockIdx.x; q < nb; q += gridDim.x) {
+        int64_t k = big_list[q];
+        int s = offset[k], e = offset[k + 1];
+        int n = e - s;
+        if (n <= BLOCK_SORT_MAX) {
+            int P = 64;
+            while (P < n)
+                P <<= 1;
+            for (int i = threadIdx.x; i < P; i += blockDim.x)
+                a[i] = i < n ? perm[s + i] : INT_MAX;
+            __syncthreads();
+            for (int kk = 2; kk <= P; kk <<= 1) {
+                for (int j = kk >> 1; j > 0; j >>= 1) {
+                    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                        int ixj = i ^ j;
+                        if (ixj > i) {
+                            int x = a[i], y = a[ixj];
+                            bool asc = (i & kk) == 0;
+                            if ((x > y) == asc) {
+                                a[i] = y;
+                                a[ixj] = x;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int i = threadIdx.x; i < n; i += blockDim.x)
+                perm[s + i] = a[i];
+            __syncthreads();
+        } else if (n <= RANK_SORT_MAX) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                int v = perm[s + i];
+                int r = 0;
+                for (int j = 0; j < n; ++j)
+                    r += perm[s + j] < v;
+                scratch[s + r] = v;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += blockDim.x)
+                perm[s + i] = scratch[s + i];
+            __syncthreads();
+        } else if (threadIdx.x == 0) {
+            set_status(status, MHDPIC_ST_SORT_CAP);
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_gather(int64_t np, int ncomp, const int32_t *__restrict__ perm,
+                         const T *__restrict__ src, T *__restrict__ dst)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < np;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = perm[r];
+        for (int q = 0; q < ncomp; ++q)
+            dst[(int64_t)q * np + r] = src[(int64_t)q * np + i];
+    }
+}
+
+__global__ void k_perm_out(int64_t np, const int32_t *__restrict__ perm, int64_t *__restrict__ out)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < np;
+         r += (int64_t)gridDim.x * blockDim.x)
+        out[r] = perm[r];
+}
+
+// Items per brick: ceil(count / ITEM_MAX_PARTICLES) near-equal pieces.
+__global__ void k_brick_items(Ctx c, const int64_t *__restrict__ brick_start,
+                              const int32_t *__restrict__ offset, int32_t *__restrict__ nitems_of)
+{
+    int64_t nbt = c.nbricks_total;
+    int vol = c.brick[0] * c.brick[1] * c.brick[2];
+    for (int64_t gb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gb < nbt;
+         gb += (int64_t)gridDim.x * blockDim.x) {
+        int bx = find_box(brick_start, c.nbox, gb);
+        const BoxDev &b = c.boxes[bx];
+        int64_t k0 = b.key0 + (gb - b.brick0) * vol;
+        int cnt = offset[k0 + vol] - offset[k0];
+        nitems_of[gb] = (cnt + ITEM_MAX_PARTICLES - 1) / ITEM_MAX_PARTICLES;
+    }
+}
+
+__global__ void k_write_items(Ctx c, const int64_t *__restrict__ brick_start,
+                              const int32_t *__restrict__ offset, const int32_t *__restrict__ nitems_of,
+                              const int32_t *__restrict__ item_off, WorkItem *__restrict__ items,
+                              int32_t *__restrict__ nitems)
+{
+    int64_t nbt = c.nbricks_total;
+    int vol = c.brick[0] * c.brick[1] * c.brick[2];
+    for (int64_t gb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gb < nbt;
+         gb += (int64_t)gridDim.x * blockDim.x) {
+        int bx = find_box(brick_start, c.nbox, gb);
+        const BoxDev &b = c.boxes[bx];
+        int64_t k0 = b.key0 + (gb - b.brick0) * vol;
+        int64_t p0 = offset[k0], p1 = offset[k0 + vol];
+        int m = nitems_of[gb];
+        if (m == 0)
+            continue;
+        int64_t chunk = (p1 - p0 + m - 1) / m;
+        int64_t o = item_off[gb];
+        for (int t = 0; t < m; ++t) {
+            WorkItem w;
+            w.box = bx;
+            w.brick = (int32_t)(gb - b.brick0);
+            w.p0 = p0 + t * chunk;
+            w.p1 = min(p1, p0 + (t + 1) * chunk);
+            items[o + t] = w;
+        }
+        if (gb == nbt - 1)
+            *nitems = item_off[nbt];
+    }
+}
+
+__global__ void k_max_count(int64_t n, const int32_t *__restrict__ count, int32_t *out)
+{
+    int m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, count[i]);
+    for (int o = 16; o > 0; o >>= 1)
+        m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(out, m);
+}
+
+int grid_for(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1)
+        b = 1;
+    if (b > 152 * 32)
+        b = 152 * 32;
+    return (int)b;
+}
+
+}  // namespace
+
+int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *counts_out,
+                cudaStream_t st)
+{
+    int launches = 0;
+    cudaMemsetAsync(s.count, 0, sizeof(int32_t) * (c.nkeys + 1), st);
+    if (c.np > 0) {
+        if (c.prec == MHDPIC_PREC_MIXED)
+            k_sort_keys<MHDPIC_PREC_MIXED><<<grid_for(c.np, 256), 256, 0, st>>>(c, s.count, s.pkey, s.pslot);
+        else
+            k_sort_keys<MHDPIC_PREC_FP64><<<grid_for(c.np, 256), 256, 0, st>>>(c, s.count, s.pkey, s.pslot);
+        ++launches;
+    }
+    launches += scan(s.count, c.nkeys, s.offset, s.scan_tmp, st);
+    if (c.np > 0) {
+        k_sort_scatter<<<grid_for(c.np, 256), 256, 0, st>>>(c.np, s.pkey, s.pslot, s.offset, s.perm);
+        cudaMemsetAsync(s.big_count, 0, sizeof(int32_t), st);
+        int64_t nw = (c.nkeys + 7) / 8;
+        int gb = (int)(nw < 152 * 16 ? (nw < 1 ? 1 : nw) : 152 * 16);
+        k_sort_segments<<<gb, 256, 0, st>>>(c.nkeys, s.offset, s.perm, s.big_list, s.big_count);
+        k_sort_big<<<152, 1024, 0, st>>>(s.offset, s.perm, s.big_list, s.big_count, s.pkey, c.status);
+        launches += 3;
+        // gather the particle arrays through the permutation (staged copy first)
+        int g = grid_for(c.np, 256);
+        char *tmp = (char *)s.tmp;
+        if (c.prec == MHDPIC_PREC_MIXED) {
+            size_t nb_cell = sizeof(int32_t) * c.np, nb_off = sizeof(float) * c.ndim * c.np,
+                   nb_p = sizeof(float) * 3 * c.np;
+            cudaMemcpyAsync(tmp, c.cell, nb_cell, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(tmp + nb_cell, c.off, nb_off, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(tmp + nb_cell + nb_off, c.p, nb_p, cudaMemcpyDeviceToDevice, st);
+            k_gather<int32_t><<<g, 256, 0, st>>>(c.np, 1, s.perm, (const int32_t *)tmp, c.cell);
+            k_gather<float><<<g, 256, 0, st>>>(c.np, c.ndim, s.perm, (const float *)(tmp + nb_cell), c.off);
+            k_gather<float><<<g, 256, 0, st>>>(c.np, 3, s.perm, (const float *)(tmp + nb_cell + nb_off), c.p);
+            launches += 3;
+        } else {
+            size_t nb_x = sizeof(double) * c.ndim * c.np, nb_p = sizeof(double) * 3 * c.np;
+            cudaMemcpyAsync(tmp, c.x, nb_x, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(tmp + nb_x, c.p64, nb_p, cudaMemcpyDeviceToDevice, st);
+            k_gather<double><<<g, 256, 0, st>>>(c.np, c.ndim, s.perm, (const double *)tmp, c.x);
+            k_gather<double><<<g, 256, 0, st>>>(c.np, 3, s.perm, (const double *)(tmp + nb_x), c.p64);
+            launches += 2;
+        }
+        if (perm_out) {
+            k_perm_out<<<g, 256, 0, st>>>(c.np, s.perm, perm_out);
+            ++launches;
+        }
+    }
+    if (counts_out)
+        cudaMemcpyAsync(counts_out, s.count, sizeof(int32_t) * c.nkeys, cudaMemcpyDeviceToDevice, st);
+    // work list
+    const int64_t *brick_start = s.brick_start;
+    int32_t *nitems_of = s.brick_items;
+    int32_t *item_off = s.item_off;
+    int gb = grid_for(c.nbricks_total, 256);
+    k_brick_items<<<gb, 256, 0, st>>>(c, brick_start, s.offset, nitems_of);
+    launches += 1 + scan(nitems_of, c.nbricks_total, item_off, s.scan_tmp, st);
+    cudaMemsetAsync(s.nitems, 0, sizeof(int32_t), st);
+    k_write_items<<<gb, 256, 0, st>>>(c, brick_start, s.offset, nitems_of, item_off, s.items, s.nitems);
+    ++launches;
+    return launches;
+}
+
+int launch_max_count(const Ctx &c, const SortScratch &s, cudaStream_t st)
+{
+    cudaMemsetAsync(s.max_count, 0, sizeof(int32_t), st);
+    k_max_count<<<grid_for(c.nkeys, 256), 256, 0, st>>>(c.nkeys, s.count, s.max_count);
+    return 1;
+}
+
+}  // namespace mhdpic

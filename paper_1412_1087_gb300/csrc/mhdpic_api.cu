@@ -1,0 +1,589 @@
+// C ABI of the sm_103a MHD-PIC cosmic-ray particle library (include/mhdpic.h).
+//
+// Host-side only: argument validation, the box table, scratch allocation,
+// host<->device staging of caller buffers in MEM_HOST mode, and the order of
+// the kernel launches of each entry point.  All arithmetic runs in the
+// kernels of k_push.cu, k_cells.cu and k_sort.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mhdpic_internal.cuh"
+
+using namespace mhdpic;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(MHDPIC_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess)                     \
+            return cuda_fail(e_, #call);           \
+    } while (0)
+
+}  // namespace
+
+struct mhdpic_ctx {
+    Ctx k{};
+    SortScratch s{};
+    cudaStream_t stream = nullptr;
+    int nbox = 0;
+    int mem = MHDPIC_MEM_DEVICE;
+    int cur = 0;              // moments buffer holding the latest deposit
+    bool next_clear = false;  // buffer cur^1 is known to be zero (the stage kernel clears it)
+    int grid_blocks = 0;      // persistent push grid
+    int nchunks = 0;          // totals reduction chunks per box
+    int32_t *work_ctr = nullptr;
+    double *partials = nullptr;
+    double *totals_dev = nullptr;
+    int64_t launches = 0;
+    std::vector<BoxDev> boxes;
+    std::vector<int64_t> part_start, cell_start, brick_start;
+    std::vector<void *> allocs;
+    // caller's host buffers in MEM_HOST mode
+    mhdpic_particles hp{};
+    mhdpic_gas hg{};
+    bool valid = false;
+
+    template <typename T>
+    int alloc(T **p, size_t count)
+    {
+        *p = nullptr;
+        if (count == 0)
+            count = 1;
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, sizeof(T) * count);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MHDPIC_E_NOMEM, "cudaMalloc of %zu bytes failed: %s", sizeof(T) * count,
+                        cudaGetErrorString(e));
+        }
+        allocs.push_back(q);
+        *p = (T *)q;
+        return MHDPIC_OK;
+    }
+
+    size_t particle_bytes() const
+    {
+        return k.prec == MHDPIC_PREC_MIXED ? (size_t)(4 + 4 * k.ndim + 12) : (size_t)(8 * k.ndim + 24);
+    }
+};
+
+namespace {
+
+int check_launch(mhdpic_ctx *c, int n)
+{
+    c->launches += n;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_fail(e, "kernel launch");
+    return MHDPIC_OK;
+}
+
+int copy_particles(mhdpic_ctx *c, bool to_device)
+{
+    if (c->mem != MHDPIC_MEM_HOST || c->k.np == 0)
+        return MHDPIC_OK;
+    const int64_t np = c->k.np;
+    cudaMemcpyKind kind = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    auto cp = [&](void *dev, void *host, size_t bytes) {
+        return to_device ? cudaMemcpyAsync(dev, host, bytes, kind, c->stream)
+                         : cudaMemcpyAsync(host, dev, bytes, kind, c->stream);
+    };
+    if (c->k.prec == MHDPIC_PREC_MIXED) {
+        CK(cp(c->k.cell, c->hp.cell, sizeof(int32_t) * np));
+        CK(cp(c->k.off, c->hp.off, sizeof(float) * c->k.ndim * np));
+        CK(cp(c->k.p, c->hp.p, sizeof(float) * 3 * np));
+    } else {
+        CK(cp(c->k.x, c->hp.x, sizeof(double) * c->k.ndim * np));
+        CK(cp(c->k.p64, c->hp.p64, sizeof(double) * 3 * np));
+    }
+    return MHDPIC_OK;
+}
+
+// all: rho, mom, egas, B; otherwise only the arrays the feedback changes
+int copy_gas(mhdpic_ctx *c, bool to_device, bool all)
+{
+    if (c->mem != MHDPIC_MEM_HOST)
+        return MHDPIC_OK;
+    const int64_t nc = c->k.nc;
+    if (to_device) {
+        if (all) {
+            CK(cudaMemcpyAsync(c->k.rho, c->hg.rho, sizeof(double) * nc, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(c->k.B, c->hg.B, sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, c->stream));
+        }
+        CK(cudaMemcpyAsync(c->k.mom, c->hg.mom, sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->k.egas, c->hg.egas, sizeof(double) * nc, cudaMemcpyHostToDevice, c->stream));
+    } else {
+        CK(cudaMemcpyAsync(c->hg.mom, c->k.mom, sizeof(double) * 3 * nc, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(c->hg.egas, c->k.egas, sizeof(double) * nc, cudaMemcpyDeviceToHost, c->stream));
+    }
+    return MHDPIC_OK;
+}
+
+// Static scales of the charge / current channels: |n| <= |qm| m / dV and
+// |J| <= |qm| m C / dV per particle, H = 3^D (4 maxcount + 64) per cell.
+void moment_scales(mhdpic_ctx *c, int maxcount)
+{
+    const double H = (c->k.ndim == 3 ? 27.0 : 9.0) * (4.0 * maxcount + 64.0);
+    for (auto &b : c->boxes) {
+        double qn = std::fabs(b.qm_cr) * std::fabs(b.m_cr) * b.inv_dV;
+        double q[4] = {qn, qn * b.C, qn * b.C, qn * b.C};
+        for (int k = 0; k < 4; ++k) {
+            double Q = std::fmax(q[k], 1e-280);
+            int e;
+            std::frexp(4611686018427387904.0 / (Q * H), &e);
+            e -= 1;
+            if (e > 1000)
+                e = 1000;
+            b.scale[CH_N + k] = std::ldexp(1.0, e);
+            b.inv_scale[CH_N + k] = std::ldexp(1.0, -e);
+            b.qmax[CH_N + k] = 4.0 * Q;
+        }
+        for (int k = 0; k < 4; ++k) {   // corrector: sized by the first push
+            b.scale[k] = 1.0;
+            b.inv_scale[k] = 1.0;
+            b.qmax[k] = 1e300;
+        }
+    }
+}
+
+int validate(int32_t nbox, const mhdpic_grid *grids, const mhdpic_params *params,
+             const mhdpic_options *opt, const mhdpic_particles *parts, const mhdpic_gas *gas)
+{
+    if (nbox < 1)
+        return fail(MHDPIC_E_ARG, "nbox must be >= 1 (got %d)", nbox);
+    if (!grids || !params || !opt || !parts || !gas)
+        return fail(MHDPIC_E_ARG, "grids, params, options, particles and gas must be non-NULL");
+    if (opt->precision != MHDPIC_PREC_MIXED && opt->precision != MHDPIC_PREC_FP64)
+        return fail(MHDPIC_E_ARG, "unknown precision %d", opt->precision);
+    if (opt->memory != MHDPIC_MEM_DEVICE && opt->memory != MHDPIC_MEM_HOST)
+        return fail(MHDPIC_E_ARG, "unknown memory kind %d", opt->memory);
+    if (!parts->box_start)
+        return fail(MHDPIC_E_ARG, "particles.box_start must be a host array of nbox+1 offsets");
+    if (parts->np < 0 || parts->np > 0x7fffffffLL)
+        return fail(MHDPIC_E_CAPACITY, "particle count %lld outside [0, 2^31)", (long long)parts->np);
+    if (parts->box_start[0] != 0 || parts->box_start[nbox] != parts->np)
+        return fail(MHDPIC_E_ARG, "box_start must run from 0 to np");
+    const int ndim = grids[0].ndim;
+    int64_t nc = 0;
+    for (int b = 0; b < nbox; ++b) {
+        const mhdpic_grid &g = grids[b];
+        const mhdpic_params &p = params[b];
+        if (parts->box_start[b + 1] < parts->box_start[b])
+            return fail(MHDPIC_E_ARG, "box_start must be non-decreasing (box %d)", b);
+        if (g.ndim != ndim || (ndim != 2 && ndim != 3))
+            return fail(MHDPIC_E_ARG, "box %d: ndim must be 2 or 3 and equal for all boxes", b);
+        for (int d = 0; d < 3; ++d) {
+            if (g.n[d] < 1)
+                return fail(MHDPIC_E_ARG, "box %d: n[%d] must be >= 1", b, d);
+            if (!(g.dx[d] > 0.0) || !std::isfinite(g.dx[d]) || !std::isfinite(g.x0[d]))
+                return fail(MHDPIC_E_ARG, "box %d: dx[%d] must be finite and > 0", b, d);
+            if (g.bc[d] != MHDPIC_BC_PERIODIC && g.bc[d] != MHDPIC_BC_REFLECT)
+                return fail(MHDPIC_E_ARG, "box %d: unknown boundary %d", b, g.bc[d]);
+        }
+        if (ndim == 2 && g.n[2] != 1)
+            return fail(MHDPIC_E_ARG, "box %d: a 2-D box must have n[2] == 1", b);
+        int64_t ncb = (int64_t)g.n[0] * g.n[1] * g.n[2];
+        if (ncb > 0x7fffffffLL)
+            return fail(MHDPIC_E_CAPACITY, "box %d: %lld cells exceed 2^31", b, (long long)ncb);
+        nc += ncb;
+        if (p.shape != MHDPIC_SHAPE_TSC)
+            return fail(MHDPIC_E_ARG, "box %d: only MHDPIC_SHAPE_TSC is supported", b);
+        if (!(p.C > 0.0) || !std::isfinite(p.C))
+            return fail(MHDPIC_E_ARG, "box %d: C must be finite and > 0", b);
+        if (!std::isfinite(p.qm_cr) || !std::isfinite(p.m_cr) || p.m_cr < 0.0)
+            return fail(MHDPIC_E_ARG, "box %d: qm_cr must be finite and m_cr finite and >= 0", b);
+        if (p.hall && !(p.qm_gas > 0.0))
+            return fail(MHDPIC_E_ARG, "box %d: the CR-Hall term needs qm_gas > 0", b);
+    }
+    if (nc > 0x7fffffffLL)
+        return fail(MHDPIC_E_CAPACITY, "%lld cells in total exceed 2^31", (long long)nc);
+    if (opt->precision == MHDPIC_PREC_MIXED) {
+        if (parts->np > 0 && (!parts->cell || !parts->off || !parts->p))
+            return fail(MHDPIC_E_ARG, "mixed precision needs particles.cell, .off and .p");
+    } else if (parts->np > 0 && (!parts->x || !parts->p64)) {
+        return fail(MHDPIC_E_ARG, "FP64 needs particles.x and .p64");
+    }
+    if (!gas->rho || !gas->mom || !gas->egas || !gas->B)
+        return fail(MHDPIC_E_ARG, "gas.rho, .mom, .egas and .B must be non-NULL");
+    for (int d = 0; d < 3; ++d)
+        if (opt->brick[d] < 0 || opt->brick[d] > 64)
+            return fail(MHDPIC_E_ARG, "options.brick[%d] must be in [0, 64]", d);
+    return MHDPIC_OK;
+}
+
+int do_prep(mhdpic_ctx *c, int apply)
+{
+    int rc = check_launch(c, launch_prep(c->k, c->cur, apply, c->stream));
+    if (rc == MHDPIC_OK)
+        c->next_clear = true;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mhdpic_strerror(int code)
+{
+    switch (code) {
+    case MHDPIC_OK: return "success";
+    case MHDPIC_E_ARG: return "invalid argument";
+    case MHDPIC_E_CUDA: return "CUDA runtime error";
+    case MHDPIC_E_NOMEM: return "device allocation failed";
+    case MHDPIC_E_STATUS: return "a device status flag is set";
+    case MHDPIC_E_CAPACITY: return "a size limit of the library was exceeded";
+    case MHDPIC_E_STATE: return "call made in the wrong state";
+    default: return "unknown error";
+    }
+}
+
+const char *mhdpic_last_error(void) { return g_last_error.c_str(); }
+
+int mhdpic_destroy(mhdpic_ctx *c)
+{
+    if (!c)
+        return MHDPIC_OK;
+    if (c->stream || c->valid)
+        cudaStreamSynchronize(c->stream);
+    for (void *p : c->allocs)
+        cudaFree(p);
+    c->valid = false;
+    delete c;
+    return MHDPIC_OK;
+}
+
+int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const mhdpic_params *params,
+                const mhdpic_options *opt, const mhdpic_particles *parts, const mhdpic_gas *gas,
+                void *stream)
+{
+    if (!out)
+        return fail(MHDPIC_E_ARG, "ctx out-pointer is NULL");
+    *out = nullptr;
+    int rc = validate(nbox, grids, params, opt, parts, gas);
+    if (rc)
+        return rc;
+    mhdpic_ctx *c = new mhdpic_ctx();
+    auto bail = [&](int code) {
+        mhdpic_destroy(c);
+        return code;
+    };
+    c->stream = (cudaStream_t)stream;
+    c->nbox = nbox;
+    c->mem = opt->memory;
+    Ctx &k = c->k;
+    k.nbox = nbox;
+    k.ndim = grids[0].ndim;
+    k.prec = opt->precision;
+    k.np = parts->np;
+    for (int d = 0; d < 3; ++d) {
+        int def = k.ndim == 3 ? 4 : (d < 2 ? 8 : 1);
+        k.brick[d] = opt->brick[d] > 0 ? opt->brick[d] : def;
+        if (d >= k.ndim)
+            k.brick[d] = 1;
+        k.tile[d] = d < k.ndim ? k.brick[d] + 2 * HALO : 1;
+    }
+    k.tile_vol = k.tile[0] * k.tile[1] * k.tile[2];
+    if (push_smem_bytes(k) > 200 * 1024)
+        return bail(fail(MHDPIC_E_CAPACITY, "brick %dx%dx%d needs %zu bytes of shared memory", k.brick[0],
+                         k.brick[1], k.brick[2], push_smem_bytes(k)));
+
+    // box table
+    c->part_start.assign(parts->box_start, parts->box_start + nbox + 1);
+    c->cell_start.assign(nbox + 1, 0);
+    c->brick_start.assign(nbox + 1, 0);
+    int64_t key0 = 0;
+    for (int b = 0; b < nbox; ++b) {
+        const mhdpic_grid &g = grids[b];
+        const mhdpic_params &p = params[b];
+        BoxDev bd{};
+        for (int d = 0; d < 3; ++d) {
+            bd.n[d] = g.n[d];
+            bd.bc[d] = g.bc[d];
+            bd.dx[d] = g.dx[d];
+            bd.inv_dx[d] = 1.0 / g.dx[d];
+            bd.x0[d] = g.x0[d];
+            bd.nb[d] = (g.n[d] + k.brick[d] - 1) / k.brick[d];
+        }
+        bd.ndim = g.ndim;
+        bd.hall = p.hall;
+        bd.dV = g.dx[0] * g.dx[1] * g.dx[2];
+        bd.inv_dV = 1.0 / bd.dV;
+        bd.qm_cr = p.qm_cr;
+        bd.qm_gas = p.qm_gas;
+        bd.C = p.C;
+        bd.m_cr = p.m_cr;
+        bd.ncell = (int64_t)g.n[0] * g.n[1] * g.n[2];
+        bd.cell0 = c->cell_start[b];
+        c->cell_start[b + 1] = bd.cell0 + bd.ncell;
+        bd.part0 = parts->box_start[b];
+        bd.part1 = parts->box_start[b + 1];
+        bd.nbricks = bd.nb[0] * bd.nb[1] * bd.nb[2];
+        bd.brick0 = c->brick_start[b];
+        c->brick_start[b + 1] = bd.brick0 + bd.nbricks;
+        bd.key0 = key0;
+        bd.nkeys = (int64_t)bd.nbricks * k.brick[0] * k.brick[1] * k.brick[2];
+        key0 += bd.nkeys;
+        bd.div_nx = make_fastdiv((uint32_t)g.n[0]);
+        bd.div_nxy = make_fastdiv((uint32_t)(g.n[0] * g.n[1]));
+        c->boxes.push_back(bd);
+    }
+    k.nc = c->cell_start[nbox];
+    k.nkeys = key0;
+    k.nbricks_total = c->brick_start[nbox];
+    if (k.nkeys >= 0x7fffffffLL)
+        return bail(fail(MHDPIC_E_CAPACITY, "%lld sort keys exceed 2^31", (long long)k.nkeys));
+
+    // device allocations
+    const int64_t np = k.np, nc = k.nc;
+    BoxDev *boxes_d;
+    int64_t *ps_d, *cs_d;
+    if ((rc = c->alloc(&boxes_d, nbox)) || (rc = c->alloc(&ps_d, nbox + 1)) || (rc = c->alloc(&cs_d, nbox + 1)) ||
+        (rc = c->alloc(&c->s.brick_start, nbox + 1)) || (rc = c->alloc(&k.stats, nbox)))
+        return bail(rc);
+    k.boxes = boxes_d;
+    k.boxes_rw = boxes_d;
+    k.box_part_start = ps_d;
+    k.box_cell_start = cs_d;
+    if ((rc = c->alloc(&k.corr, 4 * nc)) || (rc = c->alloc(&k.momdep[0], 4 * nc)) ||
+        (rc = c->alloc(&k.momdep[1], 4 * nc)) || (rc = c->alloc(&k.status, 1)))
+        return bail(rc);
+    if (k.prec == MHDPIC_PREC_MIXED)
+        rc = c->alloc(&k.f32, 8 * nc);
+    else
+        rc = c->alloc(&k.f64, 6 * nc);
+    if (rc)
+        return bail(rc);
+    int64_t scan_n = std::max<int64_t>(k.nkeys, k.nbricks_total) / 4096 + 2;
+    if ((rc = c->alloc(&c->s.count, k.nkeys + 1)) || (rc = c->alloc(&c->s.offset, k.nkeys + 1)) ||
+        (rc = c->alloc(&c->s.pkey, np)) || (rc = c->alloc(&c->s.pslot, np)) || (rc = c->alloc(&c->s.perm, np)) ||
+        (rc = c->alloc(&c->s.scan_tmp, scan_n)) || (rc = c->alloc(&c->s.big_list, k.nkeys + 1)) ||
+        (rc = c->alloc(&c->s.big_count, 1)) ||
+        (rc = c->alloc((char **)&c->s.tmp, (size_t)np * c->particle_bytes())) ||
+        (rc = c->alloc(&c->s.brick_items, k.nbricks_total + 1)) ||
+        (rc = c->alloc(&c->s.item_off, k.nbricks_total + 1)) ||
+        (rc = c->alloc(&c->s.items, k.nbricks_total + np / ITEM_MAX_PARTICLES + 2)) ||
+        (rc = c->alloc(&c->s.nitems, 1)) || (rc = c->alloc(&c->s.max_count, 1)) ||
+        (rc = c->alloc(&c->work_ctr, 1)))
+        return bail(rc);
+    c->nchunks = 64;
+    if ((rc = c->alloc(&c->partials, (size_t)nbox * c->nchunks * 8)) || (rc = c->alloc(&c->totals_dev, 8 * nbox)))
+        return bail(rc);
+
+    // caller buffers (or device mirrors of host ones)
+    if (c->mem == MHDPIC_MEM_HOST) {
+        c->hp = *parts;
+        c->hg = *gas;
+        if (k.prec == MHDPIC_PREC_MIXED) {
+            if ((rc = c->alloc(&k.cell, np)) || (rc = c->alloc(&k.off, k.ndim * np)) || (rc = c->alloc(&k.p, 3 * np)))
+                return bail(rc);
+        } else if ((rc = c->alloc(&k.x, k.ndim * np)) || (rc = c->alloc(&k.p64, 3 * np))) {
+            return bail(rc);
+        }
+        if ((rc = c->alloc(&k.rho, nc)) || (rc = c->alloc(&k.mom, 3 * nc)) || (rc = c->alloc(&k.egas, nc)) ||
+            (rc = c->alloc(&k.B, 3 * nc)))
+            return bail(rc);
+    } else {
+        k.cell = parts->cell;
+        k.off = parts->off;
+        k.p = parts->p;
+        k.x = parts->x;
+        k.p64 = parts->p64;
+        k.rho = gas->rho;
+        k.mom = gas->mom;
+        k.egas = gas->egas;
+        k.B = gas->B;
+    }
+    cudaStream_t st = c->stream;
+    if ((rc = copy_particles(c, true)) || (rc = copy_gas(c, true, true)))
+        return bail(rc);
+    if (cudaMemcpyAsync(ps_d, c->part_start.data(), sizeof(int64_t) * (nbox + 1), cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(cs_d, c->cell_start.data(), sizeof(int64_t) * (nbox + 1), cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(c->s.brick_start, c->brick_start.data(), sizeof(int64_t) * (nbox + 1),
+                        cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(boxes_d, c->boxes.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice, st) ||
+        cudaMemsetAsync(k.corr, 0, sizeof(unsigned long long) * 4 * nc, st) ||
+        cudaMemsetAsync(k.momdep[0], 0, sizeof(unsigned long long) * 4 * nc, st) ||
+        cudaMemsetAsync(k.momdep[1], 0, sizeof(unsigned long long) * 4 * nc, st) ||
+        cudaMemsetAsync(k.status, 0, sizeof(uint32_t), st) || cudaMemsetAsync(k.stats, 0, sizeof(BoxStats) * nbox, st))
+        return bail(cuda_fail(cudaGetLastError(), "init uploads"));
+
+    // sort, then size the charge/current scales from the densest cell
+    if ((rc = check_launch(c, launch_sort(k, c->s, nullptr, nullptr, st))) ||
+        (rc = check_launch(c, launch_max_count(k, c->s, st))))
+        return bail(rc);
+    int32_t maxcount = 0;
+    if (cudaMemcpyAsync(&maxcount, c->s.max_count, sizeof(int32_t), cudaMemcpyDeviceToHost, st) ||
+        cudaStreamSynchronize(st))
+        return bail(cuda_fail(cudaGetLastError(), "init max count"));
+    moment_scales(c, maxcount);
+    if (cudaMemcpyAsync(boxes_d, c->boxes.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice, st))
+        return bail(cuda_fail(cudaGetLastError(), "init scales"));
+    std::vector<BoxStats> stats(nbox);
+    for (auto &s : stats) {
+        memset(&s, 0, sizeof s);
+        s.maxcount = maxcount;
+    }
+    if (cudaMemcpyAsync(k.stats, stats.data(), sizeof(BoxStats) * nbox, cudaMemcpyHostToDevice, st) ||
+        cudaStreamSynchronize(st))
+        return bail(cuda_fail(cudaGetLastError(), "init stats"));
+
+    int bps = push_blocks_per_sm(k);
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    c->grid_blocks = bps * (nsm > 0 ? nsm : 1);
+
+    // moments at the initial positions, maxima, staged fields
+    c->cur = 0;
+    if ((rc = check_launch(c, launch_moments(k, c->cur, st))) || (rc = check_launch(c, launch_vmax(k, st))) ||
+        (rc = do_prep(c, 0)))
+        return bail(rc);
+    if ((rc = copy_particles(c, false)))
+        return bail(rc);
+    c->valid = true;
+    *out = c;
+    return MHDPIC_OK;
+}
+
+int mhdpic_sort(mhdpic_ctx *c, int64_t *perm_out, int32_t *counts_out)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    int rc;
+    if ((rc = copy_particles(c, true)))
+        return rc;
+    if ((rc = check_launch(c, launch_sort(c->k, c->s, perm_out, counts_out, c->stream))))
+        return rc;
+    // refresh the densest-cell count used by the corrector scales
+    if ((rc = check_launch(c, launch_max_count(c->k, c->s, c->stream))))
+        return rc;
+    return copy_particles(c, false);
+}
+
+int mhdpic_interp_push(mhdpic_ctx *c, double dt, int32_t nsub)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (!(dt > 0.0) || !std::isfinite(dt))
+        return fail(MHDPIC_E_ARG, "dt must be finite and > 0");
+    if (nsub < 1)
+        return fail(MHDPIC_E_ARG, "nsub must be >= 1");
+    int rc;
+    if ((rc = copy_particles(c, true)))
+        return rc;
+    if ((rc = check_launch(c, launch_scales(c->k, dt, c->stream))))
+        return rc;
+    if (!c->next_clear)   // two pushes with no staging in between
+        CK(cudaMemsetAsync(c->k.momdep[c->cur ^ 1], 0, sizeof(unsigned long long) * 4 * c->k.nc, c->stream));
+    for (int s = 0; s < nsub; ++s) {
+        bool last = s == nsub - 1;
+        if ((rc = check_launch(c, launch_push(c->k, c->s, c->work_ctr, c->cur ^ 1, last ? 1 : 0, dt,
+                                              c->grid_blocks, c->stream))))
+            return rc;
+    }
+    c->cur ^= 1;
+    c->next_clear = false;
+    return copy_particles(c, false);
+}
+
+int mhdpic_deposit(mhdpic_ctx *c)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    int rc;
+    if ((rc = copy_particles(c, true)) || (rc = copy_gas(c, true, true)))
+        return rc;
+    // the stage kernel clears buffer cur^1, so deposit into cur and stage from it
+    if ((rc = check_launch(c, launch_moments(c->k, c->cur, c->stream))) ||
+        (rc = check_launch(c, launch_vmax(c->k, c->stream))) || (rc = do_prep(c, 0)))
+        return rc;
+    return MHDPIC_OK;
+}
+
+int mhdpic_apply_feedback(mhdpic_ctx *c, double *totals_out)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    int rc;
+    if ((rc = copy_gas(c, true, true)))
+        return rc;
+    if ((rc = do_prep(c, 1)))
+        return rc;
+    if ((rc = copy_gas(c, false, false)))
+        return rc;
+    if (totals_out) {
+        if ((rc = copy_particles(c, true)))
+            return rc;
+        if ((rc = check_launch(c, launch_totals(c->k, c->partials, c->nchunks, c->totals_dev, c->stream))))
+            return rc;
+        CK(cudaMemcpyAsync(totals_out, c->totals_dev, sizeof(double) * 8 * c->nbox, cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return MHDPIC_OK;
+}
+
+int mhdpic_get_deposits(mhdpic_ctx *c, int32_t which, double *out)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (!out || (which != 0 && which != 1))
+        return fail(MHDPIC_E_ARG, "which must be 0 or 1 and out non-NULL");
+    const unsigned long long *src = which == 0 ? c->k.corr : c->k.momdep[c->cur];
+    return check_launch(c, launch_fixed_to_double(c->k, src, which == 0 ? CH_MX : CH_N, out, c->stream));
+}
+
+int mhdpic_get_fields(mhdpic_ctx *c, double *out)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (!out)
+        return fail(MHDPIC_E_ARG, "out must be non-NULL");
+    return check_launch(c, launch_fields_to_double(c->k, out, c->stream));
+}
+
+int64_t mhdpic_num_keys(const mhdpic_ctx *c) { return c && c->valid ? c->k.nkeys : -1; }
+
+int64_t mhdpic_launch_count(const mhdpic_ctx *c) { return c && c->valid ? c->launches : -1; }
+
+int mhdpic_get_status(mhdpic_ctx *c, uint32_t *flags)
+{
+    if (!c || !c->valid || !flags)
+        return fail(MHDPIC_E_ARG, "invalid context or flags pointer");
+    CK(cudaMemcpyAsync(flags, c->k.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MHDPIC_OK;
+}
+
+int mhdpic_clear_status(mhdpic_ctx *c)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    CK(cudaMemsetAsync(c->k.status, 0, sizeof(uint32_t), c->stream));
+    return MHDPIC_OK;
+}
+
+}  // extern "C"

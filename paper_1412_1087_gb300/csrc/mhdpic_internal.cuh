@@ -1,0 +1,168 @@
+// Internal declarations of the sm_103a MHD-PIC particle library.
+//
+// The device-side box table, the work items of the push, fixed-point helpers
+// and the host-side launchers that the C-ABI layer (mhdpic_api.cu) calls.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mhdpic.h"
+
+namespace mhdpic {
+
+// ---------------------------------------------------------------------------
+// channel numbering of the fixed-point deposit grids
+// ---------------------------------------------------------------------------
+// corrector (momentum and energy given to the gas, App. A.3): 0..3
+// moments (charge and current densities, eq:nJCR):          4..7
+enum { CH_MX = 0, CH_MY, CH_MZ, CH_E, CH_N, CH_JX, CH_JY, CH_JZ, NCH };
+
+// Push tile: a brick of cells plus a halo of HALO cells on every side.  A
+// particle whose 3^D stencil lies inside the tile deposits into shared memory;
+// any other particle takes the global-memory path, so the halo only decides
+// speed, never correctness.
+constexpr int HALO = 2;
+constexpr int PUSH_THREADS = 256;
+constexpr int ITEM_MAX_PARTICLES = 4096;
+
+// Fast unsigned division by a runtime constant (Granlund-Montgomery
+// round-up method): q = umulhi(n, mul) >> shift for n < 2^31.
+struct FastDiv {
+    uint32_t d, mul, shift;
+};
+
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    FastDiv f;
+    f.d = d;
+    uint32_t l = 0;
+    while ((1ull << l) < d)
+        ++l;
+    // mul = ceil(2^(32+l) / d) - 2^32 fits in 32 bits for d >= 1
+    uint64_t m = ((1ull << (32 + l)) + d - 1) / d;
+    f.mul = (uint32_t)(m - (1ull << 32));
+    f.shift = l;
+    if (d == 1) {
+        f.mul = 0;
+        f.shift = 0;
+    }
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f)
+{
+    uint32_t t = __umulhi(n, f.mul);
+    return (t + n) >> f.shift;   // exact for n < 2^31 (31-bit numerators)
+}
+
+// One box as the kernels see it.
+struct BoxDev {
+    int32_t n[3];
+    int32_t bc[3];
+    int32_t hall;
+    int32_t ndim;
+    double dx[3], inv_dx[3], x0[3];
+    double dV, inv_dV;
+    double qm_cr, qm_gas, C, m_cr;
+    int64_t cell0;   // first global cell of the box
+    int64_t ncell;
+    int64_t part0, part1;
+    int64_t key0;    // first sort key of the box
+    int64_t nkeys;
+    int32_t nb[3];   // bricks per dimension
+    int32_t nbricks;
+    int64_t brick0;  // first global brick number
+    FastDiv div_nx, div_nxy;
+    double scale[NCH];     // fixed-point scale (a power of two) per channel
+    double inv_scale[NCH];
+    double qmax[NCH];      // largest particle quantity the scale was sized for
+};
+
+// Per-box maxima tracked on the device; they size the corrector scales.
+// Non-negative floats are stored as their bit patterns so that an unsigned
+// atomicMax orders them correctly.
+struct BoxStats {
+    uint32_t vmax;        // max |v| of the particles (four-velocity)
+    uint32_t emax;        // max |E| of the staged cell fields
+    uint32_t bmax;        // max |B| of the staged cell fields
+    int32_t maxcount;     // max particles per cell at the last sort
+    int32_t corr_dirty;   // corrector accumulators hold data: scales locked
+    int32_t pad;
+};
+
+// A contiguous run of sorted particles that all belong to one brick.
+struct WorkItem {
+    int32_t box;
+    int32_t brick;   // brick number inside the box
+    int64_t p0, p1;  // particle range
+};
+
+// Everything a kernel needs, passed by value.
+struct Ctx {
+    int32_t nbox, ndim, prec;
+    int32_t brick[3];
+    int32_t tile[3];       // brick + 2*HALO
+    int32_t tile_vol;
+    int64_t np, nc, nkeys, nbricks_total;
+    const BoxDev *boxes;   // device
+    const int64_t *box_part_start; // device [nbox+1]
+    const int64_t *box_cell_start; // device [nbox+1]
+    // caller (or mirror) buffers, device
+    int32_t *cell;
+    float *off;
+    float *p;
+    double *x;
+    double *p64;
+    double *rho, *mom, *egas, *B;
+    // scratch
+    unsigned long long *corr;     // [4][nc]
+    unsigned long long *momdep[2];// [4][nc] each
+    float *f32;                   // [nc][8] = Ex,Ey,Ez,Bx,By,Bz,0,0
+    double *f64;                  // [nc][6]
+    uint32_t *status;
+    BoxDev *boxes_rw;             // same table, writable by the scale kernel
+    BoxStats *stats;              // [nbox]
+};
+
+// ---------------------------------------------------------------------------
+// launchers (each returns the number of kernel launches it made, or -1 on a
+// launch error; the caller checks cudaGetLastError)
+// ---------------------------------------------------------------------------
+struct SortScratch {
+    int32_t *count;     // [nkeys + 1]
+    int32_t *offset;    // [nkeys + 1]
+    int32_t *pkey;      // [np]
+    int32_t *pslot;     // [np]
+    int32_t *perm;      // [np]
+    int32_t *scan_tmp;  // block sums
+    int32_t *big_list;  // segments longer than a warp can sort
+    int32_t *big_count; // [1]
+    void *tmp;          // particle staging, np * (largest particle record)
+    int32_t *brick_items;  // [nbricks + 1] items per brick
+    int32_t *item_off;     // [nbricks + 1] exclusive scan of brick_items
+    int64_t *brick_start;  // device [nbox + 1] first global brick of each box
+    WorkItem *items;
+    int32_t *nitems;       // [1]
+    int32_t *max_count;    // [1]
+};
+
+int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *counts_out,
+                cudaStream_t st);
+int launch_max_count(const Ctx &c, const SortScratch &s, cudaStream_t st);
+int launch_vmax(const Ctx &c, cudaStream_t st);
+int launch_prep(const Ctx &c, int cur, int apply, cudaStream_t st);
+int launch_moments(const Ctx &c, int cur, cudaStream_t st);
+int launch_push(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur_out, int full,
+                double dt, int grid_blocks, cudaStream_t st);
+int launch_scales(const Ctx &c, double dt, cudaStream_t st);
+int launch_totals(const Ctx &c, double *partials, int nchunks, double *out, cudaStream_t st);
+int launch_fixed_to_double(const Ctx &c, const unsigned long long *src, int ch0, double *out,
+                           cudaStream_t st);
+int launch_fields_to_double(const Ctx &c, double *out, cudaStream_t st);
+
+// occupancy helpers
+int push_blocks_per_sm(const Ctx &c);
+size_t push_smem_bytes(const Ctx &c);
+
+}  // namespace mhdpic

@@ -1,0 +1,333 @@
+"""Thin ctypes binding of the sm_103a library ``libmhdpic.so`` (include/mhdpic.h).
+
+Argument marshalling only: every step of the particle update runs in the
+library's CUDA kernels.  PyTorch provides device memory and the stream.  If the
+library is missing the import of any entry point raises; there is no CPU
+fallback.
+
+The functions carry the C names (``mhdpic_init``, ``mhdpic_sort``,
+``mhdpic_interp_push``, ``mhdpic_deposit``, ``mhdpic_apply_feedback`` ...) and
+raise :class:`MhdpicError` on a non-zero return code.  :class:`Engine` wraps a
+context around a list of :class:`workloads.Box` objects.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmhdpic.so")
+
+MHDPIC_OK = 0
+MHDPIC_BC_PERIODIC = 0
+MHDPIC_BC_REFLECT = 1
+MHDPIC_SHAPE_TSC = 2
+MHDPIC_PREC_FP64 = 0
+MHDPIC_PREC_MIXED = 1
+MHDPIC_MEM_DEVICE = 0
+MHDPIC_MEM_HOST = 1
+STATUS_NAMES = {1: "FAST_MOVER", 2: "NONFINITE", 4: "OVERFLOW", 8: "SORT_CAP", 16: "CELL_RANGE"}
+
+
+class MhdpicError(RuntimeError):
+    pass
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("dx", ctypes.c_double * 3),
+                ("x0", ctypes.c_double * 3), ("bc", ctypes.c_int32 * 3)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("qm_cr", ctypes.c_double), ("qm_gas", ctypes.c_double), ("C", ctypes.c_double),
+                ("m_cr", ctypes.c_double), ("hall", ctypes.c_int32), ("shape", ctypes.c_int32)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("memory", ctypes.c_int32), ("brick", ctypes.c_int32 * 3),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class Particles(ctypes.Structure):
+    _fields_ = [("np", ctypes.c_int64), ("box_start", ctypes.POINTER(ctypes.c_int64)),
+                ("cell", ctypes.c_void_p), ("off", ctypes.c_void_p), ("p", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("p64", ctypes.c_void_p)]
+
+
+class Gas(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_void_p), ("mom", ctypes.c_void_p), ("egas", ctypes.c_void_p),
+                ("B", ctypes.c_void_p)]
+
+
+# every symbol the header declares, with its ctypes signature
+_V = ctypes.c_void_p
+SIGNATURES = {
+    "mhdpic_init": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int32, ctypes.POINTER(Grid),
+                                   ctypes.POINTER(Params), ctypes.POINTER(Options),
+                                   ctypes.POINTER(Particles), ctypes.POINTER(Gas), _V]),
+    "mhdpic_sort": (ctypes.c_int, [_V, _V, _V]),
+    "mhdpic_interp_push": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32]),
+    "mhdpic_deposit": (ctypes.c_int, [_V]),
+    "mhdpic_apply_feedback": (ctypes.c_int, [_V, _V]),
+    "mhdpic_get_deposits": (ctypes.c_int, [_V, ctypes.c_int32, _V]),
+    "mhdpic_get_fields": (ctypes.c_int, [_V, _V]),
+    "mhdpic_num_keys": (ctypes.c_int64, [_V]),
+    "mhdpic_get_status": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_uint32)]),
+    "mhdpic_clear_status": (ctypes.c_int, [_V]),
+    "mhdpic_launch_count": (ctypes.c_int64, [_V]),
+    "mhdpic_destroy": (ctypes.c_int, [_V]),
+    "mhdpic_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "mhdpic_last_error": (ctypes.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the library (built by ``paper_1412_1087_gb300.build``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise MhdpicError("CUDA library %s is missing: run __graft_entry__.build() "
+                                  "(there is no CPU fallback)" % path)
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int) -> None:
+    if rc != MHDPIC_OK:
+        lib = load()
+        raise MhdpicError("%s (%d): %s" % (lib.mhdpic_strerror(rc).decode(), rc,
+                                           lib.mhdpic_last_error().decode()))
+
+
+# ---------------------------------------------------------------------------
+# C-named entry points
+# ---------------------------------------------------------------------------
+
+def mhdpic_init(nbox, grids, params, options, particles, gas, stream) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(load().mhdpic_init(ctypes.byref(ctx), nbox, grids, params, ctypes.byref(options),
+                              ctypes.byref(particles), ctypes.byref(gas), stream))
+    return ctx
+
+
+def mhdpic_sort(ctx, perm_out: int = 0, counts_out: int = 0) -> None:
+    _check(load().mhdpic_sort(ctx, perm_out or None, counts_out or None))
+
+
+def mhdpic_interp_push(ctx, dt: float, nsub: int = 1) -> None:
+    _check(load().mhdpic_interp_push(ctx, float(dt), int(nsub)))
+
+
+def mhdpic_deposit(ctx) -> None:
+    _check(load().mhdpic_deposit(ctx))
+
+
+def mhdpic_apply_feedback(ctx, totals_out: Optional[np.ndarray] = None) -> None:
+    ptr = None
+    if totals_out is not None:
+        assert totals_out.dtype == np.float64 and totals_out.flags["C_CONTIGUOUS"]
+        ptr = totals_out.ctypes.data_as(ctypes.c_void_p)
+    _check(load().mhdpic_apply_feedback(ctx, ptr))
+
+
+def mhdpic_get_deposits(ctx, which: int, out_ptr: int) -> None:
+    _check(load().mhdpic_get_deposits(ctx, int(which), out_ptr))
+
+
+def mhdpic_get_fields(ctx, out_ptr: int) -> None:
+    _check(load().mhdpic_get_fields(ctx, out_ptr))
+
+
+def mhdpic_num_keys(ctx) -> int:
+    return int(load().mhdpic_num_keys(ctx))
+
+
+def mhdpic_get_status(ctx) -> int:
+    f = ctypes.c_uint32(0)
+    _check(load().mhdpic_get_status(ctx, ctypes.byref(f)))
+    return int(f.value)
+
+
+def mhdpic_clear_status(ctx) -> None:
+    _check(load().mhdpic_clear_status(ctx))
+
+
+def mhdpic_launch_count(ctx) -> int:
+    return int(load().mhdpic_launch_count(ctx))
+
+
+def mhdpic_destroy(ctx) -> None:
+    _check(load().mhdpic_destroy(ctx))
+
+
+def status_names(flags: int) -> List[str]:
+    return [name for bit, name in STATUS_NAMES.items() if flags & bit]
+
+
+# ---------------------------------------------------------------------------
+# Engine: a context over a batch of boxes held in torch tensors
+# ---------------------------------------------------------------------------
+
+class Engine:
+    """Owns torch buffers for a batch of boxes and one library context.
+
+    ``precision``: MHDPIC_PREC_MIXED or MHDPIC_PREC_FP64.
+    ``memory``: MHDPIC_MEM_DEVICE (buffers on cuda) or MHDPIC_MEM_HOST (pinned
+    host buffers; every call copies through the library).
+    """
+
+    def __init__(self, boxes: Sequence, precision: int = MHDPIC_PREC_MIXED,
+                 memory: int = MHDPIC_MEM_DEVICE, brick: Sequence[int] = (0, 0, 0),
+                 device: str = "cuda:0", stream=None,
+                 x64: Optional[np.ndarray] = None, v64: Optional[np.ndarray] = None):
+        import torch
+
+        self.torch = torch
+        self.boxes = list(boxes)
+        self.precision = precision
+        self.memory = memory
+        nb = len(self.boxes)
+        self.ndim = self.boxes[0].ndim
+        counts = [b.np for b in self.boxes]
+        self.box_start = np.zeros(nb + 1, dtype=np.int64)
+        self.box_start[1:] = np.cumsum(counts)
+        self.np = int(self.box_start[-1])
+        self.nc = int(sum(b.ncell for b in self.boxes))
+        self.device = torch.device(device)
+        if memory == MHDPIC_MEM_DEVICE:
+            def mk(a, dt):
+                return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(self.device)
+        else:
+            def mk(a, dt):
+                return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()
+        cat = np.concatenate
+        if precision == MHDPIC_PREC_MIXED:
+            self.cell = mk(cat([b.cell for b in self.boxes]), np.int32)
+            self.off = mk(cat([b.off for b in self.boxes], axis=1), np.float32)
+            self.p = mk(cat([b.p for b in self.boxes], axis=1), np.float32)
+            self.x = self.p64 = None
+        else:
+            from . import workloads as wl
+            if x64 is None:
+                x64 = cat([wl.absolute_positions(b) for b in self.boxes], axis=1)
+            if v64 is None:
+                v64 = cat([b.p.astype(np.float64) for b in self.boxes], axis=1)
+            self.x = mk(x64, np.float64)
+            self.p64 = mk(v64, np.float64)
+            self.cell = self.off = self.p = None
+        self.rho = mk(cat([b.rho for b in self.boxes]), np.float64)
+        self.mom = mk(cat([b.mom for b in self.boxes], axis=1), np.float64)
+        self.egas = mk(cat([b.egas for b in self.boxes]), np.float64)
+        self.B = mk(cat([b.B for b in self.boxes], axis=1), np.float64)
+
+        G = (Grid * nb)()
+        P = (Params * nb)()
+        for i, b in enumerate(self.boxes):
+            G[i].ndim = b.ndim
+            for d in range(3):
+                G[i].n[d] = b.n[d]
+                G[i].dx[d] = b.dx[d]
+                G[i].x0[d] = b.x0[d]
+                G[i].bc[d] = b.bc[d]
+            P[i].qm_cr, P[i].qm_gas, P[i].C, P[i].m_cr = b.qm_cr, b.qm_gas, b.C, b.m_cr
+            P[i].hall, P[i].shape = b.hall, MHDPIC_SHAPE_TSC
+        self._G, self._P = G, P
+        opt = Options()
+        opt.precision, opt.memory = precision, memory
+        for d in range(3):
+            opt.brick[d] = int(brick[d])
+        self._opt = opt
+        parts = Particles()
+        parts.np = self.np
+        parts.box_start = self.box_start.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+        def ptr(t):
+            return t.data_ptr() if t is not None else None
+
+        parts.cell, parts.off, parts.p = ptr(self.cell), ptr(self.off), ptr(self.p)
+        parts.x, parts.p64 = ptr(self.x), ptr(self.p64)
+        gas = Gas(ptr(self.rho), ptr(self.mom), ptr(self.egas), ptr(self.B))
+        self._parts, self._gas = parts, gas
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        with torch.cuda.device(self.device):
+            self.ctx = mhdpic_init(nb, G, P, opt, parts, gas, ctypes.c_void_p(stream.cuda_stream))
+
+    # -- the step ---------------------------------------------------------
+    def sort(self, want_perm: bool = False, want_counts: bool = False):
+        torch = self.torch
+        perm = torch.empty(max(self.np, 1), dtype=torch.int64, device=self.device) if want_perm else None
+        counts = (torch.empty(max(self.num_keys(), 1), dtype=torch.int32, device=self.device)
+                  if want_counts else None)
+        mhdpic_sort(self.ctx, perm.data_ptr() if perm is not None else 0,
+                    counts.data_ptr() if counts is not None else 0)
+        return perm, counts
+
+    def interp_push(self, dt: float, nsub: int = 1) -> None:
+        mhdpic_interp_push(self.ctx, dt, nsub)
+
+    def deposit(self) -> None:
+        mhdpic_deposit(self.ctx)
+
+    def apply_feedback(self, totals: bool = False) -> Optional[np.ndarray]:
+        if totals:
+            out = np.zeros(8 * len(self.boxes), dtype=np.float64)
+            mhdpic_apply_feedback(self.ctx, out)
+            return out.reshape(len(self.boxes), 8)
+        mhdpic_apply_feedback(self.ctx, None)
+        return None
+
+    def step(self, dt: float, nsub: int = 1) -> None:
+        self.interp_push(dt, nsub)
+        self.apply_feedback(False)
+
+    # -- read-back ----------------------------------------------------------
+    def deposits(self, which: int):
+        out = self.torch.empty((4, self.nc), dtype=self.torch.float64, device=self.device)
+        mhdpic_get_deposits(self.ctx, which, out.data_ptr())
+        return out
+
+    def fields(self):
+        out = self.torch.empty((6, self.nc), dtype=self.torch.float64, device=self.device)
+        mhdpic_get_fields(self.ctx, out.data_ptr())
+        return out
+
+    def num_keys(self) -> int:
+        return mhdpic_num_keys(self.ctx)
+
+    def status(self) -> int:
+        return mhdpic_get_status(self.ctx)
+
+    def clear_status(self) -> None:
+        mhdpic_clear_status(self.ctx)
+
+    def launches(self) -> int:
+        return mhdpic_launch_count(self.ctx)
+
+    def synchronize(self) -> None:
+        self.stream.synchronize()
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            mhdpic_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,336 @@
+"""Parity of the sm_103a library with the FP64 oracle (needs a GPU).
+
+Everything goes through the C ABI (ctypes binding).  Tolerances:
+  * sort permutation and counts: bit-exact;
+  * FP64 path: 1e-12 relative after one step (deposits per channel in
+    relative L2, positions and four-velocities element-wise);
+  * mixed path: deposits 1e-5 relative L2 per channel, positions 1e-5 cells,
+    four-velocities 1e-5 relative.
+The oracle is put into the library's sorted particle order with the oracle's
+own sort, whose equality with the library's sort is checked first.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_1412_1087_gb300 import workloads as wl
+from tests._parity import (default_brick, momenta_of, periodic_diff, positions_of, rel_l2,
+                           sorted_oracle_state, tilt_B)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1412_1087_gb300 import mhdpic as m  # noqa: E402
+
+MIXED, FP64 = m.MHDPIC_PREC_MIXED, m.MHDPIC_PREC_FP64
+TOL = {FP64: 1e-12, MIXED: 1e-5}
+
+
+def _boxes():
+    """Small variants of every workload shape: several tiles and a ragged tail."""
+    return {
+        "thermal2d": lambda: tilt_B(wl.periodic_thermal_2d(nx=29, ny=21, ppc=9, dv_amp=0.4, seed=1), 1),
+        "beam3d": lambda: wl.alfvenic_beam_3d(n=14, ppc=6, nmodes=16, seed=2),
+        "bell2d_hall": lambda: tilt_B(wl.bell_2d(n=24, ppc=12, seed=3), 3, amp=0.05),
+        "shock2d_reflect": lambda: tilt_B(wl.shock_2d(nx=96, ny=10, ppc=8.0, seed=4), 4, amp=0.1),
+    }
+
+
+def _engine(box, prec, **kw):
+    return m.Engine([box], precision=prec, **kw)
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+@pytest.mark.parametrize("name", list(_boxes()))
+def test_sort_matches_oracle_bit_exactly(prec, name):
+    box = _boxes()[name]()
+    eng = _engine(box, prec)
+    # put the unsorted particles back and sort through the ABI
+    if prec == MIXED:
+        eng.cell.copy_(torch.from_numpy(box.cell))
+        eng.off.copy_(torch.from_numpy(box.off))
+        eng.p.copy_(torch.from_numpy(box.p))
+    else:
+        eng.x.copy_(torch.from_numpy(wl.absolute_positions(box)))
+        eng.p64.copy_(torch.from_numpy(box.p.astype(np.float64)))
+    perm, counts = eng.sort(want_perm=True, want_counts=True)
+    g = orc.grid_of(box)
+    cells = box.cell if prec == MIXED else orc.cells_of(g, wl.absolute_positions(box))
+    operm, ocounts = orc.sort_cells(g, default_brick(box.ndim), cells)
+    np.testing.assert_array_equal(perm.cpu().numpy(), operm)
+    np.testing.assert_array_equal(counts.cpu().numpy().astype(np.int64), ocounts)
+    # the particle arrays were permuted the same way
+    if prec == MIXED:
+        np.testing.assert_array_equal(eng.cell.cpu().numpy(), box.cell[operm])
+        np.testing.assert_array_equal(eng.p.cpu().numpy(), box.p[:, operm])
+    else:
+        np.testing.assert_array_equal(eng.p64.cpu().numpy(), box.p.astype(np.float64)[:, operm])
+    assert eng.status() == 0
+    eng.close()
+
+
+def test_sort_stability_with_crowded_cells():
+    """Hundreds of particles per cell (segment sorts beyond one warp) stay stable."""
+    box = wl.periodic_thermal_2d(nx=6, ny=5, ppc=2, seed=9)
+    rng = np.random.default_rng(0)
+    npart = 9000
+    box.cell = rng.integers(0, 3, npart).astype(np.int32)   # three crowded cells
+    box.cell[:1500] = 7
+    box.off = rng.random((2, npart)).astype(np.float32)
+    box.p = rng.standard_normal((3, npart)).astype(np.float32)
+    eng = _engine(box, MIXED, brick=(2, 2, 1))
+    eng.cell.copy_(torch.from_numpy(box.cell))
+    perm, counts = eng.sort(want_perm=True, want_counts=True)
+    operm, ocounts = orc.sort_cells(orc.grid_of(box), (2, 2, 1), box.cell)
+    np.testing.assert_array_equal(perm.cpu().numpy(), operm)
+    np.testing.assert_array_equal(counts.cpu().numpy().astype(np.int64), ocounts)
+    eng.close()
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+@pytest.mark.parametrize("name", list(_boxes()))
+def test_initial_moments_and_fields(prec, name):
+    box = _boxes()[name]()
+    eng = _engine(box, prec)
+    _, _, x, v = sorted_oracle_state(box)
+    st = orc.State(box, x, v)
+    md = eng.deposits(1).cpu().numpy()
+    for q in range(4):
+        assert rel_l2(md[q], st.mom_dep[q]) < 1e-12, q
+    f = eng.fields().cpu().numpy()
+    E = st.fields()
+    tol = 1e-12 if prec == FP64 else 1e-6
+    for q in range(3):
+        assert rel_l2(f[q], E[q], floor=1e-3 * np.linalg.norm(box.B)) < tol, q
+        assert rel_l2(f[3 + q], box.B[q], floor=1e-3 * np.linalg.norm(box.B)) < tol, q
+    eng.close()
+
+
+def _compare_step(eng, box, st, corr, md, prec, tol_pos=None):
+    tol = TOL[prec]
+    gc = eng.deposits(0).cpu().numpy()
+    gm = eng.deposits(1).cpu().numpy()
+    for q in range(4):
+        assert rel_l2(gm[q], md[q]) < tol, ("moments", q, rel_l2(gm[q], md[q]))
+    for q in range(4):
+        assert rel_l2(gc[q], corr[q]) < tol, ("corrector", q, rel_l2(gc[q], corr[q]))
+    xg = positions_of(eng)
+    vg = momenta_of(eng)
+    for d in range(box.ndim):
+        L = box.n[d] * box.dx[d]
+        dx = periodic_diff(xg[d], st.x[d], L) if box.bc[d] == 0 else xg[d] - st.x[d]
+        lim = (1e-12 * (1.0 + np.abs(st.x[d]))) if prec == FP64 else (tol_pos or 1e-5) * box.dx[d]
+        assert np.all(np.abs(dx) <= lim), (d, np.abs(dx).max())
+    vscale = np.sqrt((st.v ** 2).sum(0))
+    assert np.all(np.abs(vg - st.v) <= tol * vscale + 1e-300), np.abs(vg - st.v).max()
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+@pytest.mark.parametrize("name", list(_boxes()))
+def test_one_step_matches_oracle(prec, name):
+    box = _boxes()[name]()
+    eng = _engine(box, prec)
+    _, _, x, v = sorted_oracle_state(box)
+    st = orc.State(box, x, v)
+    corr, md = st.push_only(box.dt)
+    eng.interp_push(box.dt, 1)
+    _compare_step(eng, box, st, corr, md, prec)
+    assert eng.status() == 0
+    eng.close()
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_steps_without_sorting_use_the_global_path(prec):
+    """Eight pushes with no sort and no feedback: particles drift out of their
+    bricks (up to ~3 cells) and take the global-memory path; the corrector
+    accumulated over the eight pushes, the last moments and the particle
+    states still equal the oracle's."""
+    box = tilt_B(wl.periodic_thermal_2d(nx=33, ny=17, ppc=5, dv_amp=0.3, seed=5), 5)
+    eng = _engine(box, prec)
+    _, _, x, v = sorted_oracle_state(box)
+    st = orc.State(box, x, v)
+    E = st.fields()
+    corr = np.zeros((4, box.ncell))
+    md = np.zeros((4, box.ncell))
+    for _ in range(8):
+        md[:] = 0.0
+        orc.push(st.g, st.p, box.dt, st.x, st.v, E, st.B, corr, md)
+        eng.interp_push(box.dt, 1)
+    _compare_step(eng, box, st, corr, md, prec, tol_pos=1e-4)
+    assert eng.status() == 0
+    eng.close()
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_subcycling_accumulates_the_corrector(prec):
+    box = tilt_B(wl.alfvenic_beam_3d(n=10, ppc=5, nmodes=8, seed=6), 6)
+    eng = _engine(box, prec)
+    _, _, x, v = sorted_oracle_state(box)
+    st = orc.State(box, x, v)
+    E = st.fields()
+    corr = np.zeros((4, box.ncell))
+    md = np.zeros((4, box.ncell))
+    for s in range(3):
+        md[:] = 0.0
+        orc.push(st.g, st.p, box.dt, st.x, st.v, E, st.B, corr, md)
+    eng.interp_push(box.dt, 3)
+    _compare_step(eng, box, st, corr, md, prec, tol_pos=4e-5)
+    eng.close()
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_multi_step_with_feedback(prec):
+    """Ten full steps (push, feedback, restaging, sort every 2 steps) against
+    the oracle; totals conserved."""
+    box = tilt_B(wl.periodic_thermal_2d(nx=20, ny=16, ppc=8, dv_amp=0.5, seed=7), 7)
+    box.hall = 1
+    box.m_cr = 0.02
+    eng = _engine(box, prec)
+    _, _, x, v = sorted_oracle_state(box)
+    st = orc.State(box, x, v)
+    t0 = eng.apply_feedback(totals=True)[0]
+    o0 = st.totals()
+    np.testing.assert_allclose(t0, o0, rtol=1e-12 if prec == FP64 else 1e-6, atol=1e-9)
+    for k in range(10):
+        st.step(box.dt)
+        eng.interp_push(box.dt, 1)
+        tg = eng.apply_feedback(totals=True)[0]
+        if k % 2 == 1:
+            eng.sort()
+    to = st.totals()
+    mom_scale = np.abs(st.mom).sum() + box.m_cr * np.abs(st.v).sum()
+    e_scale = abs(to[3]) + abs(to[7])
+    tol = 1e-11 if prec == FP64 else 2e-5
+    assert np.abs(tg[4:7] - to[4:7]).max() < tol * mom_scale
+    assert abs(tg[7] - to[7]) < tol * e_scale
+    # gas state
+    gm = eng.mom.cpu().numpy()
+    assert rel_l2(gm, st.mom) < (1e-12 if prec == FP64 else 1e-6)
+    # conservation of the GPU's own totals
+    P0, P1 = t0[0:3] + t0[4:7], tg[0:3] + tg[4:7]
+    assert np.abs(P1 - P0).max() < (1e-12 if prec == FP64 else 1e-6) * mom_scale
+    E0, E1 = t0[3] + t0[7], tg[3] + tg[7]
+    assert abs(E1 - E0) < (1e-12 if prec == FP64 else 1e-6) * e_scale
+    assert eng.status() == 0
+    eng.close()
+
+
+def test_deposits_are_bit_identical_run_to_run():
+    box = tilt_B(wl.alfvenic_beam_3d(n=12, ppc=8, nmodes=8, seed=8), 8)
+    outs = []
+    for _ in range(2):
+        eng = _engine(box, MIXED)
+        eng.interp_push(box.dt, 1)
+        outs.append((eng.deposits(0).cpu().numpy(), eng.deposits(1).cpu().numpy(),
+                     eng.p.cpu().numpy(), eng.off.cpu().numpy()))
+        eng.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_host_buffers_give_identical_results(prec):
+    box = tilt_B(wl.periodic_thermal_2d(nx=18, ny=14, ppc=6, dv_amp=0.3, seed=10), 10)
+    res = []
+    for mem in (m.MHDPIC_MEM_DEVICE, m.MHDPIC_MEM_HOST):
+        eng = _engine(box, prec, memory=mem)
+        eng.interp_push(box.dt, 1)
+        t = eng.apply_feedback(totals=True)
+        eng.synchronize()
+        parts = momenta_of(eng)
+        res.append((t, parts, eng.mom.cpu().numpy()))
+        eng.close()
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+
+
+def test_ensemble_of_boxes_with_an_empty_one():
+    boxes = wl.ensemble_2d(nbox=5, seed0=11, max_side=40)
+    boxes[2].cell = boxes[2].cell[:0]
+    boxes[2].off = np.ascontiguousarray(boxes[2].off[:, :0])
+    boxes[2].p = np.ascontiguousarray(boxes[2].p[:, :0])
+    for b in boxes:
+        tilt_B(b, 12, amp=0.05)
+    dt = min(b.dt for b in boxes)
+    for prec in (MIXED, FP64):
+        eng = m.Engine(boxes, precision=prec)
+        eng.interp_push(dt, 1)
+        gc = eng.deposits(0).cpu().numpy()
+        gm = eng.deposits(1).cpu().numpy()
+        c0 = 0
+        for b in boxes:
+            _, _, x, v = sorted_oracle_state(b)
+            st = orc.State(b, x, v)
+            corr, md = st.push_only(dt)
+            sl = slice(c0, c0 + b.ncell)
+            for q in range(4):
+                if b.np:
+                    assert rel_l2(gc[q, sl], corr[q]) < TOL[prec]
+                    assert rel_l2(gm[q, sl], md[q]) < TOL[prec]
+                else:
+                    assert not gc[q, sl].any() and not gm[q, sl].any()
+            c0 += b.ncell
+        assert eng.status() == 0
+        eng.close()
+
+
+@pytest.mark.parametrize("n,ndim", [((3, 5, 1), 2), ((3, 3, 3), 3), ((13, 11, 1), 2)])
+def test_boxes_smaller_than_a_tile_and_ragged_bricks(n, ndim):
+    if ndim == 2:
+        box = tilt_B(wl.periodic_thermal_2d(nx=n[0], ny=n[1], ppc=7, dv_amp=0.3, seed=13), 13)
+    else:
+        box = tilt_B(wl.alfvenic_beam_3d(n=3, ppc=7, nmodes=4, seed=13), 13)
+    for prec in (MIXED, FP64):
+        eng = _engine(box, prec)
+        _, _, x, v = sorted_oracle_state(box)
+        st = orc.State(box, x, v)
+        corr, md = st.push_only(box.dt)
+        eng.interp_push(box.dt, 1)
+        _compare_step(eng, box, st, corr, md, prec)
+        eng.close()
+
+
+def test_gyration_phase_exact_on_gpu_fp64():
+    """App. B.1, v0 = 0, through the FP64 library path: phase 2 atan(Omega dt/2)
+    per step and |v| conserved."""
+    box = wl.gyration()
+    eng = _engine(box, FP64)
+    v0 = eng.p64.cpu().numpy()[:, 0].copy()
+    gam = math.sqrt(1.0 + v0 @ v0 / box.C ** 2)
+    om = 1.0 / gam
+    for _ in range(50):
+        eng.interp_push(box.dt, 1)
+    v = eng.p64.cpu().numpy()[:, 0]
+    phase = math.atan2(v[2], v[1]) - math.atan2(v0[2], v0[1])
+    expect = -50 * 2.0 * math.atan(om * box.dt / 2.0)
+    assert abs(math.remainder(phase - expect, 2 * math.pi)) < 1e-12
+    assert abs(np.linalg.norm(v) - np.linalg.norm(v0)) < 1e-13 * np.linalg.norm(v0)
+    eng.close()
+
+
+def test_fast_mover_sets_a_status_flag_without_faulting():
+    box = wl.periodic_thermal_2d(nx=16, ny=16, ppc=2, seed=14)
+    eng = _engine(box, MIXED)
+    eng.interp_push(box.dt * 40.0, 1)     # particles cross many cells per half step
+    flags = eng.status()
+    assert flags & 1
+    eng.clear_status()
+    assert eng.status() == 0
+    eng.close()
+
+
+def test_invalid_calls_are_rejected():
+    box = wl.periodic_thermal_2d(nx=8, ny=8, ppc=2, seed=15)
+    eng = _engine(box, MIXED)
+    with pytest.raises(m.MhdpicError):
+        eng.interp_push(-1.0, 1)
+    with pytest.raises(m.MhdpicError):
+        eng.interp_push(0.1, 0)
+    with pytest.raises(m.MhdpicError):
+        m.mhdpic_get_deposits(eng.ctx, 5, 0)
+    eng.close()
