@@ -62,6 +62,8 @@ __global__ void k_sort_keys(Ctx c, int32_t *__restrict__ count, int32_t *__restr
                 ci[d] = v;
             }
         }
+        for (int d = 0; d < 3; ++d)   // defensive: a key outside the box would index out of range
+            ci[d] = ci[d] < 0 ? 0 : (ci[d] >= b.n[d] ? b.n[d] - 1 : ci[d]);
         int32_t key = (int32_t)brick_key(b, c.brick, ci[0], ci[1], ci[2]);
         unsigned active = __activemask();
         unsigned peers = __match_any_sync(active, key);
@@ -181,11 +183,16 @@ int scan(const int32_t *in, int64_t n, int32_t *out, int32_t *tmp, cudaStream_t 
 
 __global__ void k_sort_scatter(int64_t np, const int32_t *__restrict__ pkey,
                                const int32_t *__restrict__ pslot, const int32_t *__restrict__ offset,
-                               int32_t *__restrict__ perm)
+                               int32_t *__restrict__ perm, uint32_t *status)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
-         i += (int64_t)gridDim.x * blockDim.x)
-        perm[offset[pkey[i]] + pslot[i]] = (int32_t)i;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t dst = (int64_t)offset[pkey[i]] + pslot[i];
+        if (dst >= 0 && dst < np)
+            perm[dst] = (int32_t)i;
+        else
+            set_status(status, MHDPIC_ST_SORT_CAP);
+    }
 }
 
 // Segments of up to 32 are sorted in registers, up to WARP_SORT_MAX in the
@@ -317,6 +324,8 @@ __global__ void k_gather(int64_t np, int ncomp, const int32_t *__restrict__ perm
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < np;
          r += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = perm[r];
+        if (i < 0 || i >= np)   // never taken for a valid permutation
+            i = r;
         for (int q = 0; q < ncomp; ++q)
             dst[(int64_t)q * np + r] = src[(int64_t)q * np + i];
     }
@@ -414,7 +423,8 @@ int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *
     }
     launches += scan(s.count, c.nkeys, s.offset, s.scan_tmp, st);
     if (c.np > 0) {
-        k_sort_scatter<<<grid_for(c.np, 256), 256, 0, st>>>(c.np, s.pkey, s.pslot, s.offset, s.perm);
+        cudaMemsetAsync(s.perm, 0, sizeof(int32_t) * c.np, st);
+        k_sort_scatter<<<grid_for(c.np, 256), 256, 0, st>>>(c.np, s.pkey, s.pslot, s.offset, s.perm, c.status);
         cudaMemsetAsync(s.big_count, 0, sizeof(int32_t), st);
         int64_t nw = (c.nkeys + 7) / 8;
         int gb = (int)(nw < 152 * 16 ? (nw < 1 ? 1 : nw) : 152 * 16);
