@@ -283,7 +283,7 @@ def run_native(args):
                        "l2": "inputs larger than L2 (%.2f GB particle state)" % (npart * 28 / 1e9),
                        "parallelism": "independent box per GPU" if world > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_push<3,mixed,full>",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_push_mixed<3,full>",
                          "peak_kind": peak_kind, "bytes_per_launch": bytes_push,
                          "avg_launch_ms": push_avg_s * 1e3},
             "cpu_baseline": cpu,

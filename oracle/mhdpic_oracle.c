@@ -31,9 +31,11 @@
  *   - m_CR is a per-particle mass; charge and current deposits are divided
  *     by the cell volume dV, the corrector deposit is a momentum / energy
  *     and is divided by dV when it is applied to the gas.
- *   - The kinetic-energy difference E_k(v') - E_k(v), E_k = v^2/(gamma+1),
- *     is evaluated as (v'-v).(v'+v)/(gamma'+gamma), an exact rewriting that
- *     avoids cancellation.
+ *   - The kinetic-energy difference E_k(v^(n+1)) - E_k(v^(n)) with
+ *     E_k = v^2/(gamma+1) is evaluated as the sum of the changes of the two
+ *     half kicks, each as (a-b).(a+b)/(gamma_a+gamma_b): the rotation keeps
+ *     |v| exactly, so this equals the difference of the two energies without
+ *     its cancellation.
  *   - Without an MHD solver only the corrector deposit is applied to the gas;
  *     the moments n_CR, J_CR deposited at the end of a step feed R, F_CR and
  *     the CR-Hall electric field of the next step.
@@ -369,15 +371,20 @@ void orc_push(const orc_grid *g, const orc_params *p, double dt, int64_t np, dou
         for (int d = 0; d < 3; ++d)
             vnew[d] = v1[d] + 0.5 * h * Ep[d];
 
-        /* corrector deposit: -m (v^(n+1) - v^(n)), -m (E_k^(n+1) - E_k^(n)) */
+        /* corrector deposit: -m (v^(n+1) - v^(n)), -m (E_k^(n+1) - E_k^(n)).
+         * The rotation keeps |v^1| = |v^0|, so the energy change is the sum of
+         * the two half-kick changes, E_k(a) - E_k(b) = (a-b).(a+b)/(gamma_a+gamma_b)
+         * with a - b = (h/2)E each time. */
         double g1 = orc_gamma(vnew, C);
         if (corr) {
-            double dv[3], sv[3];
+            double dv[3], s1[3], s0[3], e[3];
             for (int d = 0; d < 3; ++d) {
                 dv[d] = vnew[d] - vn[d];
-                sv[d] = vnew[d] + vn[d];
+                e[d] = 0.5 * h * Ep[d];
+                s1[d] = vnew[d] + v1[d];
+                s0[d] = v0[d] + vn[d];
             }
-            double dEk = dot3(dv, sv) / (g1 + g0);
+            double dEk = dot3(e, s1) / (g1 + gam) + dot3(e, s0) / (gam + g0);
             double q[4] = {-m * dv[0], -m * dv[1], -m * dv[2], -m * dEk};
             orc_deposit(g, xp, q, 4, corr);
         }

@@ -103,7 +103,9 @@ __global__ void k_prep(Ctx c, int cur, int apply)
 //   |v^0| <= vmax + hh Emax;
 //   rotation |v^1 - v^0| = 2|v^0| sin(theta/2) <= 2 |v^0| |b| = 2 hh |B| |u^0|;
 //   |dv| <= 2 hh Emax + 2 hh Bmax min(|v^0|, C)                       (x2 margin)
-//   |dE_k| = |dv.(v+v')|/(gamma+gamma') <= |dv| min(C, |v^0| + |dv|).
+//   the rotation keeps |v|, so dE_k is the energy change of the two half
+//   kicks, each (hh E).(a+b)/(gamma_a+gamma_b) with |a+b|/(gamma_a+gamma_b) <
+//   min(C, max|a|, |b|):  |dE_k| <= 2 hh Emax min(C, |v^0| + hh Emax)  (x2 margin).
 // With H = 3^D (4 maxcount + 64) contributions per cell at most, the scale is
 // the power of two with Q H S <= 2^62.
 __global__ void k_scales(Ctx c, double dt)
@@ -124,16 +126,18 @@ __global__ void k_scales(Ctx c, double dt)
     double qdv = 2.0 * (2.0 * hh * emax + 2.0 * hh * bmax * fmin(vb, b.C));
     double q[4];
     q[0] = q[1] = q[2] = fabs(b.m_cr) * qdv;
-    q[3] = fabs(b.m_cr) * qdv * fmin(b.C, vb + qdv);
+    q[3] = fabs(b.m_cr) * 2.0 * (2.0 * hh * emax * fmin(b.C, vb + hh * emax));
     for (int ch = 0; ch < 4; ++ch) {
-        double Q = fmax(q[ch], 1e-280);
+        double Q = fmax(q[ch], 1e-30);
         int e;
         frexp(FIXED_LIMIT / (Q * H), &e);   // 2^(e-1) <= 2^62/(Q H) < 2^e
         e -= 1;
-        if (e > 1000)
-            e = 1000;
+        if (e > SCALE_EXP_MAX)
+            e = SCALE_EXP_MAX;
+        b.escale[ch] = e;
         b.scale[ch] = ldexp(1.0, e);
         b.inv_scale[ch] = ldexp(1.0, -e);
+        b.qbound[ch] = Q;
         b.qmax[ch] = 4.0 * Q;   // a particle quantity beyond this raises the overflow flag
     }
     st.corr_dirty = 1;
@@ -291,7 +295,10 @@ __global__ void k_vmax(Ctx c)
         float vm = (float)sqrt(v2);
         if (!(vm <= 1.0e37f))
             vm = 1.0e37f;
-        atomicMax(&c.stats[bx].vmax, __float_as_uint(vm));
+        unsigned peers = __match_any_sync(__activemask(), bx);
+        unsigned m = __reduce_max_sync(peers, __float_as_uint(vm));
+        if ((threadIdx.x & 31) == __ffs(peers) - 1)
+            atomicMax(&c.stats[bx].vmax, m);
     }
 }
 

@@ -378,6 +378,8 @@ __global__ void k_write_items(Ctx c, const int64_t *__restrict__ brick_start,
             w.brick = (int32_t)(gb - b.brick0);
             w.p0 = p0 + t * chunk;
             w.p1 = min(p1, p0 + (t + 1) * chunk);
+            // a whole 64-cell brick splits at its 32nd cell (the start of the second half)
+            w.pm = (c.halves && m == 1) ? (int64_t)offset[k0 + vol / 2] : -1;
             items[o + t] = w;
         }
         if (gb == nbt - 1)

@@ -151,19 +151,23 @@ void moment_scales(mhdpic_ctx *c, int maxcount)
         double qn = std::fabs(b.qm_cr) * std::fabs(b.m_cr) * b.inv_dV;
         double q[4] = {qn, qn * b.C, qn * b.C, qn * b.C};
         for (int k = 0; k < 4; ++k) {
-            double Q = std::fmax(q[k], 1e-280);
+            double Q = std::fmax(q[k], 1e-30);
             int e;
             std::frexp(4611686018427387904.0 / (Q * H), &e);
             e -= 1;
-            if (e > 1000)
-                e = 1000;
+            if (e > SCALE_EXP_MAX)
+                e = SCALE_EXP_MAX;
+            b.escale[CH_N + k] = e;
             b.scale[CH_N + k] = std::ldexp(1.0, e);
             b.inv_scale[CH_N + k] = std::ldexp(1.0, -e);
+            b.qbound[CH_N + k] = Q;
             b.qmax[CH_N + k] = 4.0 * Q;
         }
         for (int k = 0; k < 4; ++k) {   // corrector: sized by the first push
+            b.escale[k] = 0;
             b.scale[k] = 1.0;
             b.inv_scale[k] = 1.0;
+            b.qbound[k] = 0.0;
             b.qmax[k] = 1e300;
         }
     }
@@ -306,9 +310,26 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         k.tile[d] = d < k.ndim ? k.brick[d] + 2 * HALO : 1;
     }
     k.tile_vol = k.tile[0] * k.tile[1] * k.tile[2];
-    if (push_smem_bytes(k) > 200 * 1024)
+    // Default 64-cell bricks are worked as two 32-cell halves, one lane per
+    // cell; the tile strides are padded so those 32 cells hit 32 banks.
+    k.halves = 0;
+    k.ts[0] = 1;
+    k.ts[1] = k.tile[0];
+    k.ts[2] = k.tile[0] * k.tile[1];
+    if (k.ndim == 3 && k.brick[0] == 4 && k.brick[1] == 4 && k.brick[2] == 4) {
+        k.halves = 1;
+        k.ts[1] = 12;    // (x + 12 y + 112 z) mod 32 is a bijection of a 4x4x2 half
+        k.ts[2] = 112;
+    } else if (k.ndim == 2 && k.brick[0] == 8 && k.brick[1] == 8) {
+        k.halves = 1;
+        k.ts[1] = 24;    // (x + 24 y) mod 32 is a bijection of an 8x4 half
+        k.ts[2] = 24 * k.tile[1];
+    }
+    k.tile_slots = k.ndim == 3 ? k.ts[2] * k.tile[2] : k.ts[1] * k.tile[1];
+    size_t smem = k.prec == MHDPIC_PREC_MIXED ? push_smem_bytes_mixed(k) : push_smem_bytes_f64(k);
+    if (smem > 200 * 1024)
         return bail(fail(MHDPIC_E_CAPACITY, "brick %dx%dx%d needs %zu bytes of shared memory", k.brick[0],
-                         k.brick[1], k.brick[2], push_smem_bytes(k)));
+                         k.brick[1], k.brick[2], smem));
 
     // box table
     c->part_start.assign(parts->box_start, parts->box_start + nbox + 1);
@@ -450,7 +471,7 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         cudaStreamSynchronize(st))
         return bail(cuda_fail(cudaGetLastError(), "init stats"));
 
-    int bps = push_blocks_per_sm(k);
+    int bps = k.prec == MHDPIC_PREC_MIXED ? push_blocks_per_sm_mixed(k) : push_blocks_per_sm_f64(k);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -500,8 +521,10 @@ int mhdpic_interp_push(mhdpic_ctx *c, double dt, int32_t nsub)
         CK(cudaMemsetAsync(c->k.momdep[c->cur ^ 1], 0, sizeof(unsigned long long) * 4 * c->k.nc, c->stream));
     for (int s = 0; s < nsub; ++s) {
         bool last = s == nsub - 1;
-        if ((rc = check_launch(c, launch_push(c->k, c->s, c->work_ctr, c->cur ^ 1, last ? 1 : 0, dt,
-                                              c->grid_blocks, c->stream))))
+        int n = c->k.prec == MHDPIC_PREC_MIXED
+                    ? launch_push_mixed(c->k, c->s, c->work_ctr, c->cur ^ 1, last ? 1 : 0, dt, c->grid_blocks, c->stream)
+                    : launch_push_f64(c->k, c->s, c->work_ctr, c->cur ^ 1, last ? 1 : 0, dt, c->grid_blocks, c->stream);
+        if ((rc = check_launch(c, n)))
             return rc;
     }
     c->cur ^= 1;

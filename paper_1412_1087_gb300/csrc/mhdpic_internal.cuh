@@ -76,7 +76,9 @@ struct BoxDev {
     FastDiv div_nx, div_nxy;
     double scale[NCH];     // fixed-point scale (a power of two) per channel
     double inv_scale[NCH];
-    double qmax[NCH];      // largest particle quantity the scale was sized for
+    double qmax[NCH];      // particle quantity above which the overflow flag is raised
+    double qbound[NCH];    // particle quantity bound the scale was sized for
+    int32_t escale[NCH];   // scale = 2^escale
 };
 
 // Per-box maxima tracked on the device; they size the corrector scales.
@@ -91,11 +93,13 @@ struct BoxStats {
     int32_t pad;
 };
 
-// A contiguous run of sorted particles that all belong to one brick.
+// A contiguous run of sorted particles that all belong to one brick.  When the
+// item is a whole 64-cell brick, [p0, pm) and [pm, p1) are its two 32-cell
+// halves (one lane per cell); otherwise pm = -1.
 struct WorkItem {
     int32_t box;
     int32_t brick;   // brick number inside the box
-    int64_t p0, p1;  // particle range
+    int64_t p0, pm, p1;
 };
 
 // Everything a kernel needs, passed by value.
@@ -103,7 +107,10 @@ struct Ctx {
     int32_t nbox, ndim, prec;
     int32_t brick[3];
     int32_t tile[3];       // brick + 2*HALO
-    int32_t tile_vol;
+    int32_t tile_vol;      // cells of the tile
+    int32_t ts[3];         // tile strides in slots (x, y, z); padded to spread banks
+    int32_t tile_slots;    // slots of the tile (>= tile_vol)
+    int32_t halves;        // 1: default 64-cell bricks split into 32-cell halves
     int64_t np, nc, nkeys, nbricks_total;
     const BoxDev *boxes;   // device
     const int64_t *box_part_start; // device [nbox+1]
@@ -153,8 +160,10 @@ int launch_max_count(const Ctx &c, const SortScratch &s, cudaStream_t st);
 int launch_vmax(const Ctx &c, cudaStream_t st);
 int launch_prep(const Ctx &c, int cur, int apply, cudaStream_t st);
 int launch_moments(const Ctx &c, int cur, cudaStream_t st);
-int launch_push(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur_out, int full,
-                double dt, int grid_blocks, cudaStream_t st);
+int launch_push_mixed(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur_out, int full,
+                      double dt, int grid_blocks, cudaStream_t st);
+int launch_push_f64(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur_out, int full,
+                    double dt, int grid_blocks, cudaStream_t st);
 int launch_scales(const Ctx &c, double dt, cudaStream_t st);
 int launch_totals(const Ctx &c, double *partials, int nchunks, double *out, cudaStream_t st);
 int launch_fixed_to_double(const Ctx &c, const unsigned long long *src, int ch0, double *out,
@@ -162,7 +171,11 @@ int launch_fixed_to_double(const Ctx &c, const unsigned long long *src, int ch0,
 int launch_fields_to_double(const Ctx &c, double *out, cudaStream_t st);
 
 // occupancy helpers
-int push_blocks_per_sm(const Ctx &c);
-size_t push_smem_bytes(const Ctx &c);
+int push_blocks_per_sm_mixed(const Ctx &c);
+int push_blocks_per_sm_f64(const Ctx &c);
+size_t push_smem_bytes_mixed(const Ctx &c);
+size_t push_smem_bytes_f64(const Ctx &c);
+// the largest exponent of a fixed-point scale (kept inside float range)
+constexpr int SCALE_EXP_MAX = 120;
 
 }  // namespace mhdpic

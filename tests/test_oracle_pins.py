@@ -440,3 +440,38 @@ def test_cells_of_positions():
     g = orc.make_grid(2, (10, 7, 1), dx=(0.5, 2.0, 1.0), x0=(-1.0, 3.0, 0.0))
     x = np.array([[-1.0, -0.51, 3.99, 0.0], [3.0, 4.99, 16.99, 5.0]])
     np.testing.assert_array_equal(orc.cells_of(g, x), [0, 0 + 10 * 0 + 0 * 0 + 0, 9 + 60, 2 + 10])
+
+
+def test_energy_change_equals_the_definition_in_high_precision():
+    """The corrector's dE_k equals E_k(v^(n+1)) - E_k(v^(n)) (eq:parEk,
+    App. A.3) evaluated with 50-digit decimals from the stored FP64 states, to
+    the rounding of those states."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 50
+    rng = np.random.default_rng(17)
+    g = orc.make_grid(3, (6, 6, 6), dx=(1.0, 1.0, 1.0))
+    p = orc.make_params(1.0, 1.0, 30.0, 1.0, 0)
+    nc = 216
+    E = 0.5 * rng.standard_normal((3, nc))
+    B = np.array([[1.0], [0.3], [-0.2]]) + 0.2 * rng.standard_normal((3, nc))
+
+    def ek(v, C):
+        v2 = sum(Decimal(float(a)) ** 2 for a in v)
+        Cd = Decimal(C)
+        gam = (Cd * Cd + v2).sqrt() / Cd
+        return v2 / (gam + 1)
+
+    checked = 0
+    for _ in range(40):
+        x = rng.uniform(0.5, 5.5, (3, 1))
+        v = rng.standard_normal((3, 1)) * rng.choice([0.5, 5.0, 60.0])
+        v0 = v[:, 0].copy()
+        corr = np.zeros((4, nc))
+        orc.push(g, p, 0.05, x, v, E, B, corr, None)
+        dek = -corr[3].sum()                      # m = 1
+        exact = float(ek(v[:, 0], 30.0) - ek(v0, 30.0))
+        scale = np.finfo(float).eps * (v[:, 0] @ v[:, 0] + v0 @ v0)
+        assert abs(dek - exact) < 16 * scale + 1e-15 * abs(exact)
+        assert abs(exact) > 1000 * scale          # the check is not vacuous
+        checked += 1
+    assert checked == 40
