@@ -2,24 +2,26 @@
 // Boris push, fixed-point deposits (App. A.1-A.3 of arXiv:1412.1087).
 //
 // A persistent CTA of 8 warps takes brick items from an atomic counter.  Per
-// item it stages the brick's E, B plus a halo of HALO cells in shared memory
-// and accumulates both deposits in a shared int32 fixed-point tile, which is
-// shifted exactly into the int64 global accumulators at the end.
+// item it stages the brick's E, B plus a halo of HALO cells in shared memory,
+// accumulates both deposits in a shared fixed-point tile, and adds the tile to
+// the int64 global accumulators at the end.
 //
 //  * Lane <-> cell: a 64-cell brick is two 32-cell halves; warps 0-3 work on
-//    one half and warps 4-7 on the other, and lane l works through the
-//    particles of the l-th cell of its half, so the 32 lanes of an instruction
-//    sit in 32 different cells.  The tile strides are padded (3-D: y 12, z 112
-//    slots; 2-D: y 24) so those 32 cells fall on 32 different banks for the
-//    32-bit deposit atomics and on distinct bank groups for the 128-bit and
-//    64-bit field loads.
-//  * Fixed point: the tile scale of each channel is a power of two chosen per
-//    item so that no tile cell can overflow int32 whatever the particles do
-//    (item size x largest single-cell TSC weight x the channel's per-particle
-//    bound < 2^31), and every contribution stays below 2^21 so one FFMA with
-//    1.5*2^23 rounds it to an integer.  The tile scale divides the global
-//    int64 scale by 2^k; the flush shifts by k, so the sums remain exact and
-//    independent of the order of the additions.
+//    one half and warps 4-7 on the other, lane l taking exactly the particles
+//    sorted into the l-th cell of its half (cell ranges from the sort's
+//    offsets), so the 32 lanes of an instruction sit in 32 different cells.
+//    The tile strides are padded (3-D: y 12, z 112 slots; 2-D: y 24) so those
+//    32 cells fall on 32 different banks for the 32-bit deposit atomics and on
+//    distinct bank groups for the 128-bit and 64-bit field loads.
+//  * Fixed point in the tile: each contribution x (in tile units) is split
+//    exactly into hi = round(x / 2^KLO) and lo = x - hi 2^KLO with one FFMA
+//    against 1.5*2^(23+KLO), one FFMA for the residual and one FADD against
+//    1.5*2^23, and hi, lo are added to two int32 planes.  The tile scale is
+//    chosen per item so that neither plane can overflow for that item's
+//    particle count, and the flush rebuilds hi 2^KLO + lo in int64 and shifts
+//    it to the global scale, so all sums are exact and independent of the
+//    order of the additions.  The charge density (all contributions positive,
+//    no cancellation) uses the hi plane alone.
 //  * A particle whose stencil leaves the tile, or whose quantities exceed the
 //    bound the scales were sized for, deposits straight into the int64 global
 //    accumulators at the global scale.
@@ -31,12 +33,10 @@ namespace {
 
 constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23: x + MAGIC has unit spacing for |x| < 2^22
 constexpr int MAGIC_BITS = 0x4B400000;
-
-// round(a * b) to the nearest integer (ties to even), for |a * b| < 2^22
-__device__ __forceinline__ int round_fma(float a, float b)
-{
-    return __float_as_int(fmaf(a, b, MAGIC)) - MAGIC_BITS;
-}
+constexpr int KLO = 19;               // bits of the low word of a split contribution
+constexpr float MAGIC_HI = 6597069766656.0f;  // 1.5 * 2^(23+KLO)
+constexpr int MAGIC_HI_BITS = 0x54C00000;     // bit pattern of MAGIC_HI
+constexpr int NPLANE = 2 * NCH;       // hi planes 0..7, lo planes 8..15
 
 struct MixedConst {
     float hdx[3];    // dt / (2 dx)
@@ -50,6 +50,11 @@ struct MixedConst {
     int ksh[NCH];    // flush shift: global = tile * 2^ksh
 };
 
+// TSC weights of one particle, passed by value to the global-memory path.
+struct Wts {
+    float x[3], y[3], z[3];
+};
+
 __device__ __forceinline__ void item_const(const BoxDev &b, float dt, int64_t cnt, int D, MixedConst &k)
 {
 #pragma unroll
@@ -61,12 +66,17 @@ __device__ __forceinline__ void item_const(const BoxDev &b, float dt, int64_t cn
     k.m = (float)b.m_cr;
     k.qn = (float)(b.qm_cr * b.m_cr * b.inv_dV);
     const float wmax = D == 3 ? 0.421875f : 0.5625f;   // largest TSC weight of one cell
-    float cap = fminf(2097152.f, 2147483648.f / ((float)cnt * wmax + 1.f));
+    const float fc = (float)cnt + 1.f;
+    // split channels: |hi| sums <= cnt (X/2^KLO + 1) < 2^31 and |lo| sums <= cnt 2^(KLO-1) < 2^31;
+    // the hi word also needs |x| < 2^(22+KLO) for the rounding FFMA
+    const float cap_split = fminf(1099511627776.f /* 2^40 */, 524288.f * (2147483648.f / fc - 1.f));
+    // single-word channel: |x| < 2^21 and sums <= cnt x < 2^31
+    const float cap_single = fminf(2097152.f, 2147483648.f / fc);
 #pragma unroll
     for (int ch = 0; ch < NCH; ++ch) {
         float Q = fmaxf((float)b.qbound[ch], 1e-30f);
         int eg = b.escale[ch];
-        int et = ilogbf(cap / Q);     // 2^et * Q <= cap
+        int et = ilogbf((ch == CH_N ? cap_single : cap_split) / (Q * wmax));   // 2^et Q wmax <= cap
         et = max(et, -SCALE_EXP_MAX);
         if (et > eg)
             et = eg;
@@ -78,8 +88,7 @@ __device__ __forceinline__ void item_const(const BoxDev &b, float dt, int64_t cn
 }
 
 template <int D>
-__device__ __forceinline__ void gather_tile(const Ctx &c, int base, const float wx[3], const float wy[3],
-                                            const float wz[3], const float4 *__restrict__ sFa,
+__device__ __forceinline__ void gather_tile(const Ctx &c, int base, const Wts &w, const float4 *__restrict__ sFa,
                                             const float2 *__restrict__ sFb, float E[3], float Bf[3])
 {
     E[0] = E[1] = E[2] = Bf[0] = Bf[1] = Bf[2] = 0.f;
@@ -88,70 +97,98 @@ __device__ __forceinline__ void gather_tile(const Ctx &c, int base, const float 
     for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz)
 #pragma unroll
         for (int cy = 0; cy < 3; ++cy) {
-            float wyz = D == 3 ? wy[cy] * wz[cz] : wy[cy];
+            float wyz = D == 3 ? w.y[cy] * w.z[cz] : w.y[cy];
 #pragma unroll
             for (int cx = 0; cx < 3; ++cx) {
-                float w = wx[cx] * wyz;
+                float ww = w.x[cx] * wyz;
                 int s = base + cx + SY * cy + SZ * cz;
                 float4 a = sFa[s];
                 float2 bb = sFb[s];
-                E[0] = fmaf(w, a.x, E[0]);
-                E[1] = fmaf(w, a.y, E[1]);
-                E[2] = fmaf(w, a.z, E[2]);
-                Bf[0] = fmaf(w, a.w, Bf[0]);
-                Bf[1] = fmaf(w, bb.x, Bf[1]);
-                Bf[2] = fmaf(w, bb.y, Bf[2]);
+                E[0] = fmaf(ww, a.x, E[0]);
+                E[1] = fmaf(ww, a.y, E[1]);
+                E[2] = fmaf(ww, a.z, E[2]);
+                Bf[0] = fmaf(ww, a.w, Bf[0]);
+                Bf[1] = fmaf(ww, bb.x, Bf[1]);
+                Bf[2] = fmaf(ww, bb.y, Bf[2]);
             }
         }
 }
 
+struct F6 {
+    float e[3], b[3];
+};
+
 template <int D>
-__device__ __noinline__ void gather_global(const Ctx &c, const BoxDev &b, const int ci[3], const float wx[3],
-                                           const float wy[3], const float wz[3], float E[3], float Bf[3])
+__device__ __noinline__ F6 gather_global(const Ctx &c, const BoxDev &b, int ci0, int ci1, int ci2, Wts w)
 {
-    E[0] = E[1] = E[2] = Bf[0] = Bf[1] = Bf[2] = 0.f;
+    F6 r;
+    r.e[0] = r.e[1] = r.e[2] = r.b[0] = r.b[1] = r.b[2] = 0.f;
     const float4 *__restrict__ gF = reinterpret_cast<const float4 *>(c.f32);
+    const int ci[3] = {ci0, ci1, ci2};
     int gx[3], gy[3], gz[3];
     stencil_coords<D>(b, ci, gx, gy, gz);
     for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz)
         for (int cy = 0; cy < 3; ++cy) {
-            float wyz = D == 3 ? wy[cy] * wz[cz] : wy[cy];
+            float wyz = D == 3 ? w.y[cy] * w.z[cz] : w.y[cy];
             for (int cx = 0; cx < 3; ++cx) {
-                float w = wx[cx] * wyz;
+                float ww = w.x[cx] * wyz;
                 int64_t g = b.cell0 + ((int64_t)gz[cz] * b.n[1] + gy[cy]) * b.n[0] + gx[cx];
                 float4 f1 = __ldg(gF + 2 * g), f2 = __ldg(gF + 2 * g + 1);
-                E[0] = fmaf(w, f1.x, E[0]);
-                E[1] = fmaf(w, f1.y, E[1]);
-                E[2] = fmaf(w, f1.z, E[2]);
-                Bf[0] = fmaf(w, f1.w, Bf[0]);
-                Bf[1] = fmaf(w, f2.x, Bf[1]);
-                Bf[2] = fmaf(w, f2.y, Bf[2]);
+                r.e[0] = fmaf(ww, f1.x, r.e[0]);
+                r.e[1] = fmaf(ww, f1.y, r.e[1]);
+                r.e[2] = fmaf(ww, f1.z, r.e[2]);
+                r.b[0] = fmaf(ww, f1.w, r.b[0]);
+                r.b[1] = fmaf(ww, f2.x, r.b[1]);
+                r.b[2] = fmaf(ww, f2.y, r.b[2]);
             }
         }
+    return r;
 }
 
-// Four channels into the int32 tile; q already carries the tile scale.
+// x = a * wx split exactly into hi * 2^KLO + lo, both added to the tile
+__device__ __forceinline__ void add_split(int *hi_plane, int *lo_plane, int s, float a, float wx)
+{
+    float t = fmaf(a, wx, MAGIC_HI);
+    int hi = __float_as_int(t) - MAGIC_HI_BITS;
+    float r = fmaf(a, wx, MAGIC_HI - t);   // a wx - hi 2^KLO, |r| <= 2^(KLO-1)
+    int lo = __float_as_int(r + MAGIC) - MAGIC_BITS;
+    atomicAdd(hi_plane + s, hi);
+    atomicAdd(lo_plane + s, lo);
+}
+
+// Four channels into the tile; q carries the tile scale.  Every channel is
+// split into hi and lo words except the charge density, whose contributions
+// are all positive and never cancel.
 template <int D>
-__device__ __forceinline__ void deposit_tile(const Ctx &c, int base, const float wx[3], const float wy[3],
-                                             const float wz[3], const float q[4], int *__restrict__ s0)
+__device__ __forceinline__ void deposit_tile(const Ctx &c, int base, const Wts &w, const float q[4], int ch0,
+                                             int *__restrict__ sD)
 {
     const int S = c.tile_slots, SY = c.ts[1], SZ = c.ts[2];
-    int *__restrict__ s1 = s0 + S;
-    int *__restrict__ s2 = s0 + 2 * S;
-    int *__restrict__ s3 = s0 + 3 * S;
+    int *__restrict__ h0 = sD + (ch0 + 0) * S;
+    int *__restrict__ h1 = sD + (ch0 + 1) * S;
+    int *__restrict__ h2 = sD + (ch0 + 2) * S;
+    int *__restrict__ h3 = sD + (ch0 + 3) * S;
+    int *__restrict__ l0 = h0 + NCH * S;
+    int *__restrict__ l1 = h1 + NCH * S;
+    int *__restrict__ l2 = h2 + NCH * S;
+    int *__restrict__ l3 = h3 + NCH * S;
+    const bool first_single = ch0 == CH_N;
 #pragma unroll
     for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz)
 #pragma unroll
         for (int cy = 0; cy < 3; ++cy) {
-            float wyz = D == 3 ? wy[cy] * wz[cz] : wy[cy];
+            float wyz = D == 3 ? w.y[cy] * w.z[cz] : w.y[cy];
             float a0 = q[0] * wyz, a1 = q[1] * wyz, a2 = q[2] * wyz, a3 = q[3] * wyz;
 #pragma unroll
             for (int cx = 0; cx < 3; ++cx) {
                 int s = base + cx + SY * cy + SZ * cz;
-                atomicAdd(s0 + s, round_fma(a0, wx[cx]));
-                atomicAdd(s1 + s, round_fma(a1, wx[cx]));
-                atomicAdd(s2 + s, round_fma(a2, wx[cx]));
-                atomicAdd(s3 + s, round_fma(a3, wx[cx]));
+                if (first_single)
+                    atomicAdd(h0 + s, __float_as_int(fmaf(a0, w.x[cx], MAGIC)) - MAGIC_BITS);
+                else
+                    add_split(h0, l0, s, a0, w.x[cx]);
+                add_split(h1, l1, s, a1, w.x[cx]);
+                add_split(h2, l2, s, a2, w.x[cx]);
+                add_split(h3, l3, s, a3, w.x[cx]);
             }
         }
 }
@@ -159,26 +196,28 @@ __device__ __forceinline__ void deposit_tile(const Ctx &c, int base, const float
 // Four channels straight into the int64 global accumulators; q carries the
 // global scale.
 template <int D>
-__device__ __noinline__ void deposit_global(const Ctx &c, const BoxDev &b, const int ci[3], const float wx[3],
-                                            const float wy[3], const float wz[3], const float q[4],
+__device__ __noinline__ void deposit_global(const Ctx &c, const BoxDev &b, int ci0, int ci1, int ci2, Wts w,
+                                            float q0, float q1, float q2, float q3,
                                             unsigned long long *__restrict__ g0)
 {
     const int64_t nc = c.nc;
+    const int ci[3] = {ci0, ci1, ci2};
     int gx[3], gy[3], gz[3];
     stencil_coords<D>(b, ci, gx, gy, gz);
     for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz)
         for (int cy = 0; cy < 3; ++cy) {
-            float wyz = D == 3 ? wy[cy] * wz[cz] : wy[cy];
+            float wyz = D == 3 ? w.y[cy] * w.z[cz] : w.y[cy];
             for (int cx = 0; cx < 3; ++cx) {
-                float w = wx[cx] * wyz;
+                float ww = w.x[cx] * wyz;
                 int64_t g = b.cell0 + ((int64_t)gz[cz] * b.n[1] + gy[cy]) * b.n[0] + gx[cx];
-                for (int k = 0; k < 4; ++k)
-                    red_add(g0 + k * nc + g, __float2ll_rn(q[k] * w));
+                red_add(g0 + g, __float2ll_rn(q0 * ww));
+                red_add(g0 + nc + g, __float2ll_rn(q1 * ww));
+                red_add(g0 + 2 * nc + g, __float2ll_rn(q2 * ww));
+                red_add(g0 + 3 * nc + g, __float2ll_rn(q3 * ww));
             }
         }
 }
 
-template <int D>
 __device__ __forceinline__ bool within(const float q[4], const float *qb, int ch0)
 {
     return fabsf(q[0]) <= qb[ch0] && fabsf(q[1]) <= qb[ch0 + 1] && fabsf(q[2]) <= qb[ch0 + 2] &&
@@ -209,21 +248,33 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
         renorm_mixed(b, d, ci[d], o[d], v[d], c.status);
     }
 
-    float w[3][3] = {{0.f, 1.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 1.f, 0.f}};
+    Wts w;
+    w.z[0] = 0.f;
+    w.z[1] = 1.f;
+    w.z[2] = 0.f;
     int rel[3] = {0, 0, 0};
-    bool in_tile = true;
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-        tsc_from_offset<float>(o[d], w[d]);
-        in_tile &= tile_rel(c, b, gm, d, ci[d], rel[d]);
+    bool in_tile = tile_rel(c, b, gm, 0, ci[0], rel[0]);
+    in_tile &= tile_rel(c, b, gm, 1, ci[1], rel[1]);
+    tsc_from_offset<float>(o[0], w.x);
+    tsc_from_offset<float>(o[1], w.y);
+    if (D == 3) {
+        in_tile &= tile_rel(c, b, gm, 2, ci[2], rel[2]);
+        tsc_from_offset<float>(o[2], w.z);
     }
     const int base = (rel[0] - 1) + c.ts[1] * (rel[1] - 1) + (D == 3 ? c.ts[2] * (rel[2] - 1) : 0);
 
     float E[3], Bf[3];
-    if (in_tile)
-        gather_tile<D>(c, base, w[0], w[1], w[2], sFa, sFb, E, Bf);
-    else
-        gather_global<D>(c, b, ci, w[0], w[1], w[2], E, Bf);
+    if (in_tile) {
+        gather_tile<D>(c, base, w, sFa, sFb, E, Bf);
+    } else {
+        F6 f = gather_global<D>(c, b, ci[0], ci[1], ci[2], w);
+        E[0] = f.e[0];
+        E[1] = f.e[1];
+        E[2] = f.e[2];
+        Bf[0] = f.b[0];
+        Bf[1] = f.b[1];
+        Bf[2] = f.b[2];
+    }
 
     // remove the component of E along B
     float B2 = Bf[0] * Bf[0] + Bf[1] * Bf[1] + Bf[2] * Bf[2];
@@ -255,12 +306,12 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
                       (e0 * (v00 + v[0]) + e1 * (v01 + v[1]) + e2 * (v02 + v[2])) / (g1 + gn);
     {
         const float qc[4] = {-k.m * (2.f * e0 + r0), -k.m * (2.f * e1 + r1), -k.m * (2.f * e2 + r2), -k.m * dEk};
-        if (in_tile && within<D>(qc, k.qb, CH_MX)) {
+        if (in_tile && within(qc, k.qb, CH_MX)) {
             const float qs[4] = {qc[0] * k.st[0], qc[1] * k.st[1], qc[2] * k.st[2], qc[3] * k.st[3]};
-            deposit_tile<D>(c, base, w[0], w[1], w[2], qs, sD);
+            deposit_tile<D>(c, base, w, qs, CH_MX, sD);
         } else {
-            const float qg[4] = {qc[0] * k.gs[0], qc[1] * k.gs[1], qc[2] * k.gs[2], qc[3] * k.gs[3]};
-            deposit_global<D>(c, b, ci, w[0], w[1], w[2], qg, c.corr);
+            deposit_global<D>(c, b, ci[0], ci[1], ci[2], w, qc[0] * k.gs[0], qc[1] * k.gs[1], qc[2] * k.gs[2],
+                              qc[3] * k.gs[3], c.corr);
         }
     }
 
@@ -272,23 +323,28 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
     }
 
     if (FULL) {
-        float w2[3][3] = {{0.f, 1.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 1.f, 0.f}};
+        Wts w2;
+        w2.z[0] = 0.f;
+        w2.z[1] = 1.f;
+        w2.z[2] = 0.f;
         int rel2[3] = {0, 0, 0};
-        bool in2 = true;
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            tsc_from_offset<float>(o[d], w2[d]);
-            in2 &= tile_rel(c, b, gm, d, ci[d], rel2[d]);
+        bool in2 = tile_rel(c, b, gm, 0, ci[0], rel2[0]);
+        in2 &= tile_rel(c, b, gm, 1, ci[1], rel2[1]);
+        tsc_from_offset<float>(o[0], w2.x);
+        tsc_from_offset<float>(o[1], w2.y);
+        if (D == 3) {
+            in2 &= tile_rel(c, b, gm, 2, ci[2], rel2[2]);
+            tsc_from_offset<float>(o[2], w2.z);
         }
         const float qj = k.qn * ig2;
         const float qm[4] = {k.qn, qj * vn[0], qj * vn[1], qj * vn[2]};
-        if (in2 && within<D>(qm, k.qb, CH_N)) {
+        if (in2 && within(qm, k.qb, CH_N)) {
             const int base2 = (rel2[0] - 1) + c.ts[1] * (rel2[1] - 1) + (D == 3 ? c.ts[2] * (rel2[2] - 1) : 0);
             const float qs[4] = {qm[0] * k.st[4], qm[1] * k.st[5], qm[2] * k.st[6], qm[3] * k.st[7]};
-            deposit_tile<D>(c, base2, w2[0], w2[1], w2[2], qs, sD + CH_N * c.tile_slots);
+            deposit_tile<D>(c, base2, w2, qs, CH_N, sD);
         } else {
-            const float qg[4] = {qm[0] * k.gs[4], qm[1] * k.gs[5], qm[2] * k.gs[6], qm[3] * k.gs[7]};
-            deposit_global<D>(c, b, ci, w2[0], w2[1], w2[2], qg, mout);
+            deposit_global<D>(c, b, ci[0], ci[1], ci[2], w2, qm[0] * k.gs[4], qm[1] * k.gs[5], qm[2] * k.gs[6],
+                              qm[3] * k.gs[7], mout);
         }
     }
 
@@ -313,8 +369,8 @@ __global__ void __launch_bounds__(PUSH_THREADS, 2) k_push_mixed(Ctx c, const Wor
     extern __shared__ __align__(16) unsigned char smem[];
     const int S = c.tile_slots;
     int *sD = reinterpret_cast<int *>(smem);
-    float4 *sFa = reinterpret_cast<float4 *>(smem + sizeof(int) * NCH * S);
-    float2 *sFb = reinterpret_cast<float2 *>(smem + (sizeof(int) * NCH + sizeof(float4)) * S);
+    float4 *sFa = reinterpret_cast<float4 *>(smem + sizeof(int) * NPLANE * S);
+    float2 *sFb = reinterpret_cast<float2 *>(smem + (sizeof(int) * NPLANE + sizeof(float4)) * S);
     __shared__ int s_item;
     unsigned long long *mout = c.momdep[cur_out];
     const int nit = *nitems;
@@ -333,7 +389,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, 2) k_push_mixed(Ctx c, const Wor
         const ItemGeom gm = item_geom(c, b, it.brick, D);
 
         // clear the deposit tile and stage the fields
-        for (int s = threadIdx.x; s < NCH * S; s += PUSH_THREADS)
+        for (int s = threadIdx.x; s < NPLANE * S; s += PUSH_THREADS)
             sD[s] = 0;
         const float4 *gF = reinterpret_cast<const float4 *>(c.f32);
         for (int t = threadIdx.x; t < c.tile_vol; t += PUSH_THREADS) {
@@ -349,36 +405,46 @@ __global__ void __launch_bounds__(PUSH_THREADS, 2) k_push_mixed(Ctx c, const Wor
         item_const(b, dt, it.p1 - it.p0, D, k);
         __syncthreads();
 
-        const LaneRange lr = lane_range(it, wid, NW);
         float vm2 = 0.f;
-        for (int64_t r = lr.first; r < lr.q; r += lr.stride) {
-            int64_t loc = lane * lr.q + r;
-            if (loc < lr.cnt)
-                vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, lr.base + loc, sFa, sFb, sD, mout));
+        if (it.pm >= 0) {
+            // one lane per cell of the half: its particles are [first, last)
+            const int half = wid >= NW / 2;
+            const int64_t key = b.key0 + (int64_t)it.brick * 64 + 32 * half + lane;
+            const int64_t first = c.key_off[key], last = c.key_off[key + 1];
+            const int cnt = (int)(last - first);
+            const int nmax = __reduce_max_sync(0xffffffffu, cnt);
+            for (int r = wid - half * (NW / 2); r < nmax; r += NW / 2)
+                if (r < cnt)
+                    vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, first + r, sFa, sFb, sD, mout));
+        } else {
+            const LaneRange lr = lane_range(it, wid, NW);
+            for (int64_t r = lr.first; r < lr.q; r += lr.stride) {
+                int64_t loc = lane * lr.q + r;
+                if (loc < lr.cnt)
+                    vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, lr.base + loc, sFa, sFb, sD, mout));
+            }
         }
         unsigned vb = __reduce_max_sync(0xffffffffu, __float_as_uint(sqrtf(vm2)));
         if (lane == 0 && vb)
             atomicMax(&c.stats[it.box].vmax, vb);
         __syncthreads();
 
-        // shift the tile into the global int64 accumulators
+        // rebuild hi 2^KLO + lo and shift the tile into the global accumulators
         for (int t = threadIdx.x; t < c.tile_vol; t += PUSH_THREADS) {
             int tx = t % c.tile[0], r = t / c.tile[0];
             int ty = r % c.tile[1], tz = r / c.tile[1];
             int64_t g = tile_global(c, b, gm, tx, ty, tz, D);
             int s = tile_slot(c, tx, ty, tz);
 #pragma unroll
-            for (int ch = 0; ch < 4; ++ch) {
-                int a = sD[ch * S + s];
-                if (a)
-                    atomicAdd(c.corr + ch * c.nc + g, (unsigned long long)(long long)a << k.ksh[ch]);
-            }
-            if (FULL) {
-#pragma unroll
-                for (int ch = 0; ch < 4; ++ch) {
-                    int a = sD[(CH_N + ch) * S + s];
-                    if (a)
-                        atomicAdd(mout + ch * c.nc + g, (unsigned long long)(long long)a << k.ksh[CH_N + ch]);
+            for (int ch = 0; ch < NCH; ++ch) {
+                if (!FULL && ch >= CH_N)
+                    break;
+                long long v = (long long)sD[ch * S + s] * (1ll << KLO) + sD[(NCH + ch) * S + s];
+                if (ch == CH_N)
+                    v = sD[ch * S + s];
+                if (v) {
+                    unsigned long long *dst = ch < CH_N ? c.corr + ch * c.nc + g : mout + (ch - CH_N) * c.nc + g;
+                    atomicAdd(dst, (unsigned long long)v << k.ksh[ch]);
                 }
             }
         }
@@ -401,7 +467,7 @@ int occupancy_mixed(size_t bytes)
 
 size_t push_smem_bytes_mixed(const Ctx &c)
 {
-    return (sizeof(int) * NCH + sizeof(float4) + sizeof(float2)) * (size_t)c.tile_slots;
+    return (sizeof(int) * NPLANE + sizeof(float4) + sizeof(float2)) * (size_t)c.tile_slots;
 }
 
 int push_blocks_per_sm_mixed(const Ctx &c)

@@ -409,6 +409,7 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         (rc = c->alloc(&c->s.nitems, 1)) || (rc = c->alloc(&c->s.max_count, 1)) ||
         (rc = c->alloc(&c->work_ctr, 1)))
         return bail(rc);
+    k.key_off = c->s.offset;
     c->nchunks = 64;
     if ((rc = c->alloc(&c->partials, (size_t)nbox * c->nchunks * 8)) || (rc = c->alloc(&c->totals_dev, 8 * nbox)))
         return bail(rc);

@@ -128,6 +128,7 @@ struct Ctx {
     float *f32;                   // [nc][8] = Ex,Ey,Ez,Bx,By,Bz,0,0
     double *f64;                  // [nc][6]
     uint32_t *status;
+    const int32_t *key_off;       // sort offsets: particles of key k are [key_off[k], key_off[k+1])
     BoxDev *boxes_rw;             // same table, writable by the scale kernel
     BoxStats *stats;              // [nbox]
 };
