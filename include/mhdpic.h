@@ -210,6 +210,37 @@ int64_t mhdpic_launch_count(const mhdpic_ctx *ctx);
 /* Free the context and its scratch (synchronises the stream). NULL is a no-op. */
 int mhdpic_destroy(mhdpic_ctx *ctx);
 
+/*
+ * mhdpic_deposit_moments_noalloc - the charge and current deposit of
+ * mhdpic_deposit (n_CR and J_CR of one box at the given positions, as
+ * densities) for callers that cannot allocate device memory once running:
+ * codes that reserve a fixed device-memory budget at start-up, time-step loops
+ * that must stay allocation-free, or call sites where the implicit device
+ * synchronisation of cudaMalloc/cudaFree is not acceptable.  It needs no
+ * context and calls no cudaMalloc, cudaFree or allocating library routine.
+ * The paper has no counterpart: it is an interface of this library.
+ *   grid, params: one box (host structs); precision: MHDPIC_PREC_MIXED (cell,
+ *   off, p) or MHDPIC_PREC_FP64 (x, p64), device arrays laid out as in
+ *   mhdpic_init; out: device double[4*ncell] = n, Jx, Jy, Jz, plane-major;
+ *   stream: cudaStream_t.
+ * Its int64 fixed-point accumulators, per-cell counts and scales are one
+ * file-scope device array of about 9 MiB (for MHDPIC_NOALLOC_MAX_CELLS cells)
+ * that every GPU loading the library holds until the process exits; grids with
+ * more than MHDPIC_NOALLOC_MAX_CELLS cells are rejected with MHDPIC_E_CAPACITY.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) for that device, so
+ * make that first call before any stream capture.  Every call clears and then
+ * reuses the same array, which keeps the last call's sums: calls that overlap
+ * on the GPU (other streams, or a second caller) race and corrupt each other,
+ * so serialise them.  The fixed-point scales are sized on the device from the
+ * densest cell of the call's particles.
+ * Errors: MHDPIC_E_ARG, MHDPIC_E_CAPACITY, MHDPIC_E_CUDA (message in
+ * mhdpic_last_error()).
+ */
+#define MHDPIC_NOALLOC_MAX_CELLS 262144
+int mhdpic_deposit_moments_noalloc(const mhdpic_grid *grid, const mhdpic_params *params, int32_t precision,
+                                   int64_t np, const int32_t *cell, const float *off, const float *p,
+                                   const double *x, const double *p64, double *out, void *stream);
+
 /* Static message for a return code, and the detailed message of the last
  * failure on this thread. */
 const char *mhdpic_strerror(int code);

@@ -44,6 +44,11 @@ int cuda_fail(cudaError_t e, const char *where)
 
 }  // namespace
 
+void mhdpic::set_last_error(const char *msg)
+{
+    g_last_error = msg;
+}
+
 struct mhdpic_ctx {
     Ctx k{};
     SortScratch s{};

@@ -171,6 +171,9 @@ int launch_fixed_to_double(const Ctx &c, const unsigned long long *src, int ch0,
                            cudaStream_t st);
 int launch_fields_to_double(const Ctx &c, double *out, cudaStream_t st);
 
+// sets the message mhdpic_last_error() returns on this thread
+void set_last_error(const char *msg);
+
 // occupancy helpers
 int push_blocks_per_sm_mixed(const Ctx &c);
 int push_blocks_per_sm_f64(const Ctx &c);

@@ -80,6 +80,8 @@ SIGNATURES = {
     "mhdpic_clear_status": (ctypes.c_int, [_V]),
     "mhdpic_launch_count": (ctypes.c_int64, [_V]),
     "mhdpic_destroy": (ctypes.c_int, [_V]),
+    "mhdpic_deposit_moments_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Params), ctypes.c_int32,
+                                                       ctypes.c_int64, _V, _V, _V, _V, _V, _V, _V]),
     "mhdpic_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mhdpic_last_error": (ctypes.c_char_p, []),
 }
@@ -171,6 +173,14 @@ def mhdpic_launch_count(ctx) -> int:
 
 def mhdpic_destroy(ctx) -> None:
     _check(load().mhdpic_destroy(ctx))
+
+
+def mhdpic_deposit_moments_noalloc(grid: Grid, params: Params, precision: int, np_: int, cell=0, off=0,
+                                   p=0, x=0, p64=0, out=0, stream=None) -> None:
+    """Allocation-free charge/current deposit of one box (device pointers as ints)."""
+    _check(load().mhdpic_deposit_moments_noalloc(ctypes.byref(grid), ctypes.byref(params), int(precision),
+                                                 int(np_), cell or None, off or None, p or None, x or None,
+                                                 p64 or None, out or None, stream))
 
 
 def status_names(flags: int) -> List[str]:
