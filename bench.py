@@ -42,6 +42,12 @@ PARTICLE_BYTES = {(3, "mixed"): 28, (2, "mixed"): 24, (3, "fp64"): 48, (2, "fp64
 # read-modify-written once (8 B each, twice)
 CELL_FIELD_BYTES = {"mixed": 24, "fp64": 48}
 CELL_DEPOSIT_BYTES = 8 * 8 * 2
+# DRAM bytes (read + write) per particle of one k_push_mixed<3, full> launch,
+# measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on a
+# 64^3 x 32 launch of the current kernel version: 465.3 MB / 8,388,608 CRs.
+# Traffic scales with the particle count (cells scale alike at fixed ppc).
+# Set to None whenever the push kernel changes, until it is measured again.
+PUSH_TRAFFIC_BYTES_PER_PARTICLE = 465.3e6 / 8388608
 
 
 def _rank_env():
@@ -283,7 +289,10 @@ def run_native(args):
                        "l2": "inputs larger than L2 (%.2f GB particle state)" % (npart * 28 / 1e9),
                        "parallelism": "independent box per GPU" if world > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_push_mixed<3,full>",
+                         "frac": achieved / peak,
+                         "traffic": (PUSH_TRAFFIC_BYTES_PER_PARTICLE * npart
+                                     if PUSH_TRAFFIC_BYTES_PER_PARTICLE else None),
+                         "kernel": "k_push_mixed<3,full>",
                          "peak_kind": peak_kind, "bytes_per_launch": bytes_push,
                          "avg_launch_ms": push_avg_s * 1e3},
             "cpu_baseline": cpu,
