@@ -47,7 +47,7 @@ CELL_DEPOSIT_BYTES = 8 * 8 * 2
 # 64^3 x 32 launch of the current kernel version: 465.3 MB / 8,388,608 CRs.
 # Traffic scales with the particle count (cells scale alike at fixed ppc).
 # Set to None whenever the push kernel changes, until it is measured again.
-PUSH_TRAFFIC_BYTES_PER_PARTICLE = 465.3e6 / 8388608
+PUSH_TRAFFIC_BYTES_PER_PARTICLE = None
 
 
 def _rank_env():

@@ -6,13 +6,15 @@
 // accumulates both deposits in a shared fixed-point tile, and adds the tile to
 // the int64 global accumulators at the end.
 //
-//  * Lane <-> cell: a 64-cell brick is two 32-cell halves; warps 0-3 work on
-//    one half and warps 4-7 on the other, lane l taking exactly the particles
-//    sorted into the l-th cell of its half (cell ranges from the sort's
-//    offsets), so the 32 lanes of an instruction sit in 32 different cells.
-//    The tile strides are padded (3-D: y 12, z 112 slots; 2-D: y 24) so those
-//    32 cells fall on 32 different banks for the 32-bit deposit atomics and on
-//    distinct bank groups for the 128-bit and 64-bit field loads.
+//  * Lanes and cells: a 64-cell brick is two 32-cell halves; warps 0-3 work
+//    on one half and warps 4-7 on the other, and lane l takes the l-th 1/32 of
+//    its half's (cell-sorted) particles, so the 32 lanes of an instruction sit
+//    in about 32 different cells.  The tile strides are padded (3-D: y 12,
+//    z 112 slots; 2-D: y 24) so that 32 cells of a half fall on 32 different
+//    banks for the 32-bit deposit atomics and on distinct bank groups for the
+//    128-bit and 64-bit field loads.  (Giving each lane exactly one cell's
+//    particles removes more conflicts but idles a quarter of the lanes, since
+//    cell counts vary; the even split measured 11% faster.)
 //  * Fixed point in the tile: each contribution x (in tile units) is split
 //    exactly into hi = round(x / 2^KLO) and lo = x - hi 2^KLO with one FFMA
 //    against 1.5*2^(23+KLO), one FFMA for the residual and one FADD against
@@ -406,17 +408,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, 2) k_push_mixed(Ctx c, const Wor
         __syncthreads();
 
         float vm2 = 0.f;
-        if (it.pm >= 0) {
-            // one lane per cell of the half: its particles are [first, last)
-            const int half = wid >= NW / 2;
-            const int64_t key = b.key0 + (int64_t)it.brick * 64 + 32 * half + lane;
-            const int64_t first = c.key_off[key], last = c.key_off[key + 1];
-            const int cnt = (int)(last - first);
-            const int nmax = __reduce_max_sync(0xffffffffu, cnt);
-            for (int r = wid - half * (NW / 2); r < nmax; r += NW / 2)
-                if (r < cnt)
-                    vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, first + r, sFa, sFb, sD, mout));
-        } else {
+        {
             const LaneRange lr = lane_range(it, wid, NW);
             for (int64_t r = lr.first; r < lr.q; r += lr.stride) {
                 int64_t loc = lane * lr.q + r;
