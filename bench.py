@@ -57,15 +57,38 @@ def _rank_env():
     return r, w, lr
 
 
+WORKLOADS = {
+    "alfvenic_beam_3d": "3-D periodic {n}^3 grid, {ppc} CR/cell, uniform gas + random-phase Alfvenic dB/B0=0.1 "
+                        "(64 modes), beam |p|=100 boosted 10 v_A along B, C=300, TSC, no Hall term",
+    "bell_2d": "2-D periodic 1024^2 grid, 64 CR/cell, B along x, dN/dp ~ p^-2 on [10, 1e4] drifting 0.5 v_A, "
+               "C=300, CR-Hall term on",
+    "shock_2d": "2-D 16384x128 grid, reflecting x walls, 40 CR/cell average with 80% in the 5% of cells "
+                "nearest the wall, upstream v=-20 v_A, dN/dp ~ p^-2 on [1, 1e5], C=200",
+    "ensemble_2d": "96 independent 2-D periodic boxes, sides log-uniform in [32, 512], 4-64 CR/cell, "
+                   "dB/B0 in [0, 0.3], |p|=10, C=100, advanced together",
+    "periodic_thermal_2d": "2-D periodic 64^2 grid, 16 CR/cell, uniform gas, B along x, |p|=10, C=100",
+}
+
+
 def _workload(args, seed):
+    """The boxes of the selected workload and their common time step."""
     from paper_1412_1087_gb300 import workloads as wl
-    return wl.alfvenic_beam_3d(seed=seed, n=args.n, ppc=args.ppc)
+    if args.workload == "alfvenic_beam_3d":
+        boxes = [wl.alfvenic_beam_3d(seed=seed, n=args.n, ppc=args.ppc)]
+    elif args.workload == "bell_2d":
+        boxes = [wl.bell_2d(seed=seed)]
+    elif args.workload == "shock_2d":
+        boxes = [wl.shock_2d(seed=seed)]
+    elif args.workload == "ensemble_2d":
+        boxes = wl.ensemble_2d(nbox=96, seed0=seed * 1000)
+    else:
+        boxes = [wl.periodic_thermal_2d(seed=seed)]
+    return boxes, min(b.dt for b in boxes)
 
 
 def _workload_desc(args):
-    return ("alfvenic_beam_3d: 3-D periodic %d^3 grid, %d CR/cell (%d CRs), uniform gas + random-phase "
-            "Alfvenic dB/B0=0.1 (64 modes), beam |p|=100 boosted 10 v_A along B, C=300, TSC"
-            % (args.n, args.ppc, args.n ** 3 * args.ppc))
+    d = WORKLOADS[args.workload].format(n=args.n, ppc=args.ppc)
+    return args.workload + ": " + d
 
 
 class ClockSampler:
@@ -123,6 +146,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def aggregate_ranks(total_ms: float, particle_steps: float, dist=None, device=None):
+    """Whole-job figures over ranks: the slowest rank's time and the sum of the
+    particle-steps all ranks advanced (weak scaling, no data-path collective)."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return total_ms, particle_steps
+    dev = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    n = torch.tensor([particle_steps], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -132,11 +169,11 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _time_engine(eng, box, steps, warmup, sort_every, torch, per_push=True):
+def _time_engine(eng, dt, steps, warmup, sort_every, torch, per_push=True):
     """Run warmup + timed steps; returns (total_ms, push_ms_sum, launches)."""
     st = eng.stream
     for k in range(warmup):
-        eng.interp_push(box.dt, 1)
+        eng.interp_push(dt, 1)
         eng.apply_feedback(False)
         if sort_every and (k + 1) % sort_every == 0:
             eng.sort()
@@ -148,7 +185,7 @@ def _time_engine(eng, box, steps, warmup, sort_every, torch, per_push=True):
     for k in range(steps):
         if per_push:
             ev[k][0].record(st)
-        eng.interp_push(box.dt, 1)
+        eng.interp_push(dt, 1)
         if per_push:
             ev[k][1].record(st)
         eng.apply_feedback(False)
@@ -161,46 +198,66 @@ def _time_engine(eng, box, steps, warmup, sort_every, torch, per_push=True):
     return total, push, eng.launches() - l0
 
 
+def _sample_box(args, seed, size):
+    """A bounded sample of the selected workload's recipe ('cpu' or 'err' size)."""
+    from paper_1412_1087_gb300 import workloads as wl
+    big = size == "cpu"
+    if args.workload == "alfvenic_beam_3d":
+        n = args.sample_n if big else args.err_n
+        return wl.alfvenic_beam_3d(seed=seed, n=n, ppc=args.ppc), "%d^3 x %d CR/cell" % (n, args.ppc)
+    if args.workload == "bell_2d":
+        n = 176 if big else 64
+        return wl.bell_2d(seed=seed, n=n), "%d^2 x 64 CR/cell" % n
+    if args.workload == "shock_2d":
+        nx, ny = (2048, 32) if big else (512, 16)
+        return wl.shock_2d(seed=seed, nx=nx, ny=ny), "%d x %d, 40 CR/cell average" % (nx, ny)
+    if args.workload == "ensemble_2d":
+        side = 256 if big else 64
+        b = wl.ensemble_2d(nbox=1, seed0=seed * 1000, max_side=side)[0]
+        return b, "one ensemble box, side %d" % b.n[0]
+    return wl.periodic_thermal_2d(seed=seed), "64^2 x 16 CR/cell"
+
+
 def _cpu_baseline(args, seed, nsteps):
     import oracle as orc
     from paper_1412_1087_gb300 import workloads as wl
-    box = wl.alfvenic_beam_3d(seed=seed, n=args.sample_n, ppc=args.ppc)
-    x = wl.absolute_positions(box)
-    v = box.p.astype(np.float64)
-    st = orc.State(box, x, v)
+    box, what = _sample_box(args, seed, "cpu")
+    st = orc.State(box, wl.absolute_positions(box), box.p.astype(np.float64))
     t0 = time.perf_counter()
     for _ in range(nsteps):
         st.step(box.dt)
     dt = time.perf_counter() - t0
-    ps = box.np * nsteps
-    return {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "alfvenic_beam_3d recipe at %d^3 x %d CR/cell (%d CRs), %d full steps, single thread"
-                      % (args.sample_n, args.ppc, box.np, nsteps), "seconds": dt}
+    return {"value": box.np * nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%s recipe at %s (%d CRs), %d full steps, single thread"
+                      % (args.workload, what, box.np, nsteps), "seconds": dt}
 
 
 def _error_vs_oracle(args, seed, torch):
-    """One step of the mixed and FP64 GPU paths against the oracle on the sample box."""
+    """One step of the mixed and FP64 GPU paths against the oracle on a sample box."""
     import oracle as orc
     from paper_1412_1087_gb300 import mhdpic as m
     from paper_1412_1087_gb300 import workloads as wl
-    box = wl.alfvenic_beam_3d(seed=seed, n=args.err_n, ppc=args.ppc)
+    box, what = _sample_box(args, seed, "err")
     g = orc.grid_of(box)
-    perm, _ = orc.sort_cells(g, (4, 4, 4), box.cell)
+    perm, _ = orc.sort_cells(g, (4, 4, 4) if box.ndim == 3 else (8, 8, 1), box.cell)
     x = np.ascontiguousarray(wl.absolute_positions(box)[:, perm])
     v = np.ascontiguousarray(box.p.astype(np.float64)[:, perm])
     st = orc.State(box, x, v)
     corr, md = st.push_only(box.dt)
     out = {}
+
+    def rl(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
     for name, prec in (("mixed", m.MHDPIC_PREC_MIXED), ("fp64", m.MHDPIC_PREC_FP64)):
         eng = m.Engine([box], precision=prec)
         eng.interp_push(box.dt, 1)
         gc = eng.deposits(0).cpu().numpy()
         gm = eng.deposits(1).cpu().numpy()
         eng.close()
-        rl = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
         out[name] = {"corrector_rel_l2_max": max(rl(gc[q], corr[q]) for q in range(4)),
                      "moments_rel_l2_max": max(rl(gm[q], md[q]) for q in range(4))}
-    out["sample"] = "one step at %d^3 x %d CR/cell" % (args.err_n, args.ppc)
+    out["sample"] = "one step at %s" % what
     return out
 
 
@@ -219,61 +276,77 @@ def run_native(args):
     if world > 1:
         dist.barrier()
     m.load()
-    box = _workload(args, seed=rank)
-    eng = m.Engine([box], precision=m.MHDPIC_PREC_MIXED, device="cuda:%d" % lrank)
-    npart = box.np
+    dev = "cuda:%d" % lrank
+    boxes, dt = _workload(args, seed=rank)
+    npart = sum(b.np for b in boxes)
+    ncell = sum(b.ncell for b in boxes)
+    ndim = boxes[0].ndim
+    stream = torch.cuda.Stream(device=dev)
+    eng = m.Engine(boxes, precision=m.MHDPIC_PREC_MIXED, device=dev, stream=stream)
 
-    # timed region (device time, max over ranks)
+    # timed region (device time, max over ranks): one call per step so that
+    # the push kernel can be bracketed by events on the library's stream
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(lrank) as clk:
-        total_ms, push_ms, launches = _time_engine(eng, box, args.steps, args.warmup, args.sort_every, torch)
+        total_ms, push_ms, launches = _time_engine(eng, dt, args.steps, args.warmup, args.sort_every, torch)
     clocks = clk.summary()
+    total_ms, job_steps = aggregate_ranks(total_ms, float(npart) * args.steps,
+                                          dist if world > 1 else None, dev)
+    value = job_steps / (total_ms / 1e3)
+
+    # the same steps replayed from a CUDA graph (mhdpic_run)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eng.run(dt, 2 * args.sort_every, args.sort_every)      # capture + one replay
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    eng.run(dt, args.steps, args.sort_every)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = ev0.elapsed_time(ev1) / args.steps
     flags = eng.status()
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda:%d" % lrank)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = npart * world * args.steps / (total_ms / 1e3)
 
     # roofline of the push kernel (the dominant kernel)
     peak, peak_kind = _peaks()
-    nc = box.ncell
-    bytes_push = npart * 2 * PARTICLE_BYTES[(3, "mixed")] + nc * (CELL_FIELD_BYTES["mixed"] + CELL_DEPOSIT_BYTES)
+    prec = "mixed"
+    bytes_push = npart * 2 * PARTICLE_BYTES[(ndim, prec)] + ncell * (CELL_FIELD_BYTES[prec] + CELL_DEPOSIT_BYTES)
     push_avg_s = push_ms / args.steps / 1e3
     achieved = bytes_push / push_avg_s / 1e9
-    eng_stats = {"push_ms_per_step": push_ms / args.steps}
+    traffic = None
+    if PUSH_TRAFFIC_BYTES_PER_PARTICLE and args.workload == "alfvenic_beam_3d":
+        traffic = PUSH_TRAFFIC_BYTES_PER_PARTICLE * npart
+    eng_stats = {"push_ms_per_step": push_ms / args.steps, "graph_run_ms_per_step": graph_ms,
+                 "particles": npart, "cells": ncell, "dt": dt}
 
-    # plain FP64 GPU path on the same workload
+    # plain FP64 GPU path on the same boxes
     fp64 = None
+    eng.close()
+    del eng
+    torch.cuda.empty_cache()
     if args.fp64_steps > 0:
-        eng.close()
-        del eng
-        torch.cuda.empty_cache()
-        e64 = m.Engine([box], precision=m.MHDPIC_PREC_FP64, device="cuda:%d" % lrank)
-        t64, p64, _ = _time_engine(e64, box, args.fp64_steps, 1, args.sort_every, torch)
+        e64 = m.Engine(boxes, precision=m.MHDPIC_PREC_FP64, device=dev, stream=stream)
+        t64, _, _ = _time_engine(e64, dt, args.fp64_steps, 1, args.sort_every, torch)
         v64 = npart * args.fp64_steps / (t64 / 1e3)
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": t64 / args.fp64_steps,
                 "steps": args.fp64_steps, "speedup_mixed_over_fp64": value / world / v64}
         e64.close()
         del e64
         torch.cuda.empty_cache()
-    else:
-        eng.close()
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
     if args.e2e_steps > 0:
-        eh = m.Engine([box], precision=m.MHDPIC_PREC_MIXED, memory=m.MHDPIC_MEM_HOST, device="cuda:%d" % lrank)
-        te, _, _ = _time_engine(eh, box, args.e2e_steps, 1, args.sort_every, torch, per_push=False)
+        eh = m.Engine(boxes, precision=m.MHDPIC_PREC_MIXED, memory=m.MHDPIC_MEM_HOST, device=dev, stream=stream)
+        te, _, _ = _time_engine(eh, dt, args.e2e_steps, 1, args.sort_every, torch, per_push=False)
         eh.close()
-        pbytes = npart * PARTICLE_BYTES[(3, "mixed")]
-        h2d = pbytes + nc * 8 * 8            # push: particles; feedback: rho, mom(3), egas, B(3)
-        d2h = pbytes + nc * 4 * 8            # push: particles; feedback: mom(3), egas
-        sort_extra = (2 * pbytes) / args.sort_every if args.sort_every else 0
-        e2e = {"value": npart * world * args.e2e_steps / (te / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d + sort_extra / 2), "d2h_bytes_per_step": int(d2h + sort_extra / 2),
+        pbytes = npart * PARTICLE_BYTES[(ndim, prec)]
+        h2d = pbytes + ncell * 8 * 8            # push: particles; feedback: rho, mom(3), egas, B(3)
+        d2h = pbytes + ncell * 4 * 8            # push: particles; feedback: mom(3), egas
+        sort_extra = pbytes / args.sort_every if args.sort_every else 0   # the sort copies particles both ways
+        te, e2e_steps = aggregate_ranks(te, float(npart) * args.e2e_steps, dist if world > 1 else None, dev)
+        e2e = {"value": e2e_steps / (te / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d + sort_extra), "d2h_bytes_per_step": int(d2h + sort_extra),
                "steps": args.e2e_steps, "ms_per_step": te / args.e2e_steps}
 
     out = None
@@ -286,15 +359,13 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 push + i64 fixed-point deposits",
             "data": "synthetic",
             "config": {"workload": _workload_desc(args), "precision": "mixed", "sort_every": args.sort_every,
-                       "l2": "inputs larger than L2 (%.2f GB particle state)" % (npart * 28 / 1e9),
+                       "l2": "inputs larger than L2 (%.2f GB particle state)"
+                             % (npart * PARTICLE_BYTES[(ndim, prec)] / 1e9),
                        "parallelism": "independent box per GPU" if world > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak,
-                         "traffic": (PUSH_TRAFFIC_BYTES_PER_PARTICLE * npart
-                                     if PUSH_TRAFFIC_BYTES_PER_PARTICLE else None),
-                         "kernel": "k_push_mixed<3,full>",
-                         "peak_kind": peak_kind, "bytes_per_launch": bytes_push,
-                         "avg_launch_ms": push_avg_s * 1e3},
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_push_mixed<%d,full>" % ndim, "peak_kind": peak_kind,
+                         "bytes_per_launch": bytes_push, "avg_launch_ms": push_avg_s * 1e3},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -317,9 +388,9 @@ def run_reference(args):
         return None
     import oracle
     oracle.build()
-    from paper_1412_1087_gb300 import workloads as wl
     import oracle as orc
-    box = wl.alfvenic_beam_3d(seed=0, n=args.sample_n, ppc=args.ppc)
+    from paper_1412_1087_gb300 import workloads as wl
+    box, what = _sample_box(args, 0, "cpu")
     st = orc.State(box, wl.absolute_positions(box), box.p.astype(np.float64))
     for _ in range(args.warmup):
         st.step(box.dt)
@@ -328,8 +399,7 @@ def run_reference(args):
         st.step(box.dt)
     dt = time.perf_counter() - t0
     value = box.np * args.steps / dt
-    sample = ("FP64 CPU oracle, alfvenic_beam_3d recipe at %d^3 x %d CR/cell (%d CRs) per step, single thread"
-              % (args.sample_n, args.ppc, box.np))
+    sample = "FP64 CPU oracle, %s recipe at %s (%d CRs) per step, single thread" % (args.workload, what, box.np)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -346,6 +416,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="alfvenic_beam_3d")
     ap.add_argument("--n", type=int, default=128, help="cells per side of the 3-D box")
     ap.add_argument("--ppc", type=int, default=32)
     ap.add_argument("--sort-every", type=int, default=2)

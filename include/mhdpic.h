@@ -185,6 +185,21 @@ int mhdpic_deposit(mhdpic_ctx *ctx);
 int mhdpic_apply_feedback(mhdpic_ctx *ctx, double *totals_out);
 
 /*
+ * mhdpic_run - nsteps full steps, each mhdpic_interp_push(dt, 1) followed by
+ * mhdpic_apply_feedback(NULL), with mhdpic_sort after every sort_every-th
+ * step (counted across calls).  sort_every = 0 lets the library choose the
+ * cadence: the first call times cycles of 1, 2, 3 and 4 steps on real steps
+ * (they count toward nsteps) and keeps the fastest (mhdpic_sort_cadence).
+ * Whole cycles are captured once into a CUDA graph and replayed (re-captured
+ * when dt or the cadence changes); with the legacy default stream or host
+ * buffers the steps run eagerly.  Asynchronous except while tuning.
+ */
+int mhdpic_run(mhdpic_ctx *ctx, double dt, int32_t nsteps, int32_t sort_every);
+
+/* Sort cadence chosen by mhdpic_run's tuner (0 before tuning, -1: bad ctx). */
+int32_t mhdpic_sort_cadence(const mhdpic_ctx *ctx);
+
+/*
  * mhdpic_get_deposits - convert fixed-point accumulators to double.
  *   which 0: corrector (dMx, dMy, dMz, dE) as accumulated since the last
  *            apply (momentum and energy, not densities; the sign is the gas's)

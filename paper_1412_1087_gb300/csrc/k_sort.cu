@@ -213,6 +213,9 @@ __global__ void __launch_bounds__(256) k_sort_segments(int64_t nkeys, const int3
             continue;
         if (n <= 32) {
             int v = lane < n ? perm[s + lane] : INT_MAX;
+            int nxt = __shfl_down_sync(0xffffffffu, v, 1);
+            if (__all_sync(0xffffffffu, lane >= n - 1 || v < nxt))
+                continue;   // already in ascending order
 #pragma unroll
             for (int kk = 2; kk <= 32; kk <<= 1) {
 #pragma unroll
@@ -317,17 +320,31 @@ __global__ void __launch_bounds__(1024) k_sort_big(const int32_t *__restrict__ o
     }
 }
 
-template <typename T>
-__global__ void k_gather(int64_t np, int ncomp, const int32_t *__restrict__ perm,
-                         const T *__restrict__ src, T *__restrict__ dst)
+// All particle arrays gathered through the permutation in one pass: every
+// plane q of element size esz[q] (4 or 8 bytes) is read at perm[r] and written
+// at r.
+struct Planes {
+    const void *src[8];
+    void *dst[8];
+    int esz[8];
+    int n;
+};
+
+__global__ void k_gather_all(int64_t np, const int32_t *__restrict__ perm, Planes pl)
 {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < np;
          r += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = perm[r];
         if (i < 0 || i >= np)   // never taken for a valid permutation
             i = r;
-        for (int q = 0; q < ncomp; ++q)
-            dst[(int64_t)q * np + r] = src[(int64_t)q * np + i];
+        for (int q = 0; q < pl.n; ++q) {
+            if (pl.esz[q] == 8)
+                reinterpret_cast<unsigned long long *>(pl.dst[q])[r] =
+                    __ldg(reinterpret_cast<const unsigned long long *>(pl.src[q]) + i);
+            else
+                reinterpret_cast<unsigned int *>(pl.dst[q])[r] =
+                    __ldg(reinterpret_cast<const unsigned int *>(pl.src[q]) + i);
+        }
     }
 }
 
@@ -433,26 +450,40 @@ int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *
         k_sort_segments<<<gb, 256, 0, st>>>(c.nkeys, s.offset, s.perm, s.big_list, s.big_count);
         k_sort_big<<<152, 1024, 0, st>>>(s.offset, s.perm, s.big_list, s.big_count, s.pkey, c.status);
         launches += 3;
-        // gather the particle arrays through the permutation (staged copy first)
+        // gather every particle array into scratch through the permutation,
+        // then copy the sorted arrays back into the caller's buffers
         int g = grid_for(c.np, 256);
         char *tmp = (char *)s.tmp;
+        Planes pl{};
+        struct Arr {
+            void *p;
+            int esz, ncomp;
+        } arrs[3];
+        int na = 0;
         if (c.prec == MHDPIC_PREC_MIXED) {
-            size_t nb_cell = sizeof(int32_t) * c.np, nb_off = sizeof(float) * c.ndim * c.np,
-                   nb_p = sizeof(float) * 3 * c.np;
-            cudaMemcpyAsync(tmp, c.cell, nb_cell, cudaMemcpyDeviceToDevice, st);
-            cudaMemcpyAsync(tmp + nb_cell, c.off, nb_off, cudaMemcpyDeviceToDevice, st);
-            cudaMemcpyAsync(tmp + nb_cell + nb_off, c.p, nb_p, cudaMemcpyDeviceToDevice, st);
-            k_gather<int32_t><<<g, 256, 0, st>>>(c.np, 1, s.perm, (const int32_t *)tmp, c.cell);
-            k_gather<float><<<g, 256, 0, st>>>(c.np, c.ndim, s.perm, (const float *)(tmp + nb_cell), c.off);
-            k_gather<float><<<g, 256, 0, st>>>(c.np, 3, s.perm, (const float *)(tmp + nb_cell + nb_off), c.p);
-            launches += 3;
+            arrs[na++] = {c.cell, 4, 1};
+            arrs[na++] = {c.off, 4, c.ndim};
+            arrs[na++] = {c.p, 4, 3};
         } else {
-            size_t nb_x = sizeof(double) * c.ndim * c.np, nb_p = sizeof(double) * 3 * c.np;
-            cudaMemcpyAsync(tmp, c.x, nb_x, cudaMemcpyDeviceToDevice, st);
-            cudaMemcpyAsync(tmp + nb_x, c.p64, nb_p, cudaMemcpyDeviceToDevice, st);
-            k_gather<double><<<g, 256, 0, st>>>(c.np, c.ndim, s.perm, (const double *)tmp, c.x);
-            k_gather<double><<<g, 256, 0, st>>>(c.np, 3, s.perm, (const double *)(tmp + nb_x), c.p64);
-            launches += 2;
+            arrs[na++] = {c.x, 8, c.ndim};
+            arrs[na++] = {c.p64, 8, 3};
+        }
+        size_t off = 0;
+        for (int a = 0; a < na; ++a)
+            for (int q = 0; q < arrs[a].ncomp; ++q) {
+                pl.src[pl.n] = (const char *)arrs[a].p + (size_t)q * c.np * arrs[a].esz;
+                pl.dst[pl.n] = tmp + off;
+                pl.esz[pl.n] = arrs[a].esz;
+                off += (size_t)c.np * arrs[a].esz;
+                ++pl.n;
+            }
+        k_gather_all<<<g, 256, 0, st>>>(c.np, s.perm, pl);
+        ++launches;
+        off = 0;
+        for (int a = 0; a < na; ++a) {
+            size_t bytes = (size_t)c.np * arrs[a].esz * arrs[a].ncomp;
+            cudaMemcpyAsync(arrs[a].p, tmp + off, bytes, cudaMemcpyDeviceToDevice, st);
+            off += bytes;
         }
         if (perm_out) {
             k_perm_out<<<g, 256, 0, st>>>(c.np, s.perm, perm_out);

@@ -70,6 +70,14 @@ struct mhdpic_ctx {
     mhdpic_particles hp{};
     mhdpic_gas hg{};
     bool valid = false;
+    // mhdpic_run: captured step cycle and sort cadence
+    cudaGraphExec_t graph = nullptr;
+    double graph_dt = 0.0;
+    int graph_k = 0;
+    int graph_cur = -1;
+    int64_t graph_launches = 0;   // kernel launches inside one replay
+    int step_in_cycle = 0;        // steps since the last sort done by mhdpic_run
+    int tuned_k = 0;
 
     template <typename T>
     int alloc(T **p, size_t count)
@@ -277,6 +285,8 @@ int mhdpic_destroy(mhdpic_ctx *c)
         return MHDPIC_OK;
     if (c->stream || c->valid)
         cudaStreamSynchronize(c->stream);
+    if (c->graph)
+        cudaGraphExecDestroy(c->graph);
     for (void *p : c->allocs)
         cudaFree(p);
     c->valid = false;
@@ -593,6 +603,148 @@ int mhdpic_get_fields(mhdpic_ctx *c, double *out)
         return fail(MHDPIC_E_ARG, "out must be non-NULL");
     return check_launch(c, launch_fields_to_double(c->k, out, c->stream));
 }
+
+}  // extern "C"
+
+namespace {
+
+// One full step of mhdpic_run: push, feedback, and the sort at the end of a cycle.
+int run_one_step(mhdpic_ctx *c, double dt, int k)
+{
+    int rc;
+    if ((rc = mhdpic_interp_push(c, dt, 1)) || (rc = mhdpic_apply_feedback(c, nullptr)))
+        return rc;
+    if (++c->step_in_cycle >= k) {
+        c->step_in_cycle = 0;
+        if ((rc = mhdpic_sort(c, nullptr, nullptr)))
+            return rc;
+    }
+    return MHDPIC_OK;
+}
+
+// Sort cadence with the shortest measured time per step: each candidate runs
+// one full cycle of real steps, timed with events on the context's stream.
+int tune_sort_cadence(mhdpic_ctx *c, double dt, int32_t *steps_left)
+{
+    static const int cands[] = {1, 2, 3, 4};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 0.f;
+    int best_k = 2;
+    for (int k : cands) {
+        if (*steps_left < k)
+            break;
+        // align to the start of a cycle of length k (sort now)
+        int rc = mhdpic_sort(c, nullptr, nullptr);
+        c->step_in_cycle = 0;
+        if (rc)
+            return rc;
+        cudaEventRecord(e0, c->stream);
+        for (int s = 0; s < k; ++s)
+            if ((rc = run_one_step(c, dt, k)))
+                return rc;
+        cudaEventRecord(e1, c->stream);
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *steps_left -= k;
+        if (best == 0.f || ms / k < best) {
+            best = ms / k;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tuned_k = best_k;
+    return MHDPIC_OK;
+}
+
+int capture_cycle(mhdpic_ctx *c, double dt, int k, int cycle)
+{
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    const int64_t l0 = c->launches;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = MHDPIC_OK;
+    for (int s = 0; s < cycle && rc == MHDPIC_OK; ++s)
+        rc = run_one_step(c, dt, k);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->graph_launches = c->launches - l0;
+    c->launches = l0;   // captured, not yet executed
+    if (rc) {
+        if (g)
+            cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    c->graph_dt = dt;
+    c->graph_k = k;
+    c->graph_cur = c->cur;
+    return MHDPIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mhdpic_run(mhdpic_ctx *c, double dt, int32_t nsteps, int32_t sort_every)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (!(dt > 0.0) || !std::isfinite(dt))
+        return fail(MHDPIC_E_ARG, "dt must be finite and > 0");
+    if (nsteps < 0 || sort_every < 0)
+        return fail(MHDPIC_E_ARG, "nsteps and sort_every must be >= 0");
+    int rc;
+    int32_t left = nsteps;
+    if (sort_every == 0 && !c->tuned_k)
+        if ((rc = tune_sort_cadence(c, dt, &left)))
+            return rc;
+    const int k = sort_every ? sort_every : c->tuned_k;
+    if (c->step_in_cycle >= k)
+        c->step_in_cycle = 0;
+    // finish the current cycle eagerly (and a first step when the next
+    // moments buffer has not been cleared by a staging pass yet)
+    while (left > 0 && (c->step_in_cycle != 0 || !c->next_clear)) {
+        if ((rc = run_one_step(c, dt, k)))
+            return rc;
+        --left;
+    }
+    // whole cycles from a graph (an even number of pushes, so the moments
+    // buffers alternate back to where the capture started); the legacy default
+    // stream and host buffers cannot be captured and run eagerly
+    const int cycle = (k % 2) ? 2 * k : k;
+    const bool graphs = c->stream != nullptr && c->mem == MHDPIC_MEM_DEVICE;
+    if (graphs && left >= cycle) {
+        if (!c->graph || c->graph_dt != dt || c->graph_k != k || c->graph_cur != c->cur)
+            if ((rc = capture_cycle(c, dt, k, cycle)))
+                return rc;
+        while (left >= cycle) {
+            CK(cudaGraphLaunch(c->graph, c->stream));
+            c->launches += c->graph_launches;
+            left -= cycle;
+        }
+    }
+    while (left > 0) {
+        if ((rc = run_one_step(c, dt, k)))
+            return rc;
+        --left;
+    }
+    return MHDPIC_OK;
+}
+
+int32_t mhdpic_sort_cadence(const mhdpic_ctx *c) { return c && c->valid ? c->tuned_k : -1; }
 
 int64_t mhdpic_num_keys(const mhdpic_ctx *c) { return c && c->valid ? c->k.nkeys : -1; }
 

@@ -73,6 +73,8 @@ SIGNATURES = {
     "mhdpic_interp_push": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32]),
     "mhdpic_deposit": (ctypes.c_int, [_V]),
     "mhdpic_apply_feedback": (ctypes.c_int, [_V, _V]),
+    "mhdpic_run": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32, ctypes.c_int32]),
+    "mhdpic_sort_cadence": (ctypes.c_int32, [_V]),
     "mhdpic_get_deposits": (ctypes.c_int, [_V, ctypes.c_int32, _V]),
     "mhdpic_get_fields": (ctypes.c_int, [_V, _V]),
     "mhdpic_num_keys": (ctypes.c_int64, [_V]),
@@ -143,6 +145,14 @@ def mhdpic_apply_feedback(ctx, totals_out: Optional[np.ndarray] = None) -> None:
         assert totals_out.dtype == np.float64 and totals_out.flags["C_CONTIGUOUS"]
         ptr = totals_out.ctypes.data_as(ctypes.c_void_p)
     _check(load().mhdpic_apply_feedback(ctx, ptr))
+
+
+def mhdpic_run(ctx, dt: float, nsteps: int, sort_every: int = 0) -> None:
+    _check(load().mhdpic_run(ctx, float(dt), int(nsteps), int(sort_every)))
+
+
+def mhdpic_sort_cadence(ctx) -> int:
+    return int(load().mhdpic_sort_cadence(ctx))
 
 
 def mhdpic_get_deposits(ctx, which: int, out_ptr: int) -> None:
@@ -304,6 +314,13 @@ class Engine:
     def step(self, dt: float, nsub: int = 1) -> None:
         self.interp_push(dt, nsub)
         self.apply_feedback(False)
+
+    def run(self, dt: float, nsteps: int, sort_every: int = 0) -> None:
+        """nsteps full steps replayed from a CUDA graph (sort cadence tuned when 0)."""
+        mhdpic_run(self.ctx, dt, nsteps, sort_every)
+
+    def sort_cadence(self) -> int:
+        return mhdpic_sort_cadence(self.ctx)
 
     # -- read-back ----------------------------------------------------------
     def deposits(self, which: int):

@@ -334,3 +334,113 @@ def test_invalid_calls_are_rejected():
     with pytest.raises(m.MhdpicError):
         m.mhdpic_get_deposits(eng.ctx, 5, 0)
     eng.close()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_graph_replayed_run_equals_eager_steps(k):
+    """mhdpic_run replays whole sort cycles from a CUDA graph: the result is
+    bit-identical to the same steps issued one call at a time."""
+    box = tilt_B(wl.alfvenic_beam_3d(n=12, ppc=6, nmodes=8, seed=40), 40)
+    stream = torch.cuda.Stream()
+    outs = []
+    for mode in ("eager", "graph"):
+        eng = m.Engine([box], precision=MIXED, stream=stream)
+        nsteps = 2 * k * 2 + 1
+        if mode == "eager":
+            for s in range(nsteps):
+                eng.step(box.dt)
+                if (s + 1) % k == 0:
+                    eng.sort()
+        else:
+            eng.run(box.dt, nsteps, k)
+        stream.synchronize()
+        outs.append((eng.p.cpu().numpy(), eng.cell.cpu().numpy(), eng.mom.cpu().numpy(),
+                     eng.deposits(1).cpu().numpy(), eng.fields().cpu().numpy()))
+        assert eng.status() == 0
+        eng.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_run_tunes_the_sort_cadence():
+    box = wl.periodic_thermal_2d(nx=48, ny=40, ppc=8, seed=41)
+    stream = torch.cuda.Stream()
+    eng = m.Engine([box], precision=MIXED, stream=stream)
+    assert eng.sort_cadence() == 0
+    eng.run(box.dt, 16, 0)
+    assert eng.sort_cadence() in (1, 2, 3, 4)
+    t = eng.apply_feedback(totals=True)[0]
+    assert np.all(np.isfinite(t)) and eng.status() == 0
+    eng.close()
+
+
+def test_mixed_conservation_over_1000_steps():
+    """Total gas + CR momentum and energy drift by <= 1e-6 over 1000 mixed
+    steps (graph-replayed, sort every 2 steps), with a substantial CR share."""
+    box = tilt_B(wl.periodic_thermal_2d(nx=32, ny=24, ppc=8, dv_amp=0.5, seed=42), 42)
+    box.hall = 1
+    box.m_cr = 0.05
+    stream = torch.cuda.Stream()
+    eng = m.Engine([box], precision=MIXED, stream=stream)
+    t0 = eng.apply_feedback(totals=True)[0]
+    eng.run(box.dt, 1000, 2)
+    t1 = eng.apply_feedback(totals=True)[0]
+    assert eng.status() == 0
+    mom = eng.mom.cpu().numpy()
+    scaleP = np.abs(mom).sum() + box.m_cr * np.abs(eng.p.cpu().numpy().astype(np.float64)).sum()
+    dP = np.abs((t1[0:3] + t1[4:7]) - (t0[0:3] + t0[4:7])).max()
+    dE = abs((t1[3] + t1[7]) - (t0[3] + t0[7]))
+    assert dP <= 1e-6 * scaleP, (dP / scaleP)
+    assert dE <= 1e-6 * abs(t0[3] + t0[7]), (dE / abs(t0[3] + t0[7]))
+    # the CR and gas shares really exchanged momentum and energy
+    assert np.abs(t1[4:7] - t0[4:7]).max() > 1e-3 * box.m_cr * box.np
+    eng.close()
+
+
+def test_full_size_bench_configuration_sampled():
+    """The bench's workload and launch configuration (128^3 x 32 = 67,108,864
+    CRs, mixed): 4096 sampled particles after one push match the oracle's push
+    of the same particles in the same fields, the charge deposit sums to
+    (q/mc) m N / dV, and the corrector momentum equals minus the particles'
+    momentum change."""
+    box = wl.alfvenic_beam_3d()          # the bench workload, seed 0
+    eng = m.Engine([box], precision=MIXED)
+    rng = np.random.default_rng(43)
+    idx = np.sort(rng.choice(box.np, 4096, replace=False))
+    cell0 = eng.cell.cpu().numpy()
+    off0 = eng.off.cpu().numpy()
+    p0 = eng.p.cpu().numpy()
+    eng.interp_push(box.dt, 1)
+    cell1 = eng.cell.cpu().numpy()
+    off1 = eng.off.cpu().numpy()
+    p1 = eng.p.cpu().numpy()
+    corr = eng.deposits(0).cpu().numpy()
+    mdep = eng.deposits(1).cpu().numpy()
+    assert eng.status() == 0
+    eng.close()
+    # oracle push of the sampled particles (fields from the same gas)
+    n = box.n[0]
+
+    def absx(cell, off, sel):
+        c = cell[sel].astype(np.int64)
+        co = [c % n, (c // n) % n, c // (n * n)]
+        return np.stack([co[d] + off[d, sel].astype(np.float64) for d in range(3)])
+
+    g, p = orc.grid_of(box), orc.params_of(box)
+    E = orc.field_prep(g, p, box.rho, box.mom, box.B, np.zeros((4, box.ncell)))
+    x = np.ascontiguousarray(absx(cell0, off0, idx))
+    v = np.ascontiguousarray(p0[:, idx].astype(np.float64))
+    orc.push(g, p, box.dt, x, v, E, box.B, None, None)
+    xg = absx(cell1, off1, idx)
+    dx = periodic_diff(xg, x, float(n))
+    assert np.abs(dx).max() < 1e-5
+    vg = p1[:, idx].astype(np.float64)
+    assert np.all(np.abs(vg - v) <= 1e-5 * np.sqrt((v ** 2).sum(0)))
+    # whole-grid invariants
+    qn = box.qm_cr * box.m_cr
+    # each particle's three f32 TSC weights per dimension sum to 1 within a few
+    # ulps, so the total charge agrees to f32 precision
+    assert abs(mdep[0].sum() - qn * box.np) < 1e-6 * qn * box.np
+    dpart = box.m_cr * (p1.astype(np.float64) - p0.astype(np.float64)).sum(axis=1)
+    gross = box.m_cr * np.abs(p1.astype(np.float64) - p0.astype(np.float64)).sum(axis=1)
+    assert np.all(np.abs(corr[:3].sum(axis=1) + dpart) <= 1e-5 * gross)
