@@ -60,7 +60,7 @@ def _rank_env():
 WORKLOADS = {
     "alfvenic_beam_3d": "3-D periodic {n}^3 grid, {ppc} CR/cell, uniform gas + random-phase Alfvenic dB/B0=0.1 "
                         "(64 modes), beam |p|=100 boosted 10 v_A along B, C=300, TSC, no Hall term",
-    "bell_2d": "2-D periodic 1024^2 grid, 64 CR/cell, B along x, dN/dp ~ p^-2 on [10, 1e4] drifting 0.5 v_A, "
+    "bell_2d": "2-D periodic {n2d}^2 grid, 64 CR/cell, B along x, dN/dp ~ p^-2 on [10, 1e4] drifting 0.5 v_A, "
                "C=300, CR-Hall term on",
     "shock_2d": "2-D 16384x128 grid, reflecting x walls, 40 CR/cell average with 80% in the 5% of cells "
                 "nearest the wall, upstream v=-20 v_A, dN/dp ~ p^-2 on [1, 1e5], C=200",
@@ -76,7 +76,7 @@ def _workload(args, seed):
     if args.workload == "alfvenic_beam_3d":
         boxes = [wl.alfvenic_beam_3d(seed=seed, n=args.n, ppc=args.ppc)]
     elif args.workload == "bell_2d":
-        boxes = [wl.bell_2d(seed=seed)]
+        boxes = [wl.bell_2d(seed=seed, n=args.n2d)]
     elif args.workload == "shock_2d":
         boxes = [wl.shock_2d(seed=seed)]
     elif args.workload == "ensemble_2d":
@@ -87,7 +87,7 @@ def _workload(args, seed):
 
 
 def _workload_desc(args):
-    d = WORKLOADS[args.workload].format(n=args.n, ppc=args.ppc)
+    d = WORKLOADS[args.workload].format(n=args.n, ppc=args.ppc, n2d=args.n2d)
     return args.workload + ": " + d
 
 
@@ -419,6 +419,7 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="alfvenic_beam_3d")
     ap.add_argument("--n", type=int, default=128, help="cells per side of the 3-D box")
     ap.add_argument("--ppc", type=int, default=32)
+    ap.add_argument("--n2d", type=int, default=1024, help="cells per side of the 2-D Bell box")
     ap.add_argument("--sort-every", type=int, default=2)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=4)

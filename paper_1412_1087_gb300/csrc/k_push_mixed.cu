@@ -27,6 +27,8 @@
 //  * A particle whose stencil leaves the tile, or whose quantities exceed the
 //    bound the scales were sized for, deposits straight into the int64 global
 //    accumulators at the global scale.
+//  * 2-D: each thread copies its next particle's words into a two-stage
+//    shared-memory ring with cp.async while it pushes the current one.
 #include "push_common.cuh"
 
 namespace mhdpic {
@@ -226,21 +228,100 @@ __device__ __forceinline__ bool within(const float q[4], const float *qb, int ch
            fabsf(q[3]) <= qb[ch0 + 3];
 }
 
+// Particle words staged per thread: cell, D offsets, 3 momenta.
+template <int D>
+constexpr int ring_planes()
+{
+    return 1 + D + 3;
+}
+constexpr int RING_STAGES = 2;
+// Per dimension: 2-D pushes are short, so the kernel hides the particle
+// loads behind a shared-memory ring and runs 4 CTAs per SM with the item
+// constants in shared memory; 3-D pushes are bound by the shared-memory
+// deposits and keep everything in registers at 2 CTAs per SM (the ring
+// measured no faster there and takes shared memory from L1).
+template <int D>
+constexpr bool STAGED = D == 2;
+template <int D>
+constexpr int MIN_BLOCKS = D == 3 ? 2 : 4;
+template <int D>
+constexpr bool CONST_IN_SMEM = D == 2;
+
+__device__ __forceinline__ void cp_async4(uint32_t *dst, const void *src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_prev()
+{
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+// Start the copy of particle j into one stage of this thread's ring (one
+// word per plane, planes PUSH_THREADS words apart).
+template <int D>
+__device__ __forceinline__ void stage_particle(const Ctx &c, int64_t j, uint32_t *dst)
+{
+    const int64_t np = c.np;
+    cp_async4(dst, c.cell + j);
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+        cp_async4(dst + (1 + d) * PUSH_THREADS, c.off + d * np + j);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        cp_async4(dst + (1 + D + d) * PUSH_THREADS, c.p + d * np + j);
+}
+
+struct PIn {
+    int32_t cell;
+    float o[3], v[3];
+};
+
+template <int D>
+__device__ __forceinline__ PIn load_staged(const uint32_t *in)
+{
+    PIn r;
+    r.cell = (int32_t)in[0];
+    r.o[0] = r.o[1] = r.o[2] = 0.f;
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+        r.o[d] = __uint_as_float(in[(1 + d) * PUSH_THREADS]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        r.v[d] = __uint_as_float(in[(1 + D + d) * PUSH_THREADS]);
+    return r;
+}
+
+template <int D>
+__device__ __forceinline__ PIn load_global(const Ctx &c, int64_t j)
+{
+    PIn r;
+    r.cell = c.cell[j];
+    r.o[0] = r.o[1] = r.o[2] = 0.f;
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+        r.o[d] = c.off[d * c.np + j];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        r.v[d] = c.p[d * c.np + j];
+    return r;
+}
+
 template <int D, bool FULL>
 __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const ItemGeom &gm, const MixedConst &k,
-                                          int64_t j, const float4 *sFa, const float2 *sFb, int *sD,
-                                          unsigned long long *mout)
+                                          int64_t j, const PIn &pin, const float4 *sFa, const float2 *sFb,
+                                          int *sD, unsigned long long *mout)
 {
     const int64_t np = c.np;
     int ci[3];
-    decode_cell(b, c.cell[j], ci);
-    float o[3] = {0.f, 0.f, 0.f}, v[3];
-#pragma unroll
-    for (int d = 0; d < D; ++d)
-        o[d] = c.off[d * np + j];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-        v[d] = c.p[d * np + j];
+    decode_cell(b, pin.cell, ci);
+    float o[3] = {pin.o[0], pin.o[1], pin.o[2]}, v[3] = {pin.v[0], pin.v[1], pin.v[2]};
 
     // drift to x^(n+1/2) with u = v / gamma
     const float ign = rsqrtf(fmaf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2], k.invC2, 1.f));
@@ -363,7 +444,7 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
 }
 
 template <int D, bool FULL>
-__global__ void __launch_bounds__(PUSH_THREADS, 2) k_push_mixed(Ctx c, const WorkItem *__restrict__ items,
+__global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_push_mixed(Ctx c, const WorkItem *__restrict__ items,
                                                                  const int32_t *__restrict__ nitems,
                                                                  int32_t *__restrict__ work_ctr, int cur_out,
                                                                  float dt)
@@ -373,7 +454,11 @@ __global__ void __launch_bounds__(PUSH_THREADS, 2) k_push_mixed(Ctx c, const Wor
     int *sD = reinterpret_cast<int *>(smem);
     float4 *sFa = reinterpret_cast<float4 *>(smem + sizeof(int) * NPLANE * S);
     float2 *sFb = reinterpret_cast<float2 *>(smem + (sizeof(int) * NPLANE + sizeof(float4)) * S);
+    uint32_t *ring = reinterpret_cast<uint32_t *>(smem + (sizeof(int) * NPLANE + sizeof(float4) + sizeof(float2)) * S) +
+                     threadIdx.x;
+    constexpr int RS = ring_planes<D>() * PUSH_THREADS;   // words per ring stage
     __shared__ int s_item;
+    __shared__ MixedConst s_k;
     unsigned long long *mout = c.momdep[cur_out];
     const int nit = *nitems;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -403,17 +488,43 @@ __global__ void __launch_bounds__(PUSH_THREADS, 2) k_push_mixed(Ctx c, const Wor
             sFa[s] = f1;
             sFb[s] = make_float2(f2.x, f2.y);
         }
-        MixedConst k;
-        item_const(b, dt, it.p1 - it.p0, D, k);
+        if (threadIdx.x == 0)
+            item_const(b, dt, it.p1 - it.p0, D, s_k);
         __syncthreads();
+        // the item constants stay in shared memory where registers are short
+        MixedConst kreg;
+        if (!CONST_IN_SMEM<D>)
+            kreg = s_k;
+        const MixedConst &k = CONST_IN_SMEM<D> ? s_k : kreg;
 
         float vm2 = 0.f;
         {
             const LaneRange lr = lane_range(it, wid, NW);
-            for (int64_t r = lr.first; r < lr.q; r += lr.stride) {
-                int64_t loc = lane * lr.q + r;
-                if (loc < lr.cnt)
-                    vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, lr.base + loc, sFa, sFb, sD, mout));
+            const int64_t base = lr.base, cnt = lr.cnt, lane0 = lane * lr.q, rb = lr.first, re = lr.q,
+                          rs = lr.stride;
+            if (STAGED<D>) {
+                // the next particle's words are copied into shared memory
+                // while the current one is pushed
+                if (rb < re) {
+                    if (lane0 + rb < cnt)
+                        stage_particle<D>(c, base + lane0 + rb, ring);
+                    cp_async_commit();
+                }
+                int st = 0;
+                for (int64_t r = rb; r < re; r += rs, st ^= 1) {
+                    if (r + rs < re && lane0 + r + rs < cnt)
+                        stage_particle<D>(c, base + lane0 + r + rs, ring + (st ^ 1) * RS);
+                    cp_async_commit();
+                    cp_async_wait_prev();
+                    if (lane0 + r < cnt)
+                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + lane0 + r, load_staged<D>(ring + st * RS),
+                                                           sFa, sFb, sD, mout));
+                }
+            } else {
+                for (int64_t r = rb; r < re; r += rs)
+                    if (lane0 + r < cnt)
+                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + lane0 + r,
+                                                           load_global<D>(c, base + lane0 + r), sFa, sFb, sD, mout));
             }
         }
         unsigned vb = __reduce_max_sync(0xffffffffu, __float_as_uint(sqrtf(vm2)));
@@ -459,7 +570,9 @@ int occupancy_mixed(size_t bytes)
 
 size_t push_smem_bytes_mixed(const Ctx &c)
 {
-    return (sizeof(int) * NPLANE + sizeof(float4) + sizeof(float2)) * (size_t)c.tile_slots;
+    const bool staged = c.ndim == 3 ? STAGED<3> : STAGED<2>;
+    const size_t ring = staged ? sizeof(uint32_t) * RING_STAGES * (size_t)(1 + c.ndim + 3) * PUSH_THREADS : 0;
+    return (sizeof(int) * NPLANE + sizeof(float4) + sizeof(float2)) * (size_t)c.tile_slots + ring;
 }
 
 int push_blocks_per_sm_mixed(const Ctx &c)
