@@ -22,8 +22,9 @@
  * last failure on the calling thread.
  *
  * Ownership: the caller owns every particle and gas buffer (plain pointers,
- * device memory unless options.memory == MHDPIC_MEM_HOST).  The library owns
- * only its scratch (sort keys, permutation, staged fields, fixed-point deposit
+ * device memory unless options.memory is MHDPIC_MEM_HOST, where all of them
+ * are host memory, or MHDPIC_MEM_HOST_GAS, where the gas buffers are).  The
+ * library owns only its scratch (sort keys, permutation, staged fields, fixed-point deposit
  * grids, work list, status word), allocated by mhdpic_init and freed by
  * mhdpic_destroy.  Buffers must stay valid and unmoved between init and
  * destroy.
@@ -68,6 +69,9 @@ extern "C" {
 #define MHDPIC_PREC_MIXED 1 /* int32 cell + f32 offset, f32 push, int64 fixed-point deposits */
 #define MHDPIC_MEM_DEVICE 0 /* caller buffers are device pointers */
 #define MHDPIC_MEM_HOST 1   /* caller buffers are (pinned) host pointers; each call copies */
+#define MHDPIC_MEM_HOST_GAS 2 /* particle buffers on the device, gas buffers (pinned) host pointers:
+                               * the particles stay resident and each call copies only the gas
+                               * arrays it reads or writes (a host MHD solver coupled to the push) */
 
 /* ---- device status flags (sticky until mhdpic_clear_status) ---- */
 #define MHDPIC_ST_FAST_MOVER 1u /* a particle moved more than 2 cells in one half step (App. A.4) */
@@ -101,7 +105,7 @@ typedef struct {
 /* Library options, shared by all boxes of a context. */
 typedef struct {
     int32_t precision; /* MHDPIC_PREC_MIXED or MHDPIC_PREC_FP64 */
-    int32_t memory;    /* MHDPIC_MEM_DEVICE or MHDPIC_MEM_HOST */
+    int32_t memory;    /* MHDPIC_MEM_DEVICE, MHDPIC_MEM_HOST or MHDPIC_MEM_HOST_GAS */
     int32_t brick[3];  /* cells per sort brick and per push tile (0: 4x4x4 in 3-D, 8x8 in 2-D) */
     int32_t reserved[8];
 } mhdpic_options;

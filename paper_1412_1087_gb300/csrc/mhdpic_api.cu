@@ -138,7 +138,7 @@ int copy_particles(mhdpic_ctx *c, bool to_device)
 // all: rho, mom, egas, B; otherwise only the arrays the feedback changes
 int copy_gas(mhdpic_ctx *c, bool to_device, bool all)
 {
-    if (c->mem != MHDPIC_MEM_HOST)
+    if (c->mem == MHDPIC_MEM_DEVICE)
         return MHDPIC_OK;
     const int64_t nc = c->k.nc;
     if (to_device) {
@@ -195,7 +195,7 @@ int validate(int32_t nbox, const mhdpic_grid *grids, const mhdpic_params *params
         return fail(MHDPIC_E_ARG, "grids, params, options, particles and gas must be non-NULL");
     if (opt->precision != MHDPIC_PREC_MIXED && opt->precision != MHDPIC_PREC_FP64)
         return fail(MHDPIC_E_ARG, "unknown precision %d", opt->precision);
-    if (opt->memory != MHDPIC_MEM_DEVICE && opt->memory != MHDPIC_MEM_HOST)
+    if (opt->memory != MHDPIC_MEM_DEVICE && opt->memory != MHDPIC_MEM_HOST && opt->memory != MHDPIC_MEM_HOST_GAS)
         return fail(MHDPIC_E_ARG, "unknown memory kind %d", opt->memory);
     if (!parts->box_start)
         return fail(MHDPIC_E_ARG, "particles.box_start must be a host array of nbox+1 offsets");
@@ -432,22 +432,25 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
     // caller buffers (or device mirrors of host ones)
     if (c->mem == MHDPIC_MEM_HOST) {
         c->hp = *parts;
-        c->hg = *gas;
         if (k.prec == MHDPIC_PREC_MIXED) {
             if ((rc = c->alloc(&k.cell, np)) || (rc = c->alloc(&k.off, k.ndim * np)) || (rc = c->alloc(&k.p, 3 * np)))
                 return bail(rc);
         } else if ((rc = c->alloc(&k.x, k.ndim * np)) || (rc = c->alloc(&k.p64, 3 * np))) {
             return bail(rc);
         }
-        if ((rc = c->alloc(&k.rho, nc)) || (rc = c->alloc(&k.mom, 3 * nc)) || (rc = c->alloc(&k.egas, nc)) ||
-            (rc = c->alloc(&k.B, 3 * nc)))
-            return bail(rc);
     } else {
         k.cell = parts->cell;
         k.off = parts->off;
         k.p = parts->p;
         k.x = parts->x;
         k.p64 = parts->p64;
+    }
+    if (c->mem != MHDPIC_MEM_DEVICE) {
+        c->hg = *gas;
+        if ((rc = c->alloc(&k.rho, nc)) || (rc = c->alloc(&k.mom, 3 * nc)) || (rc = c->alloc(&k.egas, nc)) ||
+            (rc = c->alloc(&k.B, 3 * nc)))
+            return bail(rc);
+    } else {
         k.rho = gas->rho;
         k.mom = gas->mom;
         k.egas = gas->egas;

@@ -30,6 +30,7 @@ MHDPIC_PREC_FP64 = 0
 MHDPIC_PREC_MIXED = 1
 MHDPIC_MEM_DEVICE = 0
 MHDPIC_MEM_HOST = 1
+MHDPIC_MEM_HOST_GAS = 2
 STATUS_NAMES = {1: "FAST_MOVER", 2: "NONFINITE", 4: "OVERFLOW", 8: "SORT_CAP", 16: "CELL_RANGE"}
 
 
@@ -205,8 +206,9 @@ class Engine:
     """Owns torch buffers for a batch of boxes and one library context.
 
     ``precision``: MHDPIC_PREC_MIXED or MHDPIC_PREC_FP64.
-    ``memory``: MHDPIC_MEM_DEVICE (buffers on cuda) or MHDPIC_MEM_HOST (pinned
-    host buffers; every call copies through the library).
+    ``memory``: MHDPIC_MEM_DEVICE (buffers on cuda), MHDPIC_MEM_HOST (pinned
+    host buffers; every call copies through the library) or MHDPIC_MEM_HOST_GAS
+    (particles on cuda, gas in pinned host buffers copied by each call).
     """
 
     def __init__(self, boxes: Sequence, precision: int = MHDPIC_PREC_MIXED,
@@ -227,12 +229,16 @@ class Engine:
         self.np = int(self.box_start[-1])
         self.nc = int(sum(b.ncell for b in self.boxes))
         self.device = torch.device(device)
-        if memory == MHDPIC_MEM_DEVICE:
-            def mk(a, dt):
-                return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(self.device)
-        else:
-            def mk(a, dt):
-                return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()
+        def on_device(a, dt):
+            return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(self.device)
+
+        def pinned(a, dt):
+            return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()
+
+        if memory not in (MHDPIC_MEM_DEVICE, MHDPIC_MEM_HOST, MHDPIC_MEM_HOST_GAS):
+            raise ValueError("unknown memory kind %r" % (memory,))
+        mk = pinned if memory == MHDPIC_MEM_HOST else on_device
+        mk_gas = on_device if memory == MHDPIC_MEM_DEVICE else pinned
         cat = np.concatenate
         if precision == MHDPIC_PREC_MIXED:
             self.cell = mk(cat([b.cell for b in self.boxes]), np.int32)
@@ -248,10 +254,10 @@ class Engine:
             self.x = mk(x64, np.float64)
             self.p64 = mk(v64, np.float64)
             self.cell = self.off = self.p = None
-        self.rho = mk(cat([b.rho for b in self.boxes]), np.float64)
-        self.mom = mk(cat([b.mom for b in self.boxes], axis=1), np.float64)
-        self.egas = mk(cat([b.egas for b in self.boxes]), np.float64)
-        self.B = mk(cat([b.B for b in self.boxes], axis=1), np.float64)
+        self.rho = mk_gas(cat([b.rho for b in self.boxes]), np.float64)
+        self.mom = mk_gas(cat([b.mom for b in self.boxes], axis=1), np.float64)
+        self.egas = mk_gas(cat([b.egas for b in self.boxes]), np.float64)
+        self.B = mk_gas(cat([b.B for b in self.boxes], axis=1), np.float64)
 
         G = (Grid * nb)()
         P = (Params * nb)()
