@@ -24,10 +24,12 @@
  * Ownership: the caller owns every particle and gas buffer (plain pointers,
  * device memory unless options.memory is MHDPIC_MEM_HOST, where all of them
  * are host memory, or MHDPIC_MEM_HOST_GAS, where the gas buffers are).  The
- * library owns only its scratch (sort keys, permutation, staged fields, fixed-point deposit
- * grids, work list, status word), allocated by mhdpic_init and freed by
- * mhdpic_destroy.  Buffers must stay valid and unmoved between init and
- * destroy.
+ * library owns only its scratch (sort keys, permutation, a second particle
+ * set, staged fields, fixed-point deposit grids, work list, status word),
+ * allocated by mhdpic_init and freed by mhdpic_destroy.  The particle state
+ * alternates between the caller's buffers and the second set (see
+ * mhdpic_sort); mhdpic_sync_particles brings it back into the caller's.
+ * Buffers must stay valid and unmoved between init and destroy.
  *
  * Layouts (np = total particles of all boxes, nc = total cells of all boxes):
  *   particles, box-major: box b owns particles [box_start[b], box_start[b+1]);
@@ -136,8 +138,9 @@ typedef struct {
  *   ctx     out: new context (NULL on failure)
  *   grids, params: host arrays [nbox]
  *   stream: cudaStream_t (NULL = legacy default stream) used by every call
- * Positions must lie inside their box; particle data are permuted in place.
- * Synchronises the stream once (it reads per-cell counts back).
+ * Positions must lie inside their box; the caller's particle buffers are
+ * sorted in place.  Synchronises the stream once (it reads per-cell counts
+ * back).
  */
 int mhdpic_init(mhdpic_ctx **ctx, int32_t nbox, const mhdpic_grid *grids,
                 const mhdpic_params *params, const mhdpic_options *options,
@@ -147,10 +150,16 @@ int mhdpic_init(mhdpic_ctx **ctx, int32_t nbox, const mhdpic_grid *grids,
  * mhdpic_sort - stable counting sort of each box's particles by cell key: the
  * brick number (bricks of options.brick cells, numbered x fastest) times the
  * brick volume plus the cell's x-fastest number inside its brick.  The paper
- * has no sort (cell ordering is this library's layout); positions and
- * four-velocities are permuted in place and the push work list is rebuilt.
- *   perm_out   device int64[np] or NULL: perm_out[r] = old index of the
- *              particle now at rank r (global indices)
+ * has no sort (cell ordering is this library's layout).  The push work list is
+ * rebuilt at once; the particle arrays are permuted by the next
+ * mhdpic_interp_push, which reads its particles through the permutation and
+ * writes them, sorted and advanced, into the library's second particle set
+ * (no separate pass over the particles).  Until mhdpic_sync_particles the
+ * caller's device buffers may therefore hold an earlier state; in
+ * MHDPIC_MEM_HOST mode the host buffers are sorted on return.
+ *   perm_out   device int64[np] or NULL: perm_out[r] = index, in the order
+ *              the caller last saw, of the particle now at rank r (global
+ *              indices); asking for it applies any earlier pending sort
  *   counts_out device int32[nkeys] or NULL: particles per key, keys of box b
  *              after those of earlier boxes (nkeys from mhdpic_num_keys)
  */
@@ -166,6 +175,17 @@ int mhdpic_sort(mhdpic_ctx *ctx, int64_t *perm_out, int32_t *counts_out);
  * which the next field staging uses.  dt must be > 0, nsub >= 1.
  */
 int mhdpic_interp_push(mhdpic_ctx *ctx, double dt, int32_t nsub);
+
+/*
+ * mhdpic_sync_particles - make the caller's particle buffers hold the current
+ * particle state: apply a pending sort and copy the library's second set back
+ * if it is the current one.  Call it before reading or writing the caller's
+ * particle buffers in MHDPIC_MEM_DEVICE / MHDPIC_MEM_HOST_GAS mode; the
+ * caller's buffers then stay current until the next mhdpic_sort (a no-op in
+ * MHDPIC_MEM_HOST mode, where the host buffers are current after every call).
+ * Asynchronous; ordered on the context's stream.
+ */
+int mhdpic_sync_particles(mhdpic_ctx *ctx);
 
 /*
  * mhdpic_deposit - TSC deposit of n_CR = (q/mc) m_CR W/dV and

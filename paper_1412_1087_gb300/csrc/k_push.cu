@@ -103,11 +103,12 @@ __device__ __forceinline__ float push_one_f64(const Ctx &c, const BoxDev &b, con
 {
     const int64_t np = c.np;
     const double C = k.C;
+    const int64_t src = c.perm_src ? (int64_t)c.perm_src[j] : j;
     double x[3] = {0.0, 0.0, 0.0}, v[3];
     for (int d = 0; d < D; ++d)
-        x[d] = c.x[d * np + j];
+        x[d] = c.src_x[d * np + src];
     for (int d = 0; d < 3; ++d)
-        v[d] = c.p64[d * np + j];
+        v[d] = c.src_p64[d * np + src];
 
     double g0 = sqrt(C * C + (v[0] * v[0] + v[1] * v[1] + v[2] * v[2])) / C;
     for (int d = 0; d < D; ++d) {

@@ -263,19 +263,19 @@ __device__ __forceinline__ void cp_async_wait_prev()
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
 }
 
-// Start the copy of particle j into one stage of this thread's ring (one
-// word per plane, planes PUSH_THREADS words apart).
+// Start the copy of source particle i into one stage of this thread's ring
+// (one word per plane, planes PUSH_THREADS words apart).
 template <int D>
-__device__ __forceinline__ void stage_particle(const Ctx &c, int64_t j, uint32_t *dst)
+__device__ __forceinline__ void stage_particle(const Ctx &c, int64_t i, uint32_t *dst)
 {
     const int64_t np = c.np;
-    cp_async4(dst, c.cell + j);
+    cp_async4(dst, c.src_cell + i);
 #pragma unroll
     for (int d = 0; d < D; ++d)
-        cp_async4(dst + (1 + d) * PUSH_THREADS, c.off + d * np + j);
+        cp_async4(dst + (1 + d) * PUSH_THREADS, c.src_off + d * np + i);
 #pragma unroll
     for (int d = 0; d < 3; ++d)
-        cp_async4(dst + (1 + D + d) * PUSH_THREADS, c.p + d * np + j);
+        cp_async4(dst + (1 + D + d) * PUSH_THREADS, c.src_p + d * np + i);
 }
 
 struct PIn {
@@ -299,17 +299,17 @@ __device__ __forceinline__ PIn load_staged(const uint32_t *in)
 }
 
 template <int D>
-__device__ __forceinline__ PIn load_global(const Ctx &c, int64_t j)
+__device__ __forceinline__ PIn load_global(const Ctx &c, int64_t i)
 {
     PIn r;
-    r.cell = c.cell[j];
+    r.cell = c.src_cell[i];
     r.o[0] = r.o[1] = r.o[2] = 0.f;
 #pragma unroll
     for (int d = 0; d < D; ++d)
-        r.o[d] = c.off[d * c.np + j];
+        r.o[d] = c.src_off[d * c.np + i];
 #pragma unroll
     for (int d = 0; d < 3; ++d)
-        r.v[d] = c.p[d * c.np + j];
+        r.v[d] = c.src_p[d * c.np + i];
     return r;
 }
 
@@ -502,18 +502,31 @@ __global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_push_mixed(Ctx 
             const LaneRange lr = lane_range(it, wid, NW);
             const int64_t base = lr.base, cnt = lr.cnt, lane0 = lane * lr.q, rb = lr.first, re = lr.q,
                           rs = lr.stride;
+            // source particle of sorted position base + lane0 + r; when the
+            // push applies a sort the permutation entry is loaded one
+            // iteration early.  (One code path for both cases, so that the
+            // arithmetic is the same instruction for instruction.)
+            const bool gather = c.perm_src != nullptr;
+            auto valid = [&](int64_t r) { return r < re && lane0 + r < cnt; };
+            auto src_of = [&](int64_t r) -> int64_t {
+                const int64_t j = base + lane0 + r;
+                return gather ? (int64_t)__ldg(c.perm_src + j) : j;
+            };
             if (STAGED<D>) {
                 // the next particle's words are copied into shared memory
                 // while the current one is pushed
                 if (rb < re) {
-                    if (lane0 + rb < cnt)
-                        stage_particle<D>(c, base + lane0 + rb, ring);
+                    if (valid(rb))
+                        stage_particle<D>(c, src_of(rb), ring);
                     cp_async_commit();
                 }
+                int64_t sn = valid(rb + rs) ? src_of(rb + rs) : 0;
                 int st = 0;
                 for (int64_t r = rb; r < re; r += rs, st ^= 1) {
-                    if (r + rs < re && lane0 + r + rs < cnt)
-                        stage_particle<D>(c, base + lane0 + r + rs, ring + (st ^ 1) * RS);
+                    if (valid(r + rs))
+                        stage_particle<D>(c, sn, ring + (st ^ 1) * RS);
+                    if (valid(r + 2 * rs))
+                        sn = src_of(r + 2 * rs);
                     cp_async_commit();
                     cp_async_wait_prev();
                     if (lane0 + r < cnt)
@@ -521,10 +534,15 @@ __global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_push_mixed(Ctx 
                                                            sFa, sFb, sD, mout));
                 }
             } else {
+                int64_t sn = valid(rb) ? src_of(rb) : 0;
                 for (int64_t r = rb; r < re; r += rs)
-                    if (lane0 + r < cnt)
-                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + lane0 + r,
-                                                           load_global<D>(c, base + lane0 + r), sFa, sFb, sD, mout));
+                    if (lane0 + r < cnt) {
+                        const int64_t src = sn;
+                        if (valid(r + rs))
+                            sn = src_of(r + rs);
+                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + lane0 + r, load_global<D>(c, src), sFa,
+                                                           sFb, sD, mout));
+                    }
             }
         }
         unsigned vb = __reduce_max_sync(0xffffffffu, __float_as_uint(sqrtf(vm2)));
@@ -566,6 +584,23 @@ int occupancy_mixed(size_t bytes)
     return nb;
 }
 
+template <int D>
+int occupancy_all(size_t bytes)
+{
+    occupancy_mixed<D, false>(bytes);
+    return occupancy_mixed<D, true>(bytes);
+}
+
+template <int D>
+void launch_d(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur_out, int full, float dt, int grid,
+              size_t bytes, cudaStream_t st)
+{
+    if (full)
+        k_push_mixed<D, true><<<grid, PUSH_THREADS, bytes, st>>>(c, s.items, s.nitems, work_ctr, cur_out, dt);
+    else
+        k_push_mixed<D, false><<<grid, PUSH_THREADS, bytes, st>>>(c, s.items, s.nitems, work_ctr, cur_out, dt);
+}
+
 }  // namespace
 
 size_t push_smem_bytes_mixed(const Ctx &c)
@@ -577,32 +612,20 @@ size_t push_smem_bytes_mixed(const Ctx &c)
 
 int push_blocks_per_sm_mixed(const Ctx &c)
 {
-    size_t bytes = push_smem_bytes_mixed(c);
-    occupancy_mixed<3, false>(bytes);
-    occupancy_mixed<2, false>(bytes);
-    occupancy_mixed<3, true>(bytes);
-    occupancy_mixed<2, true>(bytes);
-    int nb = c.ndim == 3 ? occupancy_mixed<3, true>(bytes) : occupancy_mixed<2, true>(bytes);
+    const size_t bytes = push_smem_bytes_mixed(c);
+    const int nb = c.ndim == 3 ? occupancy_all<3>(bytes) : occupancy_all<2>(bytes);
     return nb < 1 ? 1 : nb;
 }
 
 int launch_push_mixed(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur_out, int full, double dt,
                       int grid_blocks, cudaStream_t st)
 {
-    size_t bytes = push_smem_bytes_mixed(c);
+    const size_t bytes = push_smem_bytes_mixed(c);
     cudaMemsetAsync(work_ctr, 0, sizeof(int32_t), st);
-    float fdt = (float)dt;
-    if (c.ndim == 3) {
-        if (full)
-            k_push_mixed<3, true><<<grid_blocks, PUSH_THREADS, bytes, st>>>(c, s.items, s.nitems, work_ctr, cur_out, fdt);
-        else
-            k_push_mixed<3, false><<<grid_blocks, PUSH_THREADS, bytes, st>>>(c, s.items, s.nitems, work_ctr, cur_out, fdt);
-    } else {
-        if (full)
-            k_push_mixed<2, true><<<grid_blocks, PUSH_THREADS, bytes, st>>>(c, s.items, s.nitems, work_ctr, cur_out, fdt);
-        else
-            k_push_mixed<2, false><<<grid_blocks, PUSH_THREADS, bytes, st>>>(c, s.items, s.nitems, work_ctr, cur_out, fdt);
-    }
+    if (c.ndim == 3)
+        launch_d<3>(c, s, work_ctr, cur_out, full, (float)dt, grid_blocks, bytes, st);
+    else
+        launch_d<2>(c, s, work_ctr, cur_out, full, (float)dt, grid_blocks, bytes, st);
     return 1;
 }
 

@@ -8,9 +8,10 @@
 //   2. exclusive scan of the per-key counts;
 //   3. scatter of the particle indices to their key segment;
 //   4. sort of each key segment by particle index, which makes the result the
-//      stable order: the permutation equals a stable sort by key;
-//   5. gather of the particle arrays through the permutation;
-//   6. the push work list: every brick's particle range cut into items of at
+//      stable order: the permutation equals a stable sort by key.
+// The particle arrays are permuted later: by the next push, which reads its
+// particles through the permutation, or by launch_gather.
+//   5. the push work list: every brick's particle range cut into items of at
 //      most ITEM_MAX_PARTICLES.
 #include <climits>
 
@@ -450,43 +451,8 @@ int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *
         k_sort_segments<<<gb, 256, 0, st>>>(c.nkeys, s.offset, s.perm, s.big_list, s.big_count);
         k_sort_big<<<152, 1024, 0, st>>>(s.offset, s.perm, s.big_list, s.big_count, s.pkey, c.status);
         launches += 3;
-        // gather every particle array into scratch through the permutation,
-        // then copy the sorted arrays back into the caller's buffers
-        int g = grid_for(c.np, 256);
-        char *tmp = (char *)s.tmp;
-        Planes pl{};
-        struct Arr {
-            void *p;
-            int esz, ncomp;
-        } arrs[3];
-        int na = 0;
-        if (c.prec == MHDPIC_PREC_MIXED) {
-            arrs[na++] = {c.cell, 4, 1};
-            arrs[na++] = {c.off, 4, c.ndim};
-            arrs[na++] = {c.p, 4, 3};
-        } else {
-            arrs[na++] = {c.x, 8, c.ndim};
-            arrs[na++] = {c.p64, 8, 3};
-        }
-        size_t off = 0;
-        for (int a = 0; a < na; ++a)
-            for (int q = 0; q < arrs[a].ncomp; ++q) {
-                pl.src[pl.n] = (const char *)arrs[a].p + (size_t)q * c.np * arrs[a].esz;
-                pl.dst[pl.n] = tmp + off;
-                pl.esz[pl.n] = arrs[a].esz;
-                off += (size_t)c.np * arrs[a].esz;
-                ++pl.n;
-            }
-        k_gather_all<<<g, 256, 0, st>>>(c.np, s.perm, pl);
-        ++launches;
-        off = 0;
-        for (int a = 0; a < na; ++a) {
-            size_t bytes = (size_t)c.np * arrs[a].esz * arrs[a].ncomp;
-            cudaMemcpyAsync(arrs[a].p, tmp + off, bytes, cudaMemcpyDeviceToDevice, st);
-            off += bytes;
-        }
         if (perm_out) {
-            k_perm_out<<<g, 256, 0, st>>>(c.np, s.perm, perm_out);
+            k_perm_out<<<grid_for(c.np, 256), 256, 0, st>>>(c.np, s.perm, perm_out);
             ++launches;
         }
     }
@@ -503,6 +469,31 @@ int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *
     k_write_items<<<gb, 256, 0, st>>>(c, brick_start, s.offset, nitems_of, item_off, s.items, s.nitems);
     ++launches;
     return launches;
+}
+
+int launch_gather(const Ctx &c, const int32_t *perm, const PSet &src, const PSet &dst, cudaStream_t st)
+{
+    if (c.np <= 0)
+        return 0;
+    Planes pl{};
+    auto add = [&](const void *sp, void *dp, int esz, int ncomp) {
+        for (int q = 0; q < ncomp; ++q) {
+            pl.src[pl.n] = (const char *)sp + (size_t)q * c.np * esz;
+            pl.dst[pl.n] = (char *)dp + (size_t)q * c.np * esz;
+            pl.esz[pl.n] = esz;
+            ++pl.n;
+        }
+    };
+    if (c.prec == MHDPIC_PREC_MIXED) {
+        add(src.cell, dst.cell, 4, 1);
+        add(src.off, dst.off, 4, c.ndim);
+        add(src.p, dst.p, 4, 3);
+    } else {
+        add(src.x, dst.x, 8, c.ndim);
+        add(src.p64, dst.p64, 8, 3);
+    }
+    k_gather_all<<<grid_for(c.np, 256), 256, 0, st>>>(c.np, perm, pl);
+    return 1;
 }
 
 int launch_max_count(const Ctx &c, const SortScratch &s, cudaStream_t st)

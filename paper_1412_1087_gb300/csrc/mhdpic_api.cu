@@ -66,6 +66,14 @@ struct mhdpic_ctx {
     std::vector<BoxDev> boxes;
     std::vector<int64_t> part_start, cell_start, brick_start;
     std::vector<void *> allocs;
+    // particle sets: 0 = the caller's buffers (their device mirrors in
+    // MEM_HOST mode), 1 = the library's second set; k's particle pointers
+    // are sets[cur_set]'s.  A sort only computes the permutation (pending);
+    // the next push reads through it from the current set and writes the
+    // other one, which then becomes current.
+    PSet sets[2]{};
+    int cur_set = 0;
+    bool pending = false;
     // caller's host buffers in MEM_HOST mode
     mhdpic_particles hp{};
     mhdpic_gas hg{};
@@ -75,6 +83,8 @@ struct mhdpic_ctx {
     double graph_dt = 0.0;
     int graph_k = 0;
     int graph_cur = -1;
+    int graph_set = -1;
+    bool graph_pending = false;
     int64_t graph_launches = 0;   // kernel launches inside one replay
     int step_in_cycle = 0;        // steps since the last sort done by mhdpic_run
     int tuned_k = 0;
@@ -152,6 +162,61 @@ int copy_gas(mhdpic_ctx *c, bool to_device, bool all)
         CK(cudaMemcpyAsync(c->hg.mom, c->k.mom, sizeof(double) * 3 * nc, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaMemcpyAsync(c->hg.egas, c->k.egas, sizeof(double) * nc, cudaMemcpyDeviceToHost, c->stream));
     }
+    return MHDPIC_OK;
+}
+
+void use_set(mhdpic_ctx *c, int set)
+{
+    c->cur_set = set;
+    const PSet &q = c->sets[set];
+    Ctx &k = c->k;
+    k.cell = q.cell;
+    k.off = q.off;
+    k.p = q.p;
+    k.x = q.x;
+    k.p64 = q.p64;
+    k.perm_src = nullptr;
+    k.src_cell = q.cell;
+    k.src_off = q.off;
+    k.src_p = q.p;
+    k.src_x = q.x;
+    k.src_p64 = q.p64;
+}
+
+// Apply a pending sort to the particle arrays (gather into the other set).
+int materialize(mhdpic_ctx *c)
+{
+    if (!c->pending)
+        return MHDPIC_OK;
+    int rc = check_launch(c, launch_gather(c->k, c->s.perm, c->sets[c->cur_set], c->sets[c->cur_set ^ 1], c->stream));
+    if (rc)
+        return rc;
+    use_set(c, c->cur_set ^ 1);
+    c->pending = false;
+    return MHDPIC_OK;
+}
+
+// Materialize, then make the caller's buffers the current set.
+int sync_to_caller(mhdpic_ctx *c)
+{
+    int rc;
+    if ((rc = materialize(c)))
+        return rc;
+    if (c->cur_set == 0 || c->k.np == 0) {
+        use_set(c, 0);
+        return MHDPIC_OK;
+    }
+    const int64_t np = c->k.np;
+    const PSet &a = c->sets[1], &b = c->sets[0];
+    if (c->k.prec == MHDPIC_PREC_MIXED) {
+        CK(cudaMemcpyAsync(b.cell, a.cell, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(b.off, a.off, sizeof(float) * c->k.ndim * np, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(b.p, a.p, sizeof(float) * 3 * np, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        CK(cudaMemcpyAsync(b.x, a.x, sizeof(double) * c->k.ndim * np, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(b.p64, a.p64, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    use_set(c, 0);
     return MHDPIC_OK;
 }
 
@@ -430,21 +495,36 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         return bail(rc);
 
     // caller buffers (or device mirrors of host ones)
+    PSet &s0 = c->sets[0], &s1 = c->sets[1];
     if (c->mem == MHDPIC_MEM_HOST) {
         c->hp = *parts;
         if (k.prec == MHDPIC_PREC_MIXED) {
-            if ((rc = c->alloc(&k.cell, np)) || (rc = c->alloc(&k.off, k.ndim * np)) || (rc = c->alloc(&k.p, 3 * np)))
+            if ((rc = c->alloc(&s0.cell, np)) || (rc = c->alloc(&s0.off, k.ndim * np)) ||
+                (rc = c->alloc(&s0.p, 3 * np)))
                 return bail(rc);
-        } else if ((rc = c->alloc(&k.x, k.ndim * np)) || (rc = c->alloc(&k.p64, 3 * np))) {
+        } else if ((rc = c->alloc(&s0.x, k.ndim * np)) || (rc = c->alloc(&s0.p64, 3 * np))) {
             return bail(rc);
         }
     } else {
-        k.cell = parts->cell;
-        k.off = parts->off;
-        k.p = parts->p;
-        k.x = parts->x;
-        k.p64 = parts->p64;
+        s0.cell = parts->cell;
+        s0.off = parts->off;
+        s0.p = parts->p;
+        s0.x = parts->x;
+        s0.p64 = parts->p64;
     }
+    // the second set lives in the particle staging scratch
+    {
+        char *t = (char *)c->s.tmp;
+        if (k.prec == MHDPIC_PREC_MIXED) {
+            s1.cell = (int32_t *)t;
+            s1.off = (float *)(t + sizeof(int32_t) * np);
+            s1.p = s1.off + (size_t)k.ndim * np;
+        } else {
+            s1.x = (double *)t;
+            s1.p64 = s1.x + (size_t)k.ndim * np;
+        }
+    }
+    use_set(c, 0);
     if (c->mem != MHDPIC_MEM_DEVICE) {
         c->hg = *gas;
         if ((rc = c->alloc(&k.rho, nc)) || (rc = c->alloc(&k.mom, 3 * nc)) || (rc = c->alloc(&k.egas, nc)) ||
@@ -470,9 +550,13 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         cudaMemsetAsync(k.status, 0, sizeof(uint32_t), st) || cudaMemsetAsync(k.stats, 0, sizeof(BoxStats) * nbox, st))
         return bail(cuda_fail(cudaGetLastError(), "init uploads"));
 
-    // sort, then size the charge/current scales from the densest cell
+    // sort (into the caller's buffers), then size the charge/current scales
+    // from the densest cell
     if ((rc = check_launch(c, launch_sort(k, c->s, nullptr, nullptr, st))) ||
         (rc = check_launch(c, launch_max_count(k, c->s, st))))
+        return bail(rc);
+    c->pending = true;
+    if ((rc = sync_to_caller(c)))
         return bail(rc);
     int32_t maxcount = 0;
     if (cudaMemcpyAsync(&maxcount, c->s.max_count, sizeof(int32_t), cudaMemcpyDeviceToHost, st) ||
@@ -515,10 +599,16 @@ int mhdpic_sort(mhdpic_ctx *c, int64_t *perm_out, int32_t *counts_out)
     int rc;
     if ((rc = copy_particles(c, true)))
         return rc;
+    // a permutation asked for is relative to the order the caller sees
+    if (perm_out && (rc = materialize(c)))
+        return rc;
     if ((rc = check_launch(c, launch_sort(c->k, c->s, perm_out, counts_out, c->stream))))
         return rc;
+    c->pending = true;
     // refresh the densest-cell count used by the corrector scales
     if ((rc = check_launch(c, launch_max_count(c->k, c->s, c->stream))))
+        return rc;
+    if (c->mem == MHDPIC_MEM_HOST && (rc = materialize(c)))
         return rc;
     return copy_particles(c, false);
 }
@@ -540,11 +630,33 @@ int mhdpic_interp_push(mhdpic_ctx *c, double dt, int32_t nsub)
         CK(cudaMemsetAsync(c->k.momdep[c->cur ^ 1], 0, sizeof(unsigned long long) * 4 * c->k.nc, c->stream));
     for (int s = 0; s < nsub; ++s) {
         bool last = s == nsub - 1;
+        // after a sort the first push reads the current set through the
+        // permutation and writes the other set
+        Ctx kk = c->k;
+        const bool gather = c->pending;
+        if (gather) {
+            const PSet &src = c->sets[c->cur_set], &dst = c->sets[c->cur_set ^ 1];
+            kk.cell = dst.cell;
+            kk.off = dst.off;
+            kk.p = dst.p;
+            kk.x = dst.x;
+            kk.p64 = dst.p64;
+            kk.perm_src = c->s.perm;
+            kk.src_cell = src.cell;
+            kk.src_off = src.off;
+            kk.src_p = src.p;
+            kk.src_x = src.x;
+            kk.src_p64 = src.p64;
+        }
         int n = c->k.prec == MHDPIC_PREC_MIXED
-                    ? launch_push_mixed(c->k, c->s, c->work_ctr, c->cur ^ 1, last ? 1 : 0, dt, c->grid_blocks, c->stream)
-                    : launch_push_f64(c->k, c->s, c->work_ctr, c->cur ^ 1, last ? 1 : 0, dt, c->grid_blocks, c->stream);
+                    ? launch_push_mixed(kk, c->s, c->work_ctr, c->cur ^ 1, last ? 1 : 0, dt, c->grid_blocks, c->stream)
+                    : launch_push_f64(kk, c->s, c->work_ctr, c->cur ^ 1, last ? 1 : 0, dt, c->grid_blocks, c->stream);
         if ((rc = check_launch(c, n)))
             return rc;
+        if (gather) {
+            use_set(c, c->cur_set ^ 1);
+            c->pending = false;
+        }
     }
     c->cur ^= 1;
     c->next_clear = false;
@@ -556,7 +668,7 @@ int mhdpic_deposit(mhdpic_ctx *c)
     if (!c || !c->valid)
         return fail(MHDPIC_E_STATE, "invalid context");
     int rc;
-    if ((rc = copy_particles(c, true)) || (rc = copy_gas(c, true, true)))
+    if ((rc = copy_particles(c, true)) || (rc = copy_gas(c, true, true)) || (rc = materialize(c)))
         return rc;
     // the stage kernel clears buffer cur^1, so deposit into cur and stage from it
     if ((rc = check_launch(c, launch_moments(c->k, c->cur, c->stream))) ||
@@ -577,7 +689,7 @@ int mhdpic_apply_feedback(mhdpic_ctx *c, double *totals_out)
     if ((rc = copy_gas(c, false, false)))
         return rc;
     if (totals_out) {
-        if ((rc = copy_particles(c, true)))
+        if ((rc = copy_particles(c, true)) || (rc = materialize(c)))
             return rc;
         if ((rc = check_launch(c, launch_totals(c->k, c->partials, c->nchunks, c->totals_dev, c->stream))))
             return rc;
@@ -586,6 +698,15 @@ int mhdpic_apply_feedback(mhdpic_ctx *c, double *totals_out)
         CK(cudaStreamSynchronize(c->stream));
     }
     return MHDPIC_OK;
+}
+
+int mhdpic_sync_particles(mhdpic_ctx *c)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (c->mem == MHDPIC_MEM_HOST)   // the host buffers are current after every call
+        return MHDPIC_OK;
+    return sync_to_caller(c);
 }
 
 int mhdpic_get_deposits(mhdpic_ctx *c, int32_t which, double *out)
@@ -670,6 +791,8 @@ int capture_cycle(mhdpic_ctx *c, double dt, int k, int cycle)
         c->graph = nullptr;
     }
     const int64_t l0 = c->launches;
+    const int cur0 = c->cur, set0 = c->cur_set, sic0 = c->step_in_cycle;
+    const bool pend0 = c->pending, clear0 = c->next_clear;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int rc = MHDPIC_OK;
     for (int s = 0; s < cycle && rc == MHDPIC_OK; ++s)
@@ -685,6 +808,18 @@ int capture_cycle(mhdpic_ctx *c, double dt, int k, int cycle)
     }
     if (e != cudaSuccess)
         return cuda_fail(e, "cudaStreamEndCapture");
+    // a replay must leave the state it starts from; otherwise nothing was
+    // run, so restore the state and let the caller go on eagerly
+    if (c->cur != cur0 || c->cur_set != set0 || c->step_in_cycle != sic0 || c->pending != pend0 ||
+        c->next_clear != clear0) {
+        cudaGraphDestroy(g);
+        c->cur = cur0;
+        c->step_in_cycle = sic0;
+        c->pending = pend0;
+        c->next_clear = clear0;
+        use_set(c, set0);
+        return MHDPIC_OK;
+    }
     e = cudaGraphInstantiate(&c->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
@@ -694,6 +829,8 @@ int capture_cycle(mhdpic_ctx *c, double dt, int k, int cycle)
     c->graph_dt = dt;
     c->graph_k = k;
     c->graph_cur = c->cur;
+    c->graph_set = c->cur_set;
+    c->graph_pending = c->pending;
     return MHDPIC_OK;
 }
 
@@ -718,22 +855,26 @@ int mhdpic_run(mhdpic_ctx *c, double dt, int32_t nsteps, int32_t sort_every)
     if (c->step_in_cycle >= k)
         c->step_in_cycle = 0;
     // finish the current cycle eagerly (and a first step when the next
-    // moments buffer has not been cleared by a staging pass yet)
-    while (left > 0 && (c->step_in_cycle != 0 || !c->next_clear)) {
+    // moments buffer has not been cleared by a staging pass yet), up to a
+    // sort whose permutation the next push applies: the state every cycle
+    // starts from
+    while (left > 0 && (c->step_in_cycle != 0 || !c->next_clear || !c->pending)) {
         if ((rc = run_one_step(c, dt, k)))
             return rc;
         --left;
     }
-    // whole cycles from a graph (an even number of pushes, so the moments
-    // buffers alternate back to where the capture started); the legacy default
-    // stream and host buffers cannot be captured and run eagerly
-    const int cycle = (k % 2) ? 2 * k : k;
-    const bool graphs = c->stream != nullptr && c->mem == MHDPIC_MEM_DEVICE;
+    // whole cycles from a graph: two sorts and 2k pushes, so that the moments
+    // buffers and the particle sets alternate back to where the capture
+    // started; the legacy default stream and host buffers cannot be captured
+    // and run eagerly
+    const int cycle = 2 * k;
+    const bool graphs = c->stream != nullptr && c->mem != MHDPIC_MEM_HOST && c->mem != MHDPIC_MEM_HOST_GAS;
     if (graphs && left >= cycle) {
-        if (!c->graph || c->graph_dt != dt || c->graph_k != k || c->graph_cur != c->cur)
+        if (!c->graph || c->graph_dt != dt || c->graph_k != k || c->graph_cur != c->cur ||
+            c->graph_set != c->cur_set || c->graph_pending != c->pending)
             if ((rc = capture_cycle(c, dt, k, cycle)))
                 return rc;
-        while (left >= cycle) {
+        while (c->graph && left >= cycle) {
             CK(cudaGraphLaunch(c->graph, c->stream));
             c->launches += c->graph_launches;
             left -= cycle;

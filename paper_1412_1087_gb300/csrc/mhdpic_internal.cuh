@@ -115,12 +115,22 @@ struct Ctx {
     const BoxDev *boxes;   // device
     const int64_t *box_part_start; // device [nbox+1]
     const int64_t *box_cell_start; // device [nbox+1]
-    // caller (or mirror) buffers, device
+    // current particle set, device: the caller's buffers (or their mirrors in
+    // host-memory mode) or the library's second set
     int32_t *cell;
     float *off;
     float *p;
     double *x;
     double *p64;
+    // what a push reads: the current set itself (perm_src null), or right
+    // after a sort the previous set through the permutation, sorted position
+    // j taking particle perm_src[j]; the push then writes the current set
+    const int32_t *perm_src;
+    const int32_t *src_cell;
+    const float *src_off;
+    const float *src_p;
+    const double *src_x;
+    const double *src_p64;
     double *rho, *mom, *egas, *B;
     // scratch
     unsigned long long *corr;     // [4][nc]
@@ -155,8 +165,19 @@ struct SortScratch {
     int32_t *max_count;    // [1]
 };
 
+// One set of particle arrays (the precision's planes; the others null).
+struct PSet {
+    int32_t *cell;
+    float *off;
+    float *p;
+    double *x;
+    double *p64;
+};
+
 int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *counts_out,
                 cudaStream_t st);
+// dst[j] = src[perm[j]] for every particle plane
+int launch_gather(const Ctx &c, const int32_t *perm, const PSet &src, const PSet &dst, cudaStream_t st);
 int launch_max_count(const Ctx &c, const SortScratch &s, cudaStream_t st);
 int launch_vmax(const Ctx &c, cudaStream_t st);
 int launch_prep(const Ctx &c, int cur, int apply, cudaStream_t st);

@@ -75,6 +75,7 @@ SIGNATURES = {
     "mhdpic_deposit": (ctypes.c_int, [_V]),
     "mhdpic_apply_feedback": (ctypes.c_int, [_V, _V]),
     "mhdpic_run": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32, ctypes.c_int32]),
+    "mhdpic_sync_particles": (ctypes.c_int, [_V]),
     "mhdpic_sort_cadence": (ctypes.c_int32, [_V]),
     "mhdpic_get_deposits": (ctypes.c_int, [_V, ctypes.c_int32, _V]),
     "mhdpic_get_fields": (ctypes.c_int, [_V, _V]),
@@ -150,6 +151,10 @@ def mhdpic_apply_feedback(ctx, totals_out: Optional[np.ndarray] = None) -> None:
 
 def mhdpic_run(ctx, dt: float, nsteps: int, sort_every: int = 0) -> None:
     _check(load().mhdpic_run(ctx, float(dt), int(nsteps), int(sort_every)))
+
+
+def mhdpic_sync_particles(ctx) -> None:
+    _check(load().mhdpic_sync_particles(ctx))
 
 
 def mhdpic_sort_cadence(ctx) -> int:
@@ -241,19 +246,19 @@ class Engine:
         mk_gas = on_device if memory == MHDPIC_MEM_DEVICE else pinned
         cat = np.concatenate
         if precision == MHDPIC_PREC_MIXED:
-            self.cell = mk(cat([b.cell for b in self.boxes]), np.int32)
-            self.off = mk(cat([b.off for b in self.boxes], axis=1), np.float32)
-            self.p = mk(cat([b.p for b in self.boxes], axis=1), np.float32)
-            self.x = self.p64 = None
+            self._cell = mk(cat([b.cell for b in self.boxes]), np.int32)
+            self._off = mk(cat([b.off for b in self.boxes], axis=1), np.float32)
+            self._p = mk(cat([b.p for b in self.boxes], axis=1), np.float32)
+            self._x = self._p64 = None
         else:
             from . import workloads as wl
             if x64 is None:
                 x64 = cat([wl.absolute_positions(b) for b in self.boxes], axis=1)
             if v64 is None:
                 v64 = cat([b.p.astype(np.float64) for b in self.boxes], axis=1)
-            self.x = mk(x64, np.float64)
-            self.p64 = mk(v64, np.float64)
-            self.cell = self.off = self.p = None
+            self._x = mk(x64, np.float64)
+            self._p64 = mk(v64, np.float64)
+            self._cell = self._off = self._p = None
         self.rho = mk_gas(cat([b.rho for b in self.boxes]), np.float64)
         self.mom = mk_gas(cat([b.mom for b in self.boxes], axis=1), np.float64)
         self.egas = mk_gas(cat([b.egas for b in self.boxes]), np.float64)
@@ -283,8 +288,8 @@ class Engine:
         def ptr(t):
             return t.data_ptr() if t is not None else None
 
-        parts.cell, parts.off, parts.p = ptr(self.cell), ptr(self.off), ptr(self.p)
-        parts.x, parts.p64 = ptr(self.x), ptr(self.p64)
+        parts.cell, parts.off, parts.p = ptr(self._cell), ptr(self._off), ptr(self._p)
+        parts.x, parts.p64 = ptr(self._x), ptr(self._p64)
         gas = Gas(ptr(self.rho), ptr(self.mom), ptr(self.egas), ptr(self.B))
         self._parts, self._gas = parts, gas
         if stream is None:
@@ -292,6 +297,27 @@ class Engine:
         self.stream = stream
         with torch.cuda.device(self.device):
             self.ctx = mhdpic_init(nb, G, P, opt, parts, gas, ctypes.c_void_p(stream.cuda_stream))
+
+    # -- the caller's particle buffers ------------------------------------
+    # The particle state alternates between these buffers and the library's
+    # second set; reading an attribute first brings it back here
+    # (mhdpic_sync_particles) and orders torch's current stream after it.
+    def sync_particles(self) -> None:
+        mhdpic_sync_particles(self.ctx)
+        cur = self.torch.cuda.current_stream(self.device)
+        if self.memory != MHDPIC_MEM_HOST and cur != self.stream:
+            cur.wait_stream(self.stream)
+
+    def _synced(self, t):
+        if t is not None and getattr(self, "ctx", None):
+            self.sync_particles()
+        return t
+
+    cell = property(lambda self: self._synced(self._cell))
+    off = property(lambda self: self._synced(self._off))
+    p = property(lambda self: self._synced(self._p))
+    x = property(lambda self: self._synced(self._x))
+    p64 = property(lambda self: self._synced(self._p64))
 
     # -- the step ---------------------------------------------------------
     def sort(self, want_perm: bool = False, want_counts: bool = False):
@@ -355,9 +381,13 @@ class Engine:
         self.stream.synchronize()
 
     def close(self) -> None:
+        """Bring the particle state into the caller's buffers and free the context."""
         if getattr(self, "ctx", None):
-            mhdpic_destroy(self.ctx)
-            self.ctx = None
+            try:
+                mhdpic_sync_particles(self.ctx)
+            finally:
+                mhdpic_destroy(self.ctx)
+                self.ctx = None
 
     def __del__(self):
         try:
