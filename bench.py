@@ -42,12 +42,14 @@ PARTICLE_BYTES = {(3, "mixed"): 28, (2, "mixed"): 24, (3, "fp64"): 48, (2, "fp64
 # read-modify-written once (8 B each, twice)
 CELL_FIELD_BYTES = {"mixed": 24, "fp64": 48}
 CELL_DEPOSIT_BYTES = 8 * 8 * 2
-# DRAM bytes (read + write) per particle of one k_push_mixed<3, full> launch,
-# measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on a
-# 64^3 x 32 launch of the current kernel version: 465.3 MB / 8,388,608 CRs.
-# Traffic scales with the particle count (cells scale alike at fixed ppc).
-# Set to None whenever the push kernel changes, until it is measured again.
-PUSH_TRAFFIC_BYTES_PER_PARTICLE = None
+# DRAM bytes (read + write) per particle of one k_push_mixed<D, full> launch,
+# measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on a small
+# case of the current kernel version; traffic scales with the particle count
+# (cells scale alike at fixed particles per cell):
+#   3-D, 64^3 x 32 CRs:   262.0 MB + 202.2 MB over 8,388,608 CRs
+#   2-D, 512^2 x 64 CRs:  427.6 MB + 421.1 MB over 16,777,216 CRs
+# Remove an entry whenever its kernel changes, until it is measured again.
+PUSH_TRAFFIC_BYTES_PER_PARTICLE = {"alfvenic_beam_3d": 464.23e6 / 8388608, "bell_2d": 848.72e6 / 16777216}
 
 
 def _rank_env():
@@ -314,8 +316,8 @@ def run_native(args):
     push_avg_s = push_ms / args.steps / 1e3
     achieved = bytes_push / push_avg_s / 1e9
     traffic = None
-    if PUSH_TRAFFIC_BYTES_PER_PARTICLE and args.workload == "alfvenic_beam_3d":
-        traffic = PUSH_TRAFFIC_BYTES_PER_PARTICLE * npart
+    if args.workload in PUSH_TRAFFIC_BYTES_PER_PARTICLE:
+        traffic = PUSH_TRAFFIC_BYTES_PER_PARTICLE[args.workload] * npart
     eng_stats = {"push_ms_per_step": push_ms / args.steps, "graph_run_ms_per_step": graph_ms,
                  "particles": npart, "cells": ncell, "dt": dt}
 

@@ -196,7 +196,77 @@ __global__ void k_sort_scatter(int64_t np, const int32_t *__restrict__ pkey,
     }
 }
 
-// Segments of up to 32 are sorted in registers, up to WARP_SORT_MAX in the
+// Ascending bitonic sort of the 32 E values a[e*32 + lane] = v[e] held by a
+// warp: distances below 32 exchange through shuffles, larger ones between a
+// lane's own registers.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(int (&v)[E], int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int pe = e ^ (j >> 5);
+                    if (pe > e) {
+                        const bool up = ((e * 32 + lane) & k) == 0;
+                        const int x = v[e], y = v[pe];
+                        if ((x > y) == up) {
+                            v[e] = y;
+                            v[pe] = x;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int o = __shfl_xor_sync(0xffffffffu, v[e], j);
+                    const bool up = ((e * 32 + lane) & k) == 0;
+                    const bool lower = (lane & j) == 0;
+                    v[e] = (lower == up) ? min(v[e], o) : max(v[e], o);
+                }
+            }
+        }
+    }
+}
+
+// Sort of one segment [s, s + n), n <= 32 E, in registers; a segment already
+// in ascending order is left alone.
+template <int E>
+__device__ __forceinline__ void warp_sort_segment(int32_t *__restrict__ perm, int s, int n, int lane)
+{
+    int v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = e * 32 + lane;
+        v[e] = i < n ? perm[s + i] : INT_MAX;
+    }
+    bool ok = true;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        int nxt = __shfl_down_sync(0xffffffffu, v[e], 1);
+        if (e + 1 < E) {
+            const int first = __shfl_sync(0xffffffffu, v[e + 1 < E ? e + 1 : e], 0);
+            if (lane == 31)
+                nxt = first;
+        }
+        const int i = e * 32 + lane;
+        ok &= i >= n - 1 || v[e] < nxt;
+    }
+    if (__all_sync(0xffffffffu, ok))
+        return;
+    warp_bitonic<E>(v, lane);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = e * 32 + lane;
+        if (i < n)
+            perm[s + i] = v[e];
+    }
+}
+
+// Segments of up to 128 are sorted in registers, up to WARP_SORT_MAX in the
 // warp's shared memory; longer ones are listed for k_sort_big.
 __global__ void __launch_bounds__(256) k_sort_segments(int64_t nkeys, const int32_t *__restrict__ offset,
                                                        int32_t *__restrict__ perm,
@@ -213,23 +283,11 @@ __global__ void __launch_bounds__(256) k_sort_segments(int64_t nkeys, const int3
         if (n <= 1)
             continue;
         if (n <= 32) {
-            int v = lane < n ? perm[s + lane] : INT_MAX;
-            int nxt = __shfl_down_sync(0xffffffffu, v, 1);
-            if (__all_sync(0xffffffffu, lane >= n - 1 || v < nxt))
-                continue;   // already in ascending order
-#pragma unroll
-            for (int kk = 2; kk <= 32; kk <<= 1) {
-#pragma unroll
-                for (int j = kk >> 1; j > 0; j >>= 1) {
-                    int o = __shfl_xor_sync(0xffffffffu, v, j);
-                    bool up = (lane & kk) == 0;
-                    bool lower = (lane & j) == 0;
-                    int mn = min(v, o), mx = max(v, o);
-                    v = (lower == up) ? mn : mx;
-                }
-            }
-            if (lane < n)
-                perm[s + lane] = v;
+            warp_sort_segment<1>(perm, s, n, lane);
+        } else if (n <= 64) {
+            warp_sort_segment<2>(perm, s, n, lane);
+        } else if (n <= 128) {
+            warp_sort_segment<4>(perm, s, n, lane);
         } else if (n <= WARP_SORT_MAX) {
             int P = 64;
             while (P < n)
