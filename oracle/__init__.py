@@ -85,6 +85,9 @@ def _load():
             lib.orc_sort_key.argtypes = [G, _P, ctypes.c_int64]
             lib.orc_cells_of.argtypes = [G, ctypes.c_int64, _P, _P]
             lib.orc_sort_cells.argtypes = [G, _P, ctypes.c_int64, _P, _P, _P]
+            lib.orc_spectrum.argtypes = [G, Pp, ctypes.c_int64, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P,
+                                         ctypes.c_int, _P, _P]
+            lib.orc_lambda_map.argtypes = [G, Pp, _P, _P, _P, _P, _P]
             _lib = lib
     return _lib
 
@@ -241,6 +244,30 @@ def sort_cells(g: Grid, brick, cell) -> tuple:
     _load().orc_sort_cells(ctypes.byref(g), _ptr(b), cell.shape[0], _ptr(cell), _ptr(perm),
                            _ptr(counts))
     return perm, counts
+
+
+def spectrum(g: Grid, p: Params, x, v, kind: int, edges, region=None, n_moment: int = 6) -> tuple:
+    """Counts per bin and (sum q^(n+1), sum q^n) of the particles inside region
+    (Section 4.3, eq:dpdE, eq:emax); kind 0 bins E_k, kind 1 bins |v|."""
+    x = _f64(x)
+    v = _f64(v)
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    nb = edges.shape[0] - 1
+    reg = None if region is None else np.ascontiguousarray(region, dtype=np.float64)
+    counts = np.zeros(nb, dtype=np.int64)
+    sums = np.zeros(2, dtype=np.float64)
+    _load().orc_spectrum(ctypes.byref(g), ctypes.byref(p), v.shape[1], _ptr(x), _ptr(v), int(kind), nb,
+                         _ptr(edges), _ptr(reg), int(n_moment), _ptr(counts), _ptr(sums))
+    return counts, sums
+
+
+def lambda_map(g: Grid, p: Params, rho, mom, B, mom_dep) -> np.ndarray:
+    """Lambda = R (u_CR - v_g) / v_A per cell, planes (3, ncell) (eq:lambda)."""
+    rho, mom, B, mom_dep = _f64(rho), _f64(mom), _f64(B), _f64(mom_dep)
+    out = np.zeros((3, rho.shape[0]), dtype=np.float64)
+    _load().orc_lambda_map(ctypes.byref(g), ctypes.byref(p), _ptr(rho), _ptr(mom), _ptr(B), _ptr(mom_dep),
+                           _ptr(out))
+    return out
 
 
 class State:

@@ -538,3 +538,84 @@ void orc_sort_cells(const orc_grid *g, const int32_t brick[3], int64_t np, const
     }
     free(start);
 }
+
+/* ------------------------------------------------------------------ */
+/* diagnostics: spectra and E_max (Section 4.3, eq:dpdE, eq:emax),      */
+/* the CR-Hall parameter map (Section 2.2, eq:defR, eq:lambda)           */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Spectrum of the particles inside a region.  The binned quantity of a
+ * particle is q = E_k = v^2/(gamma+1) (kind 0, eq:parEk, gamma =
+ * sqrt(C^2 + v^2)/C) or q = |v| (kind 1, momentum per unit mass), with
+ * v^2 = (vx^2 + vy^2) + vz^2.  The particle counts in bin b when
+ * edges[b] <= q < edges[b+1], and, when region is given, when
+ * region[2d] <= x_d < region[2d+1] for every d < ndim.  sums[0] and sums[1]
+ * are the sums of q^(n+1) and q^n over the same particles, each power a
+ * product of n factors q taken left to right: for kind 0 their ratio is the
+ * E_max of eq:emax.  f(E) of eq:dpdE is counts[b] / (edges[b+1] - edges[b])
+ * per particle number.
+ */
+void orc_spectrum(const orc_grid *g, const orc_params *p, int64_t np, const double *x, const double *v,
+                  int kind, int nbins, const double *edges, const double *region, int n_moment,
+                  int64_t *counts, double *sums)
+{
+    memset(counts, 0, sizeof(int64_t) * (size_t)nbins);
+    sums[0] = sums[1] = 0.0;
+    for (int64_t j = 0; j < np; ++j) {
+        int inside = 1;
+        if (region)
+            for (int d = 0; d < g->ndim; ++d) {
+                double xd = x[d * np + j];
+                if (!(xd >= region[2 * d] && xd < region[2 * d + 1]))
+                    inside = 0;
+            }
+        if (!inside)
+            continue;
+        double vx = v[j], vy = v[np + j], vz = v[2 * np + j];
+        double v2 = vx * vx + vy * vy;
+        v2 = v2 + vz * vz;
+        double q;
+        if (kind == 0) {
+            double gam = sqrt(p->C * p->C + v2) / p->C;
+            q = v2 / (gam + 1.0);
+        } else {
+            q = sqrt(v2);
+        }
+        if (!(q >= edges[0] && q < edges[nbins]))
+            continue;
+        int b = 0;
+        while (b + 1 < nbins && edges[b + 1] <= q)   /* plain linear search */
+            ++b;
+        counts[b] += 1;
+        double qn = 1.0;
+        for (int k = 0; k < n_moment; ++k)
+            qn = qn * q;
+        sums[0] += qn * q;
+        sums[1] += qn;
+    }
+}
+
+/*
+ * Lambda = R (u_CR - v_g) / v_A per cell (eq:lambda) with R = n_CR /
+ * (n_g + n_CR) (eq:defR), n_g = (q/mc)_g rho (eq:ng), u_CR = J_CR / n_CR,
+ * v_g = (rho v)/rho and v_A = |B| / sqrt(rho) (code units).  Written without
+ * the division by n_CR: Lambda = (J_CR - n_CR v_g) / ((n_g + n_CR) v_A).
+ * Cells with |B| = 0 get Lambda = 0.  mom_dep holds (n, Jx, Jy, Jz).
+ */
+void orc_lambda_map(const orc_grid *g, const orc_params *p, const double *rho, const double *mom,
+                    const double *B, const double *mom_dep, double *lam)
+{
+    int64_t nc = ncell_of(g);
+    for (int64_t c = 0; c < nc; ++c) {
+        double Bc[3] = {B[c], B[nc + c], B[2 * nc + c]};
+        double vA = sqrt(dot3(Bc, Bc)) / sqrt(rho[c]);
+        double n = mom_dep[c];
+        double ng = p->qm_gas * rho[c];
+        for (int d = 0; d < 3; ++d) {
+            double vg = mom[d * nc + c] / rho[c];
+            double J = mom_dep[(1 + d) * nc + c];
+            lam[d * nc + c] = vA > 0.0 ? (J - n * vg) / ((ng + n) * vA) : 0.0;
+        }
+    }
+}

@@ -475,3 +475,107 @@ def test_energy_change_equals_the_definition_in_high_precision():
         assert abs(exact) > 1000 * scale          # the check is not vacuous
         checked += 1
     assert checked == 40
+
+
+# ---------------------------------------------------------------------------
+# diagnostics: spectra, E_max (Section 4.3), Lambda (eq:lambda)
+# ---------------------------------------------------------------------------
+
+def _v_of_energy(E, C):
+    """Four-velocity along x whose kinetic energy per unit mass is E:
+    gamma = 1 + E/C^2, v^2 = (gamma^2 - 1) C^2 = E (E + 2 C^2) / C^2."""
+    E = np.asarray(E, dtype=np.float64)
+    v = np.zeros((3, E.shape[0]))
+    v[0] = np.sqrt(E * (E + 2.0 * C * C)) / C
+    return v
+
+
+def test_spectrum_brute_force_edges_and_region():
+    """Hand-placed particles: a bin holds edges[b] <= q < edges[b+1], values
+    outside [edges[0], edges[-1]) and particles outside the half-open region
+    are not counted, and the two sums are the plain power sums."""
+    g = orc.make_grid(2, (8, 8, 1))
+    p = orc.make_params(1.0, 1.0, 1e6, 1.0, 0)
+    speeds = np.array([0.5, 1.0, 1.999, 2.0, 3.0, 4.0, 0.25, 2.5])
+    v = np.zeros((3, 8))
+    v[1] = speeds                                    # |v| along y
+    x = np.array([[0.5, 1.0, 2.0, 3.0, 3.999, 5.0, 6.0, 4.0],
+                  [0.5, 0.5, 0.5, 0.5, 7.5, 1.0, 1.0, 0.5]])
+    edges = [0.5, 1.0, 2.0, 3.0, 4.0]
+    counts, sums = orc.spectrum(g, p, x, v, 1, edges, n_moment=2)
+    # 0.5 | 1.0, 1.999 | 2.0, 2.5 | 3.0 ; 4.0 (= last edge) and 0.25 excluded
+    np.testing.assert_array_equal(counts, [1, 2, 2, 1])
+    inc = np.array([0.5, 1.0, 1.999, 2.0, 3.0, 2.5])
+    assert sums[0] == pytest.approx((inc ** 3).sum(), rel=1e-15)
+    assert sums[1] == pytest.approx((inc ** 2).sum(), rel=1e-15)
+    # region [1, 4) x [0, 1): keeps particles 1, 2, 3 (x = 1.0, 2.0, 3.0; y = 0.5);
+    # the one at x = 4.0 sits on the excluded upper face
+    counts, sums = orc.spectrum(g, p, x, v, 1, edges, region=[1.0, 4.0, 0.0, 1.0], n_moment=0)
+    np.testing.assert_array_equal(counts, [0, 2, 1, 0])
+    assert sums[1] == 3.0 and sums[0] == pytest.approx(1.0 + 1.999 + 2.0, rel=1e-15)
+
+
+def test_spectrum_energy_kind_bins_the_kinetic_energy():
+    """Energies placed at bin centres of log-spaced edges come back one per bin
+    (E_k = v^2/(gamma+1) = (gamma-1) C^2, eq:parEk, in the relativistic regime)."""
+    C = 3.0
+    edges = np.geomspace(0.01, 1e4, 13)
+    centres = np.sqrt(edges[:-1] * edges[1:])
+    g = orc.make_grid(3, (2, 2, 2))
+    p = orc.make_params(1.0, 1.0, C, 1.0, 0)
+    x = np.full((3, centres.shape[0]), 0.5)
+    counts, sums = orc.spectrum(g, p, x, _v_of_energy(centres, C), 0, edges, n_moment=1)
+    np.testing.assert_array_equal(counts, np.ones(12, dtype=np.int64))
+    assert sums[0] == pytest.approx((centres ** 2).sum(), rel=1e-12)
+    assert sums[1] == pytest.approx(centres.sum(), rel=1e-12)
+
+
+def test_emax_closed_form_of_the_paper():
+    """For f(E) ~ E^-m exp(-E/E_cut) the ratio of eq:emax is (n + 1 - m) E_cut
+    (Section 4.3).  With m = -1 (a Gamma distribution of shape 2) it is
+    (n + 2) E_cut exactly.  Energies at the distribution's quantiles reproduce
+    it up to the tail beyond the last quantile, which only lowers the ratio and
+    matters more the larger n is."""
+    from scipy import stats
+    Ecut, C, N = 2.5, 50.0, 200000
+    u = (np.arange(N) + 0.5) / N
+    E = np.where(u > 0.5, stats.gamma.isf(1.0 - u, a=2.0, scale=Ecut), stats.gamma.ppf(u, a=2.0, scale=Ecut))
+    g = orc.make_grid(3, (1, 1, 1))
+    p = orc.make_params(1.0, 1.0, C, 1.0, 0)
+    x = np.full((3, N), 0.5)
+    v = _v_of_energy(E, C)
+    edges = [0.0, 1e9]
+    for n, tol in ((1, 1e-4), (2, 3e-4)):
+        counts, sums = orc.spectrum(g, p, x, v, 0, edges, n_moment=n)
+        assert counts[0] == N
+        assert sums[0] / sums[1] == pytest.approx((n + 2) * Ecut, rel=tol)
+    # the paper's n = 6: 8 E_cut, approached from below
+    _, s6 = orc.spectrum(g, p, x, v, 0, edges, n_moment=6)
+    assert -0.01 < s6[0] / s6[1] / (8.0 * Ecut) - 1.0 < 0.0
+
+
+def test_lambda_map_matches_the_hall_field():
+    """E - E0 = -R (u_CR - v_g) x B = -v_A Lambda x B: the Lambda map against
+    the CR-Hall field of the field preparation (eq:emfcr1 vs eq:emfcr2), and
+    Lambda = 0 where the CRs move with the gas."""
+    rng = np.random.default_rng(9)
+    g = orc.make_grid(3, (3, 4, 2))
+    nc = 24
+    rho = rng.uniform(0.5, 2.0, nc)
+    vel = rng.normal(0, 1, (3, nc))
+    B = rng.normal(0, 1, (3, nc))
+    md = np.empty((4, nc))
+    md[0] = rng.uniform(0.01, 0.2, nc)
+    md[1:] = rng.normal(0, 0.3, (3, nc))
+    md[1:, :4] = md[0, :4] * vel[:, :4]          # co-moving CRs in four cells
+    p1 = orc.make_params(1.0, 0.7, 100.0, 1.0, 1)
+    p0 = orc.make_params(1.0, 0.7, 100.0, 1.0, 0)
+    lam = orc.lambda_map(g, p1, rho, rho * vel, B, md)
+    E = orc.field_prep(g, p1, rho, rho * vel, B, md)
+    E0 = orc.field_prep(g, p0, rho, rho * vel, B, md)
+    vA = np.sqrt((B * B).sum(0) / rho)
+    np.testing.assert_allclose(E - E0, -vA * np.cross(lam.T, B.T).T, rtol=1e-11, atol=1e-14)
+    np.testing.assert_allclose(lam[:, :4], 0.0, atol=1e-15)
+    # no field: Lambda is defined as zero
+    lam0 = orc.lambda_map(g, p1, rho, rho * vel, np.zeros((3, nc)), md)
+    assert not lam0.any()
