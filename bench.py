@@ -307,6 +307,55 @@ def run_native(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     graph_ms = ev0.elapsed_time(ev1) / args.steps
+
+    # sub-cycled mode (the paper's production mode, App. A.4): nsub particle
+    # sub-steps of dt with the staged fields held fixed per feedback, the
+    # corrector summed over the sub-steps, a sort every sort_every sub-steps
+    # and after every call
+    subcycled = None
+    if args.nsub > 1:
+        calls = max(2, args.steps // args.nsub)
+        eng.set_subcycle_sort(args.sort_every)
+        for _ in range(2):
+            eng.interp_push(dt, args.nsub)
+            eng.apply_feedback(False)
+            eng.sort()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(calls):
+            eng.interp_push(dt, args.nsub)
+            eng.apply_feedback(False)
+            eng.sort()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sub_ms = ev0.elapsed_time(ev1)
+        subcycled = {"nsub": args.nsub, "calls": calls,
+                     "value": float(npart) * args.nsub * calls / (sub_ms / 1e3), "unit": UNIT,
+                     "ms_per_call": sub_ms / calls}
+    # diagnostics (Section 4.3, eq:lambda): a 64-bin log energy spectrum with
+    # the E_max sums of eq:emax, and the Lambda map, timed once each after warm-up
+    diagnostics = None
+    if args.diagnostics:
+        edges = np.concatenate([[0.0], np.geomspace(1e-3, 1e6, 64)])
+        lam = None
+        for _ in range(2):
+            eng.spectrum(m.MHDPIC_SPEC_ENERGY, edges, None, 6)
+            lam = eng.lambda_map()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        counts, sums = eng.spectrum(m.MHDPIC_SPEC_ENERGY, edges, None, 6)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        spec_ms = ev0.elapsed_time(ev1)
+        ev0.record(stream)
+        lam = eng.lambda_map()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        diagnostics = {"spectrum_ms": spec_ms, "lambda_map_ms": ev0.elapsed_time(ev1),
+                       "spectrum_particles": int(counts.sum()),
+                       "E_max_n6": [float(a / b) if b > 0 else None for a, b in sums],
+                       "lambda_abs_max": float(lam.abs().max().item())}
+        del lam
     flags = eng.status()
 
     # roofline of the push kernel (the dominant kernel)
@@ -319,7 +368,8 @@ def run_native(args):
     if args.workload in PUSH_TRAFFIC_BYTES_PER_PARTICLE:
         traffic = PUSH_TRAFFIC_BYTES_PER_PARTICLE[args.workload] * npart
     eng_stats = {"push_ms_per_step": push_ms / args.steps, "graph_run_ms_per_step": graph_ms,
-                 "particles": npart, "cells": ncell, "dt": dt}
+                 "subcycled": subcycled, "diagnostics": diagnostics, "particles": npart, "cells": ncell,
+                 "dt": dt}
 
     # plain FP64 GPU path on the same boxes
     fp64 = None
@@ -438,9 +488,11 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=128, help="cells per side of the 3-D box")
     ap.add_argument("--ppc", type=int, default=32)
     ap.add_argument("--n2d", type=int, default=1024, help="cells per side of the 2-D Bell box")
-    ap.add_argument("--sort-every", type=int, default=2)
+    ap.add_argument("--sort-every", type=int, default=1)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--diagnostics", type=int, default=1, help="time the spectrum and Lambda map once")
+    ap.add_argument("--nsub", type=int, default=5, help="particle sub-steps per call of the sub-cycled figure (<2: off)")
     ap.add_argument("--e2e-all-host", type=int, default=1, help="also time the all-host-buffer mode")
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--sample-n", type=int, default=40, help="side of the oracle's sample box")

@@ -75,6 +75,10 @@ extern "C" {
                                * the particles stay resident and each call copies only the gas
                                * arrays it reads or writes (a host MHD solver coupled to the push) */
 
+#define MHDPIC_SPEC_ENERGY 0     /* spectrum of E_k = v^2/(gamma+1) per unit mass (eq:parEk) */
+#define MHDPIC_SPEC_MOMENTUM 1   /* spectrum of |v| = p/m (four-velocity magnitude) */
+#define MHDPIC_SPEC_MAX_BINS 2048
+
 /* ---- device status flags (sticky until mhdpic_clear_status) ---- */
 #define MHDPIC_ST_FAST_MOVER 1u /* a particle moved more than 2 cells in one half step (App. A.4) */
 #define MHDPIC_ST_NONFINITE 2u  /* a non-finite position or four-velocity was produced */
@@ -177,6 +181,17 @@ int mhdpic_sort(mhdpic_ctx *ctx, int64_t *perm_out, int32_t *counts_out);
 int mhdpic_interp_push(mhdpic_ctx *ctx, double dt, int32_t nsub);
 
 /*
+ * mhdpic_set_subcycle_sort - with every > 0, mhdpic_interp_push re-sorts the
+ * particles after every `every` sub-steps of one call (not after the last),
+ * so that long sub-cycles keep their particles near their cells' tiles.  The
+ * results do not depend on it, bit for bit (the fixed-point sums depend
+ * neither on the order of the particles nor on how they fall into work
+ * items); only the particle order and the speed do.  0 (the default) never sorts
+ * inside a call.  Returns MHDPIC_E_ARG for every < 0.
+ */
+int mhdpic_set_subcycle_sort(mhdpic_ctx *ctx, int32_t every);
+
+/*
  * mhdpic_sync_particles - make the caller's particle buffers hold the current
  * particle state: apply a pending sort and copy the library's second set back
  * if it is the current one.  Call it before reading or writing the caller's
@@ -186,6 +201,44 @@ int mhdpic_interp_push(mhdpic_ctx *ctx, double dt, int32_t nsub);
  * Asynchronous; ordered on the context's stream.
  */
 int mhdpic_sync_particles(mhdpic_ctx *ctx);
+
+/*
+ * mhdpic_spectrum - particle spectrum of every box (the diagnostics of
+ * Section 4.3: the energy spectrum f(E) of eq:dpdE, its momentum form, and
+ * the E_max of eq:emax).  The binned quantity q of a particle is
+ * E_k = v^2/(gamma+1) with gamma = sqrt(C^2 + v^2)/C (kind
+ * MHDPIC_SPEC_ENERGY) or |v| (MHDPIC_SPEC_MOMENTUM), v the four-velocity and
+ * v^2 = (vx^2 + vy^2) + vz^2, all in IEEE double arithmetic in this order.
+ *   kind        MHDPIC_SPEC_ENERGY or MHDPIC_SPEC_MOMENTUM
+ *   nbins       1 .. MHDPIC_SPEC_MAX_BINS
+ *   edges       host double[nbins + 1], finite and strictly ascending; a
+ *               particle counts in bin b when edges[b] <= q < edges[b+1]
+ *               (outside [edges[0], edges[nbins]) it is not counted)
+ *   region      host double[6] {lo_x, hi_x, lo_y, hi_y, lo_z, hi_z} or NULL:
+ *               only particles with lo_d <= x_d < hi_d for every d < ndim
+ *               count (x_d = x0_d + (i_d + offset_d) dx_d in double in mixed
+ *               precision); NULL counts the whole box
+ *   n_moment    the integer n of eq:emax, 0 .. 64
+ *   counts_out  host int64[nbox * nbins], box-major
+ *   sums_out    host double[2 * nbox] or NULL: per box, the sums of
+ *               q^(n+1) and q^n over the counted particles (E_max of eq:emax
+ *               is their ratio for the energy kind)
+ * Reads the current particle state (a pending sort does not change the
+ * counts).  Synchronises the stream.
+ */
+int mhdpic_spectrum(mhdpic_ctx *ctx, int32_t kind, int32_t nbins, const double *edges, const double *region,
+                    int32_t n_moment, int64_t *counts_out, double *sums_out);
+
+/*
+ * mhdpic_lambda_map - the CR-Hall parameter Lambda = R (u_CR - v_g)/v_A of
+ * eq:lambda per cell, with R = n_CR/(n_g + n_CR) (eq:defR), n_g = (q/mc)_g rho
+ * (eq:ng), u_CR = J_CR/n_CR, v_g = (rho v)/rho and v_A = |B|/sqrt(rho),
+ * evaluated as (J_CR - n_CR v_g) / ((n_g + n_CR) v_A) from the latest charge
+ * and current deposit and the gas state; 0 where |B| = 0.
+ *   out  device double[3 * nc], plane-major (component d at out[d*nc + c])
+ * In host-memory modes the gas is read from the caller's host buffers.
+ */
+int mhdpic_lambda_map(mhdpic_ctx *ctx, double *out);
 
 /*
  * mhdpic_deposit - TSC deposit of n_CR = (q/mc) m_CR W/dV and

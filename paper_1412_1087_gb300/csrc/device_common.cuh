@@ -5,6 +5,12 @@
 
 namespace mhdpic {
 
+// Value of a fixed-point accumulator word (two's complement) at 1/inv_scale.
+__device__ __forceinline__ double from_fixed(unsigned long long v, double inv_scale)
+{
+    return (double)(long long)v * inv_scale;
+}
+
 // Box that owns global index i, given CSR starts [nbox+1] (empty boxes skipped).
 __device__ __forceinline__ int find_box(const int64_t *__restrict__ starts, int nbox, int64_t i)
 {

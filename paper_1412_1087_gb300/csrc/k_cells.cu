@@ -9,10 +9,6 @@ namespace {
 
 constexpr double FIXED_LIMIT = 4611686018427387904.0;  // 2^62: accumulator headroom
 
-__device__ __forceinline__ double fx(unsigned long long v, double inv_scale)
-{
-    return (double)(long long)v * inv_scale;
-}
 
 // One pass over the cells of all boxes:
 //   apply:  rho v += dM / dV, egas += dE / dV (Section 2.1 Newton's third law,
@@ -39,13 +35,13 @@ __global__ void k_prep(Ctx c, int cur, int apply)
             for (int d = 0; d < 3; ++d) {
                 unsigned long long a = c.corr[d * nc + g];
                 over |= fabs((double)(long long)a) >= FIXED_LIMIT;
-                m[d] += fx(a, b.inv_scale[CH_MX + d]) * b.inv_dV;
+                m[d] += from_fixed(a, b.inv_scale[CH_MX + d]) * b.inv_dV;
                 c.mom[d * nc + g] = m[d];
                 c.corr[d * nc + g] = 0ull;
             }
             unsigned long long a = c.corr[3 * nc + g];
             over |= fabs((double)(long long)a) >= FIXED_LIMIT;
-            c.egas[g] += fx(a, b.inv_scale[CH_E]) * b.inv_dV;
+            c.egas[g] += from_fixed(a, b.inv_scale[CH_E]) * b.inv_dV;
             c.corr[3 * nc + g] = 0ull;
             if (over)
                 set_status(c.status, MHDPIC_ST_OVERFLOW);
@@ -57,9 +53,9 @@ __global__ void k_prep(Ctx c, int cur, int apply)
         double E[3] = {E0[0], E0[1], E0[2]};
         if (b.hall) {
             double ng = b.qm_gas * rho;
-            double n = fx(md[g], b.inv_scale[CH_N]);
-            double J[3] = {fx(md[nc + g], b.inv_scale[CH_JX]), fx(md[2 * nc + g], b.inv_scale[CH_JY]),
-                           fx(md[3 * nc + g], b.inv_scale[CH_JZ])};
+            double n = from_fixed(md[g], b.inv_scale[CH_N]);
+            double J[3] = {from_fixed(md[nc + g], b.inv_scale[CH_JX]), from_fixed(md[2 * nc + g], b.inv_scale[CH_JY]),
+                           from_fixed(md[3 * nc + g], b.inv_scale[CH_JZ])};
             double R = n / (ng + n);
             double JxB[3] = {J[1] * Bc[2] - J[2] * Bc[1], J[2] * Bc[0] - J[0] * Bc[2],
                              J[0] * Bc[1] - J[1] * Bc[0]};
@@ -266,7 +262,7 @@ __global__ void k_fixed_to_double(Ctx c, const unsigned long long *__restrict__ 
          g += (int64_t)gridDim.x * blockDim.x) {
         const BoxDev &b = c.boxes[find_box(c.box_cell_start, c.nbox, g)];
         for (int q = 0; q < 4; ++q)
-            out[q * c.nc + g] = fx(src[q * c.nc + g], b.inv_scale[ch0 + q]);
+            out[q * c.nc + g] = from_fixed(src[q * c.nc + g], b.inv_scale[ch0 + q]);
     }
 }
 

@@ -19,14 +19,17 @@
 //    exactly into hi = round(x / 2^KLO) and lo = x - hi 2^KLO with one FFMA
 //    against 1.5*2^(23+KLO), one FFMA for the residual and one FADD against
 //    1.5*2^23, and hi, lo are added to two int32 planes.  The tile scale is
-//    chosen per item so that neither plane can overflow for that item's
-//    particle count, and the flush rebuilds hi 2^KLO + lo in int64 and shifts
-//    it to the global scale, so all sums are exact and independent of the
-//    order of the additions.  The charge density (all contributions positive,
-//    no cancellation) uses the hi plane alone.
-//  * A particle whose stencil leaves the tile, or whose quantities exceed the
-//    bound the scales were sized for, deposits straight into the int64 global
-//    accumulators at the global scale.
+//    sized for the largest item (ITEM_MAX_PARTICLES), so neither plane can
+//    overflow and every item of a box rounds a contribution alike; the flush
+//    rebuilds hi 2^KLO + lo in int64 and shifts it to the global scale.  The
+//    charge density (all contributions positive, no cancellation) uses the hi
+//    plane alone.
+//  * A particle whose stencil leaves the tile adds the very integers the tile
+//    would have held, shifted, straight to the int64 global accumulators, so
+//    the sums are exact, independent of the order of the additions and of how
+//    the particles fall into items (sort cadence included).  A particle whose
+//    quantities exceed the bound the scales were sized for deposits at the
+//    global scale instead (a choice that depends on the particle alone).
 //  * 2-D: each thread copies its next particle's words into a two-stage
 //    shared-memory ring with cp.async while it pushes the current one.
 #include "push_common.cuh"
@@ -70,7 +73,10 @@ __device__ __forceinline__ void item_const(const BoxDev &b, float dt, int64_t cn
     k.m = (float)b.m_cr;
     k.qn = (float)(b.qm_cr * b.m_cr * b.inv_dV);
     const float wmax = D == 3 ? 0.421875f : 0.5625f;   // largest TSC weight of one cell
-    const float fc = (float)cnt + 1.f;
+    // sized for the largest item, so that every item of a box has the same
+    // tile scale and a contribution rounds the same whichever item holds it
+    (void)cnt;
+    const float fc = (float)ITEM_MAX_PARTICLES + 1.f;
     // split channels: |hi| sums <= cnt (X/2^KLO + 1) < 2^31 and |lo| sums <= cnt 2^(KLO-1) < 2^31;
     // the hi word also needs |x| < 2^(22+KLO) for the rounding FFMA
     const float cap_split = fminf(1099511627776.f /* 2^40 */, 524288.f * (2147483648.f / fc - 1.f));
@@ -197,8 +203,49 @@ __device__ __forceinline__ void deposit_tile(const Ctx &c, int base, const Wts &
         }
 }
 
+// Four channels into the int64 global accumulators as exactly the integers
+// the tile path would add (q carries the tile scale; each word is shifted to
+// the global scale as the flush shifts the tile): used where the stencil
+// leaves the tile, so that the sums do not depend on the tile a particle sits
+// in.
+template <int D>
+__device__ __noinline__ void deposit_global_split(const Ctx &c, const BoxDev &b, int ci0, int ci1, int ci2, Wts w,
+                                                  float q0, float q1, float q2, float q3, int ch0, int k0, int k1,
+                                                  int k2, int k3, unsigned long long *__restrict__ g0)
+{
+    const int64_t nc = c.nc;
+    const int ci[3] = {ci0, ci1, ci2};
+    const float q[4] = {q0, q1, q2, q3};
+    const int ksh[4] = {k0, k1, k2, k3};
+    int gx[3], gy[3], gz[3];
+    stencil_coords<D>(b, ci, gx, gy, gz);
+    for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz)
+        for (int cy = 0; cy < 3; ++cy) {
+            float wyz = D == 3 ? w.y[cy] * w.z[cz] : w.y[cy];
+            for (int cx = 0; cx < 3; ++cx) {
+                int64_t g = b.cell0 + ((int64_t)gz[cz] * b.n[1] + gy[cy]) * b.n[0] + gx[cx];
+                for (int k = 0; k < 4; ++k) {
+                    const float a = q[k] * wyz;
+                    long long v;
+                    if (ch0 + k == CH_N) {
+                        v = __float_as_int(fmaf(a, w.x[cx], MAGIC)) - MAGIC_BITS;
+                    } else {
+                        const float t = fmaf(a, w.x[cx], MAGIC_HI);
+                        const int hi = __float_as_int(t) - MAGIC_HI_BITS;
+                        const float r = fmaf(a, w.x[cx], MAGIC_HI - t);
+                        const int lo = __float_as_int(r + MAGIC) - MAGIC_BITS;
+                        v = (long long)hi * (1ll << KLO) + lo;
+                    }
+                    if (v)
+                        red_add(g0 + k * nc + g, (long long)((unsigned long long)v << ksh[k]));
+                }
+            }
+        }
+}
+
 // Four channels straight into the int64 global accumulators; q carries the
-// global scale.
+// global scale.  Used for particles above the bound the tile scale was sized
+// for (the choice depends only on the particle).
 template <int D>
 __device__ __noinline__ void deposit_global(const Ctx &c, const BoxDev &b, int ci0, int ci1, int ci2, Wts w,
                                             float q0, float q1, float q2, float q3,
@@ -389,9 +436,13 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
                       (e0 * (v00 + v[0]) + e1 * (v01 + v[1]) + e2 * (v02 + v[2])) / (g1 + gn);
     {
         const float qc[4] = {-k.m * (2.f * e0 + r0), -k.m * (2.f * e1 + r1), -k.m * (2.f * e2 + r2), -k.m * dEk};
-        if (in_tile && within(qc, k.qb, CH_MX)) {
+        if (within(qc, k.qb, CH_MX)) {
             const float qs[4] = {qc[0] * k.st[0], qc[1] * k.st[1], qc[2] * k.st[2], qc[3] * k.st[3]};
-            deposit_tile<D>(c, base, w, qs, CH_MX, sD);
+            if (in_tile)
+                deposit_tile<D>(c, base, w, qs, CH_MX, sD);
+            else
+                deposit_global_split<D>(c, b, ci[0], ci[1], ci[2], w, qs[0], qs[1], qs[2], qs[3], CH_MX, k.ksh[0],
+                                        k.ksh[1], k.ksh[2], k.ksh[3], c.corr);
         } else {
             deposit_global<D>(c, b, ci[0], ci[1], ci[2], w, qc[0] * k.gs[0], qc[1] * k.gs[1], qc[2] * k.gs[2],
                               qc[3] * k.gs[3], c.corr);
@@ -421,10 +472,15 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
         }
         const float qj = k.qn * ig2;
         const float qm[4] = {k.qn, qj * vn[0], qj * vn[1], qj * vn[2]};
-        if (in2 && within(qm, k.qb, CH_N)) {
-            const int base2 = (rel2[0] - 1) + c.ts[1] * (rel2[1] - 1) + (D == 3 ? c.ts[2] * (rel2[2] - 1) : 0);
+        if (within(qm, k.qb, CH_N)) {
             const float qs[4] = {qm[0] * k.st[4], qm[1] * k.st[5], qm[2] * k.st[6], qm[3] * k.st[7]};
-            deposit_tile<D>(c, base2, w2, qs, CH_N, sD);
+            if (in2) {
+                const int base2 = (rel2[0] - 1) + c.ts[1] * (rel2[1] - 1) + (D == 3 ? c.ts[2] * (rel2[2] - 1) : 0);
+                deposit_tile<D>(c, base2, w2, qs, CH_N, sD);
+            } else {
+                deposit_global_split<D>(c, b, ci[0], ci[1], ci[2], w2, qs[0], qs[1], qs[2], qs[3], CH_N, k.ksh[4],
+                                        k.ksh[5], k.ksh[6], k.ksh[7], mout);
+            }
         } else {
             deposit_global<D>(c, b, ci[0], ci[1], ci[2], w2, qm[0] * k.gs[4], qm[1] * k.gs[5], qm[2] * k.gs[6],
                               qm[3] * k.gs[7], mout);

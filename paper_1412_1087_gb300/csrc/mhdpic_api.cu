@@ -62,6 +62,8 @@ struct mhdpic_ctx {
     int32_t *work_ctr = nullptr;
     double *partials = nullptr;
     double *totals_dev = nullptr;
+    unsigned long long *spec_counts = nullptr;   // [nbox][MHDPIC_SPEC_MAX_BINS]
+    double *spec_edges = nullptr;                // [MHDPIC_SPEC_MAX_BINS + 1]
     int64_t launches = 0;
     std::vector<BoxDev> boxes;
     std::vector<int64_t> part_start, cell_start, brick_start;
@@ -74,6 +76,7 @@ struct mhdpic_ctx {
     PSet sets[2]{};
     int cur_set = 0;
     bool pending = false;
+    int sub_sort_every = 0;   // interp_push re-sorts every this many sub-steps (0: never)
     // caller's host buffers in MEM_HOST mode
     mhdpic_particles hp{};
     mhdpic_gas hg{};
@@ -491,7 +494,9 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         return bail(rc);
     k.key_off = c->s.offset;
     c->nchunks = 64;
-    if ((rc = c->alloc(&c->partials, (size_t)nbox * c->nchunks * 8)) || (rc = c->alloc(&c->totals_dev, 8 * nbox)))
+    if ((rc = c->alloc(&c->partials, (size_t)nbox * c->nchunks * 8)) || (rc = c->alloc(&c->totals_dev, 8 * nbox)) ||
+        (rc = c->alloc(&c->spec_counts, (size_t)nbox * MHDPIC_SPEC_MAX_BINS)) ||
+        (rc = c->alloc(&c->spec_edges, MHDPIC_SPEC_MAX_BINS + 1)))
         return bail(rc);
 
     // caller buffers (or device mirrors of host ones)
@@ -657,6 +662,13 @@ int mhdpic_interp_push(mhdpic_ctx *c, double dt, int32_t nsub)
             use_set(c, c->cur_set ^ 1);
             c->pending = false;
         }
+        // re-sort between sub-steps (the next sub-step applies it)
+        if (!last && c->sub_sort_every > 0 && (s + 1) % c->sub_sort_every == 0) {
+            if ((rc = check_launch(c, launch_sort(c->k, c->s, nullptr, nullptr, c->stream))) ||
+                (rc = check_launch(c, launch_max_count(c->k, c->s, c->stream))))
+                return rc;
+            c->pending = true;
+        }
     }
     c->cur ^= 1;
     c->next_clear = false;
@@ -697,6 +709,73 @@ int mhdpic_apply_feedback(mhdpic_ctx *c, double *totals_out)
                            c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
+    return MHDPIC_OK;
+}
+
+int mhdpic_spectrum(mhdpic_ctx *c, int32_t kind, int32_t nbins, const double *edges, const double *region,
+                    int32_t n_moment, int64_t *counts_out, double *sums_out)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (kind != MHDPIC_SPEC_ENERGY && kind != MHDPIC_SPEC_MOMENTUM)
+        return fail(MHDPIC_E_ARG, "unknown spectrum kind %d", kind);
+    if (nbins < 1 || nbins > MHDPIC_SPEC_MAX_BINS)
+        return fail(MHDPIC_E_ARG, "nbins must be in [1, %d]", MHDPIC_SPEC_MAX_BINS);
+    if (!edges || !counts_out)
+        return fail(MHDPIC_E_ARG, "edges and counts_out must be non-NULL");
+    if (n_moment < 0 || n_moment > 64)
+        return fail(MHDPIC_E_ARG, "n_moment must be in [0, 64]");
+    for (int b = 0; b <= nbins; ++b)
+        if (!std::isfinite(edges[b]) || (b > 0 && !(edges[b] > edges[b - 1])))
+            return fail(MHDPIC_E_ARG, "edges must be finite and strictly ascending");
+    SpecArgs a{};
+    a.kind = kind;
+    a.nbins = nbins;
+    a.n_moment = n_moment;
+    a.has_region = region != nullptr;
+    for (int q = 0; q < 6; ++q)
+        a.region[q] = region ? region[q] : 0.0;
+    if (region)
+        for (int d = 0; d < c->k.ndim; ++d)
+            if (std::isnan(region[2 * d]) || std::isnan(region[2 * d + 1]))
+                return fail(MHDPIC_E_ARG, "region bounds must not be NaN");
+    a.edges = c->spec_edges;
+    int rc;
+    if ((rc = copy_particles(c, true)))
+        return rc;
+    CK(cudaMemcpyAsync(c->spec_edges, edges, sizeof(double) * (nbins + 1), cudaMemcpyHostToDevice, c->stream));
+    if ((rc = check_launch(c, launch_spectrum(c->k, a, c->nchunks, c->spec_counts, c->partials, c->totals_dev,
+                                              c->stream))))
+        return rc;
+    static_assert(sizeof(unsigned long long) == sizeof(int64_t), "count width");
+    CK(cudaMemcpyAsync(counts_out, c->spec_counts, sizeof(int64_t) * (size_t)c->nbox * nbins,
+                       cudaMemcpyDeviceToHost, c->stream));
+    if (sums_out)
+        CK(cudaMemcpyAsync(sums_out, c->totals_dev, sizeof(double) * 2 * c->nbox, cudaMemcpyDeviceToHost,
+                           c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MHDPIC_OK;
+}
+
+int mhdpic_lambda_map(mhdpic_ctx *c, double *out)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (!out)
+        return fail(MHDPIC_E_ARG, "out must be non-NULL");
+    int rc;
+    if ((rc = copy_gas(c, true, true)))
+        return rc;
+    return check_launch(c, launch_lambda(c->k, c->cur, out, c->stream));
+}
+
+int mhdpic_set_subcycle_sort(mhdpic_ctx *c, int32_t every)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (every < 0)
+        return fail(MHDPIC_E_ARG, "every must be >= 0");
+    c->sub_sort_every = every;
     return MHDPIC_OK;
 }
 

@@ -192,6 +192,16 @@ int launch_fixed_to_double(const Ctx &c, const unsigned long long *src, int ch0,
                            cudaStream_t st);
 int launch_fields_to_double(const Ctx &c, double *out, cudaStream_t st);
 
+// Spectrum request (mhdpic_spectrum); edges is a device copy [nbins + 1].
+struct SpecArgs {
+    int32_t kind, nbins, n_moment, has_region;
+    double region[6];
+    const double *edges;
+};
+int launch_spectrum(const Ctx &c, const SpecArgs &a, int nchunks, unsigned long long *counts, double *partials,
+                    double *sums, cudaStream_t st);
+int launch_lambda(const Ctx &c, int cur, double *out, cudaStream_t st);
+
 // sets the message mhdpic_last_error() returns on this thread
 void set_last_error(const char *msg);
 

@@ -31,6 +31,9 @@ MHDPIC_PREC_MIXED = 1
 MHDPIC_MEM_DEVICE = 0
 MHDPIC_MEM_HOST = 1
 MHDPIC_MEM_HOST_GAS = 2
+MHDPIC_SPEC_ENERGY = 0
+MHDPIC_SPEC_MOMENTUM = 1
+MHDPIC_SPEC_MAX_BINS = 2048
 STATUS_NAMES = {1: "FAST_MOVER", 2: "NONFINITE", 4: "OVERFLOW", 8: "SORT_CAP", 16: "CELL_RANGE"}
 
 
@@ -76,6 +79,9 @@ SIGNATURES = {
     "mhdpic_apply_feedback": (ctypes.c_int, [_V, _V]),
     "mhdpic_run": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32, ctypes.c_int32]),
     "mhdpic_sync_particles": (ctypes.c_int, [_V]),
+    "mhdpic_set_subcycle_sort": (ctypes.c_int, [_V, ctypes.c_int32]),
+    "mhdpic_spectrum": (ctypes.c_int, [_V, ctypes.c_int32, ctypes.c_int32, _V, _V, ctypes.c_int32, _V, _V]),
+    "mhdpic_lambda_map": (ctypes.c_int, [_V, _V]),
     "mhdpic_sort_cadence": (ctypes.c_int32, [_V]),
     "mhdpic_get_deposits": (ctypes.c_int, [_V, ctypes.c_int32, _V]),
     "mhdpic_get_fields": (ctypes.c_int, [_V, _V]),
@@ -153,8 +159,28 @@ def mhdpic_run(ctx, dt: float, nsteps: int, sort_every: int = 0) -> None:
     _check(load().mhdpic_run(ctx, float(dt), int(nsteps), int(sort_every)))
 
 
+def mhdpic_set_subcycle_sort(ctx, every: int) -> None:
+    _check(load().mhdpic_set_subcycle_sort(ctx, int(every)))
+
+
 def mhdpic_sync_particles(ctx) -> None:
     _check(load().mhdpic_sync_particles(ctx))
+
+
+def mhdpic_spectrum(ctx, kind: int, edges: np.ndarray, region: Optional[np.ndarray], n_moment: int,
+                    counts_out: np.ndarray, sums_out: Optional[np.ndarray]) -> None:
+    """Host arrays: edges float64[nbins+1], region float64[6] or None,
+    counts_out int64[nbox*nbins], sums_out float64[2*nbox] or None."""
+    for a, dt in ((edges, np.float64), (region, np.float64), (counts_out, np.int64), (sums_out, np.float64)):
+        if a is not None:
+            assert a.dtype == dt and a.flags["C_CONTIGUOUS"]
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+    _check(load().mhdpic_spectrum(ctx, int(kind), int(edges.shape[0] - 1), ptr(edges), ptr(region), int(n_moment),
+                                  ptr(counts_out), ptr(sums_out)))
+
+
+def mhdpic_lambda_map(ctx, out_ptr: int) -> None:
+    _check(load().mhdpic_lambda_map(ctx, out_ptr))
 
 
 def mhdpic_sort_cadence(ctx) -> int:
@@ -358,6 +384,28 @@ class Engine:
     def deposits(self, which: int):
         out = self.torch.empty((4, self.nc), dtype=self.torch.float64, device=self.device)
         mhdpic_get_deposits(self.ctx, which, out.data_ptr())
+        return out
+
+    def set_subcycle_sort(self, every: int) -> None:
+        mhdpic_set_subcycle_sort(self.ctx, every)
+
+    def spectrum(self, kind: int, edges, region=None, n_moment: int = 6):
+        """Per-box counts (nbox, nbins) and sums (nbox, 2) of q^(n+1), q^n."""
+        edges = np.ascontiguousarray(edges, dtype=np.float64)
+        reg = None
+        if region is not None:
+            reg = np.zeros(6, dtype=np.float64)
+            r = np.asarray(region, dtype=np.float64).ravel()
+            reg[:r.shape[0]] = r
+        nb = edges.shape[0] - 1
+        counts = np.zeros(len(self.boxes) * nb, dtype=np.int64)
+        sums = np.zeros(2 * len(self.boxes), dtype=np.float64)
+        mhdpic_spectrum(self.ctx, kind, edges, reg, n_moment, counts, sums)
+        return counts.reshape(len(self.boxes), nb), sums.reshape(len(self.boxes), 2)
+
+    def lambda_map(self):
+        out = self.torch.empty((3, self.nc), dtype=self.torch.float64, device=self.device)
+        mhdpic_lambda_map(self.ctx, out.data_ptr())
         return out
 
     def fields(self):

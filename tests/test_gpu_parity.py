@@ -184,6 +184,63 @@ def test_subcycling_accumulates_the_corrector(prec):
 
 
 @pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_subcycle_resorting_changes_nothing_but_the_order(prec):
+    """Five sub-steps with a re-sort after every second one: the same
+    deposits bit for bit and the same particle states (as a set) as five
+    sub-steps without."""
+    box = tilt_B(wl.alfvenic_beam_3d(n=10, ppc=6, nmodes=8, seed=16), 16)
+    outs = []
+    for every in (0, 2):
+        eng = _engine(box, prec)
+        eng.set_subcycle_sort(every)
+        eng.interp_push(box.dt, 5)
+        dep = (eng.deposits(0).cpu().numpy(), eng.deposits(1).cpu().numpy())
+        if prec == MIXED:
+            rows = np.vstack([eng.cell.cpu().numpy().astype(np.float64)[None], eng.off.cpu().numpy(),
+                              eng.p.cpu().numpy()])
+        else:
+            rows = np.vstack([eng.x.cpu().numpy(), eng.p64.cpu().numpy()])
+        rows = rows[:, np.lexsort(rows[::-1])]
+        outs.append((dep[0], dep[1], rows, eng.status()))
+        eng.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    with pytest.raises(m.MhdpicError):
+        eng = _engine(box, prec)
+        try:
+            eng.set_subcycle_sort(-1)
+        finally:
+            eng.close()
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_results_do_not_depend_on_the_sort_cadence(prec):
+    """Four steps with a sort after every step, or with none: identical
+    corrector, moments and gas bit for bit, and the same particles as a set."""
+    box = tilt_B(wl.alfvenic_beam_3d(n=12, ppc=7, nmodes=8, seed=17), 17)
+    box.hall = 1
+    outs = []
+    for sort in (True, False):
+        eng = _engine(box, prec)
+        for _ in range(4):
+            eng.interp_push(box.dt, 1)
+            eng.apply_feedback()
+            if sort:
+                eng.sort()
+        if prec == MIXED:
+            rows = np.vstack([eng.cell.cpu().numpy().astype(np.float64)[None], eng.off.cpu().numpy(),
+                              eng.p.cpu().numpy()])
+        else:
+            rows = np.vstack([eng.x.cpu().numpy(), eng.p64.cpu().numpy()])
+        rows = rows[:, np.lexsort(rows[::-1])]
+        outs.append((eng.deposits(0).cpu().numpy(), eng.deposits(1).cpu().numpy(), eng.mom.cpu().numpy(),
+                     eng.egas.cpu().numpy(), rows, eng.status()))
+        eng.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
 def test_multi_step_with_feedback(prec):
     """Ten full steps (push, feedback, restaging, sort every 2 steps) against
     the oracle; totals conserved."""
