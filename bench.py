@@ -286,6 +286,14 @@ def run_native(args):
     stream = torch.cuda.Stream(device=dev)
     eng = m.Engine(boxes, precision=m.MHDPIC_PREC_MIXED, device=dev, stream=stream)
 
+    # sort cadence: given, or picked by the library's tuner (mhdpic_run with
+    # sort_every = 0 times one cycle of each candidate cadence on real steps)
+    tuned = args.sort_every == 0
+    if tuned:
+        eng.run(dt, 10, 0)
+        torch.cuda.synchronize()
+        args.sort_every = eng.sort_cadence()
+
     # timed region (device time, max over ranks): one call per step so that
     # the push kernel can be bracketed by events on the library's stream
     if world > 1:
@@ -426,7 +434,7 @@ def run_native(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 push + i64 fixed-point deposits",
             "data": "synthetic",
-            "config": {"workload": _workload_desc(args), "precision": "mixed", "sort_every": args.sort_every,
+            "config": {"workload": _workload_desc(args), "precision": "mixed", "sort_every": args.sort_every, "sort_every_tuned": tuned,
                        "l2": "inputs larger than L2 (%.2f GB particle state)"
                              % (npart * PARTICLE_BYTES[(ndim, prec)] / 1e9),
                        "parallelism": "independent box per GPU" if world > 1 else "1 GPU"},
@@ -488,7 +496,8 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=128, help="cells per side of the 3-D box")
     ap.add_argument("--ppc", type=int, default=32)
     ap.add_argument("--n2d", type=int, default=1024, help="cells per side of the 2-D Bell box")
-    ap.add_argument("--sort-every", type=int, default=1)
+    ap.add_argument("--sort-every", type=int, default=0,
+                    help="sort cadence in steps (0: picked by the library's tuner)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--diagnostics", type=int, default=1, help="time the spectrum and Lambda map once")

@@ -4,6 +4,7 @@
 // host<->device staging of caller buffers in MEM_HOST mode, and the order of
 // the kernel launches of each entry point.  All arithmetic runs in the
 // kernels of k_push.cu, k_cells.cu and k_sort.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -63,6 +64,8 @@ struct mhdpic_ctx {
     double *partials = nullptr;
     double *totals_dev = nullptr;
     unsigned long long *spec_counts = nullptr;   // [nbox][MHDPIC_SPEC_MAX_BINS]
+    int spec_chunks = 0;                         // particle slices per box of the spectrum
+    double *spec_partials = nullptr;             // [nbox][spec_chunks][2]
     double *spec_edges = nullptr;                // [MHDPIC_SPEC_MAX_BINS + 1]
     int64_t launches = 0;
     std::vector<BoxDev> boxes;
@@ -494,8 +497,10 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         return bail(rc);
     k.key_off = c->s.offset;
     c->nchunks = 64;
+    c->spec_chunks = std::max(1, 1216 / nbox);   // about 8 blocks per SM over all boxes
     if ((rc = c->alloc(&c->partials, (size_t)nbox * c->nchunks * 8)) || (rc = c->alloc(&c->totals_dev, 8 * nbox)) ||
         (rc = c->alloc(&c->spec_counts, (size_t)nbox * MHDPIC_SPEC_MAX_BINS)) ||
+        (rc = c->alloc(&c->spec_partials, (size_t)nbox * c->spec_chunks * 2)) ||
         (rc = c->alloc(&c->spec_edges, MHDPIC_SPEC_MAX_BINS + 1)))
         return bail(rc);
 
@@ -744,8 +749,8 @@ int mhdpic_spectrum(mhdpic_ctx *c, int32_t kind, int32_t nbins, const double *ed
     if ((rc = copy_particles(c, true)))
         return rc;
     CK(cudaMemcpyAsync(c->spec_edges, edges, sizeof(double) * (nbins + 1), cudaMemcpyHostToDevice, c->stream));
-    if ((rc = check_launch(c, launch_spectrum(c->k, a, c->nchunks, c->spec_counts, c->partials, c->totals_dev,
-                                              c->stream))))
+    if ((rc = check_launch(c, launch_spectrum(c->k, a, c->spec_chunks, c->spec_counts, c->spec_partials,
+                                              c->totals_dev, c->stream))))
         return rc;
     static_assert(sizeof(unsigned long long) == sizeof(int64_t), "count width");
     CK(cudaMemcpyAsync(counts_out, c->spec_counts, sizeof(int64_t) * (size_t)c->nbox * nbins,
