@@ -290,7 +290,7 @@ def run_native(args):
     # sort_every = 0 times one cycle of each candidate cadence on real steps)
     tuned = args.sort_every == 0
     if tuned:
-        eng.run(dt, 10, 0)
+        eng.run(dt, 20, 0)
         torch.cuda.synchronize()
         args.sort_every = eng.sort_cadence()
 

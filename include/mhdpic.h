@@ -265,8 +265,10 @@ int mhdpic_apply_feedback(mhdpic_ctx *ctx, double *totals_out);
  * mhdpic_run - nsteps full steps, each mhdpic_interp_push(dt, 1) followed by
  * mhdpic_apply_feedback(NULL), with mhdpic_sort after every sort_every-th
  * step (counted across calls).  sort_every = 0 lets the library choose the
- * cadence: the first call times cycles of 1, 2, 3 and 4 steps on real steps
- * (they count toward nsteps) and keeps the fastest (mhdpic_sort_cadence).
+ * cadence: the first call runs one warm-up step, then times whole cycles of
+ * 1, 2, 3 and 4 steps (at least four steps per candidate, 19 steps in all
+ * while nsteps lasts) on real steps that count toward nsteps, and keeps the
+ * fastest (mhdpic_sort_cadence).
  * Whole cycles are captured once into a CUDA graph and replayed (re-captured
  * when dt or the cadence changes); with the legacy default stream or host
  * buffers the steps run eagerly.  Asynchronous except while tuning.

@@ -66,16 +66,24 @@ __global__ void k_sort_keys(Ctx c, int32_t *__restrict__ count, int32_t *__restr
         for (int d = 0; d < 3; ++d)   // defensive: a key outside the box would index out of range
             ci[d] = ci[d] < 0 ? 0 : (ci[d] >= b.n[d] ? b.n[d] - 1 : ci[d]);
         int32_t key = (int32_t)brick_key(b, c.brick, ci[0], ci[1], ci[2]);
-        unsigned active = __activemask();
-        unsigned peers = __match_any_sync(active, key);
-        int leader = __ffs(peers) - 1;
-        int rank = __popc(peers & ((1u << lane) - 1u));
+        // runs of equal keys in consecutive lanes (the input is nearly
+        // sorted) take one atomic per run; the rank inside the run is the
+        // lane offset
+        const unsigned active = __activemask();
+        const int prev = __shfl_up_sync(active, key, 1);
+        const bool head = lane == 0 || !((active >> (lane - 1)) & 1u) || prev != key;
+        const unsigned heads = __ballot_sync(active, head);
+        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));   // last head at or below lane
+        const unsigned after = heads & ~(0xffffffffu >> (31 - lane));           // heads above lane
+        const int end = after ? __ffs(after) - 1 : 32;
+        const unsigned tail = (end < 32 ? (1u << end) : 0u) - 1u;               // lanes below end
+        const int len = __popc(active & tail & ~((1u << start) - 1u));
         int base = 0;
-        if (lane == leader)
-            base = atomicAdd(count + key, __popc(peers));
-        base = __shfl_sync(peers, base, leader);
+        if (head)
+            base = atomicAdd(count + key, len);
+        base = __shfl_sync(active, base, start);
         pkey[i] = key;
-        pslot[i] = base + rank;
+        pslot[i] = base + (lane - start);
     }
 }
 

@@ -830,35 +830,42 @@ int run_one_step(mhdpic_ctx *c, double dt, int k)
     return MHDPIC_OK;
 }
 
-// Sort cadence with the shortest measured time per step: each candidate runs
-// one full cycle of real steps, timed with events on the context's stream.
+// Sort cadence with the shortest measured time per step: after one untimed
+// warm-up step, each candidate runs whole cycles of real steps (at least four
+// steps), timed with events on the context's stream.
 int tune_sort_cadence(mhdpic_ctx *c, double dt, int32_t *steps_left)
 {
     static const int cands[] = {1, 2, 3, 4};
+    int rc;
+    if (*steps_left > 0) {
+        if ((rc = run_one_step(c, dt, 1)))
+            return rc;
+        --*steps_left;
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 0.f;
-    int best_k = 2;
+    int best_k = 1;
     for (int k : cands) {
-        if (*steps_left < k)
+        const int reps = (4 + k - 1) / k;
+        if (*steps_left < reps * k)
             break;
         // align to the start of a cycle of length k (sort now)
-        int rc = mhdpic_sort(c, nullptr, nullptr);
-        c->step_in_cycle = 0;
-        if (rc)
+        if ((rc = mhdpic_sort(c, nullptr, nullptr)))
             return rc;
+        c->step_in_cycle = 0;
         cudaEventRecord(e0, c->stream);
-        for (int s = 0; s < k; ++s)
+        for (int s = 0; s < reps * k; ++s)
             if ((rc = run_one_step(c, dt, k)))
                 return rc;
         cudaEventRecord(e1, c->stream);
         CK(cudaEventSynchronize(e1));
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        *steps_left -= k;
-        if (best == 0.f || ms / k < best) {
-            best = ms / k;
+        *steps_left -= reps * k;
+        if (best == 0.f || ms / (reps * k) < best) {
+            best = ms / (reps * k);
             best_k = k;
         }
     }
