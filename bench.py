@@ -44,12 +44,14 @@ CELL_FIELD_BYTES = {"mixed": 24, "fp64": 48}
 CELL_DEPOSIT_BYTES = 8 * 8 * 2
 # DRAM bytes (read + write) per particle of one k_push_mixed<D, full> launch,
 # measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on a small
-# case of the current kernel version; traffic scales with the particle count
-# (cells scale alike at fixed particles per cell):
-#   3-D, 64^3 x 32 CRs:   262.0 MB + 202.2 MB over 8,388,608 CRs
-#   2-D, 512^2 x 64 CRs:  427.6 MB + 421.1 MB over 16,777,216 CRs
+# case of the current kernel version, a push that applies a sort (reads its
+# particles through the permutation, as every push does at a sort cadence of
+# one); traffic scales with the particle count (cells scale alike at fixed
+# particles per cell):
+#   3-D, 64^3 x 32 CRs:   393.0 MB + 295.8 MB over 8,388,608 CRs
+#   2-D, 512^2 x 64 CRs:  874.5 MB + 646.5 MB over 16,777,216 CRs
 # Remove an entry whenever its kernel changes, until it is measured again.
-PUSH_TRAFFIC_BYTES_PER_PARTICLE = {"alfvenic_beam_3d": 464.23e6 / 8388608, "bell_2d": 848.72e6 / 16777216}
+PUSH_TRAFFIC_BYTES_PER_PARTICLE = {"alfvenic_beam_3d": 688.83e6 / 8388608, "bell_2d": 1521.07e6 / 16777216}
 
 
 def _rank_env():
