@@ -88,6 +88,9 @@ def _load():
             lib.orc_spectrum.argtypes = [G, Pp, ctypes.c_int64, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P,
                                          ctypes.c_int, _P, _P]
             lib.orc_lambda_map.argtypes = [G, Pp, _P, _P, _P, _P, _P]
+            lib.orc_gas_rhs.argtypes = [G, ctypes.c_int, _P, _P, _P, _P, _P, _P]
+            lib.orc_gas_predict.argtypes = [G, Pp, ctypes.c_int, ctypes.c_double] + [_P] * 13
+            lib.orc_gas_correct.argtypes = [G, Pp, ctypes.c_int, ctypes.c_double] + [_P] * 11
             _lib = lib
     return _lib
 
@@ -270,6 +273,17 @@ def lambda_map(g: Grid, p: Params, rho, mom, B, mom_dep) -> np.ndarray:
     return out
 
 
+def gas_rhs(g: Grid, model: int, rho, mom, B, H=None) -> tuple:
+    """Gas right-hand side of the coupled step's model (no CR sources):
+    (dmom, dB), each (3, ncell)."""
+    rho, mom, B = _f64(rho), _f64(mom), _f64(B)
+    H = _f64(H) if H is not None else None
+    dmom = np.zeros_like(mom)
+    dB = np.zeros_like(B)
+    _load().orc_gas_rhs(ctypes.byref(g), int(model), _ptr(rho), _ptr(mom), _ptr(B), _ptr(H), _ptr(dmom), _ptr(dB))
+    return dmom, dB
+
+
 class State:
     """A box advanced by the oracle: FP64 particles, gas and deposit planes."""
 
@@ -305,3 +319,34 @@ class State:
 
     def totals(self) -> np.ndarray:
         return totals(self.g, self.p, self.v, self.mom, self.egas)
+
+    def predict(self, dt: float, model: int):
+        """Predictor of the coupled step (eq:scheme): returns the half state
+        (rho, mom, egas, B) and the cell-centred E of it for the push."""
+        nc = self.nc
+        half = (np.zeros(nc), np.zeros((3, nc)), np.zeros(nc), np.zeros((3, nc)))
+        E = np.zeros((3, nc))
+        H, dm, dB = np.zeros((3, nc)), np.zeros((3, nc)), np.zeros((3, nc))
+        _load().orc_gas_predict(ctypes.byref(self.g), ctypes.byref(self.p), int(model), float(dt), _ptr(self.rho),
+                                _ptr(self.mom), _ptr(self.egas), _ptr(self.B), _ptr(self.mom_dep), _ptr(half[0]),
+                                _ptr(half[1]), _ptr(half[2]), _ptr(half[3]), _ptr(E), _ptr(H), _ptr(dm), _ptr(dB))
+        return half, E
+
+    def correct(self, dt: float, model: int, half) -> None:
+        """Corrector of the coupled step: applies self.corr and the gas model at
+        the half state; self.corr is zeroed."""
+        nc = self.nc
+        H, dm, dB = np.zeros((3, nc)), np.zeros((3, nc)), np.zeros((3, nc))
+        _load().orc_gas_correct(ctypes.byref(self.g), ctypes.byref(self.p), int(model), float(dt), _ptr(self.rho),
+                                _ptr(self.mom), _ptr(self.egas), _ptr(self.B), _ptr(half[0]), _ptr(half[1]),
+                                _ptr(half[3]), _ptr(self.corr), _ptr(H), _ptr(dm), _ptr(dB))
+
+    def coupled_step(self, dt: float, model: int) -> None:
+        """One step of the paper's predictor-corrector (eq:scheme): gas half
+        step with the CR sources of the moments at x^n, particle step in the
+        half-step fields (corrector deposit at x^(n+1/2), moments at
+        x^(n+1)), gas full step with the corrector deposit."""
+        half, E = self.predict(dt, model)
+        self.mom_dep[:] = 0.0
+        push(self.g, self.p, dt, self.x, self.v, E, half[3], self.corr, self.mom_dep)
+        self.correct(dt, model, half)

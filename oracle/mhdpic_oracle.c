@@ -619,3 +619,153 @@ void orc_lambda_map(const orc_grid *g, const orc_params *p, const double *rho, c
         }
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* coupled step: the predictor-corrector of App. A.3 (eq:scheme)        */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The gas part G(f, g) of eq:scheme, in one of two models:
+ *   model 0  CR sources only: the gas momentum and energy change by the CR
+ *            feedback alone and B stays as it is (no induction);
+ *   model 1  plane-parallel linear MHD along x: with rho and B_x uniform and
+ *            v_x = 0 to first order, the transverse parts of eq:gasmotion and
+ *            eq:induction are
+ *              d(rho v_y)/dt = B_x dB_y/dx,   d(rho v_z)/dt = B_x dB_z/dx,
+ *              dB_y/dt = B_x dv_y/dx,         dB_z/dt = B_x dv_z/dx,
+ *            plus, from -c curl of the CR-Hall field -F_CR/n_g (eq:emfcr2),
+ *              dB_y/dt += -d(F_z/n_g)/dx,     dB_z/dt += d(F_y/n_g)/dx,
+ *            with centred differences (a_{i+1} - a_{i-1}) / (2 dx) and x
+ *            periodic.  The gas energy takes only the CR sources (the gas is
+ *            isothermal in the paper's linear test, App. B.2).
+ *
+ * CR sources (eq:gasmotion, eq:engeq): momentum -F_CR with
+ * F_CR = (1-R)(n_CR E0 + J_CR x B) (eq:lorentz2), energy -(1-R) J_CR.E0;
+ * R = n_CR/(n_g + n_CR) with the CR-Hall term and R = 0 without it.
+ */
+
+/* F_CR and (1-R) J.E0 of one cell. */
+static void cr_source(const orc_params *p, double rho, const double mom[3], const double B[3], const double md[4],
+                      double F[3], double *P)
+{
+    double vg[3], vxb[3], E0[3], JxB[3];
+    for (int d = 0; d < 3; ++d)
+        vg[d] = mom[d] / rho;
+    cross3(vg, B, vxb);
+    for (int d = 0; d < 3; ++d)
+        E0[d] = -vxb[d];
+    double n = md[0];
+    double J[3] = {md[1], md[2], md[3]};
+    double R = p->hall ? n / (p->qm_gas * rho + n) : 0.0;
+    cross3(J, B, JxB);
+    for (int d = 0; d < 3; ++d)
+        F[d] = (1.0 - R) * (n * E0[d] + JxB[d]);
+    *P = (1.0 - R) * dot3(J, E0);
+}
+
+/* Cell of the x neighbour (s = -1 or +1) of cell c, x periodic. */
+static int64_t x_neighbour(const orc_grid *g, int64_t c, int s)
+{
+    int64_t nx = g->n[0];
+    int64_t i = c % nx;
+    int64_t j = (i + s + nx) % nx;
+    return c - i + j;
+}
+
+/*
+ * Right-hand side of model 1 at state (rho, mom, B) with the CR-Hall field
+ * H = F_CR / n_g per cell (3 planes, or NULL): dmom[3 planes], dB[3 planes].
+ * Model 0 gives zeros.
+ */
+void orc_gas_rhs(const orc_grid *g, int model, const double *rho, const double *mom, const double *B,
+                 const double *H, double *dmom, double *dB)
+{
+    int64_t nc = ncell_of(g);
+    double h = 1.0 / (2.0 * g->dx[0]);
+    for (int64_t c = 0; c < nc; ++c) {
+        for (int d = 0; d < 3; ++d) {
+            dmom[d * nc + c] = 0.0;
+            dB[d * nc + c] = 0.0;
+        }
+        if (model != 1)
+            continue;
+        int64_t l = x_neighbour(g, c, -1), r = x_neighbour(g, c, 1);
+        double Bx = B[c];
+        for (int d = 1; d < 3; ++d) {
+            dmom[d * nc + c] = Bx * (B[d * nc + r] - B[d * nc + l]) * h;
+            dB[d * nc + c] = Bx * (mom[d * nc + r] / rho[r] - mom[d * nc + l] / rho[l]) * h;
+        }
+        if (H) {
+            dB[nc + c] -= (H[2 * nc + r] - H[2 * nc + l]) * h;
+            dB[2 * nc + c] += (H[nc + r] - H[nc + l]) * h;
+        }
+    }
+}
+
+/*
+ * Predictor (eq:scheme, first line): g^(n+1/2) = g^n + G(f^n, g^n) dt/2 with
+ * the CR sources from the moments mom_dep (n, J at x^n).  Writes the half
+ * state (rho_h, mom_h, egas_h, B_h) and the cell-centred electric field E of
+ * g^(n+1/2) (with the CR-Hall term from the same moments) for the push.
+ * H is scratch of 3 planes.
+ */
+void orc_gas_predict(const orc_grid *g, const orc_params *p, int model, double dt, const double *rho,
+                     const double *mom, const double *egas, const double *B, const double *mom_dep,
+                     double *rho_h, double *mom_h, double *egas_h, double *B_h, double *E, double *H,
+                     double *dmom, double *dB)
+{
+    int64_t nc = ncell_of(g);
+    double *P = (double *)malloc(sizeof(double) * (size_t)nc);
+    double *F = (double *)malloc(sizeof(double) * 3 * (size_t)nc);
+    for (int64_t c = 0; c < nc; ++c) {
+        double m[3] = {mom[c], mom[nc + c], mom[2 * nc + c]};
+        double Bc[3] = {B[c], B[nc + c], B[2 * nc + c]};
+        double md[4] = {mom_dep[c], mom_dep[nc + c], mom_dep[2 * nc + c], mom_dep[3 * nc + c]};
+        double Fc[3];
+        cr_source(p, rho[c], m, Bc, md, Fc, &P[c]);
+        for (int d = 0; d < 3; ++d) {
+            F[d * nc + c] = Fc[d];
+            H[d * nc + c] = p->hall ? Fc[d] / (p->qm_gas * rho[c]) : 0.0;
+        }
+    }
+    orc_gas_rhs(g, model, rho, mom, B, H, dmom, dB);
+    for (int64_t c = 0; c < nc; ++c) {
+        rho_h[c] = rho[c];
+        for (int d = 0; d < 3; ++d) {
+            mom_h[d * nc + c] = mom[d * nc + c] + 0.5 * dt * (dmom[d * nc + c] - F[d * nc + c]);
+            B_h[d * nc + c] = B[d * nc + c] + 0.5 * dt * dB[d * nc + c];
+        }
+        egas_h[c] = egas[c] - 0.5 * dt * P[c];
+    }
+    free(P);
+    free(F);
+    orc_field_prep(g, p, rho_h, mom_h, B_h, mom_dep, E);
+}
+
+/*
+ * Corrector (eq:scheme, third line): g^(n+1) = g^n + G((f^n + f^(n+1))/2,
+ * g^(n+1/2)) dt, where the CR part is the corrector deposit corr (momentum and
+ * energy given to the gas over the step, App. A.3) and the CR-Hall field uses
+ * the force it implies, F_CR = -corr_M / (dV dt).  The gas arrays are updated
+ * in place (rho is unchanged); corr is zeroed.  H, dmom, dB are scratch.
+ */
+void orc_gas_correct(const orc_grid *g, const orc_params *p, int model, double dt, const double *rho,
+                     double *mom, double *egas, double *B, const double *rho_h, const double *mom_h,
+                     const double *B_h, double *corr, double *H, double *dmom, double *dB)
+{
+    int64_t nc = ncell_of(g);
+    double dV = cell_volume(g);
+    for (int64_t c = 0; c < nc; ++c)
+        for (int d = 0; d < 3; ++d)
+            H[d * nc + c] = p->hall ? (-corr[d * nc + c] / (dV * dt)) / (p->qm_gas * rho_h[c]) : 0.0;
+    orc_gas_rhs(g, model, rho_h, mom_h, B_h, H, dmom, dB);
+    (void)rho;
+    for (int64_t c = 0; c < nc; ++c) {
+        for (int d = 0; d < 3; ++d) {
+            mom[d * nc + c] += dt * dmom[d * nc + c] + corr[d * nc + c] / dV;
+            B[d * nc + c] += dt * dB[d * nc + c];
+        }
+        egas[c] += corr[3 * nc + c] / dV;
+    }
+    memset(corr, 0, sizeof(double) * 4 * (size_t)nc);
+}

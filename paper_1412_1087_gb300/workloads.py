@@ -479,6 +479,78 @@ def gyration(relativistic: bool = False, v0: float = 0.0, C: float = 10.0, n: in
     return bx
 
 
+def bell_linear(eps: float = 0.5, Lambda: float = 0.0, nx: int = 32, ny: int = 4, amp: float = 1e-3,
+                cfl: float = 0.4, ppc: int = 1) -> Box:
+    """Linear growth of the Bell instability, Appendix B.2.
+
+    A 2-D periodic box of nx x ny square cells, one most unstable wavelength
+    lambda = 1 along x (B0 = rho0 = 1, so v_A = 1), uniform in y.  Cold CRs,
+    ppc per cell spread evenly along x and placed at the cell centre in y,
+    drift at U_s = v_A/eps along x; q/mc = 1e-6 k0 makes their own motion
+    negligible, so they carry a constant current J = n_CR U_s along x, and
+    C = 100 U_s.
+
+    Without the CR-Hall term (Lambda = 0) the box wavenumber is k0 = J/(2 B0)
+    (J = 4 pi) and the gas starts on the eigenvector of eq:eigenvect.  With it,
+    R = Lambda eps (Lambda = R U_s / v_A, eq:lambda), the box wavenumber is the
+    most unstable k_m = k0/f with f = 1 + (Lambda/2)^2, so J = 2 f k_m, and the
+    gas starts on eq:eigenvect2; qm_gas is set so that n_CR/(n_g + n_CR) = R.
+    The perturbation amplitude is amp (times B0).  dt puts both the CRs and
+    an Alfven wave at cfl cells per step.
+    """
+    k = 2.0 * math.pi
+    dxv = 1.0 / nx
+    n = (nx, ny, 1)
+    nc = nx * ny
+    f = 1.0 + 0.25 * Lambda * Lambda
+    k0 = f * k
+    J = 2.0 * k0
+    U = 1.0 / eps
+    ncr = J / U
+    qm_cr = 1e-6 * k0
+    C = 100.0 * U
+    hall = 1 if Lambda > 0.0 else 0
+    if hall:
+        R = Lambda * eps
+        qm_gas = ncr * (1.0 - R) / R
+    else:
+        qm_gas = 1.0
+    xc = (np.arange(nx, dtype=np.float64) + 0.5) * dxv
+    ph = np.tile(k * xc, ny)
+    B = np.zeros((3, nc))
+    B[0] = 1.0
+    B[1] = amp * np.cos(ph)
+    B[2] = amp * np.sin(ph)
+    dv = np.zeros((3, nc))
+    if hall:
+        sf = math.sqrt(f)
+        dv[1] = amp * (0.5 * Lambda * np.cos(ph) + sf * np.sin(ph))
+        dv[2] = amp * (0.5 * Lambda * np.sin(ph) - sf * np.cos(ph))
+    else:
+        th = math.asin(eps)
+        dv[1] = amp * np.sin(ph - th)
+        dv[2] = -amp * np.cos(ph - th)
+    rho, mom, egas, Bc = _gas(n, 1.0, (0.0, 0.0, 0.0), B, 1.0, 5.0 / 3.0, dv=dv)
+    # particles: ppc per cell, evenly spaced in x, at the cell centre in y
+    npart = nc * ppc
+    ci = np.repeat(np.arange(nc, dtype=np.int64), ppc)
+    sub = np.tile(np.arange(ppc, dtype=np.float64), nc)
+    s = np.empty((2, npart))
+    s[0] = (ci % nx) + (sub + 0.5) / ppc
+    s[1] = (ci // nx) + 0.5
+    cell, off = _quantise_positions(s, n, 2)
+    gam = 1.0 / math.sqrt(1.0 - (U / C) ** 2)
+    p = np.zeros((3, npart), dtype=np.float32)
+    p[0] = np.float32(gam * U)
+    dV = dxv * dxv
+    m_cr = J * dV / (ppc * qm_cr * U)
+    dt = cfl * dxv / max(1.0, U)
+    return Box(ndim=2, n=n, dx=(dxv, dxv, 1.0), x0=(0.0, 0.0, 0.0), bc=(PERIODIC,) * 3, rho=rho,
+               mom=np.ascontiguousarray(mom), egas=egas, B=np.ascontiguousarray(Bc), cell=cell, off=off, p=p,
+               qm_cr=qm_cr, qm_gas=qm_gas, C=C, m_cr=m_cr, hall=hall, dt=dt,
+               nsteps=int(math.ceil(3.0 / (k * dt))), name="bell_linear")
+
+
 def scaled(box_fn, **kw) -> Box:
     """Call a recipe with overridden size arguments (small parity-test variants)."""
     return box_fn(**kw)
