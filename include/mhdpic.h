@@ -261,6 +261,56 @@ int mhdpic_deposit(mhdpic_ctx *ctx);
  */
 int mhdpic_apply_feedback(mhdpic_ctx *ctx, double *totals_out);
 
+/* ---- gas models of the coupled step ---- */
+#define MHDPIC_GAS_SOURCES 0   /* the gas changes by the CR sources alone; B is held */
+#define MHDPIC_GAS_LINEAR_X 1  /* plus plane-parallel linear MHD along x (below) */
+
+/*
+ * mhdpic_gas_predict - predictor of the coupled MHD-PIC step (App. A.3,
+ * eq:scheme, first line): the half-step gas state
+ *   g^(n+1/2) = g^n + G(f^n, g^n) dt/2
+ * into library scratch (the caller's gas is not changed), and the cell fields
+ * of g^(n+1/2) staged for the next mhdpic_interp_push.  The CR part of G comes
+ * from the latest charge and current deposit (n, J at x^n): momentum
+ * -F_CR = -(1-R)(n E0 + J x B) (eq:gasmotion, eq:lorentz2) and energy
+ * -(1-R) J.E0 (eq:engeq), with R = n/(n_g + n) when the box has the CR-Hall
+ * term and R = 0 otherwise; the staged field is E0 = -v_g x B, minus F_CR/n_g
+ * with the CR-Hall term (eq:emfcr2), from the half state and the same n, J.
+ *   dt     the step (> 0); the push and mhdpic_gas_correct take the same dt
+ *   model  MHDPIC_GAS_SOURCES: no other gas evolution;
+ *          MHDPIC_GAS_LINEAR_X: rho and B_x taken as uniform and v_x = 0 to
+ *          first order, the transverse momentum and field follow the 1-D
+ *          linear MHD equations d(rho v_y,z)/dt = B_x dB_y,z/dx,
+ *          dB_y,z/dt = B_x dv_y,z/dx plus the curl of the CR-Hall field
+ *          (dB_y/dt -= d(F_z/n_g)/dx, dB_z/dt += d(F_y/n_g)/dx), with centred
+ *          differences; every box must be periodic along x.  The gas energy
+ *          takes only the CR sources in both models.
+ * The first call allocates the half-state scratch (8 doubles per cell) with
+ * cudaMalloc.  Errors: MHDPIC_E_ARG for dt <= 0, an unknown model or a box
+ * that is not periodic along x under MHDPIC_GAS_LINEAR_X.
+ */
+int mhdpic_gas_predict(mhdpic_ctx *ctx, double dt, int32_t model);
+
+/*
+ * mhdpic_gas_correct - corrector of the coupled step (App. A.3, eq:scheme,
+ * third line): the caller's gas advances to
+ *   g^(n+1) = g^n + G((f^n + f^(n+1))/2, g^(n+1/2)) dt,
+ * where the CR part is the corrector deposit accumulated by the pushes since
+ * the predictor (rho v += dM/dV, egas += dE/dV, App. A.3) and the gas part is
+ * the model's, evaluated at the half state of mhdpic_gas_predict; with the
+ * CR-Hall term the induction takes the curl of -F_CR/n_g with
+ * F_CR = -dM/(dV dt), the force the deposit implies.  rho is unchanged; mom,
+ * egas and B are written (back to the caller's host buffers in host-memory
+ * modes).  The accumulators are zeroed.  The next push needs a new
+ * mhdpic_gas_predict (or mhdpic_apply_feedback / mhdpic_deposit) to stage
+ * its fields.
+ *   dt, model  as given to mhdpic_gas_predict
+ *   totals_out HOST double[8*nbox] or NULL, as for mhdpic_apply_feedback
+ * Errors: MHDPIC_E_STATE when no predictor ran since the last corrector,
+ * MHDPIC_E_ARG when dt or model differ from the predictor's.
+ */
+int mhdpic_gas_correct(mhdpic_ctx *ctx, double dt, int32_t model, double *totals_out);
+
 /*
  * mhdpic_run - nsteps full steps, each mhdpic_interp_push(dt, 1) followed by
  * mhdpic_apply_feedback(NULL), with mhdpic_sort after every sort_every-th

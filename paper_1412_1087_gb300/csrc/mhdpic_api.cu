@@ -94,6 +94,11 @@ struct mhdpic_ctx {
     int64_t graph_launches = 0;   // kernel launches inside one replay
     int step_in_cycle = 0;        // steps since the last sort done by mhdpic_run
     int tuned_k = 0;
+    // coupled step: half state of the last mhdpic_gas_predict
+    double *gas_half = nullptr;
+    bool half_valid = false;
+    double half_dt = 0.0;
+    int half_model = -1;
 
     template <typename T>
     int alloc(T **p, size_t count)
@@ -705,6 +710,62 @@ int mhdpic_apply_feedback(mhdpic_ctx *c, double *totals_out)
         return rc;
     if ((rc = copy_gas(c, false, false)))
         return rc;
+    if (totals_out) {
+        if ((rc = copy_particles(c, true)) || (rc = materialize(c)))
+            return rc;
+        if ((rc = check_launch(c, launch_totals(c->k, c->partials, c->nchunks, c->totals_dev, c->stream))))
+            return rc;
+        CK(cudaMemcpyAsync(totals_out, c->totals_dev, sizeof(double) * 8 * c->nbox, cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return MHDPIC_OK;
+}
+
+int mhdpic_gas_predict(mhdpic_ctx *c, double dt, int32_t model)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (!(dt > 0.0) || !std::isfinite(dt))
+        return fail(MHDPIC_E_ARG, "dt must be finite and > 0");
+    if (model != MHDPIC_GAS_SOURCES && model != MHDPIC_GAS_LINEAR_X)
+        return fail(MHDPIC_E_ARG, "unknown gas model %d", model);
+    if (model == MHDPIC_GAS_LINEAR_X)
+        for (int b = 0; b < c->nbox; ++b)
+            if (c->boxes[b].bc[0] != MHDPIC_BC_PERIODIC)
+                return fail(MHDPIC_E_ARG, "MHDPIC_GAS_LINEAR_X needs x-periodic boxes (box %d)", b);
+    int rc;
+    if (!c->gas_half && (rc = c->alloc(&c->gas_half, (size_t)8 * c->k.nc)))
+        return rc;
+    if ((rc = copy_gas(c, true, true)))
+        return rc;
+    if ((rc = check_launch(c, launch_gas_predict(c->k, c->cur, dt, model, c->gas_half, c->stream))))
+        return rc;
+    c->next_clear = true;
+    c->half_valid = true;
+    c->half_dt = dt;
+    c->half_model = model;
+    return MHDPIC_OK;
+}
+
+int mhdpic_gas_correct(mhdpic_ctx *c, double dt, int32_t model, double *totals_out)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (!c->half_valid)
+        return fail(MHDPIC_E_STATE, "mhdpic_gas_correct needs a mhdpic_gas_predict first");
+    if (dt != c->half_dt || model != c->half_model)
+        return fail(MHDPIC_E_ARG, "dt and model must be the predictor's (%g, %d)", c->half_dt, c->half_model);
+    int rc;
+    if ((rc = copy_gas(c, true, true)))
+        return rc;
+    if ((rc = check_launch(c, launch_gas_correct(c->k, dt, model, c->gas_half, c->stream))))
+        return rc;
+    c->half_valid = false;
+    if ((rc = copy_gas(c, false, false)))
+        return rc;
+    if (c->mem != MHDPIC_MEM_DEVICE)
+        CK(cudaMemcpyAsync(c->hg.B, c->k.B, sizeof(double) * 3 * c->k.nc, cudaMemcpyDeviceToHost, c->stream));
     if (totals_out) {
         if ((rc = copy_particles(c, true)) || (rc = materialize(c)))
             return rc;

@@ -201,6 +201,10 @@ struct SpecArgs {
 int launch_spectrum(const Ctx &c, const SpecArgs &a, int nchunks, unsigned long long *counts, double *partials,
                     double *sums, cudaStream_t st);
 int launch_lambda(const Ctx &c, int cur, double *out, cudaStream_t st);
+// coupled step (App. A.3): gas half state into half[8][nc] plus field
+// staging; gas full step from the half state and the corrector deposit
+int launch_gas_predict(const Ctx &c, int cur, double dt, int model, double *half, cudaStream_t st);
+int launch_gas_correct(const Ctx &c, double dt, int model, const double *half, cudaStream_t st);
 
 // sets the message mhdpic_last_error() returns on this thread
 void set_last_error(const char *msg);

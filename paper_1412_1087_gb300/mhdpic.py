@@ -34,6 +34,8 @@ MHDPIC_MEM_HOST_GAS = 2
 MHDPIC_SPEC_ENERGY = 0
 MHDPIC_SPEC_MOMENTUM = 1
 MHDPIC_SPEC_MAX_BINS = 2048
+MHDPIC_GAS_SOURCES = 0
+MHDPIC_GAS_LINEAR_X = 1
 STATUS_NAMES = {1: "FAST_MOVER", 2: "NONFINITE", 4: "OVERFLOW", 8: "SORT_CAP", 16: "CELL_RANGE"}
 
 
@@ -77,6 +79,8 @@ SIGNATURES = {
     "mhdpic_interp_push": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32]),
     "mhdpic_deposit": (ctypes.c_int, [_V]),
     "mhdpic_apply_feedback": (ctypes.c_int, [_V, _V]),
+    "mhdpic_gas_predict": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32]),
+    "mhdpic_gas_correct": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32, _V]),
     "mhdpic_run": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32, ctypes.c_int32]),
     "mhdpic_sync_particles": (ctypes.c_int, [_V]),
     "mhdpic_set_subcycle_sort": (ctypes.c_int, [_V, ctypes.c_int32]),
@@ -153,6 +157,18 @@ def mhdpic_apply_feedback(ctx, totals_out: Optional[np.ndarray] = None) -> None:
         assert totals_out.dtype == np.float64 and totals_out.flags["C_CONTIGUOUS"]
         ptr = totals_out.ctypes.data_as(ctypes.c_void_p)
     _check(load().mhdpic_apply_feedback(ctx, ptr))
+
+
+def mhdpic_gas_predict(ctx, dt: float, model: int) -> None:
+    _check(load().mhdpic_gas_predict(ctx, float(dt), int(model)))
+
+
+def mhdpic_gas_correct(ctx, dt: float, model: int, totals_out: Optional[np.ndarray] = None) -> None:
+    ptr = None
+    if totals_out is not None:
+        assert totals_out.dtype == np.float64 and totals_out.flags["C_CONTIGUOUS"]
+        ptr = totals_out.ctypes.data_as(ctypes.c_void_p)
+    _check(load().mhdpic_gas_correct(ctx, float(dt), int(model), ptr))
 
 
 def mhdpic_run(ctx, dt: float, nsteps: int, sort_every: int = 0) -> None:
@@ -372,6 +388,25 @@ class Engine:
     def step(self, dt: float, nsub: int = 1) -> None:
         self.interp_push(dt, nsub)
         self.apply_feedback(False)
+
+    def gas_predict(self, dt: float, model: int) -> None:
+        mhdpic_gas_predict(self.ctx, dt, model)
+
+    def gas_correct(self, dt: float, model: int, totals: bool = False) -> Optional[np.ndarray]:
+        if totals:
+            out = np.zeros(8 * len(self.boxes), dtype=np.float64)
+            mhdpic_gas_correct(self.ctx, dt, model, out)
+            return out.reshape(len(self.boxes), 8)
+        mhdpic_gas_correct(self.ctx, dt, model, None)
+        return None
+
+    def coupled_step(self, dt: float, model: int, nsub: int = 1, totals: bool = False):
+        """One step of the paper's predictor-corrector (eq:scheme): gas half
+        step and field staging, nsub particle sub-steps in the half-step
+        fields, gas full step with the corrector deposit."""
+        self.gas_predict(dt * nsub, model)
+        self.interp_push(dt, nsub)
+        return self.gas_correct(dt * nsub, model, totals)
 
     def run(self, dt: float, nsteps: int, sort_every: int = 0) -> None:
         """nsteps full steps replayed from a CUDA graph (sort cadence tuned when 0)."""
