@@ -42,6 +42,14 @@ PARTICLE_BYTES = {(3, "mixed"): 28, (2, "mixed"): 24, (3, "fp64"): 48, (2, "fp64
 # read-modify-written once (8 B each, twice)
 CELL_FIELD_BYTES = {"mixed": 24, "fp64": 48}
 CELL_DEPOSIT_BYTES = 8 * 8 * 2
+# per cell, algorithmic bytes of the coupled step's gas kernels (FP64 gas):
+# predictor reads rho, mom(3), egas, B(3) and the moments n, J (4 x int64),
+# writes the half state (8 doubles), the staged mixed fields (32 B) and clears
+# the next moments (4 x int64); corrector reads the corrector deposit
+# (4 x int64), the half state rho, mom(3), B(3) and the gas mom(3), egas, B(3),
+# writes mom, egas, B and clears the deposit (4 x int64)
+GAS_PREDICT_BYTES = 64 + 32 + 64 + 32 + 32
+GAS_CORRECT_BYTES = 32 + 56 + 56 + 56 + 32
 # DRAM bytes (read + write) per particle of one k_push_mixed<D, full> launch,
 # measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on a small
 # case of the current kernel version, a push that applies a sort (reads its
@@ -366,6 +374,52 @@ def run_native(args):
                        "E_max_n6": [float(a / b) if b > 0 else None for a, b in sums],
                        "lambda_abs_max": float(lam.abs().max().item())}
         del lam
+    # coupled MHD-PIC step (App. A.3, eq:scheme): gas predictor with the
+    # half-step field staging, push, gas corrector, sort at the cadence above;
+    # the plane-parallel linear MHD gas model where every box is x-periodic,
+    # else the CR sources alone
+    coupled = None
+    if args.coupled_steps > 0:
+        lin = all(b.bc[0] == 0 for b in boxes)
+        model = m.MHDPIC_GAS_LINEAR_X if lin else m.MHDPIC_GAS_SOURCES
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        t_pred = t_corr = t_all = 0.0
+        for k in range(2 + args.coupled_steps):
+            timed = k >= 2
+            if timed:
+                evs[0].record(stream)
+            eng.gas_predict(dt, model)
+            if timed:
+                evs[1].record(stream)
+            eng.interp_push(dt, 1)
+            if timed:
+                evs[2].record(stream)
+            eng.gas_correct(dt, model)
+            if timed:
+                evs[3].record(stream)
+            if args.sort_every and (k + 1) % args.sort_every == 0:
+                eng.sort()
+            if timed:
+                torch.cuda.synchronize()
+                t_pred += evs[0].elapsed_time(evs[1])
+                t_corr += evs[2].elapsed_time(evs[3])
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for k in range(args.coupled_steps):
+            eng.gas_predict(dt, model)
+            eng.interp_push(dt, 1)
+            eng.gas_correct(dt, model)
+            if args.sort_every and (k + 1) % args.sort_every == 0:
+                eng.sort()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_all = ev0.elapsed_time(ev1)
+        K = args.coupled_steps
+        coupled = {"model": "linear MHD along x" if lin else "CR sources only", "steps": K,
+                   "value": float(npart) * K / (t_all / 1e3), "unit": UNIT, "ms_per_step": t_all / K,
+                   "predict_ms": t_pred / K, "correct_ms": t_corr / K,
+                   "predict_gbs": ncell * GAS_PREDICT_BYTES / (t_pred / K / 1e3) / 1e9,
+                   "correct_gbs": ncell * GAS_CORRECT_BYTES / (t_corr / K / 1e3) / 1e9}
     flags = eng.status()
 
     # roofline of the push kernel (the dominant kernel)
@@ -378,7 +432,8 @@ def run_native(args):
     if args.workload in PUSH_TRAFFIC_BYTES_PER_PARTICLE:
         traffic = PUSH_TRAFFIC_BYTES_PER_PARTICLE[args.workload] * npart
     eng_stats = {"push_ms_per_step": push_ms / args.steps, "graph_run_ms_per_step": graph_ms,
-                 "subcycled": subcycled, "diagnostics": diagnostics, "particles": npart, "cells": ncell,
+                 "subcycled": subcycled, "diagnostics": diagnostics, "coupled": coupled,
+                 "particles": npart, "cells": ncell,
                  "dt": dt}
 
     # plain FP64 GPU path on the same boxes
@@ -505,6 +560,8 @@ def main(argv=None):
     ap.add_argument("--diagnostics", type=int, default=1, help="time the spectrum and Lambda map once")
     ap.add_argument("--nsub", type=int, default=5, help="particle sub-steps per call of the sub-cycled figure (<2: off)")
     ap.add_argument("--e2e-all-host", type=int, default=1, help="also time the all-host-buffer mode")
+    ap.add_argument("--coupled-steps", type=int, default=4,
+                    help="time the coupled predictor-corrector step this many steps (0: off)")
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--sample-n", type=int, default=40, help="side of the oracle's sample box")
     ap.add_argument("--err-n", type=int, default=24, help="side of the error-check box (0: skip)")
