@@ -54,7 +54,8 @@ typedef struct {
     int32_t n[3];   /* cells per dimension, n[2] = 1 in 2-D */
     double dx[3];   /* cell widths, dx[2] is the cell depth in 2-D */
     double x0[3];   /* lower corner */
-    int32_t bc[3];  /* 0 periodic, 1 reflecting walls on both faces */
+    int32_t bc[3];  /* 0 periodic, 1 reflecting walls on both faces, 2 a reflecting wall at the
+                       lower face and an open upper face (particles that cross it leave) */
 } orc_grid;
 
 typedef struct {
@@ -121,13 +122,20 @@ void orc_tsc_weights(double s, int64_t *i, double w[3])
     w[2] = 0.5 * (0.5 + delta) * (0.5 + delta);
 }
 
-/* Map a stencil cell index onto the grid: periodic wrap or mirror fold. */
+/* Map a stencil cell index onto the grid: periodic wrap or mirror fold; at an
+ * open face the cells beyond it take the values of the last cell (and receive
+ * its deposits). */
 static int64_t map_index(const orc_grid *g, int d, int64_t i)
 {
     int64_t n = g->n[d];
     if (g->bc[d] == 0) {
         int64_t r = i % n;
         return r < 0 ? r + n : r;
+    }
+    if (g->bc[d] == 2) {
+        if (i < 0)
+            i = -1 - i;
+        return i >= n ? n - 1 : i;
     }
     /* reflecting: cell -1-k mirrors cell k, cell n+k mirrors cell n-1-k */
     for (;;) {
@@ -202,13 +210,23 @@ void orc_deposit(const orc_grid *g, const double *xp, const double *q, int nq, d
 /* particle boundary                                                    */
 /* ------------------------------------------------------------------ */
 
-void orc_boundary(const orc_grid *g, double *xp, double *v)
+/*
+ * Particle boundary.  Periodic wrap; reflecting walls (specular); with bc 2 a
+ * reflecting wall at the lower face and an open upper face: a particle at or
+ * beyond the open face is put just inside it and the call returns 1 (the
+ * particle is leaving the box), else 0.
+ */
+int orc_boundary(const orc_grid *g, double *xp, double *v)
 {
+    int left = 0;
     for (int d = 0; d < g->ndim; ++d) {
         double lo = g->x0[d];
         double L = g->n[d] * g->dx[d];
         double hi = lo + L;
-        if (g->bc[d] == 0) {
+        if (g->bc[d] == 2 && xp[d] >= hi) {
+            xp[d] = nextafter(hi, lo);
+            left = 1;
+        } else if (g->bc[d] == 0) {
             double r = xp[d] - lo;
             r -= L * floor(r / L);
             if (r >= L)
@@ -228,6 +246,7 @@ void orc_boundary(const orc_grid *g, double *xp, double *v)
                 xp[d] = lo;
         }
     }
+    return left;
 }
 
 /* ------------------------------------------------------------------ */
@@ -285,6 +304,8 @@ void orc_deposit_moments(const orc_grid *g, const orc_params *p, int64_t np, con
     double dV = cell_volume(g);
     for (int64_t j = 0; j < np; ++j) {
         double xp[3] = {0, 0, 0}, vj[3];
+        if (isnan(x[j]))
+            continue;
         for (int d = 0; d < g->ndim; ++d)
             xp[d] = x[d * np + j];
         for (int d = 0; d < 3; ++d)
@@ -315,6 +336,12 @@ void orc_deposit_moments(const orc_grid *g, const orc_params *p, int64_t np, con
  * Moments deposit at x^(n+1): mom_dep += (n, J) of eq:nJCR.
  * corr holds 4 planes (Mx, My, Mz, E_k); mom_dep holds 4 planes (n, Jx, Jy, Jz).
  * Either deposit pointer may be NULL to skip it.
+ * A particle whose first coordinate is NaN is removed (it left the box through
+ * an open face) and is skipped.  A particle that reaches an open face at the
+ * half step is held just inside it for the gather and the corrector deposit;
+ * one that has reached it at the half or the full step is removed after its
+ * corrector deposit: no moments deposit, x[0] set to NaN and v to 0 (so that
+ * sums over the particles, such as orc_totals, leave it out).
  */
 void orc_push(const orc_grid *g, const orc_params *p, double dt, int64_t np, double *x, double *v,
               const double *E, const double *B, double *corr, double *mom_dep)
@@ -331,6 +358,8 @@ void orc_push(const orc_grid *g, const orc_params *p, double dt, int64_t np, dou
 
     for (int64_t j = 0; j < np; ++j) {
         double xp[3] = {0, 0, 0}, vn[3];
+        if (isnan(x[j]))
+            continue;
         for (int d = 0; d < g->ndim; ++d)
             xp[d] = x[d * np + j];
         for (int d = 0; d < 3; ++d)
@@ -340,7 +369,7 @@ void orc_push(const orc_grid *g, const orc_params *p, double dt, int64_t np, dou
         double g0 = orc_gamma(vn, C);
         for (int d = 0; d < g->ndim; ++d)
             xp[d] = xp[d] + 0.5 * dt * (vn[d] / g0);
-        orc_boundary(g, xp, vn);
+        int leaving = orc_boundary(g, xp, vn);
 
         /* fields at x^(n+1/2) */
         double f[6];
@@ -392,7 +421,13 @@ void orc_push(const orc_grid *g, const orc_params *p, double dt, int64_t np, dou
         /* drift to the full step */
         for (int d = 0; d < g->ndim; ++d)
             xp[d] = xp[d] + 0.5 * dt * (vnew[d] / g1);
-        orc_boundary(g, xp, vnew);
+        leaving |= orc_boundary(g, xp, vnew);
+        if (leaving) {
+            x[j] = NAN;
+            for (int d = 0; d < 3; ++d)
+                v[d * np + j] = 0.0;
+            continue;
+        }
 
         if (mom_dep) {
             double q[4];
@@ -506,6 +541,10 @@ void orc_cells_of(const orc_grid *g, int64_t np, const double *x, int32_t *cell)
 {
     for (int64_t j = 0; j < np; ++j) {
         int64_t idx[3] = {0, 0, 0};
+        if (isnan(x[j])) {   /* a removed particle */
+            cell[j] = -1;
+            continue;
+        }
         for (int d = 0; d < g->ndim; ++d) {
             int64_t i = (int64_t)floor((x[d * np + j] - g->x0[d]) / g->dx[d]);
             if (i < 0)
@@ -521,22 +560,25 @@ void orc_cells_of(const orc_grid *g, int64_t np, const double *x, int32_t *cell)
 /*
  * Stable counting sort of particles by key.  perm[r] = index of the particle
  * that goes to rank r; counts[key] = particles with that key (nkeys entries).
+ * Removed particles (cell -1) go after every key, in their input order.
  */
 void orc_sort_cells(const orc_grid *g, const int32_t brick[3], int64_t np, const int32_t *cell,
                     int64_t *perm, int64_t *counts)
 {
     int64_t nk = orc_sort_nkeys(g, brick);
-    int64_t *start = (int64_t *)calloc((size_t)nk + 1, sizeof(int64_t));
-    memset(counts, 0, sizeof(int64_t) * (size_t)nk);
+    int64_t *start = (int64_t *)calloc((size_t)nk + 2, sizeof(int64_t));
+    int64_t *cnt = (int64_t *)calloc((size_t)nk + 1, sizeof(int64_t));
     for (int64_t j = 0; j < np; ++j)
-        counts[orc_sort_key(g, brick, cell[j])] += 1;
-    for (int64_t k = 0; k < nk; ++k)
-        start[k + 1] = start[k] + counts[k];
+        cnt[cell[j] < 0 ? nk : orc_sort_key(g, brick, cell[j])] += 1;
+    for (int64_t k = 0; k <= nk; ++k)
+        start[k + 1] = start[k] + cnt[k];
     for (int64_t j = 0; j < np; ++j) {
-        int64_t k = orc_sort_key(g, brick, cell[j]);
+        int64_t k = cell[j] < 0 ? nk : orc_sort_key(g, brick, cell[j]);
         perm[start[k]++] = j;
     }
+    memcpy(counts, cnt, sizeof(int64_t) * (size_t)nk);
     free(start);
+    free(cnt);
 }
 
 /* ------------------------------------------------------------------ */
@@ -563,7 +605,7 @@ void orc_spectrum(const orc_grid *g, const orc_params *p, int64_t np, const doub
     memset(counts, 0, sizeof(int64_t) * (size_t)nbins);
     sums[0] = sums[1] = 0.0;
     for (int64_t j = 0; j < np; ++j) {
-        int inside = 1;
+        int inside = !isnan(x[j]);   /* removed particles are not counted */
         if (region)
             for (int d = 0; d < g->ndim; ++d) {
                 double xd = x[d * np + j];
