@@ -88,6 +88,12 @@ def _load():
             lib.orc_spectrum.argtypes = [G, Pp, ctypes.c_int64, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P,
                                          ctypes.c_int, _P, _P]
             lib.orc_lambda_map.argtypes = [G, Pp, _P, _P, _P, _P, _P]
+            lib.orc_philox.argtypes = [_P, _P, _P]
+            lib.orc_front.argtypes = [G, _P, _P, _P, _P, ctypes.c_double, _P]
+            lib.orc_inject.restype = ctypes.c_int64
+            lib.orc_inject.argtypes = [G, Pp, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32, _P, ctypes.c_int64,
+                                       _P, _P, _P, _P, _P]
             lib.orc_gas_rhs.argtypes = [G, ctypes.c_int, _P, _P, _P, _P, _P, _P]
             lib.orc_gas_predict.argtypes = [G, Pp, ctypes.c_int, ctypes.c_double] + [_P] * 13
             lib.orc_gas_correct.argtypes = [G, Pp, ctypes.c_int, ctypes.c_double] + [_P] * 11
@@ -282,6 +288,39 @@ def gas_rhs(g: Grid, model: int, rho, mom, B, H=None) -> tuple:
     dB = np.zeros_like(B)
     _load().orc_gas_rhs(ctypes.byref(g), int(model), _ptr(rho), _ptr(mom), _ptr(B), _ptr(H), _ptr(dmom), _ptr(dB))
     return dmom, dB
+
+
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x32-10 words of a 4-word counter under a 2-word key."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _load().orc_philox(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def front(g: Grid, rho, mom, egas, B, gamma_gas: float = 5.0 / 3.0) -> np.ndarray:
+    """Shock front along x: (x_s, x_t, rho_up, v_up), x_s NaN without a front."""
+    rho, mom, egas, B = _f64(rho), _f64(mom), _f64(egas), _f64(B)
+    out = np.zeros(4)
+    _load().orc_front(ctypes.byref(g), _ptr(rho), _ptr(mom), _ptr(egas), _ptr(B), float(gamma_gas), _ptr(out))
+    return out
+
+
+def inject(g: Grid, p: Params, fr, xs_prev: float, dt: float, eta: float, energy_factor: float, seed: int,
+           call: int, carry: float, cap: int, rho: np.ndarray, mom: np.ndarray, egas: np.ndarray) -> tuple:
+    """CR injection at the front fr (orc_front's output); the gas arrays are
+    updated in place.  Returns (x_new (ndim, N), v_new (3, N), carry)."""
+    fr = _f64(fr)
+    c = np.array([carry], dtype=np.float64)
+    xn = np.zeros((g.ndim, max(cap, 1)))
+    vn = np.zeros((3, max(cap, 1)))
+    for a in (rho, mom, egas):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    n = _load().orc_inject(ctypes.byref(g), ctypes.byref(p), _ptr(fr), float(xs_prev), float(dt), float(eta),
+                           float(energy_factor), int(seed), int(call) & 0xffffffff, _ptr(c), int(cap), _ptr(xn),
+                           _ptr(vn), _ptr(rho), _ptr(mom), _ptr(egas))
+    return xn[:, :n].copy(), vn[:, :n].copy(), float(c[0])
 
 
 class State:

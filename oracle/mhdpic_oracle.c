@@ -811,3 +811,231 @@ void orc_gas_correct(const orc_grid *g, const orc_params *p, int model, double d
     }
     memset(corr, 0, sizeof(double) * 4 * (size_t)nc);
 }
+
+/* ------------------------------------------------------------------ */
+/* shock front tracking and CR injection (Section 5)                    */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Counter-based random numbers: Philox4x32 with 10 rounds (Salmon, Moraes,
+ * Dror & Shaw 2011, "Parallel random numbers: as easy as 1, 2, 3").  A round
+ * multiplies words 0 and 2 by the two round multipliers, mixes the high
+ * halves with the other two words and the key, and the key advances by the
+ * two Weyl constants between rounds.
+ */
+static void philox4x32(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr_in[0], x1 = ctr_in[1], x2 = ctr_in[2], x3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * x0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * x2;
+        uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)p1;
+        uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)p0;
+        x0 = y0;
+        x1 = y1;
+        x2 = y2;
+        x3 = y3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = x0;
+    out[1] = x1;
+    out[2] = x2;
+    out[3] = x3;
+}
+
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    philox4x32(ctr, key, out);
+}
+
+/* A 32-bit random word as a double in (0, 1). */
+static double unit_open(uint32_t u)
+{
+    return ((double)u + 0.5) * (1.0 / 4294967296.0);
+}
+
+/*
+ * Shock front along x (Section 5): the transverse average of v_x = (rho v_x)/rho
+ * per x cell, smoothed with a Gaussian kernel of standard deviation 4 cells
+ * (truncated at 3 standard deviations and at the box ends, renormalised); the
+ * upstream value v_up is the smoothed value in the last cell (the inflow side);
+ * the front x_s is where, coming from upstream, the smoothed v_x first falls to
+ * 0.6 v_up in magnitude (linear interpolation between the two cell centres).
+ * The tail x_t is the centre of the first cell at or below the front cell,
+ * going downstream, whose smoothed pressure P = (gamma-1)(E - rho v^2/2 - B^2/2)
+ * reaches 2/3 of P1 = r/(r-1) rho_up v_up^2 (eq:rh, r = (gamma+1)/(gamma-1),
+ * rho_up the smoothed density of the last cell); x0 if none does.
+ * out = {x_s (NaN without a front), x_t, rho_up, v_up}.
+ */
+void orc_front(const orc_grid *g, const double *rho, const double *mom, const double *egas, const double *B,
+               double gamma_gas, double out[4])
+{
+    int64_t nx = g->n[0], nt = (int64_t)g->n[1] * g->n[2], nc = ncell_of(g);
+    double *pv = (double *)calloc((size_t)nx, sizeof(double));
+    double *pr = (double *)calloc((size_t)nx, sizeof(double));
+    double *pp = (double *)calloc((size_t)nx, sizeof(double));
+    for (int64_t t = 0; t < nt; ++t)
+        for (int64_t i = 0; i < nx; ++i) {
+            int64_t c = t * nx + i;
+            double r = rho[c];
+            double m[3] = {mom[c], mom[nc + c], mom[2 * nc + c]};
+            double b[3] = {B[c], B[nc + c], B[2 * nc + c]};
+            pv[i] += m[0] / r;
+            pr[i] += r;
+            pp[i] += (gamma_gas - 1.0) * (egas[c] - 0.5 * dot3(m, m) / r - 0.5 * dot3(b, b));
+        }
+    for (int64_t i = 0; i < nx; ++i) {
+        pv[i] /= (double)nt;
+        pr[i] /= (double)nt;
+        pp[i] /= (double)nt;
+    }
+    double *sv = (double *)calloc((size_t)nx, sizeof(double));
+    double *sr = (double *)calloc((size_t)nx, sizeof(double));
+    double *sp = (double *)calloc((size_t)nx, sizeof(double));
+    const double sig = 4.0;
+    const int half = 12;
+    for (int64_t i = 0; i < nx; ++i) {
+        double ws = 0.0, a = 0.0, b = 0.0, c = 0.0;
+        for (int k = -half; k <= half; ++k) {
+            int64_t j = i + k;
+            if (j < 0 || j >= nx)
+                continue;
+            double w = exp(-0.5 * (double)(k * k) / (sig * sig));
+            ws += w;
+            a += w * pv[j];
+            b += w * pr[j];
+            c += w * pp[j];
+        }
+        sv[i] = a / ws;
+        sr[i] = b / ws;
+        sp[i] = c / ws;
+    }
+    double vup = sv[nx - 1], rup = sr[nx - 1];
+    double thr = 0.6 * fabs(vup);
+    double xs = NAN;
+    int64_t is = -1;
+    if (vup != 0.0)
+        for (int64_t i = nx - 2; i >= 0; --i)
+            if (fabs(sv[i]) <= thr) {
+                /* crossing between centres i and i+1 */
+                double a = fabs(sv[i]), b = fabs(sv[i + 1]);
+                double f = (thr - a) / (b - a);
+                xs = g->x0[0] + ((double)i + 0.5 + f) * g->dx[0];
+                is = i;
+                break;
+            }
+    double xt = g->x0[0];
+    if (is >= 0) {
+        double r = (gamma_gas + 1.0) / (gamma_gas - 1.0);
+        double P1 = r / (r - 1.0) * rup * vup * vup;
+        for (int64_t i = is; i >= 0; --i)
+            if (sp[i] >= (2.0 / 3.0) * P1) {
+                xt = g->x0[0] + ((double)i + 0.5) * g->dx[0];
+                break;
+            }
+    }
+    out[0] = xs;
+    out[1] = xt;
+    out[2] = rup;
+    out[3] = vup;
+    free(pv);
+    free(pr);
+    free(pp);
+    free(sv);
+    free(sr);
+    free(sp);
+}
+
+/*
+ * CR injection at the front (Section 5).  front = {x_s, x_t, rho_up, v_up} of
+ * orc_front; xs_prev the front of the previous call (NaN for none) gives the
+ * front speed V = (x_s - xs_prev)/dt (0 without one).  The gas mass swept in
+ * this step is rho_up (|v_up| + max(V, 0)) dt A (A the box's cross-section);
+ * eta of it becomes CR particles of mass m_CR: N = floor(eta M / m_CR + carry),
+ * the remainder carried to the next call.  Particle k gets the Philox words of
+ * counter (k, call, 0, 0) and key (seed_lo, seed_hi): x = x_s, the transverse
+ * coordinates uniform over the box, a direction uniform on the sphere
+ * (cos theta = 2u - 1, phi = 2 pi u'), and kinetic energy per unit mass
+ * E_k = energy_factor E_sh, E_sh = v_up^2/2, in the frame of the front
+ * (gamma' = 1 + E_k/C^2, |v'| = C sqrt(gamma'^2 - 1)); its four-velocity is
+ * boosted to the box by V along x (v_x = Gamma (v'_x + V gamma')).  The gas
+ * gives the injected mass, momentum (m sum v) and energy (m sum E_k) evenly
+ * from the cells whose centres lie in [x_t, x_s) (the front's own cell column
+ * when there are none).  New particles go to x_new[d*cap + k], v_new[d*cap + k]
+ * for k < N <= cap.  Returns N (0 without a front).
+ */
+int64_t orc_inject(const orc_grid *g, const orc_params *p, const double front[4], double xs_prev, double dt,
+                   double eta, double energy_factor, uint64_t seed, uint32_t call, double *carry, int64_t cap,
+                   double *x_new, double *v_new, double *rho, double *mom, double *egas)
+{
+    double xs = front[0], xt = front[1], rup = front[2], vup = front[3];
+    if (isnan(xs))
+        return 0;
+    double V = isnan(xs_prev) ? 0.0 : (xs - xs_prev) / dt;
+    double A = 1.0;
+    for (int d = 1; d < 3; ++d)
+        A *= (d < g->ndim ? g->n[d] * g->dx[d] : g->dx[d]);
+    double M = rup * (fabs(vup) + (V > 0.0 ? V : 0.0)) * dt * A;
+    double want = eta * M / p->m_cr + *carry;
+    int64_t N = (int64_t)floor(want);
+    *carry = want - (double)N;
+    if (N > cap)
+        N = cap;
+    const double C = p->C;
+    double Ek = energy_factor * 0.5 * vup * vup;
+    double gp = 1.0 + Ek / (C * C);
+    double vmag = C * sqrt(gp * gp - 1.0);
+    double Gam = 1.0 / sqrt(1.0 - V * V / (C * C));
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    double Pin[3] = {0.0, 0.0, 0.0}, Ein = 0.0;
+    for (int64_t k = 0; k < N; ++k) {
+        uint32_t ctr[4] = {(uint32_t)k, call, 0u, 0u}, u[4];
+        philox4x32(ctr, key, u);
+        x_new[k] = xs;
+        if (g->ndim >= 2)
+            x_new[cap + k] = g->x0[1] + unit_open(u[0]) * g->n[1] * g->dx[1];
+        if (g->ndim == 3)
+            x_new[2 * cap + k] = g->x0[2] + unit_open(u[1]) * g->n[2] * g->dx[2];
+        double mu = 2.0 * unit_open(u[2]) - 1.0;
+        double ph = 6.283185307179586 * unit_open(u[3]);   /* 2 pi */
+        double st = sqrt(1.0 - mu * mu);
+        double vv[3] = {vmag * mu, vmag * st * cos(ph), vmag * st * sin(ph)};
+        vv[0] = Gam * (vv[0] + V * gp);
+        for (int d = 0; d < 3; ++d) {
+            v_new[d * cap + k] = vv[d];
+            Pin[d] += p->m_cr * vv[d];
+        }
+        Ein += p->m_cr * orc_kinetic_energy(vv, C);
+    }
+    /* compensation: the gas gives what the particles take */
+    int64_t nx = g->n[0], nt = (int64_t)g->n[1] * g->n[2], nc = ncell_of(g);
+    int64_t i0 = -1, i1 = -1;
+    for (int64_t i = 0; i < nx; ++i) {
+        double xc = g->x0[0] + ((double)i + 0.5) * g->dx[0];
+        if (xc >= xt && xc < xs) {
+            if (i0 < 0)
+                i0 = i;
+            i1 = i;
+        }
+    }
+    if (i0 < 0) {
+        i0 = i1 = (int64_t)floor((xs - g->x0[0]) / g->dx[0]);
+        if (i0 >= nx)
+            i0 = i1 = nx - 1;
+    }
+    double Vreg = (double)((i1 - i0 + 1) * nt) * cell_volume(g);
+    double Min = (double)N * p->m_cr;
+    for (int64_t t = 0; t < nt; ++t)
+        for (int64_t i = i0; i <= i1; ++i) {
+            int64_t c = t * nx + i;
+            rho[c] -= Min / Vreg;
+            for (int d = 0; d < 3; ++d)
+                mom[d * nc + c] -= Pin[d] / Vreg;
+            egas[c] -= Ein / Vreg;
+        }
+    return N;
+}

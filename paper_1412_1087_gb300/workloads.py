@@ -8,7 +8,8 @@ bit-identical states.
 Units are the paper's code units (Section 5): rho0 = B0 = (q/mc) = 1, so the
 Alfven speed is 1, and the factor c is absorbed into E and J (Section 2.2).
 
-Layout of one box (all arrays are numpy, C-contiguous):
+Layout of one box (all arrays are numpy, C-contiguous; a particle slot with
+cell -1 is free, for boxes with an open face):
 
 * cells are numbered ``c = (k*ny + j)*nx + i`` (x fastest);
 * gas: ``rho[nc]``, ``mom[3, nc]`` (momentum density rho*v), ``egas[nc]``
@@ -36,6 +37,7 @@ import numpy as np
 
 PERIODIC = 0
 REFLECT = 1
+WALL_OPEN = 2   # conducting wall at the lower face, open upper face
 
 # Particles are drawn in fixed-size chunks so that large boxes do not need a
 # full set of float64 temporaries; the chunk size is part of the recipe.
@@ -130,6 +132,7 @@ def absolute_positions(box: Box) -> np.ndarray:
     x = np.empty((box.ndim, box.np), dtype=np.float64)
     for d in range(box.ndim):
         x[d] = box.x0[d] + (coords[d].astype(np.float64) + box.off[d].astype(np.float64)) * box.dx[d]
+    x[0, c < 0] = np.nan   # a free slot (cell -1): no particle
     return x
 
 
@@ -411,6 +414,53 @@ def shock_2d(seed: int = 0, nx: int = 16384, ny: int = 128, ppc: float = 40.0,
     dt = choose_dt(part[2], C, 1.0, 1.0, 1.0)
     return _make_box("shock_2d", 2, nn, (REFLECT, PERIODIC, PERIODIC), gas, part, 1.0, 1.0, C,
                      _mass(1e-3, 1.0, 1.0, 1.0, 1.0, ppc), 0, dt, nsteps)
+
+
+def shock_front_2d(seed: int = 0, nx: int = 1024, ny: int = 32, ppc: float = 8.0, front: float = 0.25,
+                   v0: float = 20.0, free_frac: float = 0.25, nsteps: int = 100) -> Box:
+    """The shock box with open inflow (Section 5) and a shocked gas profile.
+
+    2-D nx x ny, conducting wall at x = 0 and an open (inflow) face at
+    x = nx (MHDPIC_BC_WALL_OPEN along x), y periodic.  Upstream of the front
+    (x >= front nx) the gas is rho0 = 1, v = (-v0, 0, 0), P0 = 1; downstream it
+    is the strong-shock state of eq:rh in the downstream frame: rho1 = 4,
+    v = 0, P1 = (4/3) rho0 v0^2 (gamma = 5/3, r = 4).  B = x_hat.  CRs as in
+    the shock-shaped load (dN/dp ~ p^-2 on [1, 1e5], C = 200), ppc per cell on
+    average with 80% in the 5% of cells nearest the wall; a fraction free_frac
+    of the particle slots (at the end) is free for injected particles.
+    """
+    rng = _rng(seed)
+    nn = (nx, ny, 1)
+    nc = nx * ny
+    B = np.zeros((3, nc))
+    B[0] = 1.0
+    xf = front * nx
+    xc = np.tile(np.arange(nx, dtype=np.float64) + 0.5, ny)
+    down = xc < xf
+    dv = np.zeros((3, nc))
+    dv[0] = np.where(down, 0.0, -v0)
+    rho, mom, egas, Bc = _gas(nn, 1.0, (0.0, 0.0, 0.0), B, 1.0, 5.0 / 3.0, dv=dv)
+    rho = np.where(down, 4.0, 1.0)
+    mom = np.ascontiguousarray(rho * dv)
+    P = np.where(down, 4.0 / 3.0 * v0 * v0, 1.0)
+    egas = P / (5.0 / 3.0 - 1.0) + 0.5 * rho * (dv * dv).sum(axis=0) + 0.5 * (Bc * Bc).sum(axis=0)
+    C = 200.0
+    total = int(round(ppc * nc))
+    n_dense = int(round(0.8 * total))
+    xw = 0.05 * nx
+    a = _particles_uniform(rng, nn, 2, n_dense, lo=0.0, hi=xw, kind="power", C=C, prange=(1.0, 1e5))
+    b = _particles_uniform(rng, nn, 2, total - n_dense, lo=xw, hi=float(nx), kind="power", C=C,
+                           prange=(1.0, 1e5))
+    cell = np.concatenate([a[0], b[0]])
+    off = np.concatenate([a[1], b[1]], axis=1)
+    p = np.concatenate([a[2], b[2]], axis=1)
+    nfree = int(round(free_frac * total))
+    cell = np.concatenate([cell, np.full(nfree, -1, dtype=np.int32)])
+    off = np.ascontiguousarray(np.concatenate([off, np.zeros((2, nfree), dtype=np.float32)], axis=1))
+    p = np.ascontiguousarray(np.concatenate([p, np.zeros((3, nfree), dtype=np.float32)], axis=1))
+    dt = choose_dt(p[:, :total], C, 1.0, 1.0, 1.0)
+    return _make_box("shock_front_2d", 2, nn, (WALL_OPEN, PERIODIC, PERIODIC), (rho, mom, egas, Bc),
+                     (cell, off, p), 1.0, 1.0, C, _mass(1e-3, 1.0, 1.0, 1.0, 1.0, ppc), 0, dt, nsteps)
 
 
 def ensemble_2d(nbox: int = 96, seed0: int = 0, side_lo: int = 32, side_span: float = 16.0,

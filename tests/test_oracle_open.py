@@ -96,3 +96,136 @@ def test_lower_face_is_still_a_reflecting_wall():
     assert xp[0] == 0.25 and vp[0] == 3.0
     xp, vp = orc.boundary(g, [box.n[0] * box.dx[0] + 0.1, 1.5], [3.0, 1.0, 0.0])
     assert xp[0] < box.n[0] * box.dx[0] and vp[0] == 3.0   # held inside, not reflected
+
+
+# ---------------------------------------------------------------------------
+# random numbers, front tracking and injection (Section 5)
+# ---------------------------------------------------------------------------
+
+def test_counter_based_words_are_uniform_and_independent():
+    """Statistical pins of the counter-based generator: uniform words,
+    independent counters and keys, and full avalanche on a counter bit."""
+    key = [12345, 678]
+    words = np.array([orc.philox([k, 7, 0, 0], key) for k in range(4096)], dtype=np.uint64)
+    u = (words.astype(np.float64) + 0.5) / 2.0 ** 32
+    assert abs(u.mean() - 0.5) < 0.01 and abs(u.var() - 1.0 / 12.0) < 0.005
+    hist = np.histogram(u.ravel(), bins=64, range=(0.0, 1.0))[0]
+    chi2 = ((hist - hist.mean()) ** 2 / hist.mean()).sum()
+    assert chi2 < 120.0                                     # 63 degrees of freedom
+    r = np.corrcoef(u[:-1, 0], u[1:, 0])[0, 1]
+    assert abs(r) < 0.06
+    # a different key or call gives a different stream
+    assert not np.array_equal(orc.philox([5, 7, 0, 0], key), orc.philox([5, 7, 0, 0], [12346, 678]))
+    assert not np.array_equal(orc.philox([5, 7, 0, 0], key), orc.philox([5, 8, 0, 0], key))
+    # flipping one counter bit changes about half of the 128 output bits
+    flips = []
+    for b in range(32):
+        a = orc.philox([1000, 3, 0, 0], key)
+        c = orc.philox([1000 ^ (1 << b), 3, 0, 0], key)
+        flips.append(sum(bin(int(x) ^ int(y)).count("1") for x, y in zip(a, c)))
+    assert 48 < np.mean(flips) < 80
+
+
+def _shock(nx=256, ny=8, **kw):
+    return wl.shock_front_2d(nx=nx, ny=ny, **kw)
+
+
+def test_front_of_a_sharp_shock_is_the_smoothed_step_crossing():
+    """A sharp jump of v_x from 0 to -v0 at the face x = f: smoothed with a
+    Gaussian of 4 cells it falls to 0.6 v0 where Phi((x - f)/4) = 0.6, i.e.
+    x_s = f + 0.2533 * 4 cells; the pressure step reaches 2/3 P1 where
+    Phi = 1/3, x = f - 0.4307 * 4, and x_t is the first cell centre at or
+    below that."""
+    box = _shock(nx=256, ny=8, front=0.25)
+    g = orc.grid_of(box)
+    xs, xt, rup, vup = orc.front(g, box.rho, box.mom, box.egas, box.B)
+    f = 0.25 * 256
+    assert abs(xs - (f + 0.2533 * 4.0)) < 0.02
+    xt_expect = np.floor(f - 0.4307 * 4.0 - 0.5) + 0.5
+    assert xt == xt_expect
+    assert rup == 1.0 and vup == -20.0
+    # no front in a uniform inflow
+    box.mom[0] = -20.0 * box.rho
+    xs2 = orc.front(g, box.rho * 0 + 1.0, np.ascontiguousarray(np.vstack([np.full(box.ncell, -20.0),
+                                                                          box.mom[1:]])),
+                    box.egas, box.B)[0]
+    assert np.isnan(xs2)
+
+
+def test_injection_conserves_momentum_energy_and_mass_and_places_particles():
+    box = _shock(nx=256, ny=8, front=0.25)
+    g, p = orc.grid_of(box), orc.params_of(box)
+    fr = orc.front(g, box.rho, box.mom, box.egas, box.B)
+    rho, mom, egas = box.rho.copy(), box.mom.copy(), box.egas.copy()
+    dV = box.dx[0] * box.dx[1] * box.dx[2]
+    gas0 = (rho.sum() * dV, mom.sum(axis=1) * dV, egas.sum() * dV)
+    eta, fE = 0.2, 10.0
+    xn, vn, carry = orc.inject(g, p, fr, np.nan, box.dt, eta, fE, 99, 0, 0.0, 100000, rho, mom, egas)
+    N = xn.shape[1]
+    assert N > 100
+    gam = np.sqrt(1.0 + (vn ** 2).sum(axis=0) / box.C ** 2)
+    Ek = (vn ** 2).sum(axis=0) / (gam + 1.0)
+    # static front: every particle has E_k = 10 E_sh, E_sh = v_up^2 / 2
+    np.testing.assert_allclose(Ek, fE * 0.5 * fr[3] ** 2, rtol=1e-12)
+    # at the front, spread over the box in y, isotropic
+    assert np.all(xn[0] == fr[0])
+    assert xn[1].min() >= 0.0 and xn[1].max() < box.n[1] * box.dx[1]
+    mu = vn[0] / np.sqrt((vn ** 2).sum(axis=0))
+    assert abs(mu.mean()) < 4.0 / np.sqrt(N) and abs((mu ** 2).mean() - 1.0 / 3.0) < 4.0 / np.sqrt(N)
+    # the gas gives exactly what the particles take
+    m = p.m_cr
+    np.testing.assert_allclose(rho.sum() * dV, gas0[0] - N * m, rtol=1e-13)
+    np.testing.assert_allclose(mom.sum(axis=1) * dV + m * vn.sum(axis=1), gas0[1], rtol=1e-13, atol=1e-9)
+    np.testing.assert_allclose(egas.sum() * dV + m * Ek.sum(), gas0[2], rtol=1e-13)
+    # the cells that gave are those between x_t and x_s
+    changed = np.where(rho != box.rho)[0] % box.n[0]
+    xc = changed + 0.5
+    assert np.all((xc >= fr[1]) & (xc < fr[0]))
+
+
+def test_injected_count_follows_the_swept_mass_over_many_calls():
+    """N = floor(eta M / m + carry) per call: over many calls the total is the
+    floor of eta times the total swept mass over m (the carry is exact)."""
+    box = _shock(nx=128, ny=4, front=0.5)
+    g, p = orc.grid_of(box), orc.params_of(box)
+    fr = orc.front(g, box.rho, box.mom, box.egas, box.B)
+    eta = 0.01
+    rho, mom, egas = box.rho.copy(), box.mom.copy(), box.egas.copy()
+    carry, total = 0.0, 0
+    calls = 40
+    for call in range(calls):
+        xn, vn, carry = orc.inject(g, p, fr, fr[0], box.dt, eta, 10.0, 5, call, carry, 1 << 20, rho, mom, egas)
+        total += xn.shape[1]
+    A = box.n[1] * box.dx[1] * box.dx[2]
+    M = fr[2] * abs(fr[3]) * box.dt * A * calls
+    assert total == int(np.floor(eta * M / p.m_cr + 1e-9)) or total == int(np.floor(eta * M / p.m_cr - 1e-9))
+    assert 0.0 <= carry < 1.0
+    # a front advancing at V into the inflow sweeps rho (|v_up| + V) A per unit time
+    V = 5.0
+    carry, total = 0.0, 0
+    for call in range(calls):
+        xn, vn, carry = orc.inject(g, p, fr, fr[0] - V * box.dt, box.dt, eta, 10.0, 5, call, carry, 1 << 20,
+                                   rho, mom, egas)
+        total += xn.shape[1]
+    M = fr[2] * (abs(fr[3]) + V) * box.dt * A * calls
+    assert abs(total - eta * M / p.m_cr) < 1.0 + 1e-6
+
+
+def test_moving_front_boosts_the_injected_particles():
+    """With the front moving at V the injection energy holds in the front's
+    frame: boosting the four-velocity back by -V gives E_k = 10 E_sh."""
+    box = _shock(nx=256, ny=8, front=0.25)
+    g, p = orc.grid_of(box), orc.params_of(box)
+    fr = orc.front(g, box.rho, box.mom, box.egas, box.B)
+    V = 7.0
+    xs_prev = fr[0] - V * box.dt
+    xn, vn, _ = orc.inject(g, p, fr, xs_prev, box.dt, 0.2, 10.0, 3, 1, 0.0, 100000, box.rho.copy(),
+                           box.mom.copy(), box.egas.copy())
+    C = box.C
+    Vf = (fr[0] - xs_prev) / box.dt
+    G = 1.0 / np.sqrt(1.0 - Vf * Vf / C ** 2)
+    gam = np.sqrt(1.0 + (vn ** 2).sum(axis=0) / C ** 2)
+    vx_rest = G * (vn[0] - Vf * gam)
+    vr = np.vstack([vx_rest, vn[1], vn[2]])
+    gr = np.sqrt(1.0 + (vr ** 2).sum(axis=0) / C ** 2)
+    np.testing.assert_allclose((vr ** 2).sum(axis=0) / (gr + 1.0), 10.0 * 0.5 * fr[3] ** 2, rtol=1e-9)
