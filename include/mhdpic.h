@@ -66,6 +66,15 @@ extern "C" {
 /* ---- enumerations ---- */
 #define MHDPIC_BC_PERIODIC 0
 #define MHDPIC_BC_REFLECT 1 /* conducting wall: specular particle reflection, mirror-folded stencil */
+/* conducting wall at the lower face, open (inflow) upper face, as the paper's
+ * shock box along x (Section 5): a particle that reaches the open face is held
+ * just inside it for its gather and corrector deposit, then leaves the box;
+ * stencil cells beyond the open face take the last cell's fields and deposits.
+ * Only for single-box contexts.  A particle that left is marked (MIXED:
+ * cell = -1; FP64: x[0] = NaN; four-velocity 0) and dropped to the end of the
+ * particle arrays by the next mhdpic_sort; mhdpic_live_particles counts the
+ * rest, and the free slots at the end take injected particles. */
+#define MHDPIC_BC_WALL_OPEN 2
 #define MHDPIC_SHAPE_TSC 2  /* triangular-shaped cloud (quadratic spline), Section 3 */
 #define MHDPIC_PREC_FP64 0  /* all particle arithmetic in double */
 #define MHDPIC_PREC_MIXED 1 /* int32 cell + f32 offset, f32 push, int64 fixed-point deposits */
@@ -85,6 +94,7 @@ extern "C" {
 #define MHDPIC_ST_OVERFLOW 4u   /* a fixed-point deposit exceeded its headroom */
 #define MHDPIC_ST_SORT_CAP 8u   /* a cell held more particles than the sort's segment limit */
 #define MHDPIC_ST_CELL_RANGE 16u/* a particle's cell index was outside its box */
+#define MHDPIC_ST_INJECT_CAP 32u/* mhdpic_inject ran out of free particle slots */
 
 typedef struct mhdpic_ctx mhdpic_ctx;
 
@@ -95,7 +105,7 @@ typedef struct {
     int32_t n[3];  /* cells per dimension */
     double dx[3];  /* cell widths (> 0) */
     double x0[3];  /* lower corner of the box */
-    int32_t bc[3]; /* MHDPIC_BC_PERIODIC or MHDPIC_BC_REFLECT, per dimension */
+    int32_t bc[3]; /* MHDPIC_BC_PERIODIC, MHDPIC_BC_REFLECT or MHDPIC_BC_WALL_OPEN, per dimension */
 } mhdpic_grid;
 
 /* Physical parameters of one box (Sections 2.2, App. A.1). */
@@ -260,6 +270,54 @@ int mhdpic_deposit(mhdpic_ctx *ctx);
  *   the stream to return them.
  */
 int mhdpic_apply_feedback(mhdpic_ctx *ctx, double *totals_out);
+
+/*
+ * mhdpic_live_particles - number of particles that have not left the box
+ * through an open face (MHDPIC_BC_WALL_OPEN), counted over the current state.
+ *   live_out  host int64
+ * Synchronises the stream.
+ */
+int mhdpic_live_particles(mhdpic_ctx *ctx, int64_t *live_out);
+
+/*
+ * mhdpic_inject - shock front tracking and CR injection (Section 5), for a
+ * single box with MHDPIC_BC_WALL_OPEN along x (the wall at x0, the inflow
+ * face at the far end).
+ *   front: the transverse average of v_x = (rho v_x)/rho per x cell, smoothed
+ *   with a Gaussian of standard deviation 4 cells (truncated at 3 standard
+ *   deviations and at the box ends, renormalised); v_up, rho_up are the
+ *   smoothed values of the last (inflow) cell; x_s is where, coming from
+ *   upstream, |v_x| first falls to 0.6 |v_up| (linear interpolation between
+ *   cell centres); the tail x_t is the centre of the first cell at or below
+ *   the front cell whose smoothed pressure P = (gamma-1)(egas - rho v^2/2 -
+ *   B^2/2) reaches 2/3 of P1 = r/(r-1) rho_up v_up^2 (eq:rh,
+ *   r = (gamma+1)/(gamma-1)), x0 if none.
+ *   injection: the gas mass swept in this step, rho_up (|v_up| + max(V, 0))
+ *   dt A (A the box cross-section, V the front speed since the previous call,
+ *   0 on the first), times eta, becomes CR particles of mass m_CR; the
+ *   fraction of a particle left over is carried to the next call.  Particle
+ *   k sits at x = x_s, uniform across the box, with an isotropic direction
+ *   and kinetic energy per unit mass energy_factor * v_up^2/2 in the frame of
+ *   the front (the paper: 10 E_sh), boosted by V along x.  Random numbers:
+ *   Philox4x32-10, counter (k, call number, 0, 0), key = seed.
+ *   compensation: the gas gives the injected mass, momentum (m_CR sum v) and
+ *   energy (m_CR sum E_k) evenly from the cells with centres in [x_t, x_s)
+ *   (the front's cell column when there are none), so gas + CR momentum and
+ *   energy are unchanged.
+ * The new particles take the free slots (particles that left the box, or
+ * caller slots marked free: cell -1 / x NaN); when they run out the count is
+ * cut and MHDPIC_ST_INJECT_CAP is raised.  The call sorts before and after
+ * injecting (the next push applies the sort); the charge/current deposit is
+ * not redone (mhdpic_deposit does).  Without a front nothing is injected.
+ *   dt, eta, energy_factor, gamma_gas  as above (dt > 0, eta >= 0)
+ *   seed       key of the random numbers
+ *   front_out  host double[2] {x_s (NaN without a front), x_t} or NULL
+ *   ninj_out   host int64, particles injected, or NULL
+ * Synchronises the stream.  Errors: MHDPIC_E_ARG for a context that is not a
+ * single box with MHDPIC_BC_WALL_OPEN along x, or bad arguments.
+ */
+int mhdpic_inject(mhdpic_ctx *ctx, double dt, double eta, double energy_factor, double gamma_gas, uint64_t seed,
+                  double *front_out, int64_t *ninj_out);
 
 /* ---- gas models of the coupled step ---- */
 #define MHDPIC_GAS_SOURCES 0   /* the gas changes by the CR sources alone; B is held */

@@ -26,7 +26,8 @@ __device__ __forceinline__ int find_box(const int64_t *__restrict__ starts, int 
 }
 
 // Map an unwrapped cell coordinate g along dimension d onto the box: periodic
-// wrap, or mirror fold at a reflecting wall (cell -1-k mirrors cell k).
+// wrap, or mirror fold at a reflecting wall (cell -1-k mirrors cell k); beyond
+// an open face the cells take the last cell's values (and deposits).
 __device__ __forceinline__ int map_coord(int g, int n, int bc)
 {
     if (bc == MHDPIC_BC_PERIODIC) {
@@ -34,6 +35,11 @@ __device__ __forceinline__ int map_coord(int g, int n, int bc)
             return g;
         int r = g % n;
         return r < 0 ? r + n : r;
+    }
+    if (bc == MHDPIC_BC_WALL_OPEN) {
+        if (g < 0)
+            g = -1 - g;
+        return g >= n ? n - 1 : g;
     }
     for (int it = 0; it < 64; ++it) {
         if (g < 0)
@@ -44,6 +50,16 @@ __device__ __forceinline__ int map_coord(int g, int n, int bc)
             return g;
     }
     return 0;
+}
+
+// A particle that left the box through an open face: cell -1 in mixed
+// precision, a NaN first coordinate in FP64 (its four-velocity is 0).
+constexpr int32_t DEAD_CELL = -1;
+
+template <int PREC>
+__device__ __forceinline__ bool particle_dead(const Ctx &c, int64_t i)
+{
+    return PREC == MHDPIC_PREC_MIXED ? c.cell[i] == DEAD_CELL : isnan(c.x[i]);
 }
 
 __device__ __forceinline__ void set_status(uint32_t *status, uint32_t flag)

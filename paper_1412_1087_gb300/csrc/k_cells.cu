@@ -151,6 +151,8 @@ __global__ void k_moments(Ctx c, int cur)
     const int64_t nc = c.nc;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.np;
          i += (int64_t)gridDim.x * blockDim.x) {
+        if (particle_dead<PREC>(c, i))   // left the box
+            continue;
         int bx = find_box(c.box_part_start, c.nbox, i);
         const BoxDev &b = c.boxes[bx];
         int ci[3] = {0, 0, 0};

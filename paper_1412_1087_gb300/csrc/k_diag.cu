@@ -39,6 +39,8 @@ __global__ void __launch_bounds__(SPEC_THREADS) k_spectrum_partial(Ctx c, SpecAr
     const int64_t p0 = b.part0 + chunk * ps, p1 = min(b.part1, p0 + ps);
     double s1 = 0.0, s0 = 0.0;
     for (int64_t i = p0 + threadIdx.x; i < p1; i += SPEC_THREADS) {
+        if (particle_dead<PREC>(c, i))   // left the box
+            continue;
         if (a.has_region) {
             bool inside = true;
             if (PREC == MHDPIC_PREC_MIXED) {

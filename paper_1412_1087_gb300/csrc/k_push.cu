@@ -109,11 +109,21 @@ __device__ __forceinline__ float push_one_f64(const Ctx &c, const BoxDev &b, con
         x[d] = c.src_x[d * np + src];
     for (int d = 0; d < 3; ++d)
         v[d] = c.src_p64[d * np + src];
+    if (isnan(x[0])) {   // left the box earlier (kept until the next sort)
+        for (int d = 0; d < D; ++d)
+            c.x[d * np + j] = x[d];
+        for (int d = 0; d < 3; ++d)
+            c.p64[d * np + j] = 0.0;
+        return 0.f;
+    }
 
+    // a particle at an open face is held just inside it, deposits its
+    // corrector and then leaves
     double g0 = sqrt(C * C + (v[0] * v[0] + v[1] * v[1] + v[2] * v[2])) / C;
+    bool leaving = false;
     for (int d = 0; d < D; ++d) {
         x[d] = x[d] + 0.5 * k.dt * (v[d] / g0);
-        boundary_f64(b, d, x[d], v[d]);
+        leaving |= boundary_f64(b, d, x[d], v[d]);
     }
 
     int ci[3] = {0, 0, 0}, rel[3] = {0, 0, 0};
@@ -174,7 +184,15 @@ __device__ __forceinline__ float push_one_f64(const Ctx &c, const BoxDev &b, con
 
     for (int d = 0; d < D; ++d) {
         x[d] = x[d] + 0.5 * k.dt * (vn[d] / g1);
-        boundary_f64(b, d, x[d], vn[d]);
+        leaving |= boundary_f64(b, d, x[d], vn[d]);
+    }
+    if (leaving) {   // removed: no moments deposit; the next sort drops it
+        c.x[j] = __longlong_as_double(0x7ff8000000000000ll);
+        for (int d = 1; d < D; ++d)
+            c.x[d * np + j] = x[d];
+        for (int d = 0; d < 3; ++d)
+            c.p64[d * np + j] = 0.0;
+        return 0.f;
     }
     if (FULL) {
         int ci2[3] = {0, 0, 0}, rel2[3] = {0, 0, 0};

@@ -124,6 +124,27 @@ __device__ __forceinline__ void gather_tile(const Ctx &c, int base, const Wts &w
         }
 }
 
+// An opaque register copy: the value is materialised here, once, and every
+// later use reads these bits.  The deposit's inputs (TSC weights, scaled
+// quantities) go through it, so that the inlined tile path and the global
+// path cannot each recompute them with a different contraction of the same
+// expression: the integers a particle deposits must not depend on the path.
+__device__ __forceinline__ float pinned(float x)
+{
+    asm volatile("" : "+f"(x));
+    return x;
+}
+
+__device__ __forceinline__ void pin_weights(Wts &w)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        w.x[a] = pinned(w.x[a]);
+        w.y[a] = pinned(w.y[a]);
+        w.z[a] = pinned(w.z[a]);
+    }
+}
+
 struct F6 {
     float e[3], b[3];
 };
@@ -366,16 +387,28 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
                                           int *sD, unsigned long long *mout)
 {
     const int64_t np = c.np;
+    if (pin.cell == DEAD_CELL) {   // left the box earlier (kept until the next sort)
+        c.cell[j] = DEAD_CELL;
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+            c.off[d * np + j] = 0.f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            c.p[d * np + j] = 0.f;
+        return 0.f;
+    }
     int ci[3];
     decode_cell(b, pin.cell, ci);
     float o[3] = {pin.o[0], pin.o[1], pin.o[2]}, v[3] = {pin.v[0], pin.v[1], pin.v[2]};
 
-    // drift to x^(n+1/2) with u = v / gamma
+    // drift to x^(n+1/2) with u = v / gamma (a particle at an open face is
+    // held just inside it, deposits its corrector and then leaves)
     const float ign = rsqrtf(fmaf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2], k.invC2, 1.f));
+    bool leaving = false;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
         o[d] = fmaf(k.hdx[d] * ign, v[d], o[d]);
-        renorm_mixed(b, d, ci[d], o[d], v[d], c.status);
+        leaving |= renorm_mixed(b, d, ci[d], o[d], v[d], c.status);
     }
 
     Wts w;
@@ -391,6 +424,7 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
         in_tile &= tile_rel(c, b, gm, 2, ci[2], rel[2]);
         tsc_from_offset<float>(o[2], w.z);
     }
+    pin_weights(w);
     const int base = (rel[0] - 1) + c.ts[1] * (rel[1] - 1) + (D == 3 ? c.ts[2] * (rel[2] - 1) : 0);
 
     float E[3], Bf[3];
@@ -435,9 +469,11 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
     const float dEk = (e0 * (vn[0] + v10) + e1 * (vn[1] + v11) + e2 * (vn[2] + v12)) / (g2 + g1) +
                       (e0 * (v00 + v[0]) + e1 * (v01 + v[1]) + e2 * (v02 + v[2])) / (g1 + gn);
     {
-        const float qc[4] = {-k.m * (2.f * e0 + r0), -k.m * (2.f * e1 + r1), -k.m * (2.f * e2 + r2), -k.m * dEk};
+        const float qc[4] = {pinned(-k.m * (2.f * e0 + r0)), pinned(-k.m * (2.f * e1 + r1)),
+                             pinned(-k.m * (2.f * e2 + r2)), pinned(-k.m * dEk)};
         if (within(qc, k.qb, CH_MX)) {
-            const float qs[4] = {qc[0] * k.st[0], qc[1] * k.st[1], qc[2] * k.st[2], qc[3] * k.st[3]};
+            const float qs[4] = {pinned(qc[0] * k.st[0]), pinned(qc[1] * k.st[1]), pinned(qc[2] * k.st[2]),
+                                 pinned(qc[3] * k.st[3])};
             if (in_tile)
                 deposit_tile<D>(c, base, w, qs, CH_MX, sD);
             else
@@ -453,7 +489,17 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
 #pragma unroll
     for (int d = 0; d < D; ++d) {
         o[d] = fmaf(k.hdx[d] * ig2, vn[d], o[d]);
-        renorm_mixed(b, d, ci[d], o[d], vn[d], c.status);
+        leaving |= renorm_mixed(b, d, ci[d], o[d], vn[d], c.status);
+    }
+    if (leaving) {   // removed: no moments deposit; the next sort drops it
+        c.cell[j] = DEAD_CELL;
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+            c.off[d * np + j] = 0.f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            c.p[d * np + j] = 0.f;
+        return 0.f;
     }
 
     if (FULL) {
@@ -470,10 +516,12 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
             in2 &= tile_rel(c, b, gm, 2, ci[2], rel2[2]);
             tsc_from_offset<float>(o[2], w2.z);
         }
+        pin_weights(w2);
         const float qj = k.qn * ig2;
-        const float qm[4] = {k.qn, qj * vn[0], qj * vn[1], qj * vn[2]};
+        const float qm[4] = {pinned(k.qn), pinned(qj * vn[0]), pinned(qj * vn[1]), pinned(qj * vn[2])};
         if (within(qm, k.qb, CH_N)) {
-            const float qs[4] = {qm[0] * k.st[4], qm[1] * k.st[5], qm[2] * k.st[6], qm[3] * k.st[7]};
+            const float qs[4] = {pinned(qm[0] * k.st[4]), pinned(qm[1] * k.st[5]), pinned(qm[2] * k.st[6]),
+                                 pinned(qm[3] * k.st[7])};
             if (in2) {
                 const int base2 = (rel2[0] - 1) + c.ts[1] * (rel2[1] - 1) + (D == 3 ? c.ts[2] * (rel2[2] - 1) : 0);
                 deposit_tile<D>(c, base2, w2, qs, CH_N, sD);

@@ -46,15 +46,18 @@ __global__ void k_sort_keys(Ctx c, int32_t *__restrict__ count, int32_t *__restr
         int bx = find_box(c.box_part_start, c.nbox, i);
         const BoxDev &b = c.boxes[bx];
         int ci[3] = {0, 0, 0};
+        bool dead = false;
         if (PREC == MHDPIC_PREC_MIXED) {
             int32_t cl = c.cell[i];
-            if (cl < 0 || cl >= b.ncell) {
+            dead = cl == DEAD_CELL;
+            if (!dead && (cl < 0 || cl >= b.ncell)) {
                 set_status(c.status, MHDPIC_ST_CELL_RANGE);
                 cl = cl < 0 ? 0 : (int32_t)(b.ncell - 1);
             }
             decode_cell(b, cl, ci);
         } else {
-            for (int d = 0; d < c.ndim; ++d) {
+            dead = isnan(c.x[i]);
+            for (int d = 0; d < c.ndim && !dead; ++d) {
                 double s = (c.x[(int64_t)d * c.np + i] - b.x0[d]) / b.dx[d];
                 double f = floor(s);
                 int v = f < 0.0 ? 0 : (f >= (double)b.n[d] ? b.n[d] - 1 : (int)f);
@@ -65,7 +68,8 @@ __global__ void k_sort_keys(Ctx c, int32_t *__restrict__ count, int32_t *__restr
         }
         for (int d = 0; d < 3; ++d)   // defensive: a key outside the box would index out of range
             ci[d] = ci[d] < 0 ? 0 : (ci[d] >= b.n[d] ? b.n[d] - 1 : ci[d]);
-        int32_t key = (int32_t)brick_key(b, c.brick, ci[0], ci[1], ci[2]);
+        // particles that left the box share one key after all the others
+        int32_t key = dead ? (int32_t)c.nkeys : (int32_t)brick_key(b, c.brick, ci[0], ci[1], ci[2]);
         // runs of equal keys in consecutive lanes (the input is nearly
         // sorted) take one atomic per run; the rank inside the run is the
         // lane offset
@@ -499,7 +503,7 @@ int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *
                 cudaStream_t st)
 {
     int launches = 0;
-    cudaMemsetAsync(s.count, 0, sizeof(int32_t) * (c.nkeys + 1), st);
+    cudaMemsetAsync(s.count, 0, sizeof(int32_t) * (c.nkeys + 2), st);
     if (c.np > 0) {
         if (c.prec == MHDPIC_PREC_MIXED)
             k_sort_keys<MHDPIC_PREC_MIXED><<<grid_for(c.np, 256), 256, 0, st>>>(c, s.count, s.pkey, s.pslot);
@@ -507,7 +511,9 @@ int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *
             k_sort_keys<MHDPIC_PREC_FP64><<<grid_for(c.np, 256), 256, 0, st>>>(c, s.count, s.pkey, s.pslot);
         ++launches;
     }
-    launches += scan(s.count, c.nkeys, s.offset, s.scan_tmp, st);
+    // key nkeys holds the particles that left the box: offset[nkeys] is the
+    // number of live particles
+    launches += scan(s.count, c.nkeys + 1, s.offset, s.scan_tmp, st);
     if (c.np > 0) {
         cudaMemsetAsync(s.perm, 0, sizeof(int32_t) * c.np, st);
         k_sort_scatter<<<grid_for(c.np, 256), 256, 0, st>>>(c.np, s.pkey, s.pslot, s.offset, s.perm, c.status);
@@ -559,6 +565,62 @@ int launch_gather(const Ctx &c, const int32_t *perm, const PSet &src, const PSet
         add(src.p64, dst.p64, 8, 3);
     }
     k_gather_all<<<grid_for(c.np, 256), 256, 0, st>>>(c.np, perm, pl);
+    return 1;
+}
+
+namespace {
+
+// Mark the slots [offset[nkeys], np) of the current set as free: after a push
+// that applied a sort they still hold the states of an older step.
+template <int PREC>
+__global__ void k_mark_free(Ctx c, const int32_t *__restrict__ offset)
+{
+    const int64_t live = offset[c.nkeys];
+    for (int64_t j = live + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < c.np;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (PREC == MHDPIC_PREC_MIXED) {
+            c.cell[j] = DEAD_CELL;
+            for (int d = 0; d < 3; ++d)
+                c.p[(int64_t)d * c.np + j] = 0.f;
+        } else {
+            c.x[j] = __longlong_as_double(0x7ff8000000000000ll);
+            for (int d = 0; d < 3; ++d)
+                c.p64[(int64_t)d * c.np + j] = 0.0;
+        }
+    }
+}
+
+__global__ void k_count_live(Ctx c, int prec, unsigned long long *out)
+{
+    unsigned long long n = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.np;
+         i += (int64_t)gridDim.x * blockDim.x)
+        n += prec == MHDPIC_PREC_MIXED ? (c.cell[i] != DEAD_CELL) : !isnan(c.x[i]);
+    for (int o = 16; o > 0; o >>= 1)
+        n += __shfl_xor_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0 && n)
+        atomicAdd(out, n);
+}
+
+}  // namespace
+
+int launch_mark_free(const Ctx &c, const SortScratch &s, cudaStream_t st)
+{
+    if (c.np <= 0)
+        return 0;
+    if (c.prec == MHDPIC_PREC_MIXED)
+        k_mark_free<MHDPIC_PREC_MIXED><<<grid_for(c.np, 256), 256, 0, st>>>(c, s.offset);
+    else
+        k_mark_free<MHDPIC_PREC_FP64><<<grid_for(c.np, 256), 256, 0, st>>>(c, s.offset);
+    return 1;
+}
+
+int launch_count_live(const Ctx &c, unsigned long long *out, cudaStream_t st)
+{
+    cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+    if (c.np <= 0)
+        return 0;
+    k_count_live<<<grid_for(c.np, 256), 256, 0, st>>>(c, c.prec, out);
     return 1;
 }
 

@@ -94,6 +94,11 @@ struct mhdpic_ctx {
     int64_t graph_launches = 0;   // kernel launches inside one replay
     int step_in_cycle = 0;        // steps since the last sort done by mhdpic_run
     int tuned_k = 0;
+    bool has_open = false;   // a box has an open face: particles can leave
+    void *inj_state = nullptr;      // device injection state
+    double *inj_scratch = nullptr;
+    uint32_t inj_calls = 0;
+    unsigned long long *live_dev = nullptr;
     // coupled step: half state of the last mhdpic_gas_predict
     double *gas_half = nullptr;
     bool half_valid = false;
@@ -293,8 +298,10 @@ int validate(int32_t nbox, const mhdpic_grid *grids, const mhdpic_params *params
                 return fail(MHDPIC_E_ARG, "box %d: n[%d] must be >= 1", b, d);
             if (!(g.dx[d] > 0.0) || !std::isfinite(g.dx[d]) || !std::isfinite(g.x0[d]))
                 return fail(MHDPIC_E_ARG, "box %d: dx[%d] must be finite and > 0", b, d);
-            if (g.bc[d] != MHDPIC_BC_PERIODIC && g.bc[d] != MHDPIC_BC_REFLECT)
+            if (g.bc[d] != MHDPIC_BC_PERIODIC && g.bc[d] != MHDPIC_BC_REFLECT && g.bc[d] != MHDPIC_BC_WALL_OPEN)
                 return fail(MHDPIC_E_ARG, "box %d: unknown boundary %d", b, g.bc[d]);
+            if (g.bc[d] == MHDPIC_BC_WALL_OPEN && nbox != 1)
+                return fail(MHDPIC_E_ARG, "MHDPIC_BC_WALL_OPEN needs a single-box context");
         }
         if (ndim == 2 && g.n[2] != 1)
             return fail(MHDPIC_E_ARG, "box %d: a 2-D box must have n[2] == 1", b);
@@ -489,7 +496,7 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
     if (rc)
         return bail(rc);
     int64_t scan_n = std::max<int64_t>(k.nkeys, k.nbricks_total) / 4096 + 2;
-    if ((rc = c->alloc(&c->s.count, k.nkeys + 1)) || (rc = c->alloc(&c->s.offset, k.nkeys + 1)) ||
+    if ((rc = c->alloc(&c->s.count, k.nkeys + 2)) || (rc = c->alloc(&c->s.offset, k.nkeys + 2)) ||
         (rc = c->alloc(&c->s.pkey, np)) || (rc = c->alloc(&c->s.pslot, np)) || (rc = c->alloc(&c->s.perm, np)) ||
         (rc = c->alloc(&c->s.scan_tmp, scan_n)) || (rc = c->alloc(&c->s.big_list, k.nkeys + 1)) ||
         (rc = c->alloc(&c->s.big_count, 1)) ||
@@ -602,6 +609,9 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         return bail(rc);
     if ((rc = copy_particles(c, false)))
         return bail(rc);
+    for (int b = 0; b < nbox; ++b)
+        for (int d = 0; d < 3; ++d)
+            c->has_open |= grids[b].bc[d] == MHDPIC_BC_WALL_OPEN;
     c->valid = true;
     *out = c;
     return MHDPIC_OK;
@@ -671,6 +681,8 @@ int mhdpic_interp_push(mhdpic_ctx *c, double dt, int32_t nsub)
         if (gather) {
             use_set(c, c->cur_set ^ 1);
             c->pending = false;
+            if (c->has_open && (rc = check_launch(c, launch_mark_free(c->k, c->s, c->stream))))
+                return rc;
         }
         // re-sort between sub-steps (the next sub-step applies it)
         if (!last && c->sub_sort_every > 0 && (s + 1) % c->sub_sort_every == 0) {
@@ -719,6 +731,86 @@ int mhdpic_apply_feedback(mhdpic_ctx *c, double *totals_out)
                            c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
+    return MHDPIC_OK;
+}
+
+int mhdpic_inject(mhdpic_ctx *c, double dt, double eta, double energy_factor, double gamma_gas, uint64_t seed,
+                  double *front_out, int64_t *ninj_out)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (c->nbox != 1 || c->boxes[0].bc[0] != MHDPIC_BC_WALL_OPEN)
+        return fail(MHDPIC_E_ARG, "mhdpic_inject needs a single box with MHDPIC_BC_WALL_OPEN along x");
+    if (!(dt > 0.0) || !std::isfinite(dt) || !(eta >= 0.0) || !std::isfinite(eta) || !(energy_factor > 0.0) ||
+        !std::isfinite(energy_factor) || !(gamma_gas > 1.0) || !std::isfinite(gamma_gas))
+        return fail(MHDPIC_E_ARG, "dt, eta, energy_factor and gamma_gas must be finite with dt > 0, eta >= 0, "
+                                  "energy_factor > 0, gamma_gas > 1");
+    int rc;
+    const int64_t nx = c->boxes[0].n[0];
+    if (!c->inj_state) {
+        std::vector<unsigned char> img(inject_state_bytes());
+        init_inject_state(img.data());
+        if ((rc = c->alloc(reinterpret_cast<unsigned char **>(&c->inj_state), img.size())) ||
+            (rc = c->alloc(&c->inj_scratch, inject_scratch_doubles(nx))))
+            return rc;
+        CK(cudaMemcpyAsync(c->inj_state, img.data(), img.size(), cudaMemcpyHostToDevice, c->stream));
+    }
+    if ((rc = copy_particles(c, true)) || (rc = copy_gas(c, true, true)))
+        return rc;
+    // free slots to the end: slot live + k of the sorted order is particle
+    // perm[live + k] of the current set
+    if ((rc = check_launch(c, launch_sort(c->k, c->s, nullptr, nullptr, c->stream))))
+        return rc;
+    c->pending = true;
+    if ((rc = check_launch(c, launch_inject(c->k, c->s, c->inj_state, c->inj_scratch, nx, dt, eta, energy_factor,
+                                            gamma_gas, seed, c->inj_calls, c->stream))))
+        return rc;
+    ++c->inj_calls;
+    // the new particles into their cells
+    if ((rc = check_launch(c, launch_sort(c->k, c->s, nullptr, nullptr, c->stream))) ||
+        (rc = check_launch(c, launch_max_count(c->k, c->s, c->stream))))
+        return rc;
+    std::vector<unsigned char> img(inject_state_bytes());
+    CK(cudaMemcpyAsync(img.data(), c->inj_state, img.size(), cudaMemcpyDeviceToHost, c->stream));
+    if (c->mem != MHDPIC_MEM_DEVICE) {
+        CK(cudaMemcpyAsync(c->hg.rho, c->k.rho, sizeof(double) * c->k.nc, cudaMemcpyDeviceToHost, c->stream));
+        if ((rc = copy_gas(c, false, false)))
+            return rc;
+    }
+    if (c->mem == MHDPIC_MEM_HOST && ((rc = materialize(c)) || (rc = copy_particles(c, false))))
+        return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    double fr[2];
+    int64_t n = 0;
+    int capped = 0;
+    inject_outputs(img.data(), fr, &n, &capped);
+    (void)capped;   // also raised on the device as MHDPIC_ST_INJECT_CAP
+    if (front_out) {
+        front_out[0] = fr[0];
+        front_out[1] = fr[1];
+    }
+    if (ninj_out)
+        *ninj_out = n;
+    return MHDPIC_OK;
+}
+
+int mhdpic_live_particles(mhdpic_ctx *c, int64_t *live_out)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (!live_out)
+        return fail(MHDPIC_E_ARG, "live_out must be non-NULL");
+    int rc;
+    if (!c->live_dev && (rc = c->alloc(&c->live_dev, 1)))
+        return rc;
+    if ((rc = copy_particles(c, true)))
+        return rc;
+    if ((rc = check_launch(c, launch_count_live(c->k, c->live_dev, c->stream))))
+        return rc;
+    unsigned long long n = 0;
+    CK(cudaMemcpyAsync(&n, c->live_dev, sizeof(n), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *live_out = (int64_t)n;
     return MHDPIC_OK;
 }
 

@@ -179,6 +179,10 @@ int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *
 // dst[j] = src[perm[j]] for every particle plane
 int launch_gather(const Ctx &c, const int32_t *perm, const PSet &src, const PSet &dst, cudaStream_t st);
 int launch_max_count(const Ctx &c, const SortScratch &s, cudaStream_t st);
+// after a push that applied a sort: slots past the live particles marked free
+int launch_mark_free(const Ctx &c, const SortScratch &s, cudaStream_t st);
+// number of particles that have not left the box (into out, device)
+int launch_count_live(const Ctx &c, unsigned long long *out, cudaStream_t st);
 int launch_vmax(const Ctx &c, cudaStream_t st);
 int launch_prep(const Ctx &c, int cur, int apply, cudaStream_t st);
 int launch_moments(const Ctx &c, int cur, cudaStream_t st);
@@ -203,6 +207,16 @@ int launch_spectrum(const Ctx &c, const SpecArgs &a, int nchunks, unsigned long 
 int launch_lambda(const Ctx &c, int cur, double *out, cudaStream_t st);
 // coupled step (App. A.3): gas half state into half[8][nc] plus field
 // staging; gas full step from the half state and the corrector deposit
+// shock front and CR injection (single box, open x face): the device state
+// (inject_state_bytes, initialised from init_inject_state's host image), the
+// scratch (inject_scratch_doubles(nx) doubles), the host view of the outputs
+size_t inject_state_bytes();
+void init_inject_state(void *st_host);
+size_t inject_scratch_doubles(int64_t nx);
+void inject_outputs(const void *st_host, double front[2], int64_t *n, int *capped);
+int launch_inject(const Ctx &c, const SortScratch &s, void *state, double *scratch, int64_t nx, double dt,
+                  double eta, double energy_factor, double gamma_gas, uint64_t seed, uint32_t call,
+                  cudaStream_t st);
 int launch_gas_predict(const Ctx &c, int cur, double dt, int model, double *half, cudaStream_t st);
 int launch_gas_correct(const Ctx &c, double dt, int model, const double *half, cudaStream_t st);
 

@@ -69,8 +69,9 @@ __device__ __forceinline__ int64_t tile_global(const Ctx &c, const BoxDev &b, co
 
 // Mixed representation: move the offset back into [0,1), carrying whole
 // cells, then apply the particle boundary (periodic wrap, or specular
-// reflection, which flips v[d]).
-__device__ __forceinline__ void renorm_mixed(const BoxDev &b, int d, int &ci, float &o, float &vd,
+// reflection, which flips v[d]).  At an open face the particle is held just
+// inside it and the call returns true (the particle is leaving the box).
+__device__ __forceinline__ bool renorm_mixed(const BoxDev &b, int d, int &ci, float &o, float &vd,
                                              uint32_t *status)
 {
     float f = floorf(o);
@@ -87,10 +88,15 @@ __device__ __forceinline__ void renorm_mixed(const BoxDev &b, int d, int &ci, fl
     }
     int n = b.n[d];
     if (ci >= 0 && ci < n)
-        return;
+        return false;
     if (b.bc[d] == MHDPIC_BC_PERIODIC) {
         ci = map_coord(ci, n, MHDPIC_BC_PERIODIC);
-        return;
+        return false;
+    }
+    if (b.bc[d] == MHDPIC_BC_WALL_OPEN && ci >= n) {
+        ci = n - 1;
+        o = 0x1.fffffep-1f;
+        return true;
     }
     // reflecting wall: position s = ci + o mirrors to -s or 2n - s
     if (ci < 0) {
@@ -117,14 +123,20 @@ __device__ __forceinline__ void renorm_mixed(const BoxDev &b, int d, int &ci, fl
         set_status(status, MHDPIC_ST_FAST_MOVER);
         ci = ci < 0 ? 0 : n - 1;
     }
+    return false;
 }
 
-// FP64 representation: the oracle's boundary rule on absolute positions.
-__device__ __forceinline__ void boundary_f64(const BoxDev &b, int d, double &x, double &vd)
+// FP64 representation: the oracle's boundary rule on absolute positions;
+// true when the particle reached an open face (it is held just inside).
+__device__ __forceinline__ bool boundary_f64(const BoxDev &b, int d, double &x, double &vd)
 {
     double lo = b.x0[d];
     double L = b.n[d] * b.dx[d];
     double hi = lo + L;
+    if (b.bc[d] == MHDPIC_BC_WALL_OPEN && x >= hi) {
+        x = nextafter(hi, lo);
+        return true;
+    }
     if (b.bc[d] == MHDPIC_BC_PERIODIC) {
         double r = x - lo;
         if (r < 0.0 || r >= L)
@@ -145,6 +157,7 @@ __device__ __forceinline__ void boundary_f64(const BoxDev &b, int d, double &x, 
         if (x < lo)
             x = lo;
     }
+    return false;
 }
 
 // Neighbour cells of a stencil along each dimension (global path).

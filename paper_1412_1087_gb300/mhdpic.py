@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(HERE, "libmhdpic.so")
 MHDPIC_OK = 0
 MHDPIC_BC_PERIODIC = 0
 MHDPIC_BC_REFLECT = 1
+MHDPIC_BC_WALL_OPEN = 2
 MHDPIC_SHAPE_TSC = 2
 MHDPIC_PREC_FP64 = 0
 MHDPIC_PREC_MIXED = 1
@@ -36,7 +37,7 @@ MHDPIC_SPEC_MOMENTUM = 1
 MHDPIC_SPEC_MAX_BINS = 2048
 MHDPIC_GAS_SOURCES = 0
 MHDPIC_GAS_LINEAR_X = 1
-STATUS_NAMES = {1: "FAST_MOVER", 2: "NONFINITE", 4: "OVERFLOW", 8: "SORT_CAP", 16: "CELL_RANGE"}
+STATUS_NAMES = {1: "FAST_MOVER", 2: "NONFINITE", 4: "OVERFLOW", 8: "SORT_CAP", 16: "CELL_RANGE", 32: "INJECT_CAP"}
 
 
 class MhdpicError(RuntimeError):
@@ -79,6 +80,9 @@ SIGNATURES = {
     "mhdpic_interp_push": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32]),
     "mhdpic_deposit": (ctypes.c_int, [_V]),
     "mhdpic_apply_feedback": (ctypes.c_int, [_V, _V]),
+    "mhdpic_live_particles": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int64)]),
+    "mhdpic_inject": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_uint64, _V, ctypes.POINTER(ctypes.c_int64)]),
     "mhdpic_gas_predict": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32]),
     "mhdpic_gas_correct": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32, _V]),
     "mhdpic_run": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32, ctypes.c_int32]),
@@ -157,6 +161,21 @@ def mhdpic_apply_feedback(ctx, totals_out: Optional[np.ndarray] = None) -> None:
         assert totals_out.dtype == np.float64 and totals_out.flags["C_CONTIGUOUS"]
         ptr = totals_out.ctypes.data_as(ctypes.c_void_p)
     _check(load().mhdpic_apply_feedback(ctx, ptr))
+
+
+def mhdpic_live_particles(ctx) -> int:
+    n = ctypes.c_int64(0)
+    _check(load().mhdpic_live_particles(ctx, ctypes.byref(n)))
+    return int(n.value)
+
+
+def mhdpic_inject(ctx, dt: float, eta: float, energy_factor: float = 10.0, gamma_gas: float = 5.0 / 3.0,
+                  seed: int = 0) -> tuple:
+    fr = np.zeros(2, dtype=np.float64)
+    n = ctypes.c_int64(0)
+    _check(load().mhdpic_inject(ctx, float(dt), float(eta), float(energy_factor), float(gamma_gas),
+                                int(seed) & 0xffffffffffffffff, fr.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)))
+    return int(n.value), float(fr[0]), float(fr[1])
 
 
 def mhdpic_gas_predict(ctx, dt: float, model: int) -> None:
@@ -388,6 +407,14 @@ class Engine:
     def step(self, dt: float, nsub: int = 1) -> None:
         self.interp_push(dt, nsub)
         self.apply_feedback(False)
+
+    def live_particles(self) -> int:
+        return mhdpic_live_particles(self.ctx)
+
+    def inject(self, dt: float, eta: float, energy_factor: float = 10.0, gamma_gas: float = 5.0 / 3.0,
+               seed: int = 0) -> tuple:
+        """Front tracking and CR injection (Section 5): returns (n, x_s, x_t)."""
+        return mhdpic_inject(self.ctx, dt, eta, energy_factor, gamma_gas, seed)
 
     def gas_predict(self, dt: float, model: int) -> None:
         mhdpic_gas_predict(self.ctx, dt, model)
