@@ -76,6 +76,10 @@ WORKLOADS = {
                "C=300, CR-Hall term on",
     "shock_2d": "2-D 16384x128 grid, reflecting x walls, 40 CR/cell average with 80% in the 5% of cells "
                 "nearest the wall, upstream v=-20 v_A, dN/dp ~ p^-2 on [1, 1e5], C=200",
+    "shock_front_2d": "2-D 16384x128 grid, conducting wall at x=0 and open inflow face, shocked gas (front at "
+                      "x=4096: rho 4, v 0, P1=(4/3) rho0 v0^2 behind it; rho0 1, v=-20 v_A ahead), 40 CR/cell "
+                      "average with 80% in the 5% of cells nearest the wall, 25% free slots, dN/dp ~ p^-2 on "
+                      "[1, 1e5], C=200; CR injection at the tracked front (eta 2e-3, 10 E_sh) timed apart",
     "ensemble_2d": "96 independent 2-D periodic boxes, sides log-uniform in [32, 512], 4-64 CR/cell, "
                    "dB/B0 in [0, 0.3], |p|=10, C=100, advanced together",
     "periodic_thermal_2d": "2-D periodic 64^2 grid, 16 CR/cell, uniform gas, B along x, |p|=10, C=100",
@@ -91,6 +95,8 @@ def _workload(args, seed):
         boxes = [wl.bell_2d(seed=seed, n=args.n2d)]
     elif args.workload == "shock_2d":
         boxes = [wl.shock_2d(seed=seed)]
+    elif args.workload == "shock_front_2d":
+        boxes = [wl.shock_front_2d(seed=seed, nx=16384, ny=128, ppc=40.0, front=0.25)]
     elif args.workload == "ensemble_2d":
         boxes = wl.ensemble_2d(nbox=96, seed0=seed * 1000)
     else:
@@ -223,6 +229,10 @@ def _sample_box(args, seed, size):
     if args.workload == "shock_2d":
         nx, ny = (2048, 32) if big else (512, 16)
         return wl.shock_2d(seed=seed, nx=nx, ny=ny), "%d x %d, 40 CR/cell average" % (nx, ny)
+    if args.workload == "shock_front_2d":
+        nx, ny = (2048, 32) if big else (512, 16)
+        return (wl.shock_front_2d(seed=seed, nx=nx, ny=ny, ppc=40.0, front=0.25),
+                "%d x %d, 40 CR/cell average" % (nx, ny))
     if args.workload == "ensemble_2d":
         side = 256 if big else 64
         b = wl.ensemble_2d(nbox=1, seed0=seed * 1000, max_side=side)[0]
@@ -239,9 +249,10 @@ def _cpu_baseline(args, seed, nsteps):
     for _ in range(nsteps):
         st.step(box.dt)
     dt = time.perf_counter() - t0
-    return {"value": box.np * nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    live = int((box.cell >= 0).sum())
+    return {"value": live * nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%s recipe at %s (%d CRs), %d full steps, single thread"
-                      % (args.workload, what, box.np, nsteps), "seconds": dt}
+                      % (args.workload, what, live, nsteps), "seconds": dt}
 
 
 def _error_vs_oracle(args, seed, torch):
@@ -290,7 +301,7 @@ def run_native(args):
     m.load()
     dev = "cuda:%d" % lrank
     boxes, dt = _workload(args, seed=rank)
-    npart = sum(b.np for b in boxes)
+    npart = sum(int((b.cell >= 0).sum()) for b in boxes)   # particles, not free slots
     ncell = sum(b.ncell for b in boxes)
     ndim = boxes[0].ndim
     stream = torch.cuda.Stream(device=dev)
@@ -420,6 +431,32 @@ def run_native(args):
                    "predict_ms": t_pred / K, "correct_ms": t_corr / K,
                    "predict_gbs": ncell * GAS_PREDICT_BYTES / (t_pred / K / 1e3) / 1e9,
                    "correct_gbs": ncell * GAS_CORRECT_BYTES / (t_corr / K / 1e3) / 1e9}
+    # shock boxes (open inflow face): front tracking and CR injection each
+    # step (Section 5), timed apart; every call sorts before and after
+    injection = None
+    if args.inject_steps > 0 and all(b.bc[0] == 2 for b in boxes) and len(boxes) == 1:
+        eta = 2e-3
+        for _ in range(2):
+            eng.interp_push(dt, 1)
+            eng.apply_feedback(False)
+            eng.inject(dt, eta, 10.0, 5.0 / 3.0, 11)
+        torch.cuda.synchronize()
+        t_inj = 0.0
+        n_inj = 0
+        front = None
+        for _ in range(args.inject_steps):
+            eng.interp_push(dt, 1)
+            eng.apply_feedback(False)
+            ev0.record(stream)
+            n, xs, xt = eng.inject(dt, eta, 10.0, 5.0 / 3.0, 11)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            t_inj += ev0.elapsed_time(ev1)
+            n_inj += n
+            front = (xs, xt)
+        injection = {"calls": args.inject_steps, "ms_per_call": t_inj / args.inject_steps,
+                     "particles_per_call": n_inj / args.inject_steps, "eta": eta, "energy_factor": 10.0,
+                     "front_x": front[0], "tail_x": front[1], "live_particles": eng.live_particles()}
     flags = eng.status()
 
     # roofline of the push kernel (the dominant kernel)
@@ -433,6 +470,7 @@ def run_native(args):
         traffic = PUSH_TRAFFIC_BYTES_PER_PARTICLE[args.workload] * npart
     eng_stats = {"push_ms_per_step": push_ms / args.steps, "graph_run_ms_per_step": graph_ms,
                  "subcycled": subcycled, "diagnostics": diagnostics, "coupled": coupled,
+                 "injection": injection,
                  "particles": npart, "cells": ncell,
                  "dt": dt}
 
@@ -531,8 +569,9 @@ def run_reference(args):
     for _ in range(args.steps):
         st.step(box.dt)
     dt = time.perf_counter() - t0
-    value = box.np * args.steps / dt
-    sample = "FP64 CPU oracle, %s recipe at %s (%d CRs) per step, single thread" % (args.workload, what, box.np)
+    live = int((box.cell >= 0).sum())
+    value = live * args.steps / dt
+    sample = "FP64 CPU oracle, %s recipe at %s (%d CRs) per step, single thread" % (args.workload, what, live)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -560,6 +599,8 @@ def main(argv=None):
     ap.add_argument("--diagnostics", type=int, default=1, help="time the spectrum and Lambda map once")
     ap.add_argument("--nsub", type=int, default=5, help="particle sub-steps per call of the sub-cycled figure (<2: off)")
     ap.add_argument("--e2e-all-host", type=int, default=1, help="also time the all-host-buffer mode")
+    ap.add_argument("--inject-steps", type=int, default=4,
+                    help="time front tracking + injection this many calls on shock boxes (0: off)")
     ap.add_argument("--coupled-steps", type=int, default=4,
                     help="time the coupled predictor-corrector step this many steps (0: off)")
     ap.add_argument("--cpu-steps", type=int, default=3)
