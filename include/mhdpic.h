@@ -306,7 +306,8 @@ int mhdpic_live_particles(mhdpic_ctx *ctx, int64_t *live_out);
  *   energy are unchanged.
  * The new particles take the free slots (particles that left the box, or
  * caller slots marked free: cell -1 / x NaN); when they run out the count is
- * cut and MHDPIC_ST_INJECT_CAP is raised.  The call sorts before and after
+ * cut and MHDPIC_ST_INJECT_CAP is raised.  The call sorts before (unless a
+ * sort is pending: its order is used) and after
  * injecting (the next push applies the sort); the charge/current deposit is
  * not redone (mhdpic_deposit does).  Without a front nothing is injected.
  *   dt, eta, energy_factor, gamma_gas  as above (dt > 0, eta >= 0)

@@ -43,10 +43,10 @@ __device__ __forceinline__ void cross(const double a[3], const double b[3], doub
 // Neighbour along x (s = -1 or +1) of global cell g inside box b, x periodic.
 __device__ __forceinline__ int64_t x_neighbour(const BoxDev &b, int64_t g, int s)
 {
-    const int64_t loc = g - b.cell0;
-    const int64_t nx = b.n[0];
-    const int64_t i = loc % nx;
-    const int64_t j = i + s < 0 ? nx - 1 : (i + s >= nx ? 0 : i + s);
+    const uint32_t loc = (uint32_t)(g - b.cell0);   // a box has < 2^31 cells
+    const int nx = b.n[0];
+    const int i = (int)(loc - fdiv(loc, b.div_nx) * (uint32_t)nx);
+    const int j = i + s < 0 ? nx - 1 : (i + s >= nx ? 0 : i + s);
     return g - i + j;
 }
 
@@ -65,7 +65,9 @@ __device__ __forceinline__ void moments_at(const Ctx &c, const BoxDev &b, const 
 __device__ __forceinline__ void cr_force(const BoxDev &b, double rho, const double m[3], const double B[3], double n,
                                          const double J[3], double F[3], double &P)
 {
-    const double vg[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
+    // FP64 divisions are slow on this GPU: one reciprocal per cell
+    const double ir = 1.0 / rho;
+    const double vg[3] = {m[0] * ir, m[1] * ir, m[2] * ir};
     double vxb[3], JxB[3];
     cross(vg, B, vxb);
     const double E0[3] = {-vxb[0], -vxb[1], -vxb[2]};
@@ -99,12 +101,13 @@ __device__ __forceinline__ void linear_x(const Ctx &c, const BoxDev &b, const do
                                          double dB[3])
 {
     const int64_t nc = c.nc;
-    const double h = 1.0 / (2.0 * b.dx[0]);
+    const double h = 0.5 * b.inv_dx[0];
     const double Bx = B[g];
+    const double irr = 1.0 / rho[r], irl = 1.0 / rho[l];
     dmom[0] = dB[0] = 0.0;
     for (int d = 1; d < 3; ++d) {
         dmom[d] = Bx * (B[d * nc + r] - B[d * nc + l]) * h;
-        dB[d] = Bx * (mom[d * nc + r] / rho[r] - mom[d * nc + l] / rho[l]) * h;
+        dB[d] = Bx * (mom[d * nc + r] * irr - mom[d * nc + l] * irl) * h;
     }
 }
 
@@ -157,7 +160,8 @@ __global__ void k_gas_predict(Ctx c, int cur, double dt, int model, double *__re
         half[7 * nc + g] = Bh[2];
 
         // cell fields of the half state
-        const double v[3] = {mh[0] / rho, mh[1] / rho, mh[2] / rho};
+        const double irho = 1.0 / rho;
+        const double v[3] = {mh[0] * irho, mh[1] * irho, mh[2] * irho};
         const double E0[3] = {-(v[1] * Bh[2] - v[2] * Bh[1]), -(v[2] * Bh[0] - v[0] * Bh[2]),
                               -(v[0] * Bh[1] - v[1] * Bh[0])};
         double E[3] = {E0[0], E0[1], E0[2]};

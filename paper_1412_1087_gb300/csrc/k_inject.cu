@@ -44,6 +44,8 @@ struct InjState {
 namespace {
 
 constexpr int FRONT_THREADS = 1024;
+constexpr int FRONT_CHUNKS = 16;    // row chunks of the column averages
+constexpr int SMOOTH_HALF = 12;     // 3 standard deviations of 4 cells
 constexpr int INJ_THREADS = 256;
 constexpr int INJ_BLOCKS = 152 * 4;
 
@@ -67,14 +69,18 @@ __device__ __forceinline__ double unit_open(uint32_t u)
     return ((double)u + 0.5) * (1.0 / 4294967296.0);
 }
 
-// Column averages per x cell: v_x, rho and pressure (prof[3][nx]).
-__global__ void k_front_profile(Ctx c, double gamma_gas, double *__restrict__ prof)
+// Column sums per x cell over one chunk of the rows: v_x, rho and pressure
+// (part[chunk][3][nx]); k_front_reduce adds the chunks in order.
+__global__ void k_front_profile(Ctx c, double gamma_gas, double *__restrict__ part)
 {
     const BoxDev &b = c.boxes[0];
     const int64_t nx = b.n[0], nt = (int64_t)b.n[1] * b.n[2], nc = c.nc;
+    const int64_t chunk = blockIdx.y;
+    const int64_t t0 = nt * chunk / FRONT_CHUNKS, t1 = nt * (chunk + 1) / FRONT_CHUNKS;
+    double *prof = part + chunk * 3 * nx;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nx; i += (int64_t)gridDim.x * blockDim.x) {
         double sv = 0.0, sr = 0.0, sp = 0.0;
-        for (int64_t t = 0; t < nt; ++t) {
+        for (int64_t t = t0; t < t1; ++t) {
             const int64_t g = t * nx + i;
             const double r = c.rho[g];
             const double m0 = c.mom[g], m1 = c.mom[nc + g], m2 = c.mom[2 * nc + g];
@@ -85,9 +91,53 @@ __global__ void k_front_profile(Ctx c, double gamma_gas, double *__restrict__ pr
             const double bb = __dadd_rn(__dadd_rn(__dmul_rn(b0, b0), __dmul_rn(b1, b1)), __dmul_rn(b2, b2));
             sp += (gamma_gas - 1.0) * (c.egas[g] - 0.5 * mm / r - 0.5 * bb);
         }
-        prof[i] = sv / (double)nt;
-        prof[nx + i] = sr / (double)nt;
-        prof[2 * nx + i] = sp / (double)nt;
+        prof[i] = sv;
+        prof[nx + i] = sr;
+        prof[2 * nx + i] = sp;
+    }
+}
+
+// Column averages: the chunks' sums in chunk order, over the rows.
+__global__ void k_front_reduce(Ctx c, const double *__restrict__ part, double *__restrict__ prof)
+{
+    const BoxDev &b = c.boxes[0];
+    const int64_t nx = b.n[0], nt = (int64_t)b.n[1] * b.n[2];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 3 * nx; e += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < FRONT_CHUNKS; ++k)
+            s += part[k * 3 * nx + e];
+        prof[e] = s / (double)nt;
+    }
+}
+
+// Gaussian smoothing (standard deviation 4 cells, truncated at 3 standard
+// deviations and at the box ends, renormalised) of the three profiles.
+__global__ void k_front_smooth(Ctx c, const double *__restrict__ prof, double *__restrict__ smooth)
+{
+    __shared__ double w[2 * SMOOTH_HALF + 1];
+    const BoxDev &b = c.boxes[0];
+    const int64_t nx = b.n[0];
+    const double sig = 4.0;
+    if (threadIdx.x <= 2 * SMOOTH_HALF) {
+        const int k = (int)threadIdx.x - SMOOTH_HALF;
+        w[threadIdx.x] = exp(-0.5 * (double)(k * k) / (sig * sig));
+    }
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nx; i += (int64_t)gridDim.x * blockDim.x) {
+        double ws = 0.0, a = 0.0, r = 0.0, p = 0.0;
+        for (int k = -SMOOTH_HALF; k <= SMOOTH_HALF; ++k) {
+            const int64_t j = i + k;
+            if (j < 0 || j >= nx)
+                continue;
+            const double wk = w[k + SMOOTH_HALF];
+            ws += wk;
+            a += wk * prof[j];
+            r += wk * prof[nx + j];
+            p += wk * prof[2 * nx + j];
+        }
+        smooth[i] = a / ws;
+        smooth[nx + i] = r / ws;
+        smooth[2 * nx + i] = p / ws;
     }
 }
 
@@ -105,35 +155,15 @@ __device__ __forceinline__ int64_t block_max(int64_t v, int64_t *red)
     return r;
 }
 
-// One block: smoothing, the front and the tail, the injected count and the
+// One block: the front and the tail, the injected count and the
 // compensation columns.
-__global__ void __launch_bounds__(FRONT_THREADS) k_front_scan(Ctx c, const double *__restrict__ prof,
-                                                              double *__restrict__ smooth, double gamma_gas,
-                                                              double dt, double eta, InjState *st,
+__global__ void __launch_bounds__(FRONT_THREADS) k_front_scan(Ctx c, const double *__restrict__ smooth,
+                                                              double gamma_gas, double dt, double eta, InjState *st,
                                                               const int32_t *__restrict__ offset)
 {
     __shared__ int64_t red[32];
     const BoxDev &b = c.boxes[0];
     const int64_t nx = b.n[0];
-    const double sig = 4.0;
-    const int half = 12;
-    for (int64_t i = threadIdx.x; i < nx; i += blockDim.x) {
-        double ws = 0.0, a = 0.0, r = 0.0, p = 0.0;
-        for (int k = -half; k <= half; ++k) {
-            const int64_t j = i + k;
-            if (j < 0 || j >= nx)
-                continue;
-            const double w = exp(-0.5 * (double)(k * k) / (sig * sig));
-            ws += w;
-            a += w * prof[j];
-            r += w * prof[nx + j];
-            p += w * prof[2 * nx + j];
-        }
-        smooth[i] = a / ws;
-        smooth[nx + i] = r / ws;
-        smooth[2 * nx + i] = p / ws;
-    }
-    __syncthreads();
     const double vup = smooth[nx - 1], rup = smooth[2 * nx - 1];
     const double thr = 0.6 * fabs(vup);
     int64_t best = -1;
@@ -361,8 +391,11 @@ int launch_inject(const Ctx &c, const SortScratch &s, void *state, double *scrat
 {
     InjState *is = reinterpret_cast<InjState *>(state);
     double *prof = scratch, *smooth = scratch + 3 * nx, *partials = scratch + 6 * nx;
-    k_front_profile<<<grid_of(nx, 128), 128, 0, st>>>(c, gamma_gas, prof);
-    k_front_scan<<<1, FRONT_THREADS, 0, st>>>(c, prof, smooth, gamma_gas, dt, eta, is, s.offset);
+    double *part = partials + 4 * INJ_BLOCKS;
+    k_front_profile<<<dim3(grid_of(nx, 128), FRONT_CHUNKS), 128, 0, st>>>(c, gamma_gas, part);
+    k_front_reduce<<<grid_of(3 * nx, 256), 256, 0, st>>>(c, part, prof);
+    k_front_smooth<<<grid_of(nx, 128), 128, 0, st>>>(c, prof, smooth);
+    k_front_scan<<<1, FRONT_THREADS, 0, st>>>(c, smooth, gamma_gas, dt, eta, is, s.offset);
     if (c.prec == MHDPIC_PREC_MIXED)
         k_inject_particles<MHDPIC_PREC_MIXED><<<INJ_BLOCKS, INJ_THREADS, 0, st>>>(c, s.perm, is, energy_factor, seed,
                                                                                   call, partials);
@@ -371,12 +404,12 @@ int launch_inject(const Ctx &c, const SortScratch &s, void *state, double *scrat
                                                                                  call, partials);
     k_inject_totals<<<1, 32, 0, st>>>(partials, INJ_BLOCKS, is);
     k_compensate<<<grid_of(c.nc, 256), 256, 0, st>>>(c, is);
-    return 5;
+    return 7;
 }
 
 size_t inject_scratch_doubles(int64_t nx)
 {
-    return (size_t)(6 * nx + 4 * INJ_BLOCKS);
+    return (size_t)(6 * nx + 4 * INJ_BLOCKS + 3 * FRONT_CHUNKS * nx);
 }
 
 }  // namespace mhdpic
