@@ -304,12 +304,13 @@ int mhdpic_live_particles(mhdpic_ctx *ctx, int64_t *live_out);
  *   energy (m_CR sum E_k) evenly from the cells with centres in [x_t, x_s)
  *   (the front's cell column when there are none), so gas + CR momentum and
  *   energy are unchanged.
- * The new particles take the free slots (particles that left the box, or
- * caller slots marked free: cell -1 / x NaN); when they run out the count is
- * cut and MHDPIC_ST_INJECT_CAP is raised.  The call sorts before (unless a
- * sort is pending: its order is used) and after
- * injecting (the next push applies the sort); the charge/current deposit is
- * not redone (mhdpic_deposit does).  Without a front nothing is injected.
+ * The new particles take the free slots past the live particles of the last
+ * sort (which puts particles that left the box, and caller slots marked free
+ * with cell -1 / x NaN, after all others; particles that left since are
+ * collected by the next sort); when they run out the count is cut and
+ * MHDPIC_ST_INJECT_CAP is raised.  The call sorts after injecting (the next
+ * push applies the sort); the charge/current deposit is not redone
+ * (mhdpic_deposit does).  Without a front nothing is injected.
  *   dt, eta, energy_factor, gamma_gas  as above (dt > 0, eta >= 0)
  *   seed       key of the random numbers
  *   front_out  host double[2] {x_s (NaN without a front), x_t} or NULL

@@ -20,9 +20,12 @@
 //   compensation  the gas gives the injected mass, momentum and energy evenly
 //             from the cells with centres in [x_t, x_s) (the front's cell
 //             column when there are none).
-// New particles go into the free slots: the sort that precedes injection puts
-// the particles that left the box after all others, and slot live + k of the
-// sorted order is particle perm[live + k] of the current set.
+// New particles go into the free slots past the live particles of the last
+// sort, which puts the particles that left the box after all others: with
+// that sort still pending, slot live + k of the sorted order is particle
+// perm[live + k] of the current set; once a push (or a gather) has applied
+// it, the slots live + k of the current set are free themselves.  Particles
+// that left since that sort are collected by the next one.
 #include "device_common.cuh"
 
 namespace mhdpic {
@@ -141,6 +144,20 @@ __global__ void k_front_smooth(Ctx c, const double *__restrict__ prof, double *_
     }
 }
 
+__device__ __forceinline__ int64_t block_min(int64_t v, int64_t *red)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        v = min(v, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int64_t r = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        r = min(r, red[w]);
+    return r;
+}
+
 __device__ __forceinline__ int64_t block_max(int64_t v, int64_t *red)
 {
     for (int o = 16; o > 0; o >>= 1)
@@ -187,8 +204,20 @@ __global__ void __launch_bounds__(FRONT_THREADS) k_front_scan(Ctx c, const doubl
                 it = max(it, i);
     }
     it = block_max(it, red);
+    const double xt = it >= 0 ? b.x0[0] + ((double)it + 0.5) * b.dx[0] : b.x0[0];
+    // compensation columns: centres in [x_t, x_s)
+    int64_t lo = INT64_MAX, hi = -1;
+    if (is >= 0)
+        for (int64_t i = threadIdx.x; i < nx; i += blockDim.x) {
+            const double xc = b.x0[0] + ((double)i + 0.5) * b.dx[0];
+            if (xc >= xt && xc < xs) {
+                lo = min(lo, i);
+                hi = max(hi, i);
+            }
+        }
+    lo = block_min(lo, red);
+    hi = block_max(hi, red);
     if (threadIdx.x == 0) {
-        const double xt = it >= 0 ? b.x0[0] + ((double)it + 0.5) * b.dx[0] : b.x0[0];
         st->xs = xs;
         st->xt = xt;
         st->rup = rup;
@@ -214,16 +243,7 @@ __global__ void __launch_bounds__(FRONT_THREADS) k_front_scan(Ctx c, const doubl
             }
             st->n = n;
             st->V = V;
-            // compensation columns: centres in [x_t, x_s)
-            int64_t i0 = -1, i1 = -1;
-            for (int64_t i = 0; i < nx; ++i) {
-                const double xc = b.x0[0] + ((double)i + 0.5) * b.dx[0];
-                if (xc >= xt && xc < xs) {
-                    if (i0 < 0)
-                        i0 = i;
-                    i1 = i;
-                }
-            }
+            int64_t i0 = hi >= 0 ? lo : -1, i1 = hi;
             if (i0 < 0) {
                 i0 = (int64_t)floor((xs - b.x0[0]) / b.dx[0]);
                 if (i0 >= nx)
@@ -242,7 +262,7 @@ __global__ void __launch_bounds__(FRONT_THREADS) k_front_scan(Ctx c, const doubl
 template <int PREC>
 __global__ void __launch_bounds__(INJ_THREADS) k_inject_particles(Ctx c, const int32_t *__restrict__ perm,
                                                                   const InjState *__restrict__ st, double fE,
-                                                                  uint64_t seed, uint32_t call,
+                                                                  uint64_t seed, uint32_t call, int use_perm,
                                                                   double *__restrict__ partials)
 {
     __shared__ double red[4][INJ_THREADS];
@@ -272,7 +292,7 @@ __global__ void __launch_bounds__(INJ_THREADS) k_inject_particles(Ctx c, const i
         const double s = sqrt(1.0 - mu * mu);
         double v[3] = {vmag * mu, vmag * s * cos(ph), vmag * s * sin(ph)};
         v[0] = Gam * (v[0] + V * gp);
-        const int64_t j = perm[live + k];
+        const int64_t j = use_perm ? (int64_t)perm[live + k] : live + k;
         if (PREC == MHDPIC_PREC_MIXED) {
             int ci[3] = {0, 0, 0};
             float off[3] = {0.f, 0.f, 0.f};
@@ -322,13 +342,17 @@ __global__ void __launch_bounds__(INJ_THREADS) k_inject_particles(Ctx c, const i
         partials[blockIdx.x * 4 + threadIdx.x] = red[threadIdx.x][0];
 }
 
+// One warp: lane l adds blocks l, l+32, ... in order, then a fixed tree.
 __global__ void k_inject_totals(const double *__restrict__ partials, int nblocks, InjState *st)
 {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += 32)
+        for (int q = 0; q < 4; ++q)
+            s[q] += partials[b * 4 + q];
+    for (int o = 16; o > 0; o >>= 1)
+        for (int q = 0; q < 4; ++q)
+            s[q] += __shfl_down_sync(0xffffffffu, s[q], o);
     if (threadIdx.x == 0) {
-        double s[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int b = 0; b < nblocks; ++b)
-            for (int q = 0; q < 4; ++q)
-                s[q] += partials[b * 4 + q];
         st->Pin[0] = s[0];
         st->Pin[1] = s[1];
         st->Pin[2] = s[2];
@@ -386,7 +410,7 @@ void inject_outputs(const void *st_host, double front[2], int64_t *n, int *cappe
 }
 
 int launch_inject(const Ctx &c, const SortScratch &s, void *state, double *scratch, int64_t nx, double dt,
-                  double eta, double energy_factor, double gamma_gas, uint64_t seed, uint32_t call,
+                  double eta, double energy_factor, double gamma_gas, uint64_t seed, uint32_t call, int use_perm,
                   cudaStream_t st)
 {
     InjState *is = reinterpret_cast<InjState *>(state);
@@ -398,10 +422,10 @@ int launch_inject(const Ctx &c, const SortScratch &s, void *state, double *scrat
     k_front_scan<<<1, FRONT_THREADS, 0, st>>>(c, smooth, gamma_gas, dt, eta, is, s.offset);
     if (c.prec == MHDPIC_PREC_MIXED)
         k_inject_particles<MHDPIC_PREC_MIXED><<<INJ_BLOCKS, INJ_THREADS, 0, st>>>(c, s.perm, is, energy_factor, seed,
-                                                                                  call, partials);
+                                                                                  call, use_perm, partials);
     else
         k_inject_particles<MHDPIC_PREC_FP64><<<INJ_BLOCKS, INJ_THREADS, 0, st>>>(c, s.perm, is, energy_factor, seed,
-                                                                                 call, partials);
+                                                                                 call, use_perm, partials);
     k_inject_totals<<<1, 32, 0, st>>>(partials, INJ_BLOCKS, is);
     k_compensate<<<grid_of(c.nc, 256), 256, 0, st>>>(c, is);
     return 7;

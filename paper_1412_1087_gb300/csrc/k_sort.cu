@@ -278,14 +278,108 @@ __device__ __forceinline__ void warp_sort_segment(int32_t *__restrict__ perm, in
     }
 }
 
+// A segment of the scatter is made of runs: each warp of k_sort_keys gives
+// the lanes of a run of equal keys consecutive slots, so a run is an
+// increasing interval of consecutive particle indices, and runs never
+// overlap.  Sorting such a segment only sorts its runs by their first index.
+constexpr int MERGE_RUNS = 128;   // runs a warp merges (4 per lane)
+
+// Ascending bitonic sort of the 128 values v[e] (element e*32 + lane) of a warp.
+__device__ __forceinline__ void warp_bitonic64(long long (&v)[4], int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 128; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int pe = e ^ (j >> 5);
+                    if (pe > e) {
+                        const bool up = ((e * 32 + lane) & k) == 0;
+                        const long long x = v[e], y = v[pe];
+                        if ((x > y) == up) {
+                            v[e] = y;
+                            v[pe] = x;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const long long o = __shfl_xor_sync(0xffffffffu, v[e], j);
+                    const bool up = ((e * 32 + lane) & k) == 0;
+                    const bool lower = (lane & j) == 0;
+                    v[e] = (lower == up) ? min(v[e], o) : max(v[e], o);
+                }
+            }
+        }
+    }
+}
+
+// Segment a[0, n) in the warp's shared memory, at most MERGE_RUNS runs: the
+// sorted order into perm[s, s + n).  Returns false (nothing written) with more.
+__device__ __forceinline__ bool warp_merge_runs(const int32_t *a, int n, int32_t *__restrict__ perm, int s,
+                                                int lane, int *hpos)
+{
+    int nruns = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        const bool head = i < n && (i == 0 || a[i] != a[i - 1] + 1);
+        const unsigned m = __ballot_sync(0xffffffffu, head);
+        if (head) {
+            const int pos = nruns + __popc(m & ((1u << lane) - 1u));
+            if (pos < MERGE_RUNS)
+                hpos[pos] = i;
+        }
+        nruns += __popc(m);
+    }
+    __syncwarp();
+    if (nruns > MERGE_RUNS)
+        return false;
+    // (first index, run number) of each run, sorted across the warp
+    long long v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int r = e * 32 + lane;
+        v[e] = r < nruns ? ((long long)a[hpos[r]] << 8) | r : LLONG_MAX;
+    }
+    warp_bitonic64(v, lane);
+    int carry = 0;   // elements of the sorted runs before this group of 32
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int rr = e * 32 + lane;
+        int st = 0, len = 0;
+        if (rr < nruns) {
+            const int r = (int)(v[e] & 0xff);
+            st = hpos[r];
+            len = (r + 1 < nruns ? hpos[r + 1] : n) - st;
+        }
+        int incl = len;   // inclusive scan of the lengths in sorted order
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        const int dst = carry + incl - len;
+        for (int q = 0; q < len; ++q)
+            perm[s + dst + q] = a[st + q];
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    return true;
+}
+
 // Segments of up to 128 are sorted in registers, up to WARP_SORT_MAX in the
-// warp's shared memory; longer ones are listed for k_sort_big.
+// warp's shared memory (by their runs when they have at most MERGE_RUNS, else
+// by a bitonic network); longer ones are listed for k_sort_big.
 __global__ void __launch_bounds__(256) k_sort_segments(int64_t nkeys, const int32_t *__restrict__ offset,
                                                        int32_t *__restrict__ perm,
                                                        int32_t *__restrict__ big_list,
                                                        int32_t *__restrict__ big_count)
 {
     __shared__ int32_t buf[8][WARP_SORT_MAX];
+    __shared__ int hp[8][MERGE_RUNS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int32_t *a = buf[wid];
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -307,6 +401,8 @@ __global__ void __launch_bounds__(256) k_sort_segments(int64_t nkeys, const int3
             for (int i = lane; i < P; i += 32)
                 a[i] = i < n ? perm[s + i] : INT_MAX;
             __syncwarp();
+            if (warp_merge_runs(a, n, perm, s, lane, hp[wid]))
+                continue;
             for (int kk = 2; kk <= P; kk <<= 1) {
                 for (int j = kk >> 1; j > 0; j >>= 1) {
                     for (int i = lane; i < P; i += 32) {

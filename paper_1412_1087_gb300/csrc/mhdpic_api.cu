@@ -757,15 +757,10 @@ int mhdpic_inject(mhdpic_ctx *c, double dt, double eta, double energy_factor, do
     }
     if ((rc = copy_particles(c, true)) || (rc = copy_gas(c, true, true)))
         return rc;
-    // free slots to the end: slot live + k of the sorted order is particle
-    // perm[live + k] of the current set (a sort not yet applied is current)
-    if (!c->pending) {
-        if ((rc = check_launch(c, launch_sort(c->k, c->s, nullptr, nullptr, c->stream))))
-            return rc;
-        c->pending = true;
-    }
+    // the free slots are those past the live particles of the last sort:
+    // through its permutation while it is pending, in place once applied
     if ((rc = check_launch(c, launch_inject(c->k, c->s, c->inj_state, c->inj_scratch, nx, dt, eta, energy_factor,
-                                            gamma_gas, seed, c->inj_calls, c->stream))))
+                                            gamma_gas, seed, c->inj_calls, c->pending ? 1 : 0, c->stream))))
         return rc;
     ++c->inj_calls;
     // the new particles into their cells

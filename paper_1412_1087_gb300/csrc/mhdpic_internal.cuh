@@ -215,7 +215,7 @@ void init_inject_state(void *st_host);
 size_t inject_scratch_doubles(int64_t nx);
 void inject_outputs(const void *st_host, double front[2], int64_t *n, int *capped);
 int launch_inject(const Ctx &c, const SortScratch &s, void *state, double *scratch, int64_t nx, double dt,
-                  double eta, double energy_factor, double gamma_gas, uint64_t seed, uint32_t call,
+                  double eta, double energy_factor, double gamma_gas, uint64_t seed, uint32_t call, int use_perm,
                   cudaStream_t st);
 int launch_gas_predict(const Ctx &c, int cur, double dt, int model, double *half, cudaStream_t st);
 int launch_gas_correct(const Ctx &c, double dt, int model, const double *half, cudaStream_t st);

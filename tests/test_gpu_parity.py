@@ -92,6 +92,29 @@ def test_sort_stability_with_crowded_cells():
     eng.close()
 
 
+@pytest.mark.parametrize("per_cell,movers", [(300, 0.0), (300, 0.03), (700, 0.01), (200, 0.2)])
+def test_sort_of_large_nearly_sorted_cells(per_cell, movers):
+    """Segments of 129..1024 particles made of few runs (the input nearly
+    sorted, as after a push) and of many (movers): the permutation is the
+    stable sort either way."""
+    box = wl.periodic_thermal_2d(nx=6, ny=5, ppc=2, seed=10)
+    rng = np.random.default_rng(1)
+    npart = 30 * per_cell
+    cell = (np.arange(npart) // per_cell).astype(np.int32)
+    mv = rng.random(npart) < movers
+    cell[mv] = rng.integers(0, 30, mv.sum()).astype(np.int32)
+    box.cell = cell
+    box.off = rng.random((2, npart)).astype(np.float32)
+    box.p = rng.standard_normal((3, npart)).astype(np.float32)
+    eng = _engine(box, MIXED, brick=(2, 2, 1))
+    eng.cell.copy_(torch.from_numpy(box.cell))
+    perm, counts = eng.sort(want_perm=True, want_counts=True)
+    operm, ocounts = orc.sort_cells(orc.grid_of(box), (2, 2, 1), box.cell)
+    np.testing.assert_array_equal(perm.cpu().numpy(), operm)
+    np.testing.assert_array_equal(counts.cpu().numpy().astype(np.int64), ocounts)
+    eng.close()
+
+
 @pytest.mark.parametrize("prec", [MIXED, FP64])
 @pytest.mark.parametrize("name", list(_boxes()))
 def test_initial_moments_and_fields(prec, name):
