@@ -304,8 +304,17 @@ def run_native(args):
     npart = sum(int((b.cell >= 0).sum()) for b in boxes)   # particles, not free slots
     ncell = sum(b.ncell for b in boxes)
     ndim = boxes[0].ndim
+    # the layout (brick shape, hence particles per block) picked by the
+    # project's tuner on copies of the boxes, unless given
+    brick = (0, 0, 0)
+    layout = None
+    if args.tune_layout:
+        from paper_1412_1087_gb300 import tune
+        layout = tune.tune_layout(boxes, steps=8, device=dev)
+        brick = tuple(layout["brick"])
+        torch.cuda.synchronize()
     stream = torch.cuda.Stream(device=dev)
-    eng = m.Engine(boxes, precision=m.MHDPIC_PREC_MIXED, device=dev, stream=stream)
+    eng = m.Engine(boxes, precision=m.MHDPIC_PREC_MIXED, brick=brick, device=dev, stream=stream)
 
     # sort cadence: given, or picked by the library's tuner (mhdpic_run with
     # sort_every = 0 times one cycle of each candidate cadence on real steps)
@@ -476,7 +485,7 @@ def run_native(args):
     eng_stats = {"push_ms_per_step": push_ms / args.steps, "graph_run_ms_per_step": graph_ms,
                  "eager_ms_per_step": eager_ms / args.steps,
                  "subcycled": subcycled, "diagnostics": diagnostics, "coupled": coupled,
-                 "injection": injection,
+                 "injection": injection, "layout_tuning": layout,
                  "particles": npart, "cells": ncell,
                  "dt": dt}
 
@@ -513,7 +522,7 @@ def run_native(args):
             runs.append((m.MHDPIC_MEM_HOST, gas_h2d + pbytes + sort_extra, gas_d2h + pbytes + sort_extra))
         res = []
         for mem, h2d, d2h in runs:
-            eh = m.Engine(boxes, precision=m.MHDPIC_PREC_MIXED, memory=mem, device=dev, stream=stream)
+            eh = m.Engine(boxes, precision=m.MHDPIC_PREC_MIXED, memory=mem, brick=brick, device=dev, stream=stream)
             te, _, _ = _time_engine(eh, dt, args.e2e_steps, 1, args.sort_every, torch, per_push=False)
             eh.close()
             del eh
@@ -536,6 +545,7 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 push + i64 fixed-point deposits",
             "data": "synthetic",
             "config": {"workload": _workload_desc(args), "precision": "mixed", "sort_every": args.sort_every, "sort_every_tuned": tuned,
+                       "brick": list(brick) if any(brick) else "default", "brick_tuned": bool(args.tune_layout),
                        "l2": "inputs larger than L2 (%.2f GB particle state)"
                              % (npart * PARTICLE_BYTES[(ndim, prec)] / 1e9),
                        "parallelism": "independent box per GPU" if world > 1 else "1 GPU"},
@@ -605,6 +615,8 @@ def main(argv=None):
     ap.add_argument("--diagnostics", type=int, default=1, help="time the spectrum and Lambda map once")
     ap.add_argument("--nsub", type=int, default=5, help="particle sub-steps per call of the sub-cycled figure (<2: off)")
     ap.add_argument("--e2e-all-host", type=int, default=1, help="also time the all-host-buffer mode")
+    ap.add_argument("--tune-layout", type=int, default=1,
+                    help="pick the brick shape with the layout tuner before the run (0: the default brick)")
     ap.add_argument("--inject-steps", type=int, default=4,
                     help="time front tracking + injection this many calls on shock boxes (0: off)")
     ap.add_argument("--coupled-steps", type=int, default=4,
