@@ -455,22 +455,41 @@ def run_native(args):
             eng.apply_feedback(False)
             eng.inject(dt, eta, 10.0, 5.0 / 3.0, 11)
         torch.cuda.synchronize()
-        t_inj = 0.0
-        n_inj = 0
-        front = None
-        for _ in range(args.inject_steps):
-            eng.interp_push(dt, 1)
-            eng.apply_feedback(False)
-            ev0.record(stream)
-            n, xs, xt = eng.inject(dt, eta, 10.0, 5.0 / 3.0, 11)
-            ev1.record(stream)
-            torch.cuda.synchronize()
-            t_inj += ev0.elapsed_time(ev1)
-            n_inj += n
-            front = (xs, xt)
-        injection = {"calls": args.inject_steps, "ms_per_call": t_inj / args.inject_steps,
+        ev2 = torch.cuda.Event(enable_timing=True)
+
+        def inject_steps():
+            t_step = t_inj = 0.0
+            n_inj = 0
+            front = None
+            for _ in range(args.inject_steps):
+                ev2.record(stream)
+                eng.interp_push(dt, 1)
+                eng.apply_feedback(False)
+                ev0.record(stream)
+                n, xs, xt = eng.inject(dt, eta, 10.0, 5.0 / 3.0, 11)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                t_step += ev2.elapsed_time(ev0)
+                t_inj += ev0.elapsed_time(ev1)
+                n_inj += n
+                front = (xs, xt)
+            return t_step / args.inject_steps, t_inj / args.inject_steps, n_inj, front
+
+        step_ms, inj_ms, n_inj, front = inject_steps()
+        # early-particle removal (Section 5): every particle injected from
+        # here on is early (t_early far ahead) and goes at twice its
+        # injection time; the step then also carries the injection times
+        # through the sort and checks them in the push
+        eng.set_injection_times(None, 0.0, 1e30)
+        live0 = eng.live_particles()
+        step_tr_ms, inj_tr_ms, n_tr, _ = inject_steps()
+        injection = {"calls": args.inject_steps, "ms_per_call": inj_ms,
                      "particles_per_call": n_inj / args.inject_steps, "eta": eta, "energy_factor": 10.0,
-                     "front_x": front[0], "tail_x": front[1], "live_particles": eng.live_particles()}
+                     "front_x": front[0], "tail_x": front[1], "live_particles": eng.live_particles(),
+                     "step_ms": step_ms,
+                     "removal": {"step_ms": step_tr_ms, "inject_ms_per_call": inj_tr_ms,
+                                 "injected": n_tr, "live_before": live0,
+                                 "live_after": eng.live_particles()}}
     flags = eng.status()
 
     # roofline of the push kernel (the dominant kernel)

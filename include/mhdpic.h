@@ -321,6 +321,40 @@ int mhdpic_live_particles(mhdpic_ctx *ctx, int64_t *live_out);
 int mhdpic_inject(mhdpic_ctx *ctx, double dt, double eta, double energy_factor, double gamma_gas, uint64_t seed,
                   double *front_out, int64_t *ninj_out);
 
+/*
+ * mhdpic_set_injection_times - early-particle removal (Section 5: the CRs
+ * injected before the Bell instability has grown cross the upstream
+ * unscattered, so every particle with injection time t_i < t_early is
+ * removed at t = 2 t_i).  Turns on a per-particle injection time and a
+ * clock, or resets them.
+ *   t_inj    host double[np], t_i of each slot in the order of the caller's
+ *            particle arrays as they stand after this call (the call brings
+ *            them up to date, like mhdpic_sync_particles), or NULL for +inf
+ *            (never removed); free slots' values are not used
+ *   t_now    the current time (finite)
+ *   t_early  the threshold (not NaN; -inf removes nothing)
+ * From then on each push sub-step advances the clock by its dt first; a live
+ * particle with t_i < t_early and clock >= 2 t_i is removed at the end of
+ * that push, the same way as a particle that leaves through an open face
+ * (its corrector deposit of the step stands, no charge/current deposit, cell
+ * -1 / x NaN and velocity 0, collected by the next sort).  mhdpic_inject sets
+ * t_i of each new particle to the clock.  The injection times follow every
+ * sort.  A graph captured by mhdpic_run before the call is discarded.
+ * Synchronises the stream.  Errors: MHDPIC_E_ARG for a non-finite t_now or a
+ * NaN t_early; MHDPIC_E_NOMEM.
+ */
+int mhdpic_set_injection_times(mhdpic_ctx *ctx, const double *t_inj, double t_now, double t_early);
+
+/*
+ * mhdpic_get_injection_times - read back the injection times and the clock.
+ *   t_inj  host double[np] (order of the caller's arrays after the call, which
+ *          brings them up to date), or NULL
+ *   t_now  host double, the clock, or NULL
+ * Synchronises the stream.  Errors: MHDPIC_E_STATE when
+ * mhdpic_set_injection_times was never called.
+ */
+int mhdpic_get_injection_times(mhdpic_ctx *ctx, double *t_inj, double *t_now);
+
 /* ---- gas models of the coupled step ---- */
 #define MHDPIC_GAS_SOURCES 0   /* the gas changes by the CR sources alone; B is held */
 #define MHDPIC_GAS_LINEAR_X 1  /* plus plane-parallel linear MHD along x (below) */

@@ -94,6 +94,9 @@ def _load():
             lib.orc_inject.argtypes = [G, Pp, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32, _P, ctypes.c_int64,
                                        _P, _P, _P, _P, _P]
+            lib.orc_remove_early.restype = ctypes.c_int64
+            lib.orc_remove_early.argtypes = [ctypes.c_int, ctypes.c_int64, _P, _P, _P, ctypes.c_double,
+                                             ctypes.c_double]
             lib.orc_gas_rhs.argtypes = [G, ctypes.c_int, _P, _P, _P, _P, _P, _P]
             lib.orc_gas_predict.argtypes = [G, Pp, ctypes.c_int, ctypes.c_double] + [_P] * 13
             lib.orc_gas_correct.argtypes = [G, Pp, ctypes.c_int, ctypes.c_double] + [_P] * 11
@@ -321,6 +324,16 @@ def inject(g: Grid, p: Params, fr, xs_prev: float, dt: float, eta: float, energy
                            float(energy_factor), int(seed), int(call) & 0xffffffff, _ptr(c), int(cap), _ptr(xn),
                            _ptr(vn), _ptr(rho), _ptr(mom), _ptr(egas))
     return xn[:, :n].copy(), vn[:, :n].copy(), float(c[0])
+
+
+def remove_early(x: np.ndarray, v: np.ndarray, t_inj, t: float, t_early: float) -> int:
+    """Early-particle removal at time t (in place): live particles with
+    t_inj < t_early and t >= 2 t_inj are removed.  Returns the count."""
+    t_inj = _f64(t_inj)
+    assert x.dtype == np.float64 and v.dtype == np.float64 and x.flags["C_CONTIGUOUS"] and v.flags["C_CONTIGUOUS"]
+    assert t_inj.shape == (v.shape[1],)
+    return int(_load().orc_remove_early(int(x.shape[0]), int(v.shape[1]), _ptr(x), _ptr(v), _ptr(t_inj),
+                                        float(t), float(t_early)))
 
 
 class State:

@@ -1039,3 +1039,33 @@ int64_t orc_inject(const orc_grid *g, const orc_params *p, const double front[4]
         }
     return N;
 }
+
+/* ------------------------------------------------------------------ */
+/* early-particle removal (Section 5)                                   */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The shock runs record the injection time t_i of every CR; because the
+ * first CRs meet an upstream whose Bell instability has not grown yet, every
+ * particle with t_i < t_early is removed at t = 2 t_i.  Called at time t (the
+ * end of a step): each live particle with t_inj[j] < t_early and t >= 2
+ * t_inj[j] is removed (x[0] = NaN, v = 0, as for a particle that left through
+ * an open face).  Returns the number removed.
+ */
+int64_t orc_remove_early(int ndim, int64_t np, double *x, double *v, const double *t_inj, double t,
+                         double t_early)
+{
+    (void)ndim;
+    int64_t n = 0;
+    for (int64_t j = 0; j < np; ++j) {
+        if (isnan(x[j]))
+            continue;
+        if (t_inj[j] < t_early && t >= 2.0 * t_inj[j]) {
+            x[j] = NAN;
+            for (int d = 0; d < 3; ++d)
+                v[d * np + j] = 0.0;
+            ++n;
+        }
+    }
+    return n;
+}

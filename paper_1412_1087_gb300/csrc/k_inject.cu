@@ -323,6 +323,8 @@ __global__ void __launch_bounds__(INJ_THREADS) k_inject_particles(Ctx c, const i
             for (int d = 0; d < 3; ++d)
                 c.p64[(int64_t)d * c.np + j] = v[d];
         }
+        if (c.tinj)   // injected now: t_i is the clock
+            c.tinj[j] = c.clock[0];
         const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
         const double g = sqrt(C * C + v2) / C;
         for (int d = 0; d < 3; ++d)

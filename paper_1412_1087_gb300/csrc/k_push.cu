@@ -186,6 +186,7 @@ __device__ __forceinline__ float push_one_f64(const Ctx &c, const BoxDev &b, con
         x[d] = x[d] + 0.5 * k.dt * (vn[d] / g1);
         leaving |= boundary_f64(b, d, x[d], vn[d]);
     }
+    leaving |= removed_early(c, j);
     if (leaving) {   // removed: no moments deposit; the next sort drops it
         c.x[j] = __longlong_as_double(0x7ff8000000000000ll);
         for (int d = 1; d < D; ++d)

@@ -491,6 +491,7 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
         o[d] = fmaf(k.hdx[d] * ig2, vn[d], o[d]);
         leaving |= renorm_mixed(b, d, ci[d], o[d], vn[d], c.status);
     }
+    leaving |= removed_early(c, j);
     if (leaving) {   // removed: no moments deposit; the next sort drops it
         c.cell[j] = DEAD_CELL;
 #pragma unroll

@@ -660,7 +660,32 @@ int launch_gather(const Ctx &c, const int32_t *perm, const PSet &src, const PSet
         add(src.x, dst.x, 8, c.ndim);
         add(src.p64, dst.p64, 8, 3);
     }
+    if (src.tinj && dst.tinj)
+        add(src.tinj, dst.tinj, 8, 1);
     k_gather_all<<<grid_for(c.np, 256), 256, 0, st>>>(c.np, perm, pl);
+    return 1;
+}
+
+int launch_gather_f64(int64_t np, const int32_t *perm, const double *src, double *dst, cudaStream_t st)
+{
+    if (np <= 0)
+        return 0;
+    Planes pl{};
+    pl.src[0] = src;
+    pl.dst[0] = dst;
+    pl.esz[0] = 8;
+    pl.n = 1;
+    k_gather_all<<<grid_for(np, 256), 256, 0, st>>>(np, perm, pl);
+    return 1;
+}
+
+namespace {
+__global__ void k_clock_advance(double *clock, double dt) { clock[0] = clock[0] + dt; }
+}  // namespace
+
+int launch_clock_advance(double *clock, double dt, cudaStream_t st)
+{
+    k_clock_advance<<<1, 1, 0, st>>>(clock, dt);
     return 1;
 }
 

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -99,6 +100,9 @@ struct mhdpic_ctx {
     double *inj_scratch = nullptr;
     uint32_t inj_calls = 0;
     unsigned long long *live_dev = nullptr;
+    // early-particle removal: injection times in both sets, clock {t, t_early}
+    bool track_tinj = false;
+    double *clock = nullptr;
     // coupled step: half state of the last mhdpic_gas_predict
     double *gas_half = nullptr;
     bool half_valid = false;
@@ -191,6 +195,7 @@ void use_set(mhdpic_ctx *c, int set)
     k.p = q.p;
     k.x = q.x;
     k.p64 = q.p64;
+    k.tinj = q.tinj;
     k.perm_src = nullptr;
     k.src_cell = q.cell;
     k.src_off = q.off;
@@ -232,6 +237,8 @@ int sync_to_caller(mhdpic_ctx *c)
         CK(cudaMemcpyAsync(b.x, a.x, sizeof(double) * c->k.ndim * np, cudaMemcpyDeviceToDevice, c->stream));
         CK(cudaMemcpyAsync(b.p64, a.p64, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, c->stream));
     }
+    if (c->track_tinj)
+        CK(cudaMemcpyAsync(b.tinj, a.tinj, sizeof(double) * np, cudaMemcpyDeviceToDevice, c->stream));
     use_set(c, 0);
     return MHDPIC_OK;
 }
@@ -666,13 +673,21 @@ int mhdpic_interp_push(mhdpic_ctx *c, double dt, int32_t nsub)
             kk.p = dst.p;
             kk.x = dst.x;
             kk.p64 = dst.p64;
+            kk.tinj = dst.tinj;
             kk.perm_src = c->s.perm;
             kk.src_cell = src.cell;
             kk.src_off = src.off;
             kk.src_p = src.p;
             kk.src_x = src.x;
             kk.src_p64 = src.p64;
+            // the injection times follow the permutation before the push reads them
+            if (c->track_tinj &&
+                (rc = check_launch(c, launch_gather_f64(c->k.np, c->s.perm, src.tinj, dst.tinj, c->stream))))
+                return rc;
         }
+        // the push removes early particles at the time it reaches
+        if (c->track_tinj && (rc = check_launch(c, launch_clock_advance(c->clock, dt, c->stream))))
+            return rc;
         int n = c->k.prec == MHDPIC_PREC_MIXED
                     ? launch_push_mixed(kk, c->s, c->work_ctr, c->cur ^ 1, last ? 1 : 0, dt, c->grid_blocks, c->stream)
                     : launch_push_f64(kk, c->s, c->work_ctr, c->cur ^ 1, last ? 1 : 0, dt, c->grid_blocks, c->stream);
@@ -788,6 +803,63 @@ int mhdpic_inject(mhdpic_ctx *c, double dt, double eta, double energy_factor, do
     }
     if (ninj_out)
         *ninj_out = n;
+    return MHDPIC_OK;
+}
+
+int mhdpic_set_injection_times(mhdpic_ctx *c, const double *t_inj, double t_now, double t_early)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (!std::isfinite(t_now) || std::isnan(t_early))
+        return fail(MHDPIC_E_ARG, "t_now must be finite and t_early not NaN");
+    int rc;
+    // the caller's order: the caller's buffers made current
+    if ((rc = copy_particles(c, true)) || (rc = sync_to_caller(c)))
+        return rc;
+    const int64_t np = c->k.np;
+    if (!c->track_tinj) {
+        if ((rc = c->alloc(&c->sets[0].tinj, np)) || (rc = c->alloc(&c->sets[1].tinj, np)) ||
+            (rc = c->alloc(&c->clock, 2)))
+            return rc;
+        c->k.clock = c->clock;
+        c->track_tinj = true;
+        use_set(c, c->cur_set);
+        if (c->graph) {   // a captured cycle has no removal in it
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
+    }
+    if (np > 0) {
+        if (t_inj) {
+            CK(cudaMemcpyAsync(c->k.tinj, t_inj, sizeof(double) * np, cudaMemcpyHostToDevice, c->stream));
+        } else {
+            std::vector<double> never((size_t)np, std::numeric_limits<double>::infinity());
+            CK(cudaMemcpyAsync(c->k.tinj, never.data(), sizeof(double) * np, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+    }
+    const double clk[2] = {t_now, t_early};
+    CK(cudaMemcpyAsync(c->clock, clk, sizeof clk, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MHDPIC_OK;
+}
+
+int mhdpic_get_injection_times(mhdpic_ctx *c, double *t_inj, double *t_now)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (!c->track_tinj)
+        return fail(MHDPIC_E_STATE, "injection times are not tracked (mhdpic_set_injection_times)");
+    int rc;
+    if ((rc = copy_particles(c, true)) || (rc = sync_to_caller(c)))
+        return rc;
+    if (t_inj && c->k.np > 0)
+        CK(cudaMemcpyAsync(t_inj, c->k.tinj, sizeof(double) * c->k.np, cudaMemcpyDeviceToHost, c->stream));
+    double clk[2];
+    CK(cudaMemcpyAsync(clk, c->clock, sizeof clk, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (t_now)
+        *t_now = clk[0];
     return MHDPIC_OK;
 }
 

@@ -141,6 +141,12 @@ struct Ctx {
     const int32_t *key_off;       // sort offsets: particles of key k are [key_off[k], key_off[k+1])
     BoxDev *boxes_rw;             // same table, writable by the scale kernel
     BoxStats *stats;              // [nbox]
+    // early-particle removal (null when not tracked): the injection time t_i
+    // of every slot of the set the kernel writes, and the clock
+    // {t, t_early}; a push removes a particle with t_i < t_early at the end
+    // of the step that reaches t >= 2 t_i
+    double *tinj;
+    const double *clock;
 };
 
 // ---------------------------------------------------------------------------
@@ -172,12 +178,18 @@ struct PSet {
     float *p;
     double *x;
     double *p64;
+    double *tinj;   // injection times, when tracked
 };
 
 int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *counts_out,
                 cudaStream_t st);
-// dst[j] = src[perm[j]] for every particle plane
+// dst[j] = src[perm[j]] for every particle plane (and the injection times
+// when both sets track them)
 int launch_gather(const Ctx &c, const int32_t *perm, const PSet &src, const PSet &dst, cudaStream_t st);
+// dst[j] = src[perm[j]] for one plane of np doubles
+int launch_gather_f64(int64_t np, const int32_t *perm, const double *src, double *dst, cudaStream_t st);
+// clock[0] += dt (the time a push reaches, before the push reads it)
+int launch_clock_advance(double *clock, double dt, cudaStream_t st);
 int launch_max_count(const Ctx &c, const SortScratch &s, cudaStream_t st);
 // after a push that applied a sort: slots past the live particles marked free
 int launch_mark_free(const Ctx &c, const SortScratch &s, cudaStream_t st);

@@ -6,6 +6,19 @@
 
 namespace mhdpic {
 
+// Early-particle removal (Sec. 4.1): a particle injected at t_i < t_early
+// is removed at t = 2 t_i, i.e. at the end of the first step whose end time
+// (clock[0], already advanced) reaches 2 t_i.  It has taken part in that
+// step (its corrector deposit stands) and, like a particle that left through
+// an open face, deposits no moments at the new position.
+__device__ __forceinline__ bool removed_early(const Ctx &c, int64_t j)
+{
+    if (!c.tinj)
+        return false;
+    const double ti = c.tinj[j];
+    return ti < c.clock[1] && c.clock[0] >= 2.0 * ti;
+}
+
 struct ItemGeom {
     int org[3];    // unwrapped box coordinates of tile cell (0,0,0)
     int ctr[3];    // brick centre, for periodic unwrapping of particle cells

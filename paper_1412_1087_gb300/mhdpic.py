@@ -83,6 +83,8 @@ SIGNATURES = {
     "mhdpic_live_particles": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int64)]),
     "mhdpic_inject": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_uint64, _V, ctypes.POINTER(ctypes.c_int64)]),
+    "mhdpic_set_injection_times": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_double]),
+    "mhdpic_get_injection_times": (ctypes.c_int, [_V, _V, ctypes.POINTER(ctypes.c_double)]),
     "mhdpic_gas_predict": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32]),
     "mhdpic_gas_correct": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32, _V]),
     "mhdpic_run": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32, ctypes.c_int32]),
@@ -176,6 +178,21 @@ def mhdpic_inject(ctx, dt: float, eta: float, energy_factor: float = 10.0, gamma
     _check(load().mhdpic_inject(ctx, float(dt), float(eta), float(energy_factor), float(gamma_gas),
                                 int(seed) & 0xffffffffffffffff, fr.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)))
     return int(n.value), float(fr[0]), float(fr[1])
+
+
+def mhdpic_set_injection_times(ctx, t_inj: Optional[np.ndarray], t_now: float, t_early: float) -> None:
+    ptr = None
+    if t_inj is not None:
+        assert t_inj.dtype == np.float64 and t_inj.flags["C_CONTIGUOUS"]
+        ptr = t_inj.ctypes.data_as(ctypes.c_void_p)
+    _check(load().mhdpic_set_injection_times(ctx, ptr, float(t_now), float(t_early)))
+
+
+def mhdpic_get_injection_times(ctx, np_: int) -> tuple:
+    t_inj = np.zeros(max(np_, 1), dtype=np.float64)
+    t = ctypes.c_double(0.0)
+    _check(load().mhdpic_get_injection_times(ctx, t_inj.ctypes.data_as(ctypes.c_void_p), ctypes.byref(t)))
+    return t_inj[:np_], float(t.value)
 
 
 def mhdpic_gas_predict(ctx, dt: float, model: int) -> None:
@@ -415,6 +432,17 @@ class Engine:
                seed: int = 0) -> tuple:
         """Front tracking and CR injection (Section 5): returns (n, x_s, x_t)."""
         return mhdpic_inject(self.ctx, dt, eta, energy_factor, gamma_gas, seed)
+
+    def set_injection_times(self, t_inj=None, t_now: float = 0.0, t_early: float = float("inf")) -> None:
+        """Early-particle removal (Section 5): particles with injection time
+        t_i < t_early are removed at t = 2 t_i.  t_inj (np,) in the order of
+        the particle attributes (None: never removed); t_now sets the clock."""
+        arr = None if t_inj is None else np.ascontiguousarray(t_inj, dtype=np.float64)
+        mhdpic_set_injection_times(self.ctx, arr, t_now, t_early)
+
+    def injection_times(self) -> tuple:
+        """(t_inj (np,), clock) in the order of the particle attributes."""
+        return mhdpic_get_injection_times(self.ctx, self.np)
 
     def gas_predict(self, dt: float, model: int) -> None:
         mhdpic_gas_predict(self.ctx, dt, model)

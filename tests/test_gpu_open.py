@@ -162,3 +162,146 @@ def test_injection_stops_at_the_free_slots_and_is_checked():
     with pytest.raises(m.MhdpicError):
         eng.inject(per.dt, 0.1)
     eng.close()
+
+
+def _pow2_dt(box):
+    """A step that is a power of two (clock sums exact) within the box's limit."""
+    return 2.0 ** math.floor(math.log2(box.dt))
+
+
+def _early_times(n, dt, seed):
+    """Distinct injection times: half early-ish in [0, 3 dt), half late."""
+    rng = np.random.default_rng(seed)
+    t = np.where(rng.random(n) < 0.5, rng.uniform(0.0, 3.0 * dt, n), rng.uniform(1e3, 2e3, n))
+    return np.ascontiguousarray(t)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_early_particles_are_removed_at_twice_their_injection_time(prec):
+    """Section 5's removal (t_i < t_early goes at t = 2 t_i) on the GPU against
+    the oracle: the same particles go (identified by their distinct t_i), the
+    survivors' states, the moments of the survivors and the gas match."""
+    box = _box(seed=5)
+    dt = _pow2_dt(box)
+    t_early = 2.5 * dt
+    eng = m.Engine([box], precision=prec)
+    _, _, x, v = sorted_oracle_state(box)
+    t_inj = _early_times(box.np, dt, 5)
+    eng.set_injection_times(t_inj, 0.0, t_early)
+    st = orc.State(box, x, v)
+    t = 0.0
+    removed = 0
+    for s in range(6):
+        corr, _ = st.push_only(dt)
+        t += dt
+        removed += orc.remove_early(st.x, st.v, t_inj, t, t_early)
+        st.mom_dep = orc.deposit_moments(st.g, st.p, st.x, st.v, st.nc)
+        orc.apply_feedback(st.g, st.mom, st.egas, corr)
+        eng.interp_push(dt, 1)
+        eng.apply_feedback()
+        if s % 2 == 1:
+            eng.sort()
+    assert removed > 0
+    tg, clock = eng.injection_times()
+    assert clock == t
+    live_g = (~np.isnan(eng.x.cpu().numpy()[0])) if prec == FP64 else eng.cell.cpu().numpy() >= 0
+    live_o = ~np.isnan(st.x[0])
+    set_g, set_o = set(tg[live_g].tolist()), set(t_inj[live_o].tolist())
+    early_gone = set(t_inj[(t_inj < t_early) & (2.0 * t_inj <= t)].tolist())
+    assert not early_gone & set_g
+    if prec == FP64:
+        assert set_g == set_o
+        rg = np.vstack([positions_of(eng)[:, live_g], momenta_of(eng)[:, live_g], tg[live_g]])
+        ro = np.vstack([st.x[:, live_o], st.v[:, live_o], t_inj[live_o]])
+        rg, ro = rg[:, np.argsort(rg[-1])], ro[:, np.argsort(ro[-1])]
+        np.testing.assert_allclose(rg, ro, rtol=1e-12, atol=1e-12)
+    else:
+        # only a particle within f32 rounding of the open face may differ
+        assert len(set_g ^ set_o) <= 2
+    md = eng.deposits(1).cpu().numpy()
+    for q in range(4):
+        assert rel_l2(md[q], st.mom_dep[q], floor=1e-300) < TOL[prec] * 10, q
+    gm = eng.mom.cpu().numpy()
+    for q in range(3):
+        assert rel_l2(gm[q] - box.mom[q], st.mom[q] - box.mom[q], floor=1e-300) < TOL[prec] * 10, q
+    assert eng.status() == 0
+    eng.close()
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_injected_particles_carry_the_clock_and_leave_at_twice_it(prec):
+    box = _box(seed=6)
+    dt = _pow2_dt(box)
+    eng = m.Engine([box], precision=prec)
+    n0 = eng.live_particles()
+    t0 = 2.0 * dt
+    eng.set_injection_times(None, t0, 100.0 * dt)      # the initial particles stay
+    n, _, _ = eng.inject(dt, 0.05, 10.0, 5.0 / 3.0, 9)
+    assert n > 0
+    tg, clock = eng.injection_times()
+    assert clock == t0
+    assert int((tg == t0).sum()) == n and np.all(np.isinf(tg) | (tg == t0))
+    live = [eng.live_particles()]
+    for _ in range(3):
+        eng.interp_push(dt, 1)
+        eng.apply_feedback()
+        live.append(eng.live_particles())
+    # the injected ones go at the end of the push that reaches 2 t0 = t0 + 2 dt
+    # (others may leave through the open face meanwhile)
+    assert live[0] == n0 + n
+    gone = [live[i] - live[i + 1] for i in range(3)]
+    assert gone[1] >= n
+    assert gone[0] < n and gone[2] < n
+    tg, clock = eng.injection_times()
+    assert clock == t0 + 3 * dt
+    eng.sort()
+    tg, _ = eng.injection_times()
+    live_g = (~np.isnan(eng.x.cpu().numpy()[0])) if prec == FP64 else eng.cell.cpu().numpy() >= 0
+    assert not np.any(tg[live_g] == t0)
+    assert eng.status() == 0
+    eng.close()
+
+
+def test_removal_through_graph_replay_matches_eager_steps_bit_for_bit():
+    box = _box(seed=7)
+    dt = _pow2_dt(box)
+    t_inj = _early_times(box.np, dt, 7)
+    outs = []
+    for graphs in (False, True):
+        eng = m.Engine([box], precision=MIXED)
+        eng.set_injection_times(t_inj, 0.0, 2.5 * dt)
+        if graphs:
+            eng.run(dt, 8, 2)
+        else:
+            for s in range(8):
+                eng.interp_push(dt, 1)
+                eng.apply_feedback()
+                if s % 2 == 1:
+                    eng.sort()
+        tg, clock = eng.injection_times()
+        live = eng.cell.cpu().numpy() >= 0
+        rows = np.vstack([tg[live], positions_of(eng)[:, live], momenta_of(eng)[:, live]])
+        md = eng.deposits(1).cpu().numpy()
+        outs.append((clock, rows[:, np.argsort(rows[0])], eng.mom.cpu().numpy().copy(), md))
+        assert eng.status() == 0
+        eng.close()
+    (c0, r0, m0, d0), (c1, r1, m1, d1) = outs
+    assert c0 == c1 == 8 * dt
+    np.testing.assert_array_equal(r0, r1)
+    np.testing.assert_array_equal(m0, m1)
+    np.testing.assert_array_equal(d0, d1)
+
+
+def test_injection_times_need_tracking_and_valid_arguments():
+    box = _box(seed=8)
+    eng = m.Engine([box], precision=MIXED)
+    with pytest.raises(m.MhdpicError):
+        eng.injection_times()
+    with pytest.raises(m.MhdpicError):
+        eng.set_injection_times(None, float("nan"), 1.0)
+    with pytest.raises(m.MhdpicError):
+        eng.set_injection_times(None, 0.0, float("nan"))
+    eng.set_injection_times(None, 1.5, float("-inf"))
+    tg, clock = eng.injection_times()
+    assert clock == 1.5 and np.all(np.isinf(tg))
+    eng.close()

@@ -7,6 +7,8 @@ full-step position reaches the open face; the charge density of the particles
 left is qm m N / V; the sort puts removed particles after every cell, in
 input order (compared with numpy's stable argsort).
 """
+import math
+
 import numpy as np
 
 import oracle as orc
@@ -229,3 +231,64 @@ def test_moving_front_boosts_the_injected_particles():
     vr = np.vstack([vx_rest, vn[1], vn[2]])
     gr = np.sqrt(1.0 + (vr ** 2).sum(axis=0) / C ** 2)
     np.testing.assert_allclose((vr ** 2).sum(axis=0) / (gr + 1.0), 10.0 * 0.5 * fr[3] ** 2, rtol=1e-9)
+
+
+def test_early_particles_go_exactly_at_twice_their_injection_time():
+    """Section 5's removal rule by brute force: t_i < t_early and t >= 2 t_i;
+    the boundaries (t = 2 t_i exactly, t_i = t_early) and particles already
+    removed or never injected early (t_i NaN / +inf) included."""
+    rng = np.random.default_rng(11)
+    n = 400
+    t_early = 480.0
+    x = rng.uniform(0.0, 10.0, (2, n))
+    v = rng.normal(size=(3, n))
+    t_inj = rng.uniform(0.0, 1000.0, n)
+    t = 700.0
+    t_inj[:5] = t / 2.0                    # exactly at 2 t_i: removed
+    t_inj[5:10] = np.nextafter(t / 2.0, np.inf)   # just after: kept
+    t_inj[10:15] = t_early                 # not early
+    t_inj[15:20] = np.nextafter(t_early, -np.inf)  # early, but 2 t_i > t
+    t_inj[20:25] = np.nan
+    t_inj[25:30] = np.inf
+    x[0, 30:35] = np.nan                   # already gone
+    t_inj[30:35] = 0.0
+    x, v = np.ascontiguousarray(x), np.ascontiguousarray(v)
+    x0, v0 = x.copy(), v.copy()
+    nrem = orc.remove_early(x, v, t_inj, t, t_early)
+    want = [j for j in range(n)
+            if not math.isnan(x0[0, j]) and t_inj[j] < t_early and t >= 2.0 * t_inj[j]]
+    assert nrem == len(want)
+    assert set(range(5)) <= set(want) and not set(range(5, 35)) & set(want)
+    gone = np.isnan(x[0])
+    assert sorted(np.flatnonzero(gone & ~np.isnan(x0[0]))) == want
+    assert np.all(v[:, want] == 0.0)
+    keep = ~gone
+    np.testing.assert_array_equal(x[:, keep], x0[:, keep])
+    np.testing.assert_array_equal(v[:, keep], v0[:, keep])
+    # past 2 t_early: t_i = t_early stays (strictly earlier only), just below goes
+    x2 = np.zeros((1, 3))
+    v2 = np.ones((3, 3))
+    t2 = np.array([t_early, np.nextafter(t_early, -np.inf), 0.0])
+    assert orc.remove_early(x2, v2, t2, 2.0 * t_early + 1.0, t_early) == 2
+    assert not math.isnan(x2[0, 0]) and math.isnan(x2[0, 1]) and math.isnan(x2[0, 2])
+
+
+def test_after_twice_the_threshold_no_early_particle_is_left():
+    """Injecting at every step up to t = 1200 and removing at each step's
+    end: at any t every particle with t_i < min(t_early, t/2) is gone and the
+    others remain, so after 2 t_early only particles injected at or after
+    t_early are left."""
+    dt, t_early = 10.0, 480.0
+    t_inj = np.arange(0.0, 1200.0, dt)
+    n = t_inj.size
+    x = np.zeros((1, n))
+    v = np.ones((3, n))
+    t = 0.0
+    for _ in range(n):
+        t += dt
+        orc.remove_early(x, v, t_inj, t, t_early)
+        live = ~np.isnan(x[0])
+        expect = ~((t_inj < t_early) & (2.0 * t_inj <= t))
+        np.testing.assert_array_equal(live, expect)
+    assert np.all(np.isnan(x[0][t_inj < t_early]))
+    assert not np.any(np.isnan(x[0][t_inj >= t_early]))
