@@ -255,32 +255,96 @@ def _cpu_baseline(args, seed, nsteps):
                       % (args.workload, what, live, nsteps), "seconds": dt}
 
 
-def _error_vs_oracle(args, seed, torch):
-    """One step of the mixed and FP64 GPU paths against the oracle on a sample box."""
+def _error_vs_oracle(args, seed, torch, nsteps=10):
+    """Both GPU paths against the oracle on a sample of the workload: one step
+    (relative L2 of each deposited channel, per box), then nsteps steps with
+    feedback and no sort (so the particles keep their order) for the largest
+    position and momentum deviations."""
     import oracle as orc
     from paper_1412_1087_gb300 import mhdpic as m
     from paper_1412_1087_gb300 import workloads as wl
-    box, what = _sample_box(args, seed, "err")
-    g = orc.grid_of(box)
-    perm, _ = orc.sort_cells(g, (4, 4, 4) if box.ndim == 3 else (8, 8, 1), box.cell)
-    x = np.ascontiguousarray(wl.absolute_positions(box)[:, perm])
-    v = np.ascontiguousarray(box.p.astype(np.float64)[:, perm])
-    st = orc.State(box, x, v)
-    corr, md = st.push_only(box.dt)
-    out = {}
+    if args.workload == "ensemble_2d":
+        boxes = wl.ensemble_2d(nbox=8, seed0=seed * 1000, max_side=64)
+        what = "8 ensemble boxes of side <= 64"
+    else:
+        box, what = _sample_box(args, seed, "err")
+        boxes = [box]
+    dt = min(b.dt for b in boxes)
 
     def rl(a, b):
         return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
+    states = []
+    for b in boxes:
+        g = orc.grid_of(b)
+        perm, _ = orc.sort_cells(g, (4, 4, 4) if b.ndim == 3 else (8, 8, 1), b.cell)
+        x = np.ascontiguousarray(wl.absolute_positions(b)[:, perm])
+        v = np.ascontiguousarray(b.p.astype(np.float64)[:, perm])
+        states.append((x, v))
+    one = [orc.State(b, x, v).push_only(dt) for b, (x, v) in zip(boxes, states)]
+    multi = []
+    for b, (x, v) in zip(boxes, states):
+        st = orc.State(b, x, v)
+        for _ in range(nsteps):
+            st.step(dt)
+        multi.append((st.x, st.v))
+    out = {}
     for name, prec in (("mixed", m.MHDPIC_PREC_MIXED), ("fp64", m.MHDPIC_PREC_FP64)):
-        eng = m.Engine([box], precision=prec)
-        eng.interp_push(box.dt, 1)
+        eng = m.Engine(boxes, precision=prec)
+        eng.interp_push(dt, 1)
         gc = eng.deposits(0).cpu().numpy()
         gm = eng.deposits(1).cpu().numpy()
         eng.close()
-        out[name] = {"corrector_rel_l2_max": max(rl(gc[q], corr[q]) for q in range(4)),
-                     "moments_rel_l2_max": max(rl(gm[q], md[q]) for q in range(4))}
-    out["sample"] = "one step at %s" % what
+        per_box = []
+        c0 = 0
+        for b, (corr, md) in zip(boxes, one):
+            sl = slice(c0, c0 + b.ncell)
+            per_box.append({"corrector_rel_l2_max": max(rl(gc[q, sl], corr[q]) for q in range(4)),
+                            "moments_rel_l2_max": max(rl(gm[q, sl], md[q]) for q in range(4))})
+            c0 += b.ncell
+        # nsteps with feedback, no sort
+        eng = m.Engine(boxes, precision=prec)
+        for _ in range(nsteps):
+            eng.interp_push(dt, 1)
+            eng.apply_feedback(False)
+        if prec == m.MHDPIC_PREC_FP64:
+            xg_all = eng.x.cpu().numpy()
+        else:
+            cell, off = eng.cell.cpu().numpy(), eng.off.cpu().numpy()
+        pg_all = (eng.p64 if prec == m.MHDPIC_PREC_FP64 else eng.p).cpu().numpy().astype(np.float64)
+        starts = eng.box_start.copy()
+        eng.close()
+        dxmax = dpmax = 0.0
+        for bi, (b, (xo, vo)) in enumerate(zip(boxes, multi)):
+            s, e = starts[bi], starts[bi + 1]
+            if prec == m.MHDPIC_PREC_FP64:
+                xg = xg_all[:, s:e]
+            else:
+                c = cell[s:e].astype(np.int64)
+                co = [c % b.n[0], (c // b.n[0]) % b.n[1], c // (b.n[0] * b.n[1])]
+                xg = np.stack([b.x0[d] + (co[d] + off[d, s:e].astype(np.float64)) * b.dx[d]
+                               for d in range(b.ndim)])
+                xg[:, c < 0] = np.nan
+            live = ~np.isnan(xg[0]) & ~np.isnan(xo[0])
+            for d in range(b.ndim):
+                L = b.n[d] * b.dx[d]
+                dd = xg[d, live] - xo[d, live]
+                if b.bc[d] == 0:
+                    dd = dd - L * np.round(dd / L)
+                if dd.size:
+                    dxmax = max(dxmax, float(np.abs(dd).max() / b.dx[d]))
+            pg = pg_all[:, s:e][:, live]
+            po = vo[:, live]
+            if po.size:
+                dpmax = max(dpmax, float((np.abs(pg - po).max(axis=0) / np.maximum(
+                    np.sqrt((po ** 2).sum(axis=0)), 1e-300)).max()))
+        out[name] = {"corrector_rel_l2_max": max(r["corrector_rel_l2_max"] for r in per_box),
+                     "moments_rel_l2_max": max(r["moments_rel_l2_max"] for r in per_box),
+                     "max_position_deviation_cells_after_%d_steps" % nsteps: dxmax,
+                     "max_momentum_deviation_rel_after_%d_steps" % nsteps: dpmax}
+        if len(boxes) > 1:
+            out[name]["per_box"] = per_box
+    out["sample"] = "one step, then %d steps with feedback and no sort, at %s" % (nsteps, what)
     return out
 
 
@@ -324,9 +388,15 @@ def run_native(args):
         torch.cuda.synchronize()
         args.sort_every = eng.sort_cadence()
 
+    # totals of gas + CR momentum and energy before the measured steps (no
+    # corrector is pending here, so this feedback call changes nothing)
+    tot0 = eng.apply_feedback(totals=True).sum(axis=0)
+    steps_done = 0
+
     # eager steps, one call each, so that every push kernel is bracketed by
     # events on the library's stream: the push kernel's roofline
     eager_ms, push_ms, _ = _time_engine(eng, dt, args.steps, args.warmup, args.sort_every, torch)
+    steps_done += args.steps + args.warmup
 
     # timed region (device time, max over ranks): the production step, the
     # cycle of push + feedback + sort at the tuned cadence captured once in a
@@ -345,6 +415,24 @@ def run_native(args):
         torch.cuda.synchronize()
         launches = eng.launches() - l0
     clocks = clk.summary()
+    steps_done += args.warmup * max(args.sort_every, 1) + args.steps
+    tot1 = eng.apply_feedback(totals=True).sum(axis=0)
+    # momentum scale: gross gas momentum plus gross CR momentum
+    scaleP = 0.0
+    pcr = eng.p
+    c0 = 0
+    for bi, b in enumerate(boxes):
+        dV = b.dx[0] * b.dx[1] * b.dx[2]
+        scaleP += float(eng.mom[:, c0:c0 + b.ncell].abs().sum().item()) * dV
+        s0, s1 = int(eng.box_start[bi]), int(eng.box_start[bi + 1])
+        scaleP += b.m_cr * float(pcr[:, s0:s1].double().abs().sum().item())
+        c0 += b.ncell
+    scaleP = max(scaleP, 1e-300)
+    conservation = {"steps": steps_done,
+                    "momentum_drift": float(np.abs((tot1[0:3] + tot1[4:7]) - (tot0[0:3] + tot0[4:7])).max())
+                    / scaleP,
+                    "energy_drift": float(abs((tot1[3] + tot1[7]) - (tot0[3] + tot0[7])))
+                    / max(abs(float(tot0[3] + tot0[7])), 1e-300)}
     total_ms = ev0.elapsed_time(ev1)
     graph_ms = total_ms / args.steps
     total_ms, job_steps = aggregate_ranks(total_ms, float(npart) * args.steps,
@@ -504,7 +592,7 @@ def run_native(args):
     eng_stats = {"push_ms_per_step": push_ms / args.steps, "graph_run_ms_per_step": graph_ms,
                  "eager_ms_per_step": eager_ms / args.steps,
                  "subcycled": subcycled, "diagnostics": diagnostics, "coupled": coupled,
-                 "injection": injection, "layout_tuning": layout,
+                 "injection": injection, "layout_tuning": layout, "conservation": conservation,
                  "particles": npart, "cells": ncell,
                  "dt": dt}
 
@@ -558,6 +646,8 @@ def run_native(args):
     if rank == 0:
         cpu = _cpu_baseline(args, seed=0, nsteps=args.cpu_steps) if args.cpu_steps > 0 else None
         err = _error_vs_oracle(args, 0, torch) if args.err_n > 0 else None
+        if err is not None:
+            err["conservation_drift_this_run"] = eng_stats["conservation"]
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
