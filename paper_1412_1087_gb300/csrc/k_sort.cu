@@ -28,66 +28,105 @@ constexpr int WARP_SORT_MAX = 1024;     // per-warp shared-memory bitonic sort
 constexpr int BLOCK_SORT_MAX = 8192;    // per-block shared-memory bitonic sort
 constexpr int RANK_SORT_MAX = 1 << 20;  // quadratic ranking beyond that is refused
 
-__device__ __forceinline__ int64_t brick_key(const BoxDev &b, const int32_t brick[3], int ci, int cj,
-                                             int ck)
+__device__ __forceinline__ int64_t brick_key(const BoxDev &b, const Ctx &c, int ci, int cj, int ck)
 {
-    int64_t bid = ((int64_t)(ck / brick[2]) * b.nb[1] + cj / brick[1]) * b.nb[0] + ci / brick[0];
-    int64_t in = ((int64_t)(ck % brick[2]) * brick[1] + cj % brick[1]) * brick[0] + ci % brick[0];
-    return b.key0 + bid * ((int64_t)brick[0] * brick[1] * brick[2]) + in;
+    int q[3], r[3];
+    const int cc[3] = {ci, cj, ck};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (c.brick_sh[d] >= 0) {   // power-of-two bricks: shifts and masks
+            q[d] = cc[d] >> c.brick_sh[d];
+            r[d] = cc[d] & (c.brick[d] - 1);
+        } else {
+            q[d] = cc[d] / c.brick[d];
+            r[d] = cc[d] - q[d] * c.brick[d];
+        }
+    }
+    const int64_t bid = ((int64_t)q[2] * b.nb[1] + q[1]) * b.nb[0] + q[0];
+    const int64_t in = ((int64_t)r[2] * c.brick[1] + r[1]) * c.brick[0] + r[0];
+    return b.key0 + bid * ((int64_t)c.brick[0] * c.brick[1] * c.brick[2]) + in;
 }
+
+// Sort key of particle i of box b: brick-major cell order, nkeys for a
+// particle that has left the box.
+template <int PREC>
+__device__ __forceinline__ int32_t key_in_box(const Ctx &c, const BoxDev &b, int64_t i)
+{
+    int ci[3] = {0, 0, 0};
+    bool dead = false;
+    if (PREC == MHDPIC_PREC_MIXED) {
+        int32_t cl = c.cell[i];
+        dead = cl == DEAD_CELL;
+        if (!dead && (cl < 0 || cl >= b.ncell)) {
+            set_status(c.status, MHDPIC_ST_CELL_RANGE);
+            cl = cl < 0 ? 0 : (int32_t)(b.ncell - 1);
+        }
+        decode_cell(b, cl, ci);
+    } else {
+        dead = isnan(c.x[i]);
+        for (int d = 0; d < c.ndim && !dead; ++d) {
+            double s = (c.x[(int64_t)d * c.np + i] - b.x0[d]) / b.dx[d];
+            double f = floor(s);
+            int v = f < 0.0 ? 0 : (f >= (double)b.n[d] ? b.n[d] - 1 : (int)f);
+            if (!(f >= 0.0 && f < (double)b.n[d]))
+                set_status(c.status, MHDPIC_ST_CELL_RANGE);
+            ci[d] = v;
+        }
+    }
+    for (int d = 0; d < 3; ++d)   // defensive: a key outside the box would index out of range
+        ci[d] = ci[d] < 0 ? 0 : (ci[d] >= b.n[d] ? b.n[d] - 1 : ci[d]);
+    // particles that left the box share one key after all the others
+    return dead ? (int32_t)c.nkeys : (int32_t)brick_key(b, c, ci[0], ci[1], ci[2]);
+}
+
+// Particles handled per thread and loop pass by the streaming sort kernels:
+// independent loads (and atomics) in flight hide their latency.
+constexpr int SORT_ILP = 4;
 
 template <int PREC>
 __global__ void k_sort_keys(Ctx c, int32_t *__restrict__ count, int32_t *__restrict__ pkey,
                             int32_t *__restrict__ pslot)
 {
     const int lane = threadIdx.x & 31;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.np;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int bx = find_box(c.box_part_start, c.nbox, i);
-        const BoxDev &b = c.boxes[bx];
-        int ci[3] = {0, 0, 0};
-        bool dead = false;
-        if (PREC == MHDPIC_PREC_MIXED) {
-            int32_t cl = c.cell[i];
-            dead = cl == DEAD_CELL;
-            if (!dead && (cl < 0 || cl >= b.ncell)) {
-                set_status(c.status, MHDPIC_ST_CELL_RANGE);
-                cl = cl < 0 ? 0 : (int32_t)(b.ncell - 1);
-            }
-            decode_cell(b, cl, ci);
-        } else {
-            dead = isnan(c.x[i]);
-            for (int d = 0; d < c.ndim && !dead; ++d) {
-                double s = (c.x[(int64_t)d * c.np + i] - b.x0[d]) / b.dx[d];
-                double f = floor(s);
-                int v = f < 0.0 ? 0 : (f >= (double)b.n[d] ? b.n[d] - 1 : (int)f);
-                if (!(f >= 0.0 && f < (double)b.n[d]))
-                    set_status(c.status, MHDPIC_ST_CELL_RANGE);
-                ci[d] = v;
-            }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < c.np; i0 += SORT_ILP * stride) {
+        // lanes past the end take keys no other lane has, so they form runs
+        // of their own and take no atomic
+        const unsigned active = __activemask();
+        int32_t key[SORT_ILP];
+#pragma unroll
+        for (int u = 0; u < SORT_ILP; ++u) {
+            const int64_t i = i0 + u * stride;
+            key[u] = i < c.np ? key_in_box<PREC>(c, c.boxes[find_box(c.box_part_start, c.nbox, i)], i)
+                              : -1 - lane;
         }
-        for (int d = 0; d < 3; ++d)   // defensive: a key outside the box would index out of range
-            ci[d] = ci[d] < 0 ? 0 : (ci[d] >= b.n[d] ? b.n[d] - 1 : ci[d]);
-        // particles that left the box share one key after all the others
-        int32_t key = dead ? (int32_t)c.nkeys : (int32_t)brick_key(b, c.brick, ci[0], ci[1], ci[2]);
         // runs of equal keys in consecutive lanes (the input is nearly
         // sorted) take one atomic per run; the rank inside the run is the
         // lane offset
-        const unsigned active = __activemask();
-        const int prev = __shfl_up_sync(active, key, 1);
-        const bool head = lane == 0 || !((active >> (lane - 1)) & 1u) || prev != key;
-        const unsigned heads = __ballot_sync(active, head);
-        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));   // last head at or below lane
-        const unsigned after = heads & ~(0xffffffffu >> (31 - lane));           // heads above lane
-        const int end = after ? __ffs(after) - 1 : 32;
-        const unsigned tail = (end < 32 ? (1u << end) : 0u) - 1u;               // lanes below end
-        const int len = __popc(active & tail & ~((1u << start) - 1u));
-        int base = 0;
-        if (head)
-            base = atomicAdd(count + key, len);
-        base = __shfl_sync(active, base, start);
-        pkey[i] = key;
-        pslot[i] = base + (lane - start);
+        int start[SORT_ILP], base[SORT_ILP];
+#pragma unroll
+        for (int u = 0; u < SORT_ILP; ++u) {
+            const int prev = __shfl_up_sync(active, key[u], 1);
+            const bool head = lane == 0 || !((active >> (lane - 1)) & 1u) || prev != key[u];
+            const unsigned heads = __ballot_sync(active, head);
+            start[u] = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));   // last head at or below lane
+            const unsigned after = heads & ~(0xffffffffu >> (31 - lane));  // heads above lane
+            const int end = after ? __ffs(after) - 1 : 32;
+            const unsigned tail = (end < 32 ? (1u << end) : 0u) - 1u;      // lanes below end
+            const int len = __popc(active & tail & ~((1u << start[u]) - 1u));
+            base[u] = 0;
+            if (head && key[u] >= 0)
+                base[u] = atomicAdd(count + key[u], len);
+        }
+#pragma unroll
+        for (int u = 0; u < SORT_ILP; ++u) {
+            const int b0 = __shfl_sync(active, base[u], start[u]);
+            const int64_t i = i0 + u * stride;
+            if (i < c.np) {
+                pkey[i] = key[u];
+                pslot[i] = b0 + (lane - start[u]);
+            }
+        }
     }
 }
 
@@ -198,13 +237,30 @@ __global__ void k_sort_scatter(int64_t np, const int32_t *__restrict__ pkey,
                                const int32_t *__restrict__ pslot, const int32_t *__restrict__ offset,
                                int32_t *__restrict__ perm, uint32_t *status)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t dst = (int64_t)offset[pkey[i]] + pslot[i];
-        if (dst >= 0 && dst < np)
-            perm[dst] = (int32_t)i;
-        else
-            set_status(status, MHDPIC_ST_SORT_CAP);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < np; i0 += SORT_ILP * stride) {
+        int32_t key[SORT_ILP], slot[SORT_ILP];
+#pragma unroll
+        for (int u = 0; u < SORT_ILP; ++u) {
+            const int64_t i = i0 + u * stride;
+            key[u] = i < np ? pkey[i] : 0;
+            slot[u] = i < np ? pslot[i] : 0;
+        }
+        int32_t off[SORT_ILP];
+#pragma unroll
+        for (int u = 0; u < SORT_ILP; ++u)
+            off[u] = i0 + u * stride < np ? offset[key[u]] : 0;
+#pragma unroll
+        for (int u = 0; u < SORT_ILP; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i >= np)
+                continue;
+            const int64_t dst = (int64_t)off[u] + slot[u];
+            if (dst >= 0 && dst < np)
+                perm[dst] = (int32_t)i;
+            else
+                set_status(status, MHDPIC_ST_SORT_CAP);
+        }
     }
 }
 

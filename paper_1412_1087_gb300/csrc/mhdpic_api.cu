@@ -413,6 +413,10 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         if (d >= k.ndim)
             k.brick[d] = 1;
         k.tile[d] = d < k.ndim ? k.brick[d] + 2 * HALO : 1;
+        k.brick_sh[d] = -1;
+        for (int sh = 0; sh < 31; ++sh)
+            if (k.brick[d] == (1 << sh))
+                k.brick_sh[d] = sh;
     }
     k.tile_vol = k.tile[0] * k.tile[1] * k.tile[2];
     // Default 64-cell bricks are worked as two 32-cell halves, one lane per

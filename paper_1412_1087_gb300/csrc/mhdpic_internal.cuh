@@ -106,6 +106,7 @@ struct WorkItem {
 struct Ctx {
     int32_t nbox, ndim, prec;
     int32_t brick[3];
+    int32_t brick_sh[3];   // log2 of brick[d] when it is a power of two, else -1
     int32_t tile[3];       // brick + 2*HALO
     int32_t tile_vol;      // cells of the tile
     int32_t ts[3];         // tile strides in slots (x, y, z); padded to spread banks
