@@ -310,7 +310,8 @@ int mhdpic_live_particles(mhdpic_ctx *ctx, int64_t *live_out);
  * collected by the next sort); when they run out the count is cut and
  * MHDPIC_ST_INJECT_CAP is raised.  The call sorts after injecting (the next
  * push applies the sort); the charge/current deposit is not redone
- * (mhdpic_deposit does).  Without a front nothing is injected.
+ * (mhdpic_deposit does), and the next push (or mhdpic_run) first stages the
+ * fields of the compensated gas.  Without a front nothing is injected.
  *   dt, eta, energy_factor, gamma_gas  as above (dt > 0, eta >= 0)
  *   seed       key of the random numbers
  *   front_out  host double[2] {x_s (NaN without a front), x_t} or NULL
@@ -395,9 +396,10 @@ int mhdpic_gas_predict(mhdpic_ctx *ctx, double dt, int32_t model);
  * CR-Hall term the induction takes the curl of -F_CR/n_g with
  * F_CR = -dM/(dV dt), the force the deposit implies.  rho is unchanged; mom,
  * egas and B are written (back to the caller's host buffers in host-memory
- * modes).  The accumulators are zeroed.  The next push needs a new
- * mhdpic_gas_predict (or mhdpic_apply_feedback / mhdpic_deposit) to stage
- * its fields.
+ * modes).  The accumulators are zeroed.  The staged fields are then stale:
+ * mhdpic_gas_predict stages the next step's half-step fields, and a push or
+ * mhdpic_run called first stages the fields of the corrected gas itself (as
+ * mhdpic_apply_feedback would, without a corrector to apply).
  *   dt, model  as given to mhdpic_gas_predict
  *   totals_out HOST double[8*nbox] or NULL, as for mhdpic_apply_feedback
  * Errors: MHDPIC_E_STATE when no predictor ran since the last corrector,

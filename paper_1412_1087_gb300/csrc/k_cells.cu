@@ -114,9 +114,18 @@ __global__ void k_scales(Ctx c, double dt)
         return;
     BoxDev &b = c.boxes_rw[bx];
     double hh = 0.5 * fabs(b.qm_cr) * dt;
+    // no staging since the last choice (e.g. a push right after the coupled
+    // step's corrector): the staged fields are the ones measured then
+    uint32_t eb = st.emax, bb = st.bmax;
+    if (eb == 0u && bb == 0u) {
+        eb = st.emax_used;
+        bb = st.bmax_used;
+    }
+    st.emax_used = eb;
+    st.bmax_used = bb;
     double vmax = (double)__uint_as_float(st.vmax);
-    double emax = (double)__uint_as_float(st.emax);
-    double bmax = (double)__uint_as_float(st.bmax);
+    double emax = (double)__uint_as_float(eb);
+    double bmax = (double)__uint_as_float(bb);
     double H = (c.ndim == 3 ? 27.0 : 9.0) * (4.0 * st.maxcount + 64.0);
     double vb = vmax + hh * emax;
     double qdv = 2.0 * (2.0 * hh * emax + 2.0 * hh * bmax * fmin(vb, b.C));

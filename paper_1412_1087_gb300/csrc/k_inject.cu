@@ -279,6 +279,7 @@ __global__ void __launch_bounds__(INJ_THREADS) k_inject_particles(Ctx c, const i
     const int64_t q = (n + gridDim.x - 1) / gridDim.x;
     const int64_t a0 = blockIdx.x * q, a1 = min(n, a0 + q);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    float vm = 0.f;   // largest |v| injected, for the next corrector scale
     for (int64_t k = a0 + threadIdx.x; k < a1; k += blockDim.x) {
         uint32_t x[4] = {(uint32_t)k, call, 0u, 0u};
         philox4x32(x, k0, k1);
@@ -330,7 +331,11 @@ __global__ void __launch_bounds__(INJ_THREADS) k_inject_particles(Ctx c, const i
         for (int d = 0; d < 3; ++d)
             acc[d] += b.m_cr * v[d];
         acc[3] += b.m_cr * (v2 / (g + 1.0));
+        vm = fmaxf(vm, (float)sqrt(v2));
     }
+    const unsigned vb = __reduce_max_sync(0xffffffffu, __float_as_uint(vm));
+    if ((threadIdx.x & 31) == 0 && vb)
+        atomicMax(&c.stats[0].vmax, vb);
     for (int q2 = 0; q2 < 4; ++q2)
         red[q2][threadIdx.x] = acc[q2];
     __syncthreads();

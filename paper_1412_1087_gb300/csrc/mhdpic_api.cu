@@ -106,6 +106,9 @@ struct mhdpic_ctx {
     // coupled step: half state of the last mhdpic_gas_predict
     double *gas_half = nullptr;
     bool half_valid = false;
+    // the gas changed since the fields were last staged (mhdpic_gas_correct,
+    // mhdpic_inject): the next push stages them from the current gas first
+    bool fields_stale = false;
     double half_dt = 0.0;
     int half_model = -1;
 
@@ -344,9 +347,22 @@ int validate(int32_t nbox, const mhdpic_grid *grids, const mhdpic_params *params
 int do_prep(mhdpic_ctx *c, int apply)
 {
     int rc = check_launch(c, launch_prep(c->k, c->cur, apply, c->stream));
-    if (rc == MHDPIC_OK)
+    if (rc == MHDPIC_OK) {
         c->next_clear = true;
+        c->fields_stale = false;
+    }
     return rc;
+}
+
+// Stage the fields of the current gas when a call changed it since.
+int restage_if_stale(mhdpic_ctx *c)
+{
+    if (!c->fields_stale)
+        return MHDPIC_OK;
+    int rc;
+    if ((rc = copy_gas(c, true, true)))
+        return rc;
+    return do_prep(c, 0);
 }
 
 }  // namespace
@@ -658,7 +674,7 @@ int mhdpic_interp_push(mhdpic_ctx *c, double dt, int32_t nsub)
     if (nsub < 1)
         return fail(MHDPIC_E_ARG, "nsub must be >= 1");
     int rc;
-    if ((rc = copy_particles(c, true)))
+    if ((rc = copy_particles(c, true)) || (rc = restage_if_stale(c)))
         return rc;
     if ((rc = check_launch(c, launch_scales(c->k, dt, c->stream))))
         return rc;
@@ -782,6 +798,7 @@ int mhdpic_inject(mhdpic_ctx *c, double dt, double eta, double energy_factor, do
                                             gamma_gas, seed, c->inj_calls, c->pending ? 1 : 0, c->stream))))
         return rc;
     ++c->inj_calls;
+    c->fields_stale = true;   // the compensation changed the gas
     // the new particles into their cells
     if ((rc = check_launch(c, launch_sort(c->k, c->s, nullptr, nullptr, c->stream))) ||
         (rc = check_launch(c, launch_max_count(c->k, c->s, c->stream))))
@@ -907,6 +924,7 @@ int mhdpic_gas_predict(mhdpic_ctx *c, double dt, int32_t model)
     if ((rc = check_launch(c, launch_gas_predict(c->k, c->cur, dt, model, c->gas_half, c->stream))))
         return rc;
     c->next_clear = true;
+    c->fields_stale = false;
     c->half_valid = true;
     c->half_dt = dt;
     c->half_model = model;
@@ -927,6 +945,7 @@ int mhdpic_gas_correct(mhdpic_ctx *c, double dt, int32_t model, double *totals_o
     if ((rc = check_launch(c, launch_gas_correct(c->k, dt, model, c->gas_half, c->stream))))
         return rc;
     c->half_valid = false;
+    c->fields_stale = true;
     if ((rc = copy_gas(c, false, false)))
         return rc;
     if (c->mem != MHDPIC_MEM_DEVICE)
@@ -1165,6 +1184,8 @@ int mhdpic_run(mhdpic_ctx *c, double dt, int32_t nsteps, int32_t sort_every)
         return fail(MHDPIC_E_ARG, "nsteps and sort_every must be >= 0");
     int rc;
     int32_t left = nsteps;
+    if ((rc = restage_if_stale(c)))   // before any capture
+        return rc;
     if (sort_every == 0 && !c->tuned_k)
         if ((rc = tune_sort_cadence(c, dt, &left)))
             return rc;

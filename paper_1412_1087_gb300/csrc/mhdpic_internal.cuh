@@ -86,10 +86,12 @@ struct BoxDev {
 // atomicMax orders them correctly.
 struct BoxStats {
     uint32_t vmax;        // max |v| of the particles (four-velocity)
-    uint32_t emax;        // max |E| of the staged cell fields
-    uint32_t bmax;        // max |B| of the staged cell fields
+    uint32_t emax;        // max |E| of the cell fields staged since the last scale choice
+    uint32_t bmax;        // max |B| of the cell fields staged since the last scale choice
     int32_t maxcount;     // max particles per cell at the last sort
     int32_t corr_dirty;   // corrector accumulators hold data: scales locked
+    uint32_t emax_used;   // the field maxima the last scale choice used (the
+    uint32_t bmax_used;   // fields still staged when nothing was staged since)
     int32_t pad;
 };
 

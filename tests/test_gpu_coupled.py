@@ -144,3 +144,34 @@ def test_coupled_calls_are_checked():
         eng.gas_predict(shock.dt, LINEAR_X)
     eng.gas_predict(shock.dt, SOURCES)
     eng.close()
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_plain_push_after_the_corrector_stages_the_corrected_gas(prec):
+    """A coupled step, then a plain step (push + feedback) without a new
+    predictor: the push stages the fields of the corrected gas itself (as the
+    feedback call would) and sizes its corrector scale for them, so no
+    overflow is flagged and the step matches the oracle's push in the fields
+    of the corrected gas."""
+    box = _boxes()["thermal_hall"]()
+    eng = m.Engine([box], precision=prec)
+    _, _, x, v = sorted_oracle_state(box)
+    st = orc.State(box, x, v)
+    dt = box.dt
+    st.coupled_step(dt, SOURCES)
+    eng.coupled_step(dt, SOURCES)
+    # the plain step: fields of the corrected gas and the moments of x^(n+1)
+    corr, md = st.push_only(dt)
+    corr_ref = corr.copy()
+    orc.apply_feedback(st.g, st.mom, st.egas, corr)   # zeroes corr
+    eng.interp_push(dt, 1)
+    gc = eng.deposits(0).cpu().numpy()
+    eng.apply_feedback()
+    tol = TOL[prec]
+    for q in range(4):
+        assert rel_l2(gc[q], corr_ref[q]) < tol, ("corrector", q)
+    gm = eng.mom.cpu().numpy()
+    for q in range(3):
+        assert rel_l2(gm[q] - box.mom[q], st.mom[q] - box.mom[q], floor=1e-300) < tol * 10, q
+    assert eng.status() == 0, m.status_names(eng.status())
+    eng.close()
