@@ -535,7 +535,7 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         (rc = c->alloc(&c->work_ctr, 1)))
         return bail(rc);
     k.key_off = c->s.offset;
-    c->nchunks = 64;
+    c->nchunks = std::max(1, 1216 / nbox);   // totals: about 8 blocks per SM over all boxes
     c->spec_chunks = std::max(1, 1216 / nbox);   // about 8 blocks per SM over all boxes
     if ((rc = c->alloc(&c->partials, (size_t)nbox * c->nchunks * 8)) || (rc = c->alloc(&c->totals_dev, 8 * nbox)) ||
         (rc = c->alloc(&c->spec_counts, (size_t)nbox * MHDPIC_SPEC_MAX_BINS)) ||
