@@ -207,7 +207,8 @@ int mhdpic_set_subcycle_sort(mhdpic_ctx *ctx, int32_t every);
  * if it is the current one.  Call it before reading or writing the caller's
  * particle buffers in MHDPIC_MEM_DEVICE / MHDPIC_MEM_HOST_GAS mode; the
  * caller's buffers then stay current until the next mhdpic_sort (a no-op in
- * MHDPIC_MEM_HOST mode, where the host buffers are current after every call).
+ * MHDPIC_MEM_HOST mode, where the host buffers are current once the stream
+ * has finished each call: synchronise it before reading them).
  * Asynchronous; ordered on the context's stream.
  */
 int mhdpic_sync_particles(mhdpic_ctx *ctx);
@@ -254,7 +255,13 @@ int mhdpic_lambda_map(mhdpic_ctx *ctx, double *out);
  * mhdpic_deposit - TSC deposit of n_CR = (q/mc) m_CR W/dV and
  * J_CR = (q/mc) m_CR u W/dV (App. A.1, eq:nJCR) at the current positions,
  * replacing the current moments, then restage the fields from the gas and
- * these moments.  The corrector accumulators are left untouched.
+ * these moments.  The corrector accumulators are left untouched.  Mixed
+ * precision deposits through the push's shared tile over the work list of a
+ * sort of the current particles: a pending sort is used, else the call sorts
+ * (the next push applies it; the caller's order is unchanged until then);
+ * each particle adds the same fixed-point integers as the push that put it
+ * where it is, so right after a push the moments come out bit for bit the
+ * same.  FP64 deposits straight into the global accumulators.
  */
 int mhdpic_deposit(mhdpic_ctx *ctx);
 

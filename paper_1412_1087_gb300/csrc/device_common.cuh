@@ -88,14 +88,23 @@ __device__ __forceinline__ long long to_fixed(double v)
 // TSC (quadratic spline) weights from the offset o in [0,1) inside the cell:
 // with delta = o - 1/2 the weights of cells i-1, i, i+1 are
 // (1/2)(1/2 - delta)^2 = (1/2)(1-o)^2, 3/4 - delta^2, (1/2)(1/2 + delta)^2 = (1/2)o^2.
+// The centre weight is one explicit fused multiply-add, so every kernel that
+// forms these weights gets the same bits.
 template <typename R>
 __device__ __forceinline__ void tsc_from_offset(R o, R w[3])
 {
     R a = R(1) - o;
     R dl = o - R(0.5);
     w[0] = R(0.5) * a * a;
-    w[1] = R(0.75) - dl * dl;
+    w[1] = fma(-dl, dl, R(0.75));
     w[2] = R(0.5) * o * o;
+}
+
+// |v|^2 in one fixed order of explicit operations (the same bits wherever
+// it is evaluated).
+__device__ __forceinline__ float vsq3(const float v[3])
+{
+    return fmaf(v[2], v[2], fmaf(v[1], v[1], __fmul_rn(v[0], v[0])));
 }
 
 // Box-local linear cell -> integer coordinates.

@@ -286,27 +286,46 @@ __global__ void k_fields_to_double(Ctx c, double *__restrict__ out)
     }
 }
 
-// Largest |v| per box (for the fixed-point scales).
+// Largest |v| per box (for the fixed-point scales): a running maximum per
+// thread while its particles stay in one box, one atomic per box and warp.
 template <int PREC>
 __global__ void k_vmax(Ctx c)
 {
+    float acc = 0.f;
+    int bacc = -1;
+    auto flush = [&](int bx, float vm) {
+        const unsigned active = __activemask();
+        const unsigned peers = __match_any_sync(active, bx);
+        const unsigned m = __reduce_max_sync(peers, __float_as_uint(vm));
+        if (bx >= 0 && m && (threadIdx.x & 31) == __ffs(peers) - 1)
+            atomicMax(&c.stats[bx].vmax, m);
+    };
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.np;
          i += (int64_t)gridDim.x * blockDim.x) {
-        int bx = find_box(c.box_part_start, c.nbox, i);
-        double v2 = 0.0;
-        for (int d = 0; d < 3; ++d) {
-            double v = PREC == MHDPIC_PREC_MIXED ? (double)c.p[(int64_t)d * c.np + i]
-                                                 : c.p64[(int64_t)d * c.np + i];
-            v2 += v * v;
+        const int bx = find_box(c.box_part_start, c.nbox, i);
+        float vm;
+        if (PREC == MHDPIC_PREC_MIXED) {
+            const float v[3] = {c.p[i], c.p[c.np + i], c.p[2 * c.np + i]};
+            vm = sqrtf(vsq3(v));
+        } else {
+            double v2 = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                const double v = c.p64[(int64_t)d * c.np + i];
+                v2 += v * v;
+            }
+            vm = (float)sqrt(v2);
         }
-        float vm = (float)sqrt(v2);
         if (!(vm <= 1.0e37f))
             vm = 1.0e37f;
-        unsigned peers = __match_any_sync(__activemask(), bx);
-        unsigned m = __reduce_max_sync(peers, __float_as_uint(vm));
-        if ((threadIdx.x & 31) == __ffs(peers) - 1)
-            atomicMax(&c.stats[bx].vmax, m);
+        if (bx != bacc) {   // rare: a thread's particles cross into the next box
+            if (bacc >= 0 && acc > 0.f)
+                atomicMax(&c.stats[bacc].vmax, __float_as_uint(acc));
+            bacc = bx;
+            acc = 0.f;
+        }
+        acc = fmaxf(acc, vm);
     }
+    flush(bacc, acc);
 }
 
 int grid_for(int64_t n, int threads)

@@ -381,6 +381,48 @@ __device__ __forceinline__ PIn load_global(const Ctx &c, int64_t i)
     return r;
 }
 
+// Charge and current density deposit of one particle (eq:nJCR) at cell ci,
+// offsets o, four-velocity v with ig = 1/gamma from rsqrtf(fmaf(vsq3(v),
+// invC2, 1)): n = qn W, J = qn (v/gamma) W.  The push calls it at x^(n+1) and
+// the standalone deposit at the stored positions, so the two give the same
+// integers for the same particle state.
+template <int D>
+__device__ __forceinline__ void deposit_moments_one(const Ctx &c, const BoxDev &b, const ItemGeom &gm,
+                                                    const MixedConst &k, const int ci[3], const float o[3],
+                                                    const float v[3], float ig, int *sD, unsigned long long *mout)
+{
+    Wts w2;
+    w2.z[0] = 0.f;
+    w2.z[1] = 1.f;
+    w2.z[2] = 0.f;
+    int rel2[3] = {0, 0, 0};
+    bool in2 = tile_rel(c, b, gm, 0, ci[0], rel2[0]);
+    in2 &= tile_rel(c, b, gm, 1, ci[1], rel2[1]);
+    tsc_from_offset<float>(o[0], w2.x);
+    tsc_from_offset<float>(o[1], w2.y);
+    if (D == 3) {
+        in2 &= tile_rel(c, b, gm, 2, ci[2], rel2[2]);
+        tsc_from_offset<float>(o[2], w2.z);
+    }
+    pin_weights(w2);
+    const float qj = k.qn * ig;
+    const float qm[4] = {pinned(k.qn), pinned(qj * v[0]), pinned(qj * v[1]), pinned(qj * v[2])};
+    if (within(qm, k.qb, CH_N)) {
+        const float qs[4] = {pinned(qm[0] * k.st[4]), pinned(qm[1] * k.st[5]), pinned(qm[2] * k.st[6]),
+                             pinned(qm[3] * k.st[7])};
+        if (in2) {
+            const int base2 = (rel2[0] - 1) + c.ts[1] * (rel2[1] - 1) + (D == 3 ? c.ts[2] * (rel2[2] - 1) : 0);
+            deposit_tile<D>(c, base2, w2, qs, CH_N, sD);
+        } else {
+            deposit_global_split<D>(c, b, ci[0], ci[1], ci[2], w2, qs[0], qs[1], qs[2], qs[3], CH_N, k.ksh[4],
+                                    k.ksh[5], k.ksh[6], k.ksh[7], mout);
+        }
+    } else {
+        deposit_global<D>(c, b, ci[0], ci[1], ci[2], w2, qm[0] * k.gs[4], qm[1] * k.gs[5], qm[2] * k.gs[6],
+                          qm[3] * k.gs[7], mout);
+    }
+}
+
 template <int D, bool FULL>
 __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const ItemGeom &gm, const MixedConst &k,
                                           int64_t j, const PIn &pin, const float4 *sFa, const float2 *sFb,
@@ -464,7 +506,7 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
 
     // dv = h E + rot without cancellation; the rotation keeps |v|, so dE_k is
     // the change of the two half kicks, E_k(a) - E_k(b) = (a-b).(a+b)/(ga+gb)
-    const float ig2 = rsqrtf(fmaf(vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2], k.invC2, 1.f));
+    const float ig2 = rsqrtf(fmaf(vsq3(vn), k.invC2, 1.f));
     const float gn = 1.f / ign, g1 = 1.f / ig1, g2 = 1.f / ig2;
     const float dEk = (e0 * (vn[0] + v10) + e1 * (vn[1] + v11) + e2 * (vn[2] + v12)) / (g2 + g1) +
                       (e0 * (v00 + v[0]) + e1 * (v01 + v[1]) + e2 * (v02 + v[2])) / (g1 + gn);
@@ -503,38 +545,8 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
         return 0.f;
     }
 
-    if (FULL) {
-        Wts w2;
-        w2.z[0] = 0.f;
-        w2.z[1] = 1.f;
-        w2.z[2] = 0.f;
-        int rel2[3] = {0, 0, 0};
-        bool in2 = tile_rel(c, b, gm, 0, ci[0], rel2[0]);
-        in2 &= tile_rel(c, b, gm, 1, ci[1], rel2[1]);
-        tsc_from_offset<float>(o[0], w2.x);
-        tsc_from_offset<float>(o[1], w2.y);
-        if (D == 3) {
-            in2 &= tile_rel(c, b, gm, 2, ci[2], rel2[2]);
-            tsc_from_offset<float>(o[2], w2.z);
-        }
-        pin_weights(w2);
-        const float qj = k.qn * ig2;
-        const float qm[4] = {pinned(k.qn), pinned(qj * vn[0]), pinned(qj * vn[1]), pinned(qj * vn[2])};
-        if (within(qm, k.qb, CH_N)) {
-            const float qs[4] = {pinned(qm[0] * k.st[4]), pinned(qm[1] * k.st[5]), pinned(qm[2] * k.st[6]),
-                                 pinned(qm[3] * k.st[7])};
-            if (in2) {
-                const int base2 = (rel2[0] - 1) + c.ts[1] * (rel2[1] - 1) + (D == 3 ? c.ts[2] * (rel2[2] - 1) : 0);
-                deposit_tile<D>(c, base2, w2, qs, CH_N, sD);
-            } else {
-                deposit_global_split<D>(c, b, ci[0], ci[1], ci[2], w2, qs[0], qs[1], qs[2], qs[3], CH_N, k.ksh[4],
-                                        k.ksh[5], k.ksh[6], k.ksh[7], mout);
-            }
-        } else {
-            deposit_global<D>(c, b, ci[0], ci[1], ci[2], w2, qm[0] * k.gs[4], qm[1] * k.gs[5], qm[2] * k.gs[6],
-                              qm[3] * k.gs[7], mout);
-        }
-    }
+    if (FULL)
+        deposit_moments_one<D>(c, b, gm, k, ci, o, vn, ig2, sD, mout);
 
     if (!isfinite(vn[0] + vn[1] + vn[2]))
         set_status(c.status, MHDPIC_ST_NONFINITE);
@@ -678,6 +690,83 @@ __global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_push_mixed(Ctx 
     }
 }
 
+// Standalone charge/current deposit (eq:nJCR) at the particles' positions,
+// through the same shared fixed-point tile as the push: persistent CTAs over
+// the brick items of the last sort, particles read through the pending
+// permutation when there is one (nothing is written back), each deposited by
+// deposit_moments_one, so a particle contributes the same integers as in
+// the push that put it there.  Moments go to momdep[cur], which the caller
+// has zeroed.
+template <int D>
+__global__ void __launch_bounds__(PUSH_THREADS) k_deposit_mixed(Ctx c, const WorkItem *__restrict__ items,
+                                                               const int32_t *__restrict__ nitems,
+                                                               int32_t *__restrict__ work_ctr, int cur)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int S = c.tile_slots;
+    int *sD = reinterpret_cast<int *>(smem);
+    __shared__ int s_item;
+    __shared__ MixedConst s_k;
+    unsigned long long *mout = c.momdep[cur];
+    const int nit = *nitems;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int NW = PUSH_THREADS / 32;
+    const bool gather = c.perm_src != nullptr;
+
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_item = atomicAdd(work_ctr, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nit)
+            break;
+        const WorkItem it = items[item];
+        const BoxDev &b = c.boxes[it.box];
+        const ItemGeom gm = item_geom(c, b, it.brick, D);
+        for (int s = threadIdx.x + CH_N * S; s < NCH * S; s += PUSH_THREADS)
+            sD[s] = 0;
+        for (int s = threadIdx.x + (NCH + CH_N) * S; s < NPLANE * S; s += PUSH_THREADS)
+            sD[s] = 0;
+        if (threadIdx.x == 0)
+            item_const(b, 0.f, it.p1 - it.p0, D, s_k);
+        __syncthreads();
+        const MixedConst &k = s_k;
+        {
+            const LaneRange lr = lane_range(it, wid, NW);
+            const int64_t lane0 = lane * lr.q;
+            for (int64_t r = lr.first; r < lr.q; r += lr.stride) {
+                if (lane0 + r >= lr.cnt)
+                    continue;
+                const int64_t j = lr.base + lane0 + r;
+                const int64_t src = gather ? (int64_t)__ldg(c.perm_src + j) : j;
+                const PIn pin = load_global<D>(c, src);
+                if (pin.cell == DEAD_CELL)
+                    continue;
+                int ci[3];
+                decode_cell(b, pin.cell, ci);
+                const float ig = rsqrtf(fmaf(vsq3(pin.v), k.invC2, 1.f));
+                deposit_moments_one<D>(c, b, gm, k, ci, pin.o, pin.v, ig, sD, mout);
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < c.tile_vol; t += PUSH_THREADS) {
+            int tx = t % c.tile[0], r = t / c.tile[0];
+            int ty = r % c.tile[1], tz = r / c.tile[1];
+            int64_t g = tile_global(c, b, gm, tx, ty, tz, D);
+            int s = tile_slot(c, tx, ty, tz);
+#pragma unroll
+            for (int ch = CH_N; ch < NCH; ++ch) {
+                long long v = (long long)sD[ch * S + s] * (1ll << KLO) + sD[(NCH + ch) * S + s];
+                if (ch == CH_N)
+                    v = sD[ch * S + s];
+                if (v)
+                    atomicAdd(mout + (ch - CH_N) * c.nc + g, (unsigned long long)v << k.ksh[ch]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 constexpr int PUSH_SMEM_LIMIT = 200 * 1024;
 
 template <int D, bool FULL>
@@ -720,6 +809,21 @@ int push_blocks_per_sm_mixed(const Ctx &c)
     const size_t bytes = push_smem_bytes_mixed(c);
     const int nb = c.ndim == 3 ? occupancy_all<3>(bytes) : occupancy_all<2>(bytes);
     return nb < 1 ? 1 : nb;
+}
+
+int launch_deposit_mixed(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur, int grid_blocks,
+                         cudaStream_t st)
+{
+    const size_t bytes = sizeof(int) * NPLANE * (size_t)c.tile_slots;
+    cudaMemsetAsync(work_ctr, 0, sizeof(int32_t), st);
+    if (c.ndim == 3) {
+        cudaFuncSetAttribute(k_deposit_mixed<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, PUSH_SMEM_LIMIT);
+        k_deposit_mixed<3><<<grid_blocks, PUSH_THREADS, bytes, st>>>(c, s.items, s.nitems, work_ctr, cur);
+    } else {
+        cudaFuncSetAttribute(k_deposit_mixed<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, PUSH_SMEM_LIMIT);
+        k_deposit_mixed<2><<<grid_blocks, PUSH_THREADS, bytes, st>>>(c, s.items, s.nitems, work_ctr, cur);
+    }
+    return 1;
 }
 
 int launch_push_mixed(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur_out, int full, double dt,

@@ -354,6 +354,33 @@ int do_prep(mhdpic_ctx *c, int apply)
     return rc;
 }
 
+// Charge/current deposit of the current particles into moments buffer cur.
+// Mixed precision goes through the push's tile over the work list of a sort
+// of the current particles: the list is current when `listed` (right after
+// a sort that has been applied), else a pending sort is used or one is made
+// (the next push applies it).  FP64 uses the direct global-memory deposit.
+int deposit_current(mhdpic_ctx *c, bool listed)
+{
+    int rc;
+    if (c->k.prec != MHDPIC_PREC_MIXED) {
+        if ((rc = materialize(c)))
+            return rc;
+        return check_launch(c, launch_moments(c->k, c->cur, c->stream));
+    }
+    Ctx kk = c->k;
+    if (!listed) {
+        if (!c->pending) {
+            if ((rc = check_launch(c, launch_sort(c->k, c->s, nullptr, nullptr, c->stream))) ||
+                (rc = check_launch(c, launch_max_count(c->k, c->s, c->stream))))
+                return rc;
+            c->pending = true;
+        }
+        kk.perm_src = c->s.perm;   // read through the permutation, write nothing
+    }
+    CK(cudaMemsetAsync(c->k.momdep[c->cur], 0, sizeof(unsigned long long) * 4 * c->k.nc, c->stream));
+    return check_launch(c, launch_deposit_mixed(kk, c->s, c->work_ctr, c->cur, c->grid_blocks, c->stream));
+}
+
 // Stage the fields of the current gas when a call changed it since.
 int restage_if_stale(mhdpic_ctx *c)
 {
@@ -631,7 +658,7 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
 
     // moments at the initial positions, maxima, staged fields
     c->cur = 0;
-    if ((rc = check_launch(c, launch_moments(k, c->cur, st))) || (rc = check_launch(c, launch_vmax(k, st))) ||
+    if ((rc = deposit_current(c, true)) || (rc = check_launch(c, launch_vmax(k, st))) ||
         (rc = do_prep(c, 0)))
         return bail(rc);
     if ((rc = copy_particles(c, false)))
@@ -737,11 +764,11 @@ int mhdpic_deposit(mhdpic_ctx *c)
     if (!c || !c->valid)
         return fail(MHDPIC_E_STATE, "invalid context");
     int rc;
-    if ((rc = copy_particles(c, true)) || (rc = copy_gas(c, true, true)) || (rc = materialize(c)))
+    if ((rc = copy_particles(c, true)) || (rc = copy_gas(c, true, true)))
         return rc;
     // the stage kernel clears buffer cur^1, so deposit into cur and stage from it
-    if ((rc = check_launch(c, launch_moments(c->k, c->cur, c->stream))) ||
-        (rc = check_launch(c, launch_vmax(c->k, c->stream))) || (rc = do_prep(c, 0)))
+    if ((rc = deposit_current(c, false)) || (rc = check_launch(c, launch_vmax(c->k, c->stream))) ||
+        (rc = do_prep(c, 0)))
         return rc;
     return MHDPIC_OK;
 }

@@ -205,6 +205,11 @@ int launch_push_mixed(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int
                       double dt, int grid_blocks, cudaStream_t st);
 int launch_push_f64(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur_out, int full,
                     double dt, int grid_blocks, cudaStream_t st);
+// mixed precision: charge/current deposit at the stored positions through the
+// push's tile, over the work list of the last sort (particles read through
+// c.perm_src when set); momdep[cur] must be zero
+int launch_deposit_mixed(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur, int grid_blocks,
+                         cudaStream_t st);
 int launch_scales(const Ctx &c, double dt, cudaStream_t st);
 int launch_totals(const Ctx &c, double *partials, int nchunks, double *out, cudaStream_t st);
 int launch_fixed_to_double(const Ctx &c, const unsigned long long *src, int ch0, double *out,

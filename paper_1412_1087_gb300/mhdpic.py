@@ -382,8 +382,12 @@ class Engine:
     # (mhdpic_sync_particles) and orders torch's current stream after it.
     def sync_particles(self) -> None:
         mhdpic_sync_particles(self.ctx)
+        if self.memory == MHDPIC_MEM_HOST:
+            # host buffers: the library's copies back are asynchronous
+            self.stream.synchronize()
+            return
         cur = self.torch.cuda.current_stream(self.device)
-        if self.memory != MHDPIC_MEM_HOST and cur != self.stream:
+        if cur != self.stream:
             cur.wait_stream(self.stream)
 
     def _synced(self, t):

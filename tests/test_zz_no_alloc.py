@@ -61,9 +61,13 @@ def test_noalloc_deposit_equals_context_deposit_on_two_calls(case):
         out = torch.full((4, box.ncell), float("nan"), dtype=torch.float64, device="cuda")
         _call(eng, box, prec, out)
         outs.append(out.cpu().numpy())
+    # the context deposits mixed-precision moments as the push does (f32
+    # weights), the allocation-free call in double: the parity tolerance of
+    # each precision
+    tol = 1e-5 if prec == m.MHDPIC_PREC_MIXED else 1e-12
     for o in outs:
         for q in range(4):
-            assert rel_l2(o[q], ref[q]) < 1e-12, (case, q, rel_l2(o[q], ref[q]))
+            assert rel_l2(o[q], ref[q]) < tol, (case, q, rel_l2(o[q], ref[q]))
     # the second call starts from a cleared scratch: identical to the first
     assert np.array_equal(outs[0], outs[1])
     eng.close()
