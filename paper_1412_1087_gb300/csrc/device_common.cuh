@@ -25,6 +25,16 @@ __device__ __forceinline__ int find_box(const int64_t *__restrict__ starts, int 
     return lo;
 }
 
+// Slices of a box in the chunked reductions (totals, spectrum): one per
+// per_chunk particles and cells, at least one, at most nchunks, so that
+// boxes of very different sizes keep the blocks evenly loaded.
+__device__ __forceinline__ int box_chunks(const BoxDev &b, int64_t per_chunk, int nchunks)
+{
+    const int64_t work = (b.part1 - b.part0) + b.ncell;
+    const int64_t k = (work + per_chunk - 1) / per_chunk;
+    return (int)(k < 1 ? 1 : (k > nchunks ? nchunks : k));
+}
+
 // Map an unwrapped cell coordinate g along dimension d onto the box: periodic
 // wrap, or mirror fold at a reflecting wall (cell -1-k mirrors cell k); beyond
 // an open face the cells take the last cell's values (and deposits).

@@ -213,13 +213,21 @@ __global__ void k_moments(Ctx c, int cur)
 // of the box's cells and particles in a fixed order; a second kernel adds the
 // chunks in order.  out per box: P_gas(3), E_gas, P_CR(3), E_CR.
 template <int PREC>
-__global__ void __launch_bounds__(256) k_totals_partial(Ctx c, int nchunks, double *partials)
+__global__ void __launch_bounds__(256) k_totals_partial(Ctx c, int nchunks, int64_t per_chunk, double *partials)
 {
     const int bx = blockIdx.y, chunk = blockIdx.x;
     const BoxDev &b = c.boxes[bx];
     const int64_t nc = c.nc;
+    // each box takes as many of the nchunks slices as its size asks for;
+    // the others add zeros
+    const int nbc = box_chunks(b, per_chunk, nchunks);
+    if (chunk >= nbc) {
+        if (threadIdx.x < 8)
+            partials[((int64_t)bx * nchunks + chunk) * 8 + threadIdx.x] = 0.0;
+        return;
+    }
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int64_t cs = (b.ncell + nchunks - 1) / nchunks;
+    int64_t cs = (b.ncell + nbc - 1) / nbc;
     int64_t c0 = b.cell0 + chunk * cs, c1 = min(b.cell0 + b.ncell, c0 + cs);
     for (int64_t g = c0 + threadIdx.x; g < c1; g += blockDim.x) {
         for (int d = 0; d < 3; ++d)
@@ -227,7 +235,7 @@ __global__ void __launch_bounds__(256) k_totals_partial(Ctx c, int nchunks, doub
         acc[3] += c.egas[g] * b.dV;
     }
     int64_t npb = b.part1 - b.part0;
-    int64_t ps = (npb + nchunks - 1) / nchunks;
+    int64_t ps = (npb + nbc - 1) / nbc;
     int64_t p0 = b.part0 + chunk * ps, p1 = min(b.part1, p0 + ps);
     for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
         double v[3];
@@ -369,13 +377,13 @@ int launch_moments(const Ctx &c, int cur, cudaStream_t st)
     return 1;
 }
 
-int launch_totals(const Ctx &c, double *partials, int nchunks, double *out, cudaStream_t st)
+int launch_totals(const Ctx &c, double *partials, int nchunks, int64_t per_chunk, double *out, cudaStream_t st)
 {
     dim3 grid(nchunks, c.nbox);
     if (c.prec == MHDPIC_PREC_MIXED)
-        k_totals_partial<MHDPIC_PREC_MIXED><<<grid, 256, 0, st>>>(c, nchunks, partials);
+        k_totals_partial<MHDPIC_PREC_MIXED><<<grid, 256, 0, st>>>(c, nchunks, per_chunk, partials);
     else
-        k_totals_partial<MHDPIC_PREC_FP64><<<grid, 256, 0, st>>>(c, nchunks, partials);
+        k_totals_partial<MHDPIC_PREC_FP64><<<grid, 256, 0, st>>>(c, nchunks, per_chunk, partials);
     k_totals_final<<<(c.nbox * 8 + 255) / 256, 256, 0, st>>>(c.nbox, nchunks, partials, out);
     return 2;
 }

@@ -18,7 +18,7 @@ namespace {
 constexpr int SPEC_THREADS = 256;
 
 template <int PREC>
-__global__ void __launch_bounds__(SPEC_THREADS) k_spectrum_partial(Ctx c, SpecArgs a, int nchunks,
+__global__ void __launch_bounds__(SPEC_THREADS) k_spectrum_partial(Ctx c, SpecArgs a, int nchunks, int64_t per_chunk,
                                                                     unsigned long long *__restrict__ counts,
                                                                     double *__restrict__ partials)
 {
@@ -28,6 +28,14 @@ __global__ void __launch_bounds__(SPEC_THREADS) k_spectrum_partial(Ctx c, SpecAr
     const int bx = blockIdx.y, chunk = blockIdx.x;
     const BoxDev &b = c.boxes[bx];
     const int nb = a.nbins;
+    // each box takes as many of the nchunks slices as its size asks for;
+    // the others add zeros
+    const int nbc = box_chunks(b, per_chunk, nchunks);
+    if (chunk >= nbc) {
+        if (threadIdx.x < 2)
+            partials[((int64_t)bx * nchunks + chunk) * 2 + threadIdx.x] = 0.0;
+        return;
+    }
     for (int i = threadIdx.x; i < nb; i += SPEC_THREADS)
         hist[i] = 0u;
     for (int i = threadIdx.x; i <= nb; i += SPEC_THREADS)
@@ -35,7 +43,7 @@ __global__ void __launch_bounds__(SPEC_THREADS) k_spectrum_partial(Ctx c, SpecAr
     __syncthreads();
 
     const int64_t npb = b.part1 - b.part0;
-    const int64_t ps = (npb + nchunks - 1) / nchunks;
+    const int64_t ps = (npb + nbc - 1) / nbc;
     const int64_t p0 = b.part0 + chunk * ps, p1 = min(b.part1, p0 + ps);
     double s1 = 0.0, s0 = 0.0;
     for (int64_t i = p0 + threadIdx.x; i < p1; i += SPEC_THREADS) {
@@ -154,15 +162,16 @@ int grid_for(int64_t n, int threads)
 
 }  // namespace
 
-int launch_spectrum(const Ctx &c, const SpecArgs &a, int nchunks, unsigned long long *counts, double *partials,
+int launch_spectrum(const Ctx &c, const SpecArgs &a, int nchunks, int64_t per_chunk, unsigned long long *counts,
+                    double *partials,
                     double *sums, cudaStream_t st)
 {
     cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * (size_t)c.nbox * a.nbins, st);
     dim3 grid(nchunks, c.nbox);
     if (c.prec == MHDPIC_PREC_MIXED)
-        k_spectrum_partial<MHDPIC_PREC_MIXED><<<grid, SPEC_THREADS, 0, st>>>(c, a, nchunks, counts, partials);
+        k_spectrum_partial<MHDPIC_PREC_MIXED><<<grid, SPEC_THREADS, 0, st>>>(c, a, nchunks, per_chunk, counts, partials);
     else
-        k_spectrum_partial<MHDPIC_PREC_FP64><<<grid, SPEC_THREADS, 0, st>>>(c, a, nchunks, counts, partials);
+        k_spectrum_partial<MHDPIC_PREC_FP64><<<grid, SPEC_THREADS, 0, st>>>(c, a, nchunks, per_chunk, counts, partials);
     k_spectrum_final<<<(c.nbox * 2 + 255) / 256, 256, 0, st>>>(c.nbox, nchunks, partials, sums);
     return 2;
 }

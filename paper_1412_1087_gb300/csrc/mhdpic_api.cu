@@ -60,7 +60,8 @@ struct mhdpic_ctx {
     int cur = 0;              // moments buffer holding the latest deposit
     bool next_clear = false;  // buffer cur^1 is known to be zero (the stage kernel clears it)
     int grid_blocks = 0;      // persistent push grid
-    int nchunks = 0;          // totals reduction chunks per box
+    int nchunks = 0;          // totals reduction slices per box, at most
+    int64_t chunk_work = 1;   // particles + cells per slice (chunked reductions)
     int32_t *work_ctr = nullptr;
     double *partials = nullptr;
     double *totals_dev = nullptr;
@@ -562,8 +563,19 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         (rc = c->alloc(&c->work_ctr, 1)))
         return bail(rc);
     k.key_off = c->s.offset;
-    c->nchunks = std::max(1, 1216 / nbox);   // totals: about 8 blocks per SM over all boxes
-    c->spec_chunks = std::max(1, 1216 / nbox);   // about 8 blocks per SM over all boxes
+    // chunked reductions (totals, spectrum): about 8 blocks per SM over all
+    // boxes, each box sliced in proportion to its particles and cells
+    {
+        int64_t work = 0, wmax = 0;
+        for (int b = 0; b < nbox; ++b) {
+            const int64_t w = (c->part_start[b + 1] - c->part_start[b]) + c->boxes[b].ncell;
+            work += w;
+            wmax = std::max(wmax, w);
+        }
+        c->chunk_work = std::max<int64_t>(1, (work + 1215) / 1216);
+        c->nchunks = (int)std::max<int64_t>(1, std::min<int64_t>(1216, (wmax + c->chunk_work - 1) / c->chunk_work));
+        c->spec_chunks = c->nchunks;
+    }
     if ((rc = c->alloc(&c->partials, (size_t)nbox * c->nchunks * 8)) || (rc = c->alloc(&c->totals_dev, 8 * nbox)) ||
         (rc = c->alloc(&c->spec_counts, (size_t)nbox * MHDPIC_SPEC_MAX_BINS)) ||
         (rc = c->alloc(&c->spec_partials, (size_t)nbox * c->spec_chunks * 2)) ||
@@ -787,7 +799,7 @@ int mhdpic_apply_feedback(mhdpic_ctx *c, double *totals_out)
     if (totals_out) {
         if ((rc = copy_particles(c, true)) || (rc = materialize(c)))
             return rc;
-        if ((rc = check_launch(c, launch_totals(c->k, c->partials, c->nchunks, c->totals_dev, c->stream))))
+        if ((rc = check_launch(c, launch_totals(c->k, c->partials, c->nchunks, c->chunk_work, c->totals_dev, c->stream))))
             return rc;
         CK(cudaMemcpyAsync(totals_out, c->totals_dev, sizeof(double) * 8 * c->nbox, cudaMemcpyDeviceToHost,
                            c->stream));
@@ -980,7 +992,7 @@ int mhdpic_gas_correct(mhdpic_ctx *c, double dt, int32_t model, double *totals_o
     if (totals_out) {
         if ((rc = copy_particles(c, true)) || (rc = materialize(c)))
             return rc;
-        if ((rc = check_launch(c, launch_totals(c->k, c->partials, c->nchunks, c->totals_dev, c->stream))))
+        if ((rc = check_launch(c, launch_totals(c->k, c->partials, c->nchunks, c->chunk_work, c->totals_dev, c->stream))))
             return rc;
         CK(cudaMemcpyAsync(totals_out, c->totals_dev, sizeof(double) * 8 * c->nbox, cudaMemcpyDeviceToHost,
                            c->stream));
@@ -1021,7 +1033,7 @@ int mhdpic_spectrum(mhdpic_ctx *c, int32_t kind, int32_t nbins, const double *ed
     if ((rc = copy_particles(c, true)))
         return rc;
     CK(cudaMemcpyAsync(c->spec_edges, edges, sizeof(double) * (nbins + 1), cudaMemcpyHostToDevice, c->stream));
-    if ((rc = check_launch(c, launch_spectrum(c->k, a, c->spec_chunks, c->spec_counts, c->spec_partials,
+    if ((rc = check_launch(c, launch_spectrum(c->k, a, c->spec_chunks, c->chunk_work, c->spec_counts, c->spec_partials,
                                               c->totals_dev, c->stream))))
         return rc;
     static_assert(sizeof(unsigned long long) == sizeof(int64_t), "count width");

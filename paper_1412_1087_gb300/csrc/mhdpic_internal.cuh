@@ -211,7 +211,9 @@ int launch_push_f64(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int c
 int launch_deposit_mixed(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur, int grid_blocks,
                          cudaStream_t st);
 int launch_scales(const Ctx &c, double dt, cudaStream_t st);
-int launch_totals(const Ctx &c, double *partials, int nchunks, double *out, cudaStream_t st);
+// chunked reductions: a box takes ceil((particles + cells) / per_chunk)
+// slices, at least one and at most nchunks
+int launch_totals(const Ctx &c, double *partials, int nchunks, int64_t per_chunk, double *out, cudaStream_t st);
 int launch_fixed_to_double(const Ctx &c, const unsigned long long *src, int ch0, double *out,
                            cudaStream_t st);
 int launch_fields_to_double(const Ctx &c, double *out, cudaStream_t st);
@@ -222,8 +224,8 @@ struct SpecArgs {
     double region[6];
     const double *edges;
 };
-int launch_spectrum(const Ctx &c, const SpecArgs &a, int nchunks, unsigned long long *counts, double *partials,
-                    double *sums, cudaStream_t st);
+int launch_spectrum(const Ctx &c, const SpecArgs &a, int nchunks, int64_t per_chunk, unsigned long long *counts,
+                    double *partials, double *sums, cudaStream_t st);
 int launch_lambda(const Ctx &c, int cur, double *out, cudaStream_t st);
 // coupled step (App. A.3): gas half state into half[8][nc] plus field
 // staging; gas full step from the half state and the corrector deposit
