@@ -17,8 +17,7 @@
  *   App. A.2     drift-kick-rotate-kick-drift Boris step, E-parallel cleaning
  *   App. A.3     corrector deposit of -dM, -dE_k at x^(n+1/2)
  *
- * Readings where the paper is garbled or silent (each also listed in the
- * design notes):
+ * Readings where the paper is garbled or silent:
  *   - Boris rotation vector b = (h/2) B / gamma (the standard half angle; the
  *     printed "b = h B / gamma" would double the rotation angle).
  *   - E-parallel cleaning E <- E - (E.B) B / |B|^2, skipped when |B| = 0.
