@@ -305,3 +305,34 @@ def test_injection_times_need_tracking_and_valid_arguments():
     tg, clock = eng.injection_times()
     assert clock == 1.5 and np.all(np.isinf(tg))
     eng.close()
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_removal_inside_sub_cycled_pushes(prec):
+    """Each sub-step advances the clock: four sub-steps in one call remove
+    the same particles, at the same clock, as four single pushes in the same
+    staged fields (no feedback in between)."""
+    box = _box(seed=10)
+    dt = _pow2_dt(box)
+    t_inj = _early_times(box.np, dt, 10)
+    res = []
+    for split in (False, True):
+        eng = m.Engine([box], precision=prec)
+        eng.set_injection_times(t_inj, 0.0, 2.5 * dt)
+        if split:
+            for _ in range(4):
+                eng.interp_push(dt, 1)
+        else:
+            eng.interp_push(dt, 4)
+        tg, clock = eng.injection_times()
+        live = (~np.isnan(eng.x.cpu().numpy()[0])) if prec == FP64 else eng.cell.cpu().numpy() >= 0
+        rows = np.vstack([tg[live], positions_of(eng)[:, live], momenta_of(eng)[:, live]])
+        res.append((clock, rows[:, np.argsort(rows[0])]))
+        assert eng.status() == 0
+        eng.close()
+    (c0, r0), (c1, r1) = res
+    assert c0 == c1 == 4 * dt
+    np.testing.assert_array_equal(r0[0], r1[0])          # the same particles left
+    np.testing.assert_allclose(r0, r1, rtol=0, atol=1e-12 if prec == FP64 else 1e-6)
+    gone = (t_inj < 2.5 * dt) & (2.0 * t_inj <= 4 * dt)
+    assert gone.any() and not set(t_inj[gone].tolist()) & set(r0[0].tolist())
