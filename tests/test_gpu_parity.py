@@ -664,3 +664,53 @@ def test_standalone_deposit_with_host_buffers_and_open_face():
         assert rel_l2(gm[q], md[q]) < TOL[MIXED], q
     assert eng.status() == 0
     eng.close()
+
+
+# --- degenerate inputs ------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_field_free_box_streams_particles_freely(prec):
+    """B = 0: no force, so the four-velocities come back bit for bit, the
+    corrector deposit is exactly zero and the positions follow the oracle's
+    free streaming."""
+    box = wl.periodic_thermal_2d(nx=20, ny=18, ppc=6, dv_amp=0.5, seed=6)
+    box.B = np.zeros_like(box.B)
+    box.hall = 1
+    eng = _engine(box, prec)
+    _, _, x, v = sorted_oracle_state(box)
+    st = orc.State(box, x, v)
+    v_before = momenta_of(eng).copy()
+    corr, md = st.push_only(box.dt)
+    eng.interp_push(box.dt, 1)
+    np.testing.assert_array_equal(momenta_of(eng), v_before)
+    assert np.all(eng.deposits(0).cpu().numpy() == 0.0)
+    _compare_step(eng, box, st, corr, md, prec)
+    assert eng.status() == 0
+    eng.close()
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_context_without_particles(prec):
+    """A box with no particles at all goes through every call: zero moments,
+    zero corrector, the gas totals unchanged, an empty spectrum."""
+    box = wl.periodic_thermal_2d(nx=16, ny=16, ppc=2, seed=7)
+    box.cell = box.cell[:0]
+    box.off = np.ascontiguousarray(box.off[:, :0])
+    box.p = np.ascontiguousarray(box.p[:, :0])
+    eng = _engine(box, prec)
+    t0 = eng.apply_feedback(totals=True)[0]
+    for _ in range(3):
+        eng.interp_push(box.dt, 1)
+        eng.apply_feedback()
+        eng.sort()
+    eng.deposit()
+    eng.run(box.dt, 6, 2)
+    t1 = eng.apply_feedback(totals=True)[0]
+    np.testing.assert_array_equal(t1, t0)
+    assert not t1[4:].any()
+    assert not eng.deposits(0).cpu().numpy().any() and not eng.deposits(1).cpu().numpy().any()
+    counts, _ = eng.spectrum(m.MHDPIC_SPEC_ENERGY, np.array([0.0, 1.0, 10.0]))
+    assert int(np.asarray(counts).sum()) == 0
+    assert eng.live_particles() == 0
+    assert eng.status() == 0
+    eng.close()

@@ -579,3 +579,30 @@ def test_lambda_map_matches_the_hall_field():
     # no field: Lambda is defined as zero
     lam0 = orc.lambda_map(g, p1, rho, rho * vel, np.zeros((3, nc)), md)
     assert not lam0.any()
+
+
+def test_field_free_box_streams_particles_freely():
+    """B = 0 everywhere: E0 = -v x B and the CR-Hall force vanish, so every
+    particle keeps its four-velocity exactly, moves by u dt with
+    u = v/gamma (periodic wrap), and the corrector deposit is exactly zero."""
+    b = wl.periodic_thermal_2d(nx=12, ny=10, ppc=4, dv_amp=0.5, seed=5)
+    b.B = np.zeros_like(b.B)
+    b.hall = 1
+    g, p = orc.grid_of(b), orc.params_of(b)
+    x = np.ascontiguousarray(wl.absolute_positions(b))
+    v = np.ascontiguousarray(b.p.astype(np.float64))
+    x0, v0 = x.copy(), v.copy()
+    md = orc.deposit_moments(g, p, x, v, b.ncell)
+    E = orc.field_prep(g, p, b.rho, b.mom, b.B, md)
+    assert np.all(E == 0.0)
+    corr = np.zeros((4, b.ncell))
+    dt = b.dt
+    orc.push(g, p, dt, x, v, E, b.B, corr, None)
+    np.testing.assert_array_equal(v, v0)
+    assert np.all(corr == 0.0)
+    gam = np.sqrt(1.0 + (v0 ** 2).sum(axis=0) / b.C ** 2)
+    for d in range(2):
+        L = b.n[d] * b.dx[d]
+        want = (x0[d] + v0[d] / gam * dt) % L
+        diff = (x[d] - want + L / 2) % L - L / 2
+        assert np.abs(diff).max() < 1e-12 * L
