@@ -304,14 +304,15 @@ constexpr int ring_planes()
 }
 constexpr int RING_STAGES = 2;
 // Per dimension: 2-D pushes are short, so the kernel hides the particle
-// loads behind a shared-memory ring and runs 4 CTAs per SM with the item
-// constants in shared memory; 3-D pushes are bound by the shared-memory
-// deposits and keep everything in registers at 2 CTAs per SM (the ring
-// measured no faster there and takes shared memory from L1).
+// loads behind a shared-memory ring and runs 3 CTAs per SM (80 registers, no
+// spills in the loop; 4 CTAs at 64 registers spilled and measured slower with
+// a sort every step) with the item constants in shared memory; 3-D pushes
+// keep everything in registers at 2 CTAs per SM (the ring measured no faster
+// there and takes shared memory from L1).
 template <int D>
 constexpr bool STAGED = D == 2;
 template <int D>
-constexpr int MIN_BLOCKS = D == 3 ? 2 : 4;
+constexpr int MIN_BLOCKS = D == 3 ? 2 : 3;
 template <int D>
 constexpr bool CONST_IN_SMEM = D == 2;
 
