@@ -670,7 +670,8 @@ def run_native(args):
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 push + i64 fixed-point deposits",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "dtype_detail": "f32 push, int64 fixed-point deposits, f64 gas and totals",
             "data": "synthetic",
             "config": {"workload": _workload_desc(args), "precision": "mixed", "sort_every": args.sort_every, "sort_every_tuned": tuned,
                        "brick": list(brick) if any(brick) else "default", "brick_tuned": bool(args.tune_layout),
