@@ -714,3 +714,25 @@ def test_context_without_particles(prec):
     assert eng.live_particles() == 0
     assert eng.status() == 0
     eng.close()
+
+
+def test_standalone_deposit_then_graph_replay_changes_nothing():
+    """A standalone deposit leaves a sort pending; graph-replayed steps from
+    there give the same particles (as a set) and the same deposits, bit for
+    bit, as the same steps without it."""
+    box = _lazy_box("beam3d")
+    dt = box.dt
+    outs = []
+    for with_deposit in (False, True):
+        stream = torch.cuda.Stream()
+        eng = m.Engine([box], precision=MIXED, stream=stream)
+        if with_deposit:
+            eng.deposit()
+        eng.run(dt, 8, 2)
+        rows = np.vstack([positions_of(eng), momenta_of(eng)])
+        rows = rows[:, np.lexsort(rows[::-1])]
+        outs.append((rows, eng.deposits(0).cpu().numpy(), eng.deposits(1).cpu().numpy(), eng.mom.cpu().numpy()))
+        assert eng.status() == 0
+        eng.close()
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)
