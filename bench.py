@@ -59,7 +59,7 @@ GAS_CORRECT_BYTES = 32 + 56 + 56 + 56 + 32
 #   3-D, 64^3 x 32 CRs:   393.2 MB + 296.9 MB over 8,388,608 CRs
 #   2-D, 512^2 x 64 CRs:  891.0 MB + 659.3 MB over 16,777,216 CRs
 # Remove an entry whenever its kernel changes, until it is measured again.
-PUSH_TRAFFIC_BYTES_PER_PARTICLE = {"alfvenic_beam_3d": 688.32e6 / 8388608, "bell_2d": 1325.50e6 / 16777216}
+PUSH_TRAFFIC_BYTES_PER_PARTICLE = {"alfvenic_beam_3d": 688.32e6 / 8388608, "bell_2d": 1308.98e6 / 16777216}
 
 
 def _rank_env():

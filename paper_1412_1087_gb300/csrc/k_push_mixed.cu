@@ -30,8 +30,9 @@
 //    the particles fall into items (sort cadence included).  A particle whose
 //    quantities exceed the bound the scales were sized for deposits at the
 //    global scale instead (a choice that depends on the particle alone).
-//  * 2-D: each thread copies its next particle's words into a two-stage
-//    shared-memory ring with cp.async while it pushes the current one.
+//  * 2-D: each thread copies its next two particles' words into a
+//    three-stage shared-memory ring with cp.async while it pushes the
+//    current one.
 #include "push_common.cuh"
 
 namespace mhdpic {
@@ -302,9 +303,10 @@ constexpr int ring_planes()
 {
     return 1 + D + 3;
 }
-constexpr int RING_STAGES = 2;
+constexpr int RING_STAGES = 3;
 // Per dimension: 2-D pushes are short, so the kernel hides the particle
-// loads behind a shared-memory ring and runs 3 CTAs per SM (80 registers, no
+// loads behind a three-stage shared-memory ring (two particles ahead) and
+// runs 3 CTAs per SM (80 registers, no
 // spills in the loop; 4 CTAs at 64 registers spilled and measured slower with
 // a sort every step) with the item constants in shared memory; 3-D pushes
 // keep everything in registers at 2 CTAs per SM (the ring measured no faster
@@ -329,7 +331,7 @@ __device__ __forceinline__ void cp_async_commit()
 
 __device__ __forceinline__ void cp_async_wait_prev()
 {
-    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(RING_STAGES - 1) : "memory");
 }
 
 // Start the copy of source particle i into one stage of this thread's ring
@@ -631,25 +633,29 @@ __global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_push_mixed(Ctx 
                 return gather ? (int64_t)__ldg(c.perm_src + j) : j;
             };
             if (STAGED<D>) {
-                // the next particle's words are copied into shared memory
-                // while the current one is pushed
-                if (rb < re) {
-                    if (valid(rb))
-                        stage_particle<D>(c, src_of(rb), ring);
+                // the next RING_STAGES - 1 particles' words are copied into
+                // shared memory while the current one is pushed
+                constexpr int NS = RING_STAGES;
+#pragma unroll
+                for (int s0 = 0; s0 < NS - 1; ++s0) {
+                    if (valid(rb + s0 * rs))
+                        stage_particle<D>(c, src_of(rb + s0 * rs), ring + s0 * RS);
                     cp_async_commit();
                 }
-                int64_t sn = valid(rb + rs) ? src_of(rb + rs) : 0;
+                int64_t sn = valid(rb + (NS - 1) * rs) ? src_of(rb + (NS - 1) * rs) : 0;
                 int st = 0;
-                for (int64_t r = rb; r < re; r += rs, st ^= 1) {
-                    if (valid(r + rs))
-                        stage_particle<D>(c, sn, ring + (st ^ 1) * RS);
-                    if (valid(r + 2 * rs))
-                        sn = src_of(r + 2 * rs);
+                for (int64_t r = rb; r < re; r += rs) {
+                    const int stn = st == 0 ? NS - 1 : st - 1;
+                    if (valid(r + (NS - 1) * rs))
+                        stage_particle<D>(c, sn, ring + stn * RS);
+                    if (valid(r + NS * rs))
+                        sn = src_of(r + NS * rs);
                     cp_async_commit();
                     cp_async_wait_prev();
                     if (lane0 + r < cnt)
                         vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + lane0 + r, load_staged<D>(ring + st * RS),
                                                            sFa, sFb, sD, mout));
+                    st = st + 1 == NS ? 0 : st + 1;
                 }
             } else {
                 int64_t sn = valid(rb) ? src_of(rb) : 0;
