@@ -51,3 +51,34 @@ def test_aggregate_single_rank_is_identity():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.aggregate_ranks(12.5, 7.0) == (12.5, 7.0)
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
+    """--impl reference times the oracle and prints one JSON line with the
+    contract's keys (the 64^2 x 16 box, one step)."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    bench.main(["--impl", "reference", "--steps", "1", "--warmup", "1", "--workload", "periodic_thermal_2d"])
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["config"]["workload"].startswith("periodic_thermal_2d")
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    bench.main(["--impl", "reference", "--steps", "1", "--warmup", "1", "--workload", "periodic_thermal_2d"])
+    assert capsys.readouterr().out.strip() == ""
