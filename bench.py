@@ -255,6 +255,82 @@ def _cpu_baseline(args, seed, nsteps):
                       % (args.workload, what, live, nsteps), "seconds": dt}
 
 
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _cpu_replica(workload, sample_n, ppc, seed, nsteps, barrier, queue):
+    """One host process of the all-core oracle figure: its own sample box,
+    built before the common start, then nsteps full oracle steps."""
+    try:
+        import oracle as orc
+        from paper_1412_1087_gb300 import workloads as wl
+        args = argparse.Namespace(workload=workload, sample_n=sample_n, ppc=ppc, err_n=0)
+        box, what = _sample_box(args, seed, "cpu")
+        st = orc.State(box, wl.absolute_positions(box), box.p.astype(np.float64))
+        barrier.wait(timeout=600)
+        t0 = time.time()
+        for _ in range(nsteps):
+            st.step(box.dt)
+        queue.put((seed, int((box.cell >= 0).sum()), t0, time.time(), what, None))
+    except Exception as e:  # reported to the parent, which then gives up
+        barrier.abort()
+        queue.put((seed, 0, 0.0, 0.0, "", "%s: %s" % (type(e).__name__, e)))
+
+
+def _cpu_all_cores(args, nsteps, nproc=None):
+    """The oracle as it stands on every host core: one process per core, each
+    advancing its own box of the sample recipe (seeds 1000, 1001, ...); all
+    start together after building their boxes, and the figure is the
+    particle-steps of all processes over the wall time from the common start
+    to the last finish.  Processes are spawned, never forked, so that none
+    inherits a CUDA context."""
+    import multiprocessing as mp
+    import queue as queue_mod
+    if nproc is None:
+        nproc = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(nproc)
+    q = ctx.Queue()
+    saved = {k: os.environ.get(k) for k in _THREAD_VARS}
+    os.environ.update({k: "1" for k in _THREAD_VARS})
+    procs = [ctx.Process(target=_cpu_replica, daemon=True,
+                         args=(args.workload, args.sample_n, args.ppc, 1000 + i, nsteps, barrier, q))
+             for i in range(nproc)]
+    try:
+        for p in procs:
+            p.start()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    res, err = [], None
+    try:
+        for _ in procs:
+            r = q.get(timeout=900)
+            if r[5] is not None:
+                err = r[5]
+                break
+            res.append(r)
+    except queue_mod.Empty:
+        err = "no result within 900 s"
+    for p in procs:
+        p.join(timeout=5 if err is None else 0.1)
+        if p.is_alive():
+            p.terminate()
+            p.join()
+    if err is not None:
+        return {"unavailable": err}
+    t0 = min(r[2] for r in res)
+    wall = max(r[3] for r in res) - t0
+    live = sum(r[1] for r in res)
+    return {"value": live * nsteps / wall, "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "sample": "%d processes, each the %s recipe at %s (%d CRs in all), %d full steps, "
+                      "one thread each" % (nproc, args.workload, res[0][4], live, nsteps),
+            "seconds": wall}
+
+
 def _error_vs_oracle(args, seed, torch, nsteps=10):
     """Both GPU paths against the oracle on a sample of the workload: one step
     (relative L2 of each deposited channel, per box), then nsteps steps with
@@ -663,7 +739,10 @@ def run_native(args):
 
     out = None
     if rank == 0:
-        cpu = _cpu_baseline(args, seed=0, nsteps=args.cpu_steps) if args.cpu_steps > 0 else None
+        # the oracle's host-core figures are taken at one GPU only
+        cpu = _cpu_baseline(args, seed=0, nsteps=args.cpu_steps) if args.cpu_steps > 0 and world == 1 else None
+        if cpu is not None and args.cpu_all_cores:
+            cpu["all_cores"] = _cpu_all_cores(args, args.cpu_steps)
         err = _error_vs_oracle(args, 0, torch) if args.err_n > 0 else None
         if err is not None:
             err["conservation_drift_this_run"] = eng_stats["conservation"]
@@ -751,6 +830,8 @@ def main(argv=None):
     ap.add_argument("--coupled-steps", type=int, default=4,
                     help="time the coupled predictor-corrector step this many steps (0: off)")
     ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--cpu-all-cores", type=int, default=1,
+                    help="also time the oracle on every host core, one process and box per core (0: off)")
     ap.add_argument("--sample-n", type=int, default=40, help="side of the oracle's sample box")
     ap.add_argument("--err-n", type=int, default=24, help="side of the error-check box (0: skip)")
     args = ap.parse_args(argv)

@@ -82,3 +82,27 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
     monkeypatch.setenv("LOCAL_RANK", "1")
     bench.main(["--impl", "reference", "--steps", "1", "--warmup", "1", "--workload", "periodic_thermal_2d"])
     assert capsys.readouterr().out.strip() == ""
+
+
+def test_oracle_on_every_core_figure():
+    """The all-core oracle figure: one spawned process and box per core, the
+    particle-steps of all of them over the common wall time."""
+    import argparse
+    sys.path.insert(0, ROOT)
+    import bench
+    a = argparse.Namespace(workload="periodic_thermal_2d", sample_n=0, ppc=16, err_n=0)
+    r = bench._cpu_all_cores(a, 1, nproc=2)
+    assert r["cores"] == 2 and r["kind"] == "oracle" and r["unit"] == bench.UNIT
+    assert "2 processes" in r["sample"] and "(131072 CRs in all)" in r["sample"]
+    assert r["value"] > 0 and abs(r["value"] * r["seconds"] - 131072) < 1e-6 * 131072
+
+
+def test_oracle_on_every_core_reports_a_failed_process():
+    """A process that cannot build its box ends the figure with the reason
+    instead of leaving the others waiting."""
+    import argparse
+    sys.path.insert(0, ROOT)
+    import bench
+    a = argparse.Namespace(workload="alfvenic_beam_3d", sample_n=-4, ppc=32, err_n=0)
+    r = bench._cpu_all_cores(a, 1, nproc=2)
+    assert set(r) == {"unavailable"} and r["unavailable"]
