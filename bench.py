@@ -258,7 +258,7 @@ def _cpu_baseline(args, seed, nsteps):
 _THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
 
 
-def _cpu_replica(workload, sample_n, ppc, seed, nsteps, barrier, queue):
+def _cpu_replica(workload, sample_n, ppc, seed, nsteps, barrier, queue, wait_s):
     """One host process of the all-core oracle figure: its own sample box,
     built before the common start, then nsteps full oracle steps."""
     try:
@@ -267,7 +267,7 @@ def _cpu_replica(workload, sample_n, ppc, seed, nsteps, barrier, queue):
         args = argparse.Namespace(workload=workload, sample_n=sample_n, ppc=ppc, err_n=0)
         box, what = _sample_box(args, seed, "cpu")
         st = orc.State(box, wl.absolute_positions(box), box.p.astype(np.float64))
-        barrier.wait(timeout=600)
+        barrier.wait(timeout=wait_s)
         t0 = time.time()
         for _ in range(nsteps):
             st.step(box.dt)
@@ -277,13 +277,14 @@ def _cpu_replica(workload, sample_n, ppc, seed, nsteps, barrier, queue):
         queue.put((seed, 0, 0.0, 0.0, "", "%s: %s" % (type(e).__name__, e)))
 
 
-def _cpu_all_cores(args, nsteps, nproc=None):
+def _cpu_all_cores(args, nsteps, nproc=None, limit_s=300.0):
     """The oracle as it stands on every host core: one process per core, each
     advancing its own box of the sample recipe (seeds 1000, 1001, ...); all
     start together after building their boxes, and the figure is the
     particle-steps of all processes over the wall time from the common start
     to the last finish.  Processes are spawned, never forked, so that none
-    inherits a CUDA context."""
+    inherits a CUDA context.  A process that fails, or no result within
+    limit_s, ends the figure with the reason."""
     import multiprocessing as mp
     import queue as queue_mod
     if nproc is None:
@@ -294,7 +295,7 @@ def _cpu_all_cores(args, nsteps, nproc=None):
     saved = {k: os.environ.get(k) for k in _THREAD_VARS}
     os.environ.update({k: "1" for k in _THREAD_VARS})
     procs = [ctx.Process(target=_cpu_replica, daemon=True,
-                         args=(args.workload, args.sample_n, args.ppc, 1000 + i, nsteps, barrier, q))
+                         args=(args.workload, args.sample_n, args.ppc, 1000 + i, nsteps, barrier, q, limit_s))
              for i in range(nproc)]
     try:
         for p in procs:
@@ -306,15 +307,16 @@ def _cpu_all_cores(args, nsteps, nproc=None):
             else:
                 os.environ[k] = v
     res, err = [], None
+    deadline = time.time() + limit_s
     try:
         for _ in procs:
-            r = q.get(timeout=900)
+            r = q.get(timeout=max(1.0, deadline - time.time()))
             if r[5] is not None:
                 err = r[5]
                 break
             res.append(r)
     except queue_mod.Empty:
-        err = "no result within 900 s"
+        err = "no result within %.0f s" % limit_s
     for p in procs:
         p.join(timeout=5 if err is None else 0.1)
         if p.is_alive():
@@ -743,7 +745,8 @@ def run_native(args):
         cpu = _cpu_baseline(args, seed=0, nsteps=args.cpu_steps) if args.cpu_steps > 0 and world == 1 else None
         if cpu is not None and args.cpu_all_cores:
             try:
-                cpu["all_cores"] = _cpu_all_cores(args, args.cpu_steps)
+                # box building plus the steps, a few times the single thread's time
+                cpu["all_cores"] = _cpu_all_cores(args, args.cpu_steps, limit_s=120.0 + 10.0 * cpu["seconds"])
             except Exception as e:  # the host figure never costs the GPU line
                 cpu["all_cores"] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
         err = _error_vs_oracle(args, 0, torch) if args.err_n > 0 else None

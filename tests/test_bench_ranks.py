@@ -106,3 +106,16 @@ def test_oracle_on_every_core_reports_a_failed_process():
     a = argparse.Namespace(workload="alfvenic_beam_3d", sample_n=-4, ppc=32, err_n=0)
     r = bench._cpu_all_cores(a, 1, nproc=2)
     assert set(r) == {"unavailable"} and r["unavailable"]
+
+
+def test_oracle_on_every_core_gives_up_at_its_limit():
+    """No result within the time limit (here far shorter than starting the
+    processes) ends the figure with the reason; no process is left behind."""
+    import argparse
+    import multiprocessing as mp
+    sys.path.insert(0, ROOT)
+    import bench
+    a = argparse.Namespace(workload="alfvenic_beam_3d", sample_n=40, ppc=32, err_n=0)
+    r = bench._cpu_all_cores(a, 1, nproc=2, limit_s=0.2)
+    assert set(r) == {"unavailable"}
+    assert not mp.active_children()
