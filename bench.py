@@ -60,6 +60,13 @@ GAS_CORRECT_BYTES = 32 + 56 + 56 + 56 + 32
 #   2-D, 512^2 x 64 CRs:  891.0 MB + 659.3 MB over 16,777,216 CRs
 # Remove an entry whenever its kernel changes, until it is measured again.
 PUSH_TRAFFIC_BYTES_PER_PARTICLE = {"alfvenic_beam_3d": 688.32e6 / 8388608, "bell_2d": 1308.98e6 / 16777216}
+# int32 shared-memory atomic adds per particle of the push's two TSC deposits:
+# 8 channels on 3^D cells, one word per contribution for the charge density
+# and two (hi, lo) for the other seven channels
+SMEM_ATOMICS_PER_PARTICLE = {3: 27 * (1 + 7 * 2), 2: 9 * (1 + 7 * 2)}
+# SM-cycles per warp-wide 32-bit shared atomic add with its 32 lanes on 32
+# banks, each adding its own value (standalone probe on a GB300)
+SMEM_ATOMIC_CYCLES = 1.1
 
 
 def _rank_env():
@@ -176,6 +183,21 @@ def aggregate_ranks(total_ms: float, particle_steps: float, dist=None, device=No
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(n, op=dist.ReduceOp.SUM)
     return float(t.item()), float(n.item())
+
+
+def smem_atomic_roofline(ndim, npart, push_avg_s, sm_mhz, nsm):
+    """The push against the conflict-free rate of the shared-memory atomic
+    pipe: the deposits' warp-wide atomic instructions per second over one
+    per SMEM_ATOMIC_CYCLES SM-cycles on every SM at the sampled clock.  Bank
+    conflicts (lanes whose particles share a cell) raise the cycles an
+    instruction takes above that rate, so frac < 1 counts them too."""
+    per = SMEM_ATOMICS_PER_PARTICLE[ndim]
+    achieved = per / 32.0 * npart / push_avg_s / 1e9
+    peak = nsm * sm_mhz * 1e6 / SMEM_ATOMIC_CYCLES / 1e9
+    return {"bound": "shared-memory atomics", "achieved": achieved, "peak": peak,
+            "unit": "G warp atomic instructions/s", "frac": achieved / peak,
+            "atomics_per_particle": per, "cycles_per_instruction": SMEM_ATOMIC_CYCLES,
+            "sm_mhz": sm_mhz, "sms": nsm}
 
 
 def _peaks():
@@ -682,6 +704,14 @@ def run_native(args):
     bytes_push = npart * 2 * PARTICLE_BYTES[(ndim, prec)] + ncell * (CELL_FIELD_BYTES[prec] + CELL_DEPOSIT_BYTES)
     push_avg_s = push_ms / args.steps / 1e3
     achieved = bytes_push / push_avg_s / 1e9
+    try:
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz, mhz_kind = clocks.get("sm_mhz"), "median sampled under load"
+        if not mhz:
+            mhz, mhz_kind = 2070.0, "nominal maximum"
+        smem = dict(smem_atomic_roofline(ndim, npart, push_avg_s, float(mhz), nsm), sm_mhz_kind=mhz_kind)
+    except Exception as e:  # a secondary figure never costs the line
+        smem = {"unavailable": "%s: %s" % (type(e).__name__, e)}
     traffic = None
     if args.workload in PUSH_TRAFFIC_BYTES_PER_PARTICLE:
         traffic = PUSH_TRAFFIC_BYTES_PER_PARTICLE[args.workload] * npart
@@ -767,6 +797,7 @@ def run_native(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_push_mixed<%d,full>" % ndim, "peak_kind": peak_kind,
                          "bytes_per_launch": bytes_push, "avg_launch_ms": push_avg_s * 1e3},
+            "smem_atomics": smem,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
