@@ -13,7 +13,7 @@ particle-steps of all ranks per second (weak scaling, no collective on the
 data path).
 
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
-workload instead (rank 0 only).
+workload instead (rank 0 only), one process and box per host core.
 """
 from __future__ import annotations
 
@@ -280,15 +280,18 @@ def _cpu_baseline(args, seed, nsteps):
 _THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
 
 
-def _cpu_replica(workload, sample_n, ppc, seed, nsteps, barrier, queue, wait_s):
+def _cpu_replica(workload, sample_n, ppc, seed, nsteps, warmup, barrier, queue, wait_s):
     """One host process of the all-core oracle figure: its own sample box,
-    built before the common start, then nsteps full oracle steps."""
+    built (and advanced warmup untimed steps) before the common start, then
+    nsteps full oracle steps."""
     try:
         import oracle as orc
         from paper_1412_1087_gb300 import workloads as wl
         args = argparse.Namespace(workload=workload, sample_n=sample_n, ppc=ppc, err_n=0)
         box, what = _sample_box(args, seed, "cpu")
         st = orc.State(box, wl.absolute_positions(box), box.p.astype(np.float64))
+        for _ in range(warmup):
+            st.step(box.dt)
         barrier.wait(timeout=wait_s)
         t0 = time.time()
         for _ in range(nsteps):
@@ -299,7 +302,7 @@ def _cpu_replica(workload, sample_n, ppc, seed, nsteps, barrier, queue, wait_s):
         queue.put((seed, 0, 0.0, 0.0, "", "%s: %s" % (type(e).__name__, e)))
 
 
-def _cpu_all_cores(args, nsteps, nproc=None, limit_s=300.0):
+def _cpu_all_cores(args, nsteps, nproc=None, limit_s=300.0, warmup=0):
     """The oracle as it stands on every host core: one process per core, each
     advancing its own box of the sample recipe (seeds 1000, 1001, ...); all
     start together after building their boxes, and the figure is the
@@ -317,7 +320,7 @@ def _cpu_all_cores(args, nsteps, nproc=None, limit_s=300.0):
     saved = {k: os.environ.get(k) for k in _THREAD_VARS}
     os.environ.update({k: "1" for k in _THREAD_VARS})
     procs = [ctx.Process(target=_cpu_replica, daemon=True,
-                         args=(args.workload, args.sample_n, args.ppc, 1000 + i, nsteps, barrier, q, limit_s))
+                         args=(args.workload, args.sample_n, args.ppc, 1000 + i, nsteps, warmup, barrier, q, limit_s))
              for i in range(nproc)]
     try:
         for p in procs:
@@ -815,29 +818,42 @@ def run_native(args):
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores, on the selected workload's
+    sample recipe: one process and box per core (``--ref-procs``, 0 for every
+    core), else, with one process or if the processes fail, a single thread
+    in this process."""
     rank, world, _ = _rank_env()
     if rank != 0:
         return None
     import oracle
     oracle.build()
-    import oracle as orc
-    from paper_1412_1087_gb300 import workloads as wl
-    box, what = _sample_box(args, 0, "cpu")
-    st = orc.State(box, wl.absolute_positions(box), box.p.astype(np.float64))
-    for _ in range(args.warmup):
-        st.step(box.dt)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        st.step(box.dt)
-    dt = time.perf_counter() - t0
-    live = int((box.cell >= 0).sum())
-    value = live * args.steps / dt
-    sample = "FP64 CPU oracle, %s recipe at %s (%d CRs) per step, single thread" % (args.workload, what, live)
+    r = None
+    if args.ref_procs != 1:
+        r = _cpu_all_cores(args, args.steps, nproc=args.ref_procs or None,
+                           limit_s=300.0 + 30.0 * (args.steps + args.warmup), warmup=args.warmup)
+    if r is not None and "unavailable" not in r:
+        value, cores, sample, dt = r["value"], r["cores"], "FP64 CPU oracle, " + r["sample"], r["seconds"]
+    else:
+        import oracle as orc
+        from paper_1412_1087_gb300 import workloads as wl
+        box, what = _sample_box(args, 0, "cpu")
+        st = orc.State(box, wl.absolute_positions(box), box.p.astype(np.float64))
+        for _ in range(args.warmup):
+            st.step(box.dt)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            st.step(box.dt)
+        dt = time.perf_counter() - t0
+        live = int((box.cell >= 0).sum())
+        value, cores = live * args.steps / dt, 1
+        sample = "FP64 CPU oracle, %s recipe at %s (%d CRs) per step, single thread" % (args.workload, what, live)
+        if r is not None:
+            sample += " (the processes failed: %s)" % r["unavailable"]
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": _workload_desc(args), "sample": sample},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return out
@@ -870,6 +886,8 @@ def main(argv=None):
     ap.add_argument("--cpu-all-cores", type=int, default=1,
                     help="also time the oracle on every host core, one process and box per core (0: off)")
     ap.add_argument("--sample-n", type=int, default=40, help="side of the oracle's sample box")
+    ap.add_argument("--ref-procs", type=int, default=0,
+                    help="--impl reference: oracle processes, one box each (0: one per host core)")
     ap.add_argument("--err-n", type=int, default=24, help="side of the error-check box (0: skip)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "native":

@@ -70,8 +70,27 @@ def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
         assert key in d, key
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["config"]["workload"].startswith("periodic_thermal_2d")
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+@pytest.mark.parametrize("procs", [1, 2])
+def test_reference_arm_process_count(monkeypatch, capsys, procs):
+    """One process: the single thread in place, one 64^2 x 16 box; two:
+    two boxes, their particle-steps together."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    bench.main(["--impl", "reference", "--steps", "2", "--warmup", "1", "--workload", "periodic_thermal_2d",
+                "--ref-procs", str(procs)])
+    d = json.loads([l for l in capsys.readouterr().out.splitlines() if l.startswith("{")][0])
+    assert d["cpu_baseline"]["cores"] == procs
+    assert ("single thread" in d["config"]["sample"]) == (procs == 1)
+    n = 65536 * procs
+    assert abs(d["value"] * d["ms_per_step"] / 1e3 - n) < 1e-6 * n
 
 
 def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
