@@ -100,6 +100,24 @@ def test_lower_face_is_still_a_reflecting_wall():
     assert xp[0] < box.n[0] * box.dx[0] and vp[0] == 3.0   # held inside, not reflected
 
 
+def test_deposit_folds_at_the_wall_and_keeps_charge_at_the_open_face():
+    """TSC at s = 0.2: (0.32, 0.66, 0.02) on cells -1, 0, 1, the wall
+    folding cell -1 onto cell 0; at s = n - 0.2 the weight beyond the open
+    face stays in the last cell, so no charge is lost before the particle
+    itself leaves."""
+    n = 6
+    g = orc.make_grid(2, (n, 4, 1), bc=(WALL_OPEN, 0, 0))
+    for s, cells in ((0.2, {0: 0.98, 1: 0.02}), (n - 0.2, {n - 1: 0.98, n - 2: 0.02})):
+        planes = np.zeros((1, n * 4))
+        orc.deposit(g, [s, 1.5], [1.0], planes)
+        row = planes.reshape(4, n)[1]
+        exp = np.zeros(n)
+        for c, w in cells.items():
+            exp[c] = 0.75 * w
+        np.testing.assert_allclose(row, exp, rtol=0, atol=1e-15)
+        assert abs(planes.sum() - 1.0) < 1e-15
+
+
 # ---------------------------------------------------------------------------
 # random numbers, front tracking and injection (Section 5)
 # ---------------------------------------------------------------------------

@@ -126,6 +126,14 @@ def test_reflecting_wall_folds_weight_and_mirrors_particle():
     # cell -1 folds onto cell 0: w(-1) + w(0) = (1/2)(0.8)^2 + 3/4 - 0.09
     assert abs(row[0] - 0.75 * (0.32 + 0.66)) < 1e-15
     assert abs(row[1] - 0.75 * 0.02) < 1e-15
+    # the upper wall mirrors it: s = 5.8 puts (0.02, 0.66, 0.32) on cells 4,
+    # 5 and 6, and cell 6 folds onto cell 5
+    planes[:] = 0.0
+    orc.deposit(g, [5.8, 1.5], [1.0], planes)
+    row = planes.reshape(4, 6)[1]
+    assert abs(row[5] - 0.75 * (0.66 + 0.32)) < 1e-15
+    assert abs(row[4] - 0.75 * 0.02) < 1e-15
+    assert abs(planes.sum() - 1.0) < 1e-15
     x, v = orc.boundary(g, [-0.25, 1.0], [3.0, 1.0, 2.0])
     assert x[0] == 0.25 and v[0] == -3.0 and v[1] == 1.0
     x, v = orc.boundary(g, [6.5, 1.0], [3.0, 1.0, 2.0])
