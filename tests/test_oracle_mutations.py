@@ -41,7 +41,52 @@ MUTATIONS = [
     ("open box's lower wall folds into the wrong cell", "i = -1 - i;", "i = -i;", 0),
     ("reflecting wall folds into the wrong cell", "i = -1 - i;", "i = -i;", 1),
     ("reflecting upper wall folds into the wrong cell", "i = 2 * n - 1 - i;", "i = 2 * n - 2 - i;"),
+    ("gamma with half the momentum term", "return sqrt(C * C + dot3(v, v)) / C;",
+     "return sqrt(C * C + 0.5 * dot3(v, v)) / C;"),
+    ("kinetic energy over gamma", "return dot3(v, v) / (orc_gamma(v, C) + 1.0);",
+     "return dot3(v, v) / orc_gamma(v, C);"),
+    ("TSC centre weight", "w[1] = 0.75 - delta * delta;", "w[1] = 0.75 - 0.5 * delta * delta;"),
+    ("TSC offset from the cell face, not the centre", "double delta = s - fi - 0.5;", "double delta = s - fi;"),
+    ("position in cells without the cell size", "double s = (xp[d] - g->x0[d]) / g->dx[d];",
+     "double s = xp[d] - g->x0[d];"),
+    ("stencil weight without its y factor", "wts[m] = w[0][a] * w[1][b] * wz;", "wts[m] = w[0][a] * wz;"),
+    ("gather without the weights", "acc += wts[k] * planes[q * nc + cells[k]];",
+     "acc += planes[q * nc + cells[k]] / m;"),
+    ("first drift a full step", "xp[d] = xp[d] + 0.5 * dt * (vn[d] / g0);", "xp[d] = xp[d] + dt * (vn[d] / g0);"),
+    ("parallel field kept where |B| = 1", "if (B2 > 0.0) {", "if (B2 > 1.0) {"),
+    ("first kick a full step", "v0[d] = vn[d] + 0.5 * h * Ep[d];", "v0[d] = vn[d] + h * Ep[d];"),
+    ("second kick a full step", "vnew[d] = v1[d] + 0.5 * h * Ep[d];", "vnew[d] = v1[d] + h * Ep[d];"),
+    ("rotation's gamma from the old velocity", "double gam = orc_gamma(v0, C);", "double gam = orc_gamma(vn, C);"),
+    ("rotation's inner cross product reversed", "cross3(v0, b, t);", "cross3(b, v0, t);"),
+    ("push without the charge-to-mass ratio", "const double h = p->qm_cr * dt;", "const double h = dt;"),
+    ("moments' charge without the charge-to-mass ratio", "q[0] = p->qm_cr * p->m_cr / dV;", "q[0] = p->m_cr / dV;"),
+    ("push's charge deposit without the charge-to-mass ratio", "q[0] = p->qm_cr * m / dV;", "q[0] = m / dV;"),
+    ("wall reflection keeps the normal velocity", "xp[d] = 2.0 * lo - xp[d];\n                v[d] = -v[d];",
+     "xp[d] = 2.0 * lo - xp[d];\n                v[d] = v[d];"),
+    ("periodic wrap by half the box", "r -= L * floor(r / L);", "r -= 0.5 * L * floor(r / L);"),
     # the CR-Hall term and the feedback (Sec. 2.1)
+    ("Hall field added", "E[d * nc + c] = E0[d] - F / ng;", "E[d * nc + c] = E0[d] + F / ng;"),
+    ("gas charge density without its charge-to-mass ratio", "double ng = p->qm_gas * rho[c];", "double ng = rho[c];", 0),
+    ("gas velocity from the momentum density", "vg[d] = mom[d * nc + c] / rho[c];", "vg[d] = mom[d * nc + c];"),
+    ("momentum feedback not per cell volume", "mom[d * nc + c] += corr[d * nc + c] / dV;",
+     "mom[d * nc + c] += corr[d * nc + c];"),
+    ("gas momentum total without the cell volume", "out[d] += mom[d * nc + c] * dV;", "out[d] += mom[d * nc + c];"),
+    ("CR energy total from |v|^2/2", "out[7] += p->m_cr * orc_kinetic_energy(vj, p->C);",
+     "out[7] += p->m_cr * 0.5 * dot3(vj, vj);"),
+    # diagnostics (Sec. 2.2, 4.3)
+    ("spectrum puts a value on an edge in the lower bin", "while (b + 1 < nbins && edges[b + 1] <= q)",
+     "while (b + 1 < nbins && edges[b + 1] < q)"),
+    ("spectrum's upper moment without its last factor", "sums[0] += qn * q;", "sums[0] += qn;"),
+    ("spectrum energy over gamma", "q = v2 / (gam + 1.0);", "q = v2 / gam;"),
+    ("spectrum region open at its lower edge", "if (!(xd >= region[2 * d] && xd < region[2 * d + 1]))",
+     "if (!(xd > region[2 * d] && xd < region[2 * d + 1]))"),
+    ("Lambda without the CR density", "lam[d * nc + c] = vA > 0.0 ? (J - n * vg) / ((ng + n) * vA) : 0.0;",
+     "lam[d * nc + c] = vA > 0.0 ? (J - n * vg) / (ng * vA) : 0.0;"),
+    ("Lambda's gas density without its charge-to-mass ratio", "double ng = p->qm_gas * rho[c];",
+     "double ng = rho[c];", 1),
+    ("Alfven speed over rho", "double vA = sqrt(dot3(Bc, Bc)) / sqrt(rho[c]);",
+     "double vA = sqrt(dot3(Bc, Bc)) / rho[c];"),
+    # the CR-Hall term and the feedback (Sec. 2.1), continued
     ("CR fraction without the CR density", "double R = n / (ng + n);", "double R = n / ng;"),
     ("Hall force with J x B of the wrong sign", "double F = (1.0 - R) * (n * E0[d] + JxB[d]);",
      "double F = (1.0 - R) * (n * E0[d] - JxB[d]);"),

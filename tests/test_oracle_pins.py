@@ -370,11 +370,14 @@ def test_hall_field_identities():
     np.testing.assert_allclose(rhs, mid, rtol=1e-11, atol=1e-13)
 
 
-def test_parallel_field_is_cleaned_before_the_kick():
-    """A field with E parallel to B at the particle does no work (App. A.2 cleaning)."""
+@pytest.mark.parametrize("bmag,axis", [(2.0, True), (1.0, True), (0.25, True), (1.0, False)])
+def test_parallel_field_is_cleaned_before_the_kick(bmag, axis):
+    """A field with E parallel to B at the particle does no work (App. A.2
+    cleaning), whatever |B| (cleaning applies for every |B| > 0)."""
     g = orc.make_grid(3, (4, 4, 4))
     p = orc.make_params(1.0, 1.0, 50.0, 1.0, 0)
-    E, B = _uniform_fields((4, 4, 4), 3, E=(0.7, 0.0, 0.0), B=(2.0, 0.0, 0.0))
+    u = np.array([1.0, 0.0, 0.0]) if axis else np.array([1.0, -2.0, 2.0]) / 3.0
+    E, B = _uniform_fields((4, 4, 4), 3, E=tuple(0.7 * u), B=tuple(bmag * u))
     x = np.array([[1.3], [2.2], [0.7]])
     v = np.array([[3.0], [1.0], [-2.0]])
     ek0 = orc.kinetic_energy(v[:, 0], 50.0)
