@@ -56,8 +56,8 @@ GAS_CORRECT_BYTES = 32 + 56 + 56 + 56 + 32
 # particles through the permutation, as every push does at a sort cadence of
 # one); traffic scales with the particle count (cells scale alike at fixed
 # particles per cell):
-#   3-D, 64^3 x 32 CRs:   393.2 MB + 296.9 MB over 8,388,608 CRs
-#   2-D, 512^2 x 64 CRs:  891.0 MB + 659.3 MB over 16,777,216 CRs
+#   3-D, 64^3 x 32 CRs:   392.7 MB + 295.6 MB over 8,388,608 CRs
+#   2-D, 512^2 x 64 CRs:  735.3 MB + 573.7 MB over 16,777,216 CRs
 # Remove an entry whenever its kernel changes, until it is measured again.
 PUSH_TRAFFIC_BYTES_PER_PARTICLE = {"alfvenic_beam_3d": 688.32e6 / 8388608, "bell_2d": 1308.98e6 / 16777216}
 # int32 shared-memory atomic adds per particle of the push's two TSC deposits:
