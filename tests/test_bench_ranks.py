@@ -153,3 +153,38 @@ def test_shared_atomic_roofline_arithmetic():
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15
     r2 = bench.smem_atomic_roofline(2, 32, 1.0, 2000.0, 152)
     assert r2["atomics_per_particle"] == 135 and abs(r2["achieved"] - 135e-9) < 1e-20
+
+
+def test_clock_record_parsing(tmp_path):
+    """The nvidia-smi rows sampled during the timed region: median SM clock
+    under load, the maximum clock, and every throttle reason seen active."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rows = ["0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 2010, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",
+            "garbage line"]
+    f = tmp_path / "clocks.csv"
+    f.write_text("\n".join(rows) + "\n")
+
+    class _File:
+        name = str(f)
+
+        def flush(self):
+            pass
+
+    c = bench.ClockSampler(0)
+    c.proc, c.f = object(), _File()
+    s = c.summary()
+    assert s["sm_mhz"] == 2010.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 4
+    f.write_text("0, 1100, 2070, 500.0, 0x0, Active, Not Active, Active, Not Active\n")
+    c.f = _File()
+    s = c.summary()
+    assert s["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and s["sm_mhz"] == 1100.0
+    f.write_text("")
+    c.f = _File()
+    assert c.summary()["reasons"] == ["no samples"]
+    c.proc = None
+    assert c.summary()["reasons"] == ["nvidia-smi unavailable"]
