@@ -120,7 +120,28 @@ MUTATIONS = [
      "dB[d * nc + c] = Bx * (mom[d * nc + r] / rho[r] - mom[d * nc + c] / rho[c]) * h;"),
     ("predictor energy source with the wrong sign", "egas_h[c] = egas[c] - 0.5 * dt * P[c];",
      "egas_h[c] = egas[c] + 0.5 * dt * P[c];"),
+    ("gas momentum driven by dB_y for both components", "dmom[d * nc + c] = Bx * (B[d * nc + r] - B[d * nc + l]) * h;",
+     "dmom[d * nc + c] = Bx * (B[nc + r] - B[nc + l]) * h;"),
+    ("Hall induction's z part with the wrong sign", "dB[2 * nc + c] += (H[nc + r] - H[nc + l]) * h;",
+     "dB[2 * nc + c] -= (H[nc + r] - H[nc + l]) * h;"),
+    ("predictor's Hall field without the gas charge-to-mass ratio",
+     "H[d * nc + c] = p->hall ? Fc[d] / (p->qm_gas * rho[c]) : 0.0;", "H[d * nc + c] = p->hall ? Fc[d] / rho[c] : 0.0;"),
+    ("predictor's B a full step", "B_h[d * nc + c] = B[d * nc + c] + 0.5 * dt * dB[d * nc + c];",
+     "B_h[d * nc + c] = B[d * nc + c] + dt * dB[d * nc + c];"),
+    ("source power without (1 - R)", "*P = (1.0 - R) * dot3(J, E0);", "*P = dot3(J, E0);"),
+    ("periodic x neighbour off by one", "int64_t j = (i + s + nx) % nx;", "int64_t j = (i + 2 * s + nx) % nx;"),
     # the open face, front tracking and injection (Sec. 5)
+    ("injection direction cosine from [0, 1)", "double mu = 2.0 * unit_open(u[2]) - 1.0;",
+     "double mu = unit_open(u[2]);"),
+    ("injection azimuth over half a turn", "double ph = 6.283185307179586 * unit_open(u[3]);",
+     "double ph = 3.141592653589793 * unit_open(u[3]);"),
+    ("injected speed from gamma, not four-velocity", "double vmag = C * sqrt(gp * gp - 1.0);",
+     "double vmag = C * sqrt(1.0 - 1.0 / (gp * gp));"),
+    ("injected y positions over half the box", "x_new[cap + k] = g->x0[1] + unit_open(u[0]) * g->n[1] * g->dx[1];",
+     "x_new[cap + k] = g->x0[1] + 0.5 * unit_open(u[0]) * g->n[1] * g->dx[1];"),
+    ("injected energy removed from the gas twice", "egas[c] -= Ein / Vreg;", "egas[c] -= 2.0 * Ein / Vreg;"),
+    ("front speed from one step only", "double V = isnan(xs_prev) ? 0.0 : (xs - xs_prev) / dt;",
+     "double V = isnan(xs_prev) ? 0.0 : (xs - xs_prev) / (2.0 * dt);"),
     ("front smoothing width", "const double sig = 4.0;", "const double sig = 3.0;"),
     ("front threshold", "double thr = 0.6 * fabs(vup);", "double thr = 0.4 * fabs(vup);"),
     ("injected mass added to the gas", "rho[c] -= Min / Vreg;", "rho[c] += Min / Vreg;"),

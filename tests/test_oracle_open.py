@@ -189,9 +189,16 @@ def test_injection_conserves_momentum_energy_and_mass_and_places_particles():
     np.testing.assert_allclose(Ek, fE * 0.5 * fr[3] ** 2, rtol=1e-12)
     # at the front, spread over the box in y, isotropic
     assert np.all(xn[0] == fr[0])
-    assert xn[1].min() >= 0.0 and xn[1].max() < box.n[1] * box.dx[1]
-    mu = vn[0] / np.sqrt((vn ** 2).sum(axis=0))
-    assert abs(mu.mean()) < 4.0 / np.sqrt(N) and abs((mu ** 2).mean() - 1.0 / 3.0) < 4.0 / np.sqrt(N)
+    Ly = box.n[1] * box.dx[1]
+    assert xn[1].min() >= 0.0 and xn[1].max() < Ly
+    u = np.sort(xn[1] / Ly)                       # uniform in y: Kolmogorov-Smirnov at the 0.1% level
+    ks = max(np.max(np.arange(1, N + 1) / N - u), np.max(u - np.arange(N) / N))
+    assert ks < 1.95 / np.sqrt(N)
+    # isotropic: every component of the direction has mean 0 and mean square 1/3
+    n_hat = vn / np.sqrt((vn ** 2).sum(axis=0))
+    for d in range(3):
+        assert abs(n_hat[d].mean()) < 4.0 / np.sqrt(3.0 * N), d
+        assert abs((n_hat[d] ** 2).mean() - 1.0 / 3.0) < 4.0 * np.sqrt(4.0 / 45.0 / N), d
     # the gas gives exactly what the particles take
     m = p.m_cr
     np.testing.assert_allclose(rho.sum() * dV, gas0[0] - N * m, rtol=1e-13)
