@@ -61,6 +61,10 @@ MUTATIONS = [
     ("push without the charge-to-mass ratio", "const double h = p->qm_cr * dt;", "const double h = dt;"),
     ("moments' charge without the charge-to-mass ratio", "q[0] = p->qm_cr * p->m_cr / dV;", "q[0] = p->m_cr / dV;"),
     ("push's charge deposit without the charge-to-mass ratio", "q[0] = p->qm_cr * m / dV;", "q[0] = m / dV;"),
+    ("upper wall reflection keeps the normal velocity", "xp[d] = 2.0 * hi - xp[d];\n                v[d] = -v[d];",
+     "xp[d] = 2.0 * hi - xp[d];\n                v[d] = v[d];"),
+    ("leaving particle put outside the open face", "xp[d] = nextafter(hi, lo);\n            left = 1;",
+     "xp[d] = hi;\n            left = 1;"),
     ("wall reflection keeps the normal velocity", "xp[d] = 2.0 * lo - xp[d];\n                v[d] = -v[d];",
      "xp[d] = 2.0 * lo - xp[d];\n                v[d] = v[d];"),
     ("periodic wrap by half the box", "r -= L * floor(r / L);", "r -= 0.5 * L * floor(r / L);"),
@@ -131,6 +135,19 @@ MUTATIONS = [
     ("source power without (1 - R)", "*P = (1.0 - R) * dot3(J, E0);", "*P = dot3(J, E0);"),
     ("periodic x neighbour off by one", "int64_t j = (i + s + nx) % nx;", "int64_t j = (i + 2 * s + nx) % nx;"),
     # the open face, front tracking and injection (Sec. 5)
+    ("front smoothing kernel's width squared dropped", "double w = exp(-0.5 * (double)(k * k) / (sig * sig));",
+     "double w = exp(-0.5 * (double)(k * k) / sig);"),
+    ("front smoothing not renormalised", "sv[i] = a / ws;", "sv[i] = a;"),
+    ("upstream taken from the first cell", "double vup = sv[nx - 1], rup = sr[nx - 1];",
+     "double vup = sv[nx - 1], rup = sr[0];"),
+    ("front crossing interpolated from the wrong cell", "double f = (thr - a) / (b - a);",
+     "double f = (thr - b) / (a - b);"),
+    ("front position a cell centre too far", "xs = g->x0[0] + ((double)i + 0.5 + f) * g->dx[0];",
+     "xs = g->x0[0] + ((double)i + 1.5 + f) * g->dx[0];"),
+    ("jump pressure without the compression factor", "double P1 = r / (r - 1.0) * rup * vup * vup;",
+     "double P1 = rup * vup * vup;"),
+    ("tail at the cell's lower face", "xt = g->x0[0] + ((double)i + 0.5) * g->dx[0];",
+     "xt = g->x0[0] + ((double)i) * g->dx[0];"),
     ("injection direction cosine from [0, 1)", "double mu = 2.0 * unit_open(u[2]) - 1.0;",
      "double mu = unit_open(u[2]);"),
     ("injection azimuth over half a turn", "double ph = 6.283185307179586 * unit_open(u[3]);",
