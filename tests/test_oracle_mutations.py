@@ -6,7 +6,6 @@ one pin fail.  An unmutated copy must pass them all (the control).  Nothing
 here touches the oracle in the tree or any GPU.
 """
 import os
-import shutil
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -183,13 +182,33 @@ MUTATIONS = [
      "if (t_inj[j] < t_early && t >= t_inj[j]) {"),
 ]
 
+# the same for the oracle's Python layer (oracle/__init__.py)
+PY_MUTATIONS = [
+    ("coupled step pushes in the old magnetic field",
+     "push(self.g, self.p, dt, self.x, self.v, E, half[3], self.corr, self.mom_dep)",
+     "push(self.g, self.p, dt, self.x, self.v, E, self.B, self.corr, self.mom_dep)"),
+    ("coupled step keeps the old moments", "        self.mom_dep[:] = 0.0\n        push(", "        push("),
+    ("box parameters with the two charge-to-mass ratios swapped",
+     "make_params(box.qm_cr, box.qm_gas, box.C, box.m_cr, box.hall)",
+     "make_params(box.qm_gas, box.qm_cr, box.C, box.m_cr, box.hall)"),
+]
 
-def _run_pins(work, src):
+
+def _mutate(src, name, old, new, nth=0):
+    k = -1
+    for _ in range(nth + 1):
+        k = src.find(old, k + 1)
+        assert k >= 0, "not in the oracle: " + name
+    return src[:k] + new + src[k + len(old):]
+
+
+def _run_pins(work, src, py_src):
     """Build the oracle from src in a directory of its own and run the pin
     files against it; pytest's exit code (0 all passed, 1 some failed)."""
     d = os.path.join(work, "oracle")
     os.makedirs(d)
-    shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), d)
+    with open(os.path.join(d, "__init__.py"), "w") as f:
+        f.write(py_src)
     with open(os.path.join(d, "mhdpic_oracle.c"), "w") as f:
         f.write(src)
     env = dict(os.environ, PYTHONPATH=work + os.pathsep + ROOT, PYTHONDONTWRITEBYTECODE="1")
@@ -211,15 +230,14 @@ def _run_pins(work, src):
 def test_every_planted_mistake_fails_a_pin(tmp_path):
     with open(os.path.join(ROOT, "oracle", "mhdpic_oracle.c")) as f:
         src = f.read()
-    jobs = [("control", src)]
-    for name, old, new, *nth in MUTATIONS:
-        k = -1
-        for _ in range((nth or [0])[0] + 1):
-            k = src.find(old, k + 1)
-            assert k >= 0, "not in the oracle: " + name
-        jobs.append((name, src[:k] + new + src[k + len(old):]))
+    with open(os.path.join(ROOT, "oracle", "__init__.py")) as f:
+        py_src = f.read()
+    jobs = [("control", src, py_src)]
+    jobs += [(m[0], _mutate(src, *m), py_src) for m in MUTATIONS]
+    jobs += [(m[0], src, _mutate(py_src, *m)) for m in PY_MUTATIONS]
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        res = list(ex.map(lambda k: _run_pins(str(tmp_path / ("m%02d" % k)), jobs[k][1]), range(len(jobs))))
+        res = list(ex.map(lambda k: _run_pins(str(tmp_path / ("m%03d" % k)), jobs[k][1], jobs[k][2]),
+                          range(len(jobs))))
     rc0, out0 = res[0]
     assert rc0 == 0, "the unmutated copy fails its pins:\n" + out0
     survived = [(jobs[k][0], res[k][1]) for k in range(1, len(jobs)) if res[k][0] != 1]
