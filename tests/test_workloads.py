@@ -42,8 +42,14 @@ def test_thermal_box_recipe():
     # isotropic: each component has mean 0 and mean square 100/3
     assert np.abs(b.p.astype(np.float64).mean(axis=1)).max() < 4 * 10.0 / np.sqrt(3 * b.np)
     np.testing.assert_allclose((b.p.astype(np.float64) ** 2).mean(axis=1), 100.0 / 3.0, rtol=0.03)
-    # positions uniform: offsets uniform in [0, 1), cell counts Poisson(16)
+    # isotropic to fourth order as well: <n_d^4> = 1/5 on the sphere (a cube's
+    # normalised points share the first two moments but give ~0.18)
+    n4 = ((b.p.astype(np.float64) / 10.0) ** 4).mean(axis=1)
+    assert np.all(np.abs(n4 - 0.2) < 4.0 * np.sqrt(16.0 / 225.0 / b.np))
+    # positions uniform: across the box and inside the cells, cell counts Poisson(16)
+    xy = wl.absolute_positions(b)
     for d in range(2):
+        assert _uniform_ks(xy[d] / (b.n[d] * b.dx[d])) < KS999 / np.sqrt(b.np)
         assert _uniform_ks(b.off[d].astype(np.float64)) < KS999 / np.sqrt(b.np)
     counts = np.bincount(b.cell, minlength=b.ncell)
     assert abs(counts.mean() - 16.0) < 1e-12 and abs(counts.var() / 16.0 - 1.0) < 0.1
