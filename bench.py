@@ -859,7 +859,7 @@ def run_reference(args):
     return out
 
 
-def main(argv=None):
+def build_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -889,6 +889,11 @@ def main(argv=None):
     ap.add_argument("--ref-procs", type=int, default=0,
                     help="--impl reference: oracle processes, one box each (0: one per host core)")
     ap.add_argument("--err-n", type=int, default=24, help="side of the error-check box (0: skip)")
+    return ap
+
+
+def main(argv=None):
+    ap = build_parser()
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "native":
         ap.error("at least 3 warm-up steps")

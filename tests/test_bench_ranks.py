@@ -188,3 +188,23 @@ def test_clock_record_parsing(tmp_path):
     assert c.summary()["reasons"] == ["no samples"]
     c.proc = None
     assert c.summary()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_profile_commands_use_the_current_bench_flags():
+    """Every bench command quoted in the committed ncu summaries still parses
+    with the bench's flags, so the summaries can be re-made as written."""
+    import glob
+    import re
+    import shlex
+    sys.path.insert(0, ROOT)
+    import bench
+    ap = bench.build_parser()
+    found = 0
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        text = open(path).read().replace("\\\n", " ")
+        for cmd in re.findall(r"python bench\.py([^&\n`]*)", text):
+            ap.parse_args(shlex.split(cmd))
+            found += 1
+        for ncu in re.findall(r"^ncu [^\n]*", text, flags=re.M):    # never one that locks the clocks
+            assert "--clock-control none" in ncu, (path, ncu)
+    assert found >= 4
