@@ -459,6 +459,19 @@ int64_t mhdpic_num_keys(const mhdpic_ctx *ctx);
 int mhdpic_get_status(mhdpic_ctx *ctx, uint32_t *flags);
 int mhdpic_clear_status(mhdpic_ctx *ctx);
 
+/*
+ * mhdpic_debug_fail_launch - host-side fault injection for testing the
+ * library's error paths (no GPU fault is made): the n-th kernel-launch check
+ * of this context from now on reports MHDPIC_E_CUDA as though that launch had
+ * failed, and the call making it returns the error; n = 0 disarms.  The
+ * launch itself is issued, so after an eager call fails this way the
+ * context's state is unspecified; a failure inside the graph capture of
+ * mhdpic_run leaves the context as it was before the capture (nothing
+ * captured runs).  The paper has no counterpart: it is a testing interface of
+ * this library.  Errors: MHDPIC_E_STATE, MHDPIC_E_ARG for n < 0.
+ */
+int mhdpic_debug_fail_launch(mhdpic_ctx *ctx, int64_t n);
+
 /* Count of this library's kernel launches since init (for benchmarks). */
 int64_t mhdpic_launch_count(const mhdpic_ctx *ctx);
 
@@ -474,22 +487,27 @@ int mhdpic_destroy(mhdpic_ctx *ctx);
  * synchronisation of cudaMalloc/cudaFree is not acceptable.  It needs no
  * context and calls no cudaMalloc, cudaFree or allocating library routine.
  * The paper has no counterpart: it is an interface of this library.
- *   grid, params: one box (host structs); precision: MHDPIC_PREC_MIXED (cell,
- *   off, p) or MHDPIC_PREC_FP64 (x, p64), device arrays laid out as in
- *   mhdpic_init; out: device double[4*ncell] = n, Jx, Jy, Jz, plane-major;
- *   stream: cudaStream_t.
+ *   grid, params: one box (host structs; any boundary, particles that left
+ *   through an open face, cell -1 / x NaN, deposit nothing); precision:
+ *   MHDPIC_PREC_MIXED (cell, off, p) or MHDPIC_PREC_FP64 (x, p64), device
+ *   arrays laid out as in mhdpic_init; out: device double[4*ncell] = n, Jx,
+ *   Jy, Jz, plane-major; stream: cudaStream_t.
  * Its int64 fixed-point accumulators, per-cell counts and scales are one
  * file-scope device array of about 9 MiB (for MHDPIC_NOALLOC_MAX_CELLS cells)
  * that every GPU loading the library holds until the process exits; grids with
- * more than MHDPIC_NOALLOC_MAX_CELLS cells are rejected with MHDPIC_E_CAPACITY.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) for that device, so
- * make that first call before any stream capture.  Every call clears and then
- * reuses the same array, which keeps the last call's sums: calls that overlap
- * on the GPU (other streams, or a second caller) race and corrupt each other,
- * so serialise them.  The fixed-point scales are sized on the device from the
- * densest cell of the call's particles.
- * Errors: MHDPIC_E_ARG, MHDPIC_E_CAPACITY, MHDPIC_E_CUDA (message in
- * mhdpic_last_error()).
+ * more than MHDPIC_NOALLOC_MAX_CELLS cells (or a side longer than that) are
+ * rejected with MHDPIC_E_CAPACITY.  Each call made while the stream is not
+ * capturing looks up the array's device address on the current device
+ * (cudaGetSymbolAddress; a device reset reloads the module, so the address is
+ * never kept across one); a call made during a stream capture reuses the
+ * address of the last call on that device, so make the first call on a device
+ * before any stream capture (MHDPIC_E_STATE otherwise).  Every call clears and
+ * then reuses the same array, which keeps the last call's sums: calls that
+ * overlap on the GPU (other streams, or a second caller) race and corrupt each
+ * other, so serialise them.  The fixed-point scales are sized on the device
+ * from the densest cell of the call's particles.
+ * Errors: MHDPIC_E_ARG, MHDPIC_E_CAPACITY, MHDPIC_E_STATE, MHDPIC_E_CUDA
+ * (message in mhdpic_last_error()).
  */
 #define MHDPIC_NOALLOC_MAX_CELLS 262144
 int mhdpic_deposit_moments_noalloc(const mhdpic_grid *grid, const mhdpic_params *params, int32_t precision,

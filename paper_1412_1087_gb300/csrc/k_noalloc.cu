@@ -86,6 +86,8 @@ __device__ __forceinline__ bool particle_cell(const NoallocBox &b, int64_t np, i
         ci[1] = (int)j;
         ci[2] = (int)k;
     } else {
+        if (isnan(x[i]))   // left the box through an open face
+            return false;
         for (int d = 0; d < D; ++d)
             ci[d] = (int)floor((x[(int64_t)d * np + i] - b.x0[d]) * b.inv_dx[d]);
     }
@@ -157,6 +159,8 @@ __global__ void k_noalloc_deposit(NoallocBox b, int64_t np, const int32_t *__res
             for (int d = 0; d < 3; ++d)
                 v[d] = (double)p[(int64_t)d * np + i];
         } else {
+            if (isnan(x[i]))   // left the box through an open face
+                continue;
             for (int d = 0; d < D; ++d) {
                 double s = (x[(int64_t)d * np + i] - b.x0[d]) * b.inv_dx[d];
                 double f = floor(s);
@@ -195,8 +199,13 @@ __global__ void k_noalloc_to_double(ScratchView sv, int64_t ncell, double *__res
         out[g] = (double)(long long)sv.acc[g] * sv.scale[4 + g / ncell];
 }
 
-// The device address of the scratch array on the current device, set up once.
-int scratch_on_current_device(unsigned long long **out)
+// The device address of the scratch array on the current device.  Outside a
+// stream capture it is looked up again on every call (cheap), so that a
+// device reset, which reloads the module, cannot leave a stale address; a
+// call made while `st` is capturing uses the address of the last call on
+// this device, since the lookup may load the module, which a capture does
+// not allow.
+int scratch_on_current_device(cudaStream_t st, unsigned long long **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -204,21 +213,24 @@ int scratch_on_current_device(unsigned long long **out)
         return noalloc_fail(MHDPIC_E_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= MAX_DEVICES)
         return noalloc_fail(MHDPIC_E_CAPACITY, "device %d beyond the %d devices supported", dev, MAX_DEVICES);
-    unsigned long long *ptr = g_acc_ptr[dev].load();
-    if (!ptr) {
-        std::lock_guard<std::mutex> lock(g_setup_mutex);
-        ptr = g_acc_ptr[dev].load();
-        if (!ptr) {
-            void *addr = nullptr;
-            e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
-            if (e != cudaSuccess || !addr)
-                return noalloc_fail(MHDPIC_E_CUDA, "cudaGetSymbolAddress of the scratch array: %s",
-                                    cudaGetErrorString(e));
-            ptr = (unsigned long long *)addr;
-            g_acc_ptr[dev].store(ptr);
-        }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess)
+        return noalloc_fail(MHDPIC_E_CUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
+    if (cap != cudaStreamCaptureStatusNone) {
+        unsigned long long *ptr = g_acc_ptr[dev].load();
+        if (!ptr)
+            return noalloc_fail(MHDPIC_E_STATE, "the first call on a device must come before any stream capture");
+        *out = ptr;
+        return MHDPIC_OK;
     }
-    *out = ptr;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    void *addr = nullptr;
+    e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+    if (e != cudaSuccess || !addr)
+        return noalloc_fail(MHDPIC_E_CUDA, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
+    g_acc_ptr[dev].store((unsigned long long *)addr);
+    *out = (unsigned long long *)addr;
     return MHDPIC_OK;
 }
 
@@ -239,12 +251,18 @@ int mhdpic_deposit_moments_noalloc(const mhdpic_grid *grid, const mhdpic_params 
     for (int d = 0; d < 3; ++d) {
         if (grid->n[d] < 1 || !(grid->dx[d] > 0.0))
             return noalloc_fail(MHDPIC_E_ARG, "n[%d] must be >= 1 and dx[%d] > 0", d, d);
-        if (grid->bc[d] != MHDPIC_BC_PERIODIC && grid->bc[d] != MHDPIC_BC_REFLECT)
+        if (grid->bc[d] != MHDPIC_BC_PERIODIC && grid->bc[d] != MHDPIC_BC_REFLECT &&
+            grid->bc[d] != MHDPIC_BC_WALL_OPEN)
             return noalloc_fail(MHDPIC_E_ARG, "unknown boundary %d", grid->bc[d]);
+        // each side on its own first, so that the product below cannot overflow
+        if (grid->n[d] > MHDPIC_NOALLOC_MAX_CELLS)
+            return noalloc_fail(MHDPIC_E_CAPACITY,
+                                "grid side n[%d] = %d exceeds the allocation-free limit of %d cells", d,
+                                grid->n[d], MHDPIC_NOALLOC_MAX_CELLS);
     }
     if (grid->ndim == 2 && grid->n[2] != 1)
         return noalloc_fail(MHDPIC_E_ARG, "a 2-D grid must have n[2] == 1");
-    const int64_t ncell = (int64_t)grid->n[0] * grid->n[1] * grid->n[2];
+    const int64_t ncell = (int64_t)grid->n[0] * grid->n[1] * grid->n[2];   // < 2^54: no overflow
     if (ncell > MHDPIC_NOALLOC_MAX_CELLS)
         return noalloc_fail(MHDPIC_E_CAPACITY,
                             "grid of %lld cells exceeds the allocation-free limit of %d cells",
@@ -257,7 +275,7 @@ int mhdpic_deposit_moments_noalloc(const mhdpic_grid *grid, const mhdpic_params 
         return noalloc_fail(MHDPIC_E_ARG, "C must be > 0, qm_cr and m_cr finite");
 
     unsigned long long *acc = nullptr;
-    int rc = scratch_on_current_device(&acc);
+    int rc = scratch_on_current_device((cudaStream_t)stream, &acc);
     if (rc)
         return rc;
 

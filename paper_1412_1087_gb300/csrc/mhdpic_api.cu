@@ -70,6 +70,7 @@ struct mhdpic_ctx {
     double *spec_partials = nullptr;             // [nbox][spec_chunks][2]
     double *spec_edges = nullptr;                // [MHDPIC_SPEC_MAX_BINS + 1]
     int64_t launches = 0;
+    int64_t fail_countdown = 0;   // mhdpic_debug_fail_launch: launch checks left before a reported failure
     std::vector<BoxDev> boxes;
     std::vector<int64_t> part_start, cell_start, brick_start;
     std::vector<void *> allocs;
@@ -145,6 +146,8 @@ int check_launch(mhdpic_ctx *c, int n)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_fail(e, "kernel launch");
+    if (c->fail_countdown > 0 && --c->fail_countdown == 0)
+        return fail(MHDPIC_E_CUDA, "kernel launch: failure injected by mhdpic_debug_fail_launch");
     return MHDPIC_OK;
 }
 
@@ -1126,9 +1129,18 @@ int tune_sort_cadence(mhdpic_ctx *c, double dt, int32_t *steps_left)
             return rc;
         --*steps_left;
     }
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
+    // the two events are destroyed on every way out
+    struct Events {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Events()
+        {
+            for (cudaEvent_t x : e)
+                if (x)
+                    cudaEventDestroy(x);
+        }
+    } ev;
+    CK(cudaEventCreate(&ev.e[0]));
+    CK(cudaEventCreate(&ev.e[1]));
     float best = 0.f;
     int best_k = 1;
     for (int k : cands) {
@@ -1139,22 +1151,20 @@ int tune_sort_cadence(mhdpic_ctx *c, double dt, int32_t *steps_left)
         if ((rc = mhdpic_sort(c, nullptr, nullptr)))
             return rc;
         c->step_in_cycle = 0;
-        cudaEventRecord(e0, c->stream);
+        CK(cudaEventRecord(ev.e[0], c->stream));
         for (int s = 0; s < reps * k; ++s)
             if ((rc = run_one_step(c, dt, k)))
                 return rc;
-        cudaEventRecord(e1, c->stream);
-        CK(cudaEventSynchronize(e1));
+        CK(cudaEventRecord(ev.e[1], c->stream));
+        CK(cudaEventSynchronize(ev.e[1]));
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
+        CK(cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]));
         *steps_left -= reps * k;
         if (best == 0.f || ms / (reps * k) < best) {
             best = ms / (reps * k);
             best_k = k;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     c->tuned_k = best_k;
     return MHDPIC_OK;
 }
@@ -1168,6 +1178,15 @@ int capture_cycle(mhdpic_ctx *c, double dt, int k, int cycle)
     const int64_t l0 = c->launches;
     const int cur0 = c->cur, set0 = c->cur_set, sic0 = c->step_in_cycle;
     const bool pend0 = c->pending, clear0 = c->next_clear;
+    // nothing captured ever runs unless the graph is kept: put the host
+    // bookkeeping back where the capture started
+    auto restore = [&]() {
+        c->cur = cur0;
+        c->step_in_cycle = sic0;
+        c->pending = pend0;
+        c->next_clear = clear0;
+        use_set(c, set0);
+    };
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int rc = MHDPIC_OK;
     for (int s = 0; s < cycle && rc == MHDPIC_OK; ++s)
@@ -1176,23 +1195,20 @@ int capture_cycle(mhdpic_ctx *c, double dt, int k, int cycle)
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     c->graph_launches = c->launches - l0;
     c->launches = l0;   // captured, not yet executed
-    if (rc) {
+    if (rc || e != cudaSuccess) {
         if (g)
             cudaGraphDestroy(g);
-        return rc;
-    }
-    if (e != cudaSuccess)
+        restore();
+        if (rc)
+            return rc;
         return cuda_fail(e, "cudaStreamEndCapture");
+    }
     // a replay must leave the state it starts from; otherwise nothing was
     // run, so restore the state and let the caller go on eagerly
     if (c->cur != cur0 || c->cur_set != set0 || c->step_in_cycle != sic0 || c->pending != pend0 ||
         c->next_clear != clear0) {
         cudaGraphDestroy(g);
-        c->cur = cur0;
-        c->step_in_cycle = sic0;
-        c->pending = pend0;
-        c->next_clear = clear0;
-        use_set(c, set0);
+        restore();
         return MHDPIC_OK;
     }
     e = cudaGraphInstantiate(&c->graph, g, 0);
@@ -1277,6 +1293,16 @@ int mhdpic_get_status(mhdpic_ctx *c, uint32_t *flags)
         return fail(MHDPIC_E_ARG, "invalid context or flags pointer");
     CK(cudaMemcpyAsync(flags, c->k.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return MHDPIC_OK;
+}
+
+int mhdpic_debug_fail_launch(mhdpic_ctx *c, int64_t n)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (n < 0)
+        return fail(MHDPIC_E_ARG, "n must be >= 0");
+    c->fail_countdown = n;
     return MHDPIC_OK;
 }
 

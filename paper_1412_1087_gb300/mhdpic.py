@@ -99,6 +99,7 @@ SIGNATURES = {
     "mhdpic_get_status": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_uint32)]),
     "mhdpic_clear_status": (ctypes.c_int, [_V]),
     "mhdpic_launch_count": (ctypes.c_int64, [_V]),
+    "mhdpic_debug_fail_launch": (ctypes.c_int, [_V, ctypes.c_int64]),
     "mhdpic_destroy": (ctypes.c_int, [_V]),
     "mhdpic_deposit_moments_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Params), ctypes.c_int32,
                                                        ctypes.c_int64, _V, _V, _V, _V, _V, _V, _V]),
@@ -263,6 +264,10 @@ def mhdpic_clear_status(ctx) -> None:
 
 def mhdpic_launch_count(ctx) -> int:
     return int(load().mhdpic_launch_count(ctx))
+
+
+def mhdpic_debug_fail_launch(ctx, n: int) -> None:
+    _check(load().mhdpic_debug_fail_launch(ctx, int(n)))
 
 
 def mhdpic_destroy(ctx) -> None:

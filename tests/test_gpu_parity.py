@@ -447,6 +447,35 @@ def test_graph_replayed_run_equals_eager_steps(k):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("fail_at", [1, 3, 7])
+def test_failed_graph_capture_leaves_the_context_as_it_was(fail_at):
+    """A launch failure injected on the host inside the graph capture of
+    mhdpic_run (nothing captured runs): the call reports the error, the
+    context keeps the state it had before the capture, and the steps issued
+    afterwards are bit-identical to those of a context that never failed."""
+    box = tilt_B(wl.alfvenic_beam_3d(n=12, ppc=6, nmodes=8, seed=43), 43)
+    stream = torch.cuda.Stream()
+    outs = []
+    for mode in ("clean", "failed"):
+        eng = m.Engine([box], precision=MIXED, stream=stream)
+        eng.run(box.dt, 1, 1)           # one eager step, ending on a pending sort
+        if mode == "failed":
+            m.mhdpic_debug_fail_launch(eng.ctx, fail_at)
+            with pytest.raises(m.MhdpicError, match="failure injected"):
+                eng.run(box.dt, 2, 1)   # the capture of a two-step cycle fails
+            m.mhdpic_debug_fail_launch(eng.ctx, 0)
+        for s in range(3):
+            eng.step(box.dt)
+            eng.sort()
+        stream.synchronize()
+        outs.append((eng.p.cpu().numpy(), eng.cell.cpu().numpy(), eng.off.cpu().numpy(), eng.mom.cpu().numpy(),
+                     eng.deposits(1).cpu().numpy(), eng.fields().cpu().numpy()))
+        assert eng.status() == 0
+        eng.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
 def test_run_tunes_the_sort_cadence():
     box = wl.periodic_thermal_2d(nx=48, ny=40, ppc=8, seed=41)
     stream = torch.cuda.Stream()
