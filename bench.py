@@ -35,9 +35,14 @@ sys.path.insert(0, ROOT)
 METRIC = "CR particle-steps/s (push+deposit), % HBM roofline; mixed vs FP64 at stated err"
 UNIT = "particle-steps/s"
 
-# bytes the method must move per particle-step in the push kernel (3-D mixed):
-# particle state read + write (int32 cell, 3 f32 offsets, 3 f32 four-velocity)
-PARTICLE_BYTES = {(3, "mixed"): 28, (2, "mixed"): 24, (3, "fp64"): 48, (2, "fp64"): 40}
+# bytes the method must move per particle-step in the push kernel: particle
+# state read + write (mixed: int32 cell, D f32 offsets, the two-word
+# four-velocity as 3 f32 leading words and one packed residual word; FP64:
+# D + 3 doubles)
+PARTICLE_BYTES = {(3, "mixed"): 32, (2, "mixed"): 28, (3, "fp64"): 48, (2, "fp64"): 40}
+# bytes a mixed-precision particle occupies (two 16-byte records; in 2-D the
+# third offset slot is padding), what host copies move
+RECORD_BYTES = {(3, "mixed"): 32, (2, "mixed"): 32, (3, "fp64"): 48, (2, "fp64"): 40}
 # per cell and launch: staged E, B read once (6 words) + 8 deposit channels
 # read-modify-written once (8 B each, twice)
 CELL_FIELD_BYTES = {"mixed": 24, "fp64": 48}
@@ -55,11 +60,9 @@ GAS_CORRECT_BYTES = 32 + 56 + 56 + 56 + 32
 # case of the current kernel version, a push that applies a sort (reads its
 # particles through the permutation, as every push does at a sort cadence of
 # one); traffic scales with the particle count (cells scale alike at fixed
-# particles per cell):
-#   3-D, 64^3 x 32 CRs:   392.7 MB + 295.6 MB over 8,388,608 CRs
-#   2-D, 512^2 x 64 CRs:  735.3 MB + 573.7 MB over 16,777,216 CRs
-# Remove an entry whenever its kernel changes, until it is measured again.
-PUSH_TRAFFIC_BYTES_PER_PARTICLE = {"alfvenic_beam_3d": 688.32e6 / 8388608, "bell_2d": 1308.98e6 / 16777216}
+# particles per cell).  Remove an entry whenever its kernel changes, until it
+# is measured again.
+PUSH_TRAFFIC_BYTES_PER_PARTICLE = {}
 # int32 shared-memory atomic adds per particle of the push's two TSC deposits:
 # 8 channels on 3^D cells, one word per contribution for the charge density
 # and two (hi, lo) for the other seven channels
@@ -414,7 +417,7 @@ def _error_vs_oracle(args, seed, torch, nsteps=10):
             xg_all = eng.x.cpu().numpy()
         else:
             cell, off = eng.cell.cpu().numpy(), eng.off.cpu().numpy()
-        pg_all = (eng.p64 if prec == m.MHDPIC_PREC_FP64 else eng.p).cpu().numpy().astype(np.float64)
+        pg_all = eng.velocities().cpu().numpy()
         starts = eng.box_start.copy()
         eng.close()
         dxmax = dpmax = 0.0
@@ -522,13 +525,13 @@ def run_native(args):
     tot1 = eng.apply_feedback(totals=True).sum(axis=0)
     # momentum scale: gross gas momentum plus gross CR momentum
     scaleP = 0.0
-    pcr = eng.p
+    pcr = eng.velocities()
     c0 = 0
     for bi, b in enumerate(boxes):
         dV = b.dx[0] * b.dx[1] * b.dx[2]
         scaleP += float(eng.mom[:, c0:c0 + b.ncell].abs().sum().item()) * dV
         s0, s1 = int(eng.box_start[bi]), int(eng.box_start[bi + 1])
-        scaleP += b.m_cr * float(pcr[:, s0:s1].double().abs().sum().item())
+        scaleP += b.m_cr * float(pcr[:, s0:s1].abs().sum().item())
         c0 += b.ncell
     scaleP = max(scaleP, 1e-300)
     # only what the boxes conserve: momentum along periodic (and unresolved)
@@ -751,7 +754,7 @@ def run_native(args):
     if args.e2e_steps > 0:
         gas_h2d = ncell * 8 * 8                 # feedback reads rho, mom(3), egas, B(3)
         gas_d2h = ncell * 4 * 8                 # and writes mom(3), egas
-        pbytes = npart * PARTICLE_BYTES[(ndim, prec)]
+        pbytes = npart * RECORD_BYTES[(ndim, prec)]
         runs = [(m.MHDPIC_MEM_HOST_GAS, gas_h2d, gas_d2h)]
         if args.e2e_all_host:
             # push moves the particles both ways, and so does every sort
@@ -794,7 +797,7 @@ def run_native(args):
             "config": {"workload": _workload_desc(args), "precision": "mixed", "sort_every": args.sort_every, "sort_every_tuned": tuned,
                        "brick": list(brick) if any(brick) else "default", "brick_tuned": bool(args.tune_layout),
                        "l2": "inputs larger than L2 (%.2f GB particle state)"
-                             % (npart * PARTICLE_BYTES[(ndim, prec)] / 1e9),
+                             % (npart * RECORD_BYTES[(ndim, prec)] / 1e9),
                        "parallelism": "independent box per GPU" if world > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

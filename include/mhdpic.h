@@ -33,11 +33,14 @@
  *
  * Layouts (np = total particles of all boxes, nc = total cells of all boxes):
  *   particles, box-major: box b owns particles [box_start[b], box_start[b+1]);
- *   MIXED:  cell[np] int32   linear cell of the particle inside its box,
- *                            c = (k*ny + j)*nx + i;
- *           off[ndim*np]     float, plane d holds the offset in [0,1) of the
- *                            particle inside its cell along dimension d;
- *           p[3*np]          float, four-velocity v = gamma*u (eq:4vel);
+ *   MIXED:  pos[np]          mhdpic_pos, 16 bytes: the linear cell of the
+ *                            particle inside its box, c = (k*ny + j)*nx + i,
+ *                            and its offset in [0,1) inside the cell along
+ *                            each dimension (off[2] = 0 in 2-D);
+ *           vel[np]          mhdpic_vel, 16 bytes: the four-velocity
+ *                            v = gamma*u (eq:4vel) as a two-word number, an
+ *                            FP32 leading word per component plus a packed
+ *                            residual (below);
  *   FP64:   x[ndim*np]       double, absolute position, plane-major;
  *           p64[3*np]        double, four-velocity;
  *   gas (cells box-major, box b's cells start at the sum of earlier boxes'
@@ -77,7 +80,7 @@ extern "C" {
 #define MHDPIC_BC_WALL_OPEN 2
 #define MHDPIC_SHAPE_TSC 2  /* triangular-shaped cloud (quadratic spline), Section 3 */
 #define MHDPIC_PREC_FP64 0  /* all particle arithmetic in double */
-#define MHDPIC_PREC_MIXED 1 /* int32 cell + f32 offset, f32 push, int64 fixed-point deposits */
+#define MHDPIC_PREC_MIXED 1 /* int32 cell + f32 offsets, f32 push, two-word four-velocity, int64 fixed-point deposits */
 #define MHDPIC_MEM_DEVICE 0 /* caller buffers are device pointers */
 #define MHDPIC_MEM_HOST 1   /* caller buffers are (pinned) host pointers; each call copies */
 #define MHDPIC_MEM_HOST_GAS 2 /* particle buffers on the device, gas buffers (pinned) host pointers:
@@ -126,13 +129,37 @@ typedef struct {
     int32_t reserved[8];
 } mhdpic_options;
 
+/* Mixed-precision particle position: 16 bytes, one 128-bit load or store. */
+typedef struct {
+    int32_t cell;  /* linear cell inside the box; -1 marks a free slot or a particle that left */
+    float off[3];  /* offset in [0,1) inside the cell per dimension (unused entries 0) */
+} mhdpic_pos;
+
+/*
+ * Mixed-precision four-velocity: 16 bytes, one 128-bit load or store.  The
+ * value of component d is the exact sum
+ *     v[d] + r_d * 2^(e_d - 33),
+ * with e_d the binary exponent of v[d] (|v[d]| in [2^e_d, 2^(e_d+1)), taken
+ * as -90 when |v[d]| < 2^-90, zero included) and r_d the signed 10-bit field
+ * of lo in bits 10d .. 10d+9 (|r_d| <= 511): 34 significant bits, about
+ * 2^-35 of |v[d]| per rounding.  The push adds each step's change dv, the
+ * very value it deposits as the corrector (App. A.3), to this two-word
+ * number, so what the particle stores changes by what the gas is given up to
+ * that last rounding (an FP32 word alone would round every step at 2^-25 and
+ * drift measurably over 1000 steps).  The leading words alone are the FP32
+ * four-velocity the push computes with; lo = 0 is a plain FP32 value.
+ */
+typedef struct {
+    float v[3];
+    uint32_t lo;
+} mhdpic_vel;
+
 /* Caller-owned particle buffers (see the layout above). */
 typedef struct {
     int64_t np;               /* total particles (may be 0) */
     const int64_t *box_start; /* HOST array [nbox+1], box_start[0] = 0, box_start[nbox] = np */
-    int32_t *cell;            /* MIXED */
-    float *off;               /* MIXED */
-    float *p;                 /* MIXED */
+    mhdpic_pos *pos;          /* MIXED, 16-byte aligned */
+    mhdpic_vel *vel;          /* MIXED, 16-byte aligned */
     double *x;                /* FP64 */
     double *p64;              /* FP64 */
 } mhdpic_particles;
@@ -191,10 +218,10 @@ int mhdpic_sort(mhdpic_ctx *ctx, int64_t *perm_out, int32_t *counts_out);
  * particle stores, so gas + CR momentum and energy pass through
  * mhdpic_apply_feedback to roundoff.  With MHDPIC_PREC_MIXED dv is formed
  * without cancellation from the two kicks and the rotation (accurate to
- * about 1e-7 of dv itself) while the particle keeps its four-velocity in
- * FP32, so the exchange is conservative up to the rounding of the stored
- * state: of order 1e-6 of the gross momentum over 1000 steps for a beam
- * with |v| ~ 100 moving along B, far less for slower particles.
+ * about 1e-7 of dv itself), deposited, and added to the particle's two-word
+ * four-velocity (mhdpic_vel), which holds it to about 2^-35 of |v|: the
+ * stored change is the deposited one to that rounding, and dE_k is the
+ * change of the two half kicks (the rotation keeps |v|).
  */
 int mhdpic_interp_push(mhdpic_ctx *ctx, double dt, int32_t nsub);
 
@@ -448,6 +475,15 @@ int32_t mhdpic_sort_cadence(const mhdpic_ctx *ctx);
  */
 int mhdpic_get_deposits(mhdpic_ctx *ctx, int32_t which, double *out);
 
+/*
+ * mhdpic_get_velocities - the current four-velocities as double, out device
+ * double[3*np] plane-major (component d of particle i at out[d*np + i]), in
+ * the order of the caller's particle arrays after the call (which brings them
+ * up to date, as mhdpic_sync_particles).  MIXED: the exact value of each
+ * two-word mhdpic_vel component; FP64: a copy of p64.
+ */
+int mhdpic_get_velocities(mhdpic_ctx *ctx, double *out);
+
 /* Staged cell-centred fields as double: out device double[6*nc] = Ex,Ey,Ez,Bx,By,Bz. */
 int mhdpic_get_fields(mhdpic_ctx *ctx, double *out);
 
@@ -489,7 +525,7 @@ int mhdpic_destroy(mhdpic_ctx *ctx);
  * The paper has no counterpart: it is an interface of this library.
  *   grid, params: one box (host structs; any boundary, particles that left
  *   through an open face, cell -1 / x NaN, deposit nothing); precision:
- *   MHDPIC_PREC_MIXED (cell, off, p) or MHDPIC_PREC_FP64 (x, p64), device
+ *   MHDPIC_PREC_MIXED (pos, vel) or MHDPIC_PREC_FP64 (x, p64), device
  *   arrays laid out as in mhdpic_init; out: device double[4*ncell] = n, Jx,
  *   Jy, Jz, plane-major; stream: cudaStream_t.
  * Its int64 fixed-point accumulators, per-cell counts and scales are one
@@ -511,7 +547,7 @@ int mhdpic_destroy(mhdpic_ctx *ctx);
  */
 #define MHDPIC_NOALLOC_MAX_CELLS 262144
 int mhdpic_deposit_moments_noalloc(const mhdpic_grid *grid, const mhdpic_params *params, int32_t precision,
-                                   int64_t np, const int32_t *cell, const float *off, const float *p,
+                                   int64_t np, const mhdpic_pos *pos, const mhdpic_vel *vel,
                                    const double *x, const double *p64, double *out, void *stream);
 
 /* Static message for a return code, and the detailed message of the last

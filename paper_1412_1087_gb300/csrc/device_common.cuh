@@ -69,7 +69,72 @@ constexpr int32_t DEAD_CELL = -1;
 template <int PREC>
 __device__ __forceinline__ bool particle_dead(const Ctx &c, int64_t i)
 {
-    return PREC == MHDPIC_PREC_MIXED ? c.cell[i] == DEAD_CELL : isnan(c.x[i]);
+    return PREC == MHDPIC_PREC_MIXED ? c.pos[i].x == DEAD_CELL : isnan(c.x[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Two-word four-velocity of the mixed-precision particle record (mhdpic_vel):
+// component d is v[d] + r_d 2^(e_d - 33), e_d the binary exponent of v[d]
+// (at least RES_EMIN) and r_d the signed 10-bit field d of the residual word.
+// ---------------------------------------------------------------------------
+constexpr int RES_EMIN = -90;
+constexpr int RES_SHIFT = 33;   // 23 mantissa bits + 10 residual bits
+constexpr int RES_QMAX = 511;
+
+__device__ __forceinline__ int res_exp(float h)
+{
+    const int e = ((__float_as_int(h) >> 23) & 0xff) - 127;   // 0 and subnormals give -127
+    return e < RES_EMIN ? RES_EMIN : e;
+}
+
+// 2^(e - 33) and 2^(33 - e) for e in [RES_EMIN, 127]: both normal floats
+__device__ __forceinline__ float res_quantum(int e) { return __int_as_float((e - RES_SHIFT + 127) << 23); }
+__device__ __forceinline__ float res_inv_quantum(int e) { return __int_as_float((RES_SHIFT - e + 127) << 23); }
+
+__device__ __forceinline__ int res_field(uint32_t w, int d)
+{
+    return (int)(w << (22 - 10 * d)) >> 22;
+}
+
+// Error-free sum a + b = s + t (Knuth's TwoSum), in explicitly rounded
+// operations so that no contraction changes it.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &t)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (hi, r) += d: the exact sum hi + r q + d is rounded once, to the nearest
+// number the record can hold (34 significant bits).  TwoSum gives the
+// leading word and the exact remainder; the remainder is quantised to the
+// new word's residual grid.
+__device__ __forceinline__ void two_word_add(float &hi, int &r, float d)
+{
+    const float rv = __fmul_rn((float)r, res_quantum(res_exp(hi)));   // exact
+    float s, t;
+    two_sum(hi, d, s, t);
+    const float rem = __fadd_rn(t, rv);
+    float h2, rem2;
+    two_sum(s, rem, h2, rem2);
+    const int e2 = res_exp(h2);
+    const float q = rintf(__fmul_rn(rem2, res_inv_quantum(e2)));
+    const int qi = q > (float)RES_QMAX ? RES_QMAX : (q < -(float)RES_QMAX ? -RES_QMAX : (int)q);
+    hi = h2;
+    r = isfinite(h2) ? qi : 0;
+}
+
+__device__ __forceinline__ uint32_t res_pack(const int r[3])
+{
+    return ((uint32_t)r[0] & 0x3ffu) | (((uint32_t)r[1] & 0x3ffu) << 10) | (((uint32_t)r[2] & 0x3ffu) << 20);
+}
+
+// Exact double value of component d of a record.
+__device__ __forceinline__ double vel_f64(const float4 &w, int d)
+{
+    const float h = d == 0 ? w.x : (d == 1 ? w.y : w.z);
+    const int r = res_field(__float_as_uint(w.w), d);
+    return (double)h + (double)r * (double)res_quantum(res_exp(h));
 }
 
 __device__ __forceinline__ void set_status(uint32_t *status, uint32_t flag)

@@ -168,11 +168,14 @@ __global__ void k_moments(Ctx c, int cur)
         double w[3][3] = {{0, 1, 0}, {0, 1, 0}, {0, 1, 0}};
         double v[3];
         if (PREC == MHDPIC_PREC_MIXED) {
-            decode_cell(b, c.cell[i], ci);
+            const int4 ps = c.pos[i];
+            const float4 vs = c.vel[i];
+            const float o[3] = {__int_as_float(ps.y), __int_as_float(ps.z), __int_as_float(ps.w)};
+            decode_cell(b, ps.x, ci);
             for (int d = 0; d < D; ++d)
-                tsc_from_offset<double>((double)c.off[(int64_t)d * c.np + i], w[d]);
+                tsc_from_offset<double>((double)o[d], w[d]);
             for (int d = 0; d < 3; ++d)
-                v[d] = (double)c.p[(int64_t)d * c.np + i];
+                v[d] = vel_f64(vs, d);
         } else {
             for (int d = 0; d < D; ++d) {
                 double s = (c.x[(int64_t)d * c.np + i] - b.x0[d]) * b.inv_dx[d];
@@ -239,9 +242,14 @@ __global__ void __launch_bounds__(256) k_totals_partial(Ctx c, int nchunks, int6
     int64_t p0 = b.part0 + chunk * ps, p1 = min(b.part1, p0 + ps);
     for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
         double v[3];
-        for (int d = 0; d < 3; ++d)
-            v[d] = PREC == MHDPIC_PREC_MIXED ? (double)c.p[(int64_t)d * c.np + i]
-                                             : c.p64[(int64_t)d * c.np + i];
+        if (PREC == MHDPIC_PREC_MIXED) {
+            const float4 vs = c.vel[i];   // the exact value of the two-word four-velocity
+            for (int d = 0; d < 3; ++d)
+                v[d] = vel_f64(vs, d);
+        } else {
+            for (int d = 0; d < 3; ++d)
+                v[d] = c.p64[(int64_t)d * c.np + i];
+        }
         double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
         double gam = sqrt(b.C * b.C + v2) / b.C;
         for (int d = 0; d < 3; ++d)
@@ -294,6 +302,23 @@ __global__ void k_fields_to_double(Ctx c, double *__restrict__ out)
     }
 }
 
+// The current four-velocities as double, plane-major: the exact value of each
+// two-word record in mixed precision, a copy in FP64.
+__global__ void k_velocities_to_double(Ctx c, double *__restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.np;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (c.prec == MHDPIC_PREC_MIXED) {
+            const float4 vs = c.vel[i];
+            for (int d = 0; d < 3; ++d)
+                out[d * c.np + i] = vel_f64(vs, d);
+        } else {
+            for (int d = 0; d < 3; ++d)
+                out[d * c.np + i] = c.p64[d * c.np + i];
+        }
+    }
+}
+
 // Largest |v| per box (for the fixed-point scales): a running maximum per
 // thread while its particles stay in one box, one atomic per box and warp.
 template <int PREC>
@@ -313,7 +338,8 @@ __global__ void k_vmax(Ctx c)
         const int bx = find_box(c.box_part_start, c.nbox, i);
         float vm;
         if (PREC == MHDPIC_PREC_MIXED) {
-            const float v[3] = {c.p[i], c.p[c.np + i], c.p[2 * c.np + i]};
+            const float4 vs = c.vel[i];
+            const float v[3] = {vs.x, vs.y, vs.z};
             vm = sqrtf(vsq3(v));
         } else {
             double v2 = 0.0;
@@ -398,6 +424,14 @@ int launch_fixed_to_double(const Ctx &c, const unsigned long long *src, int ch0,
 int launch_fields_to_double(const Ctx &c, double *out, cudaStream_t st)
 {
     k_fields_to_double<<<grid_for(c.nc, 256), 256, 0, st>>>(c, out);
+    return 1;
+}
+
+int launch_velocities_to_double(const Ctx &c, double *out, cudaStream_t st)
+{
+    if (c.np == 0)
+        return 0;
+    k_velocities_to_double<<<grid_for(c.np, 256), 256, 0, st>>>(c, out);
     return 1;
 }
 

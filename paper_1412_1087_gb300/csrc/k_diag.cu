@@ -53,9 +53,11 @@ __global__ void __launch_bounds__(SPEC_THREADS) k_spectrum_partial(Ctx c, SpecAr
             bool inside = true;
             if (PREC == MHDPIC_PREC_MIXED) {
                 int ci[3];
-                decode_cell(b, c.cell[i], ci);
+                const int4 ps = c.pos[i];
+                const float o[3] = {__int_as_float(ps.y), __int_as_float(ps.z), __int_as_float(ps.w)};
+                decode_cell(b, ps.x, ci);
                 for (int d = 0; d < c.ndim; ++d) {
-                    const double s = __dadd_rn((double)ci[d], (double)c.off[(int64_t)d * c.np + i]);
+                    const double s = __dadd_rn((double)ci[d], (double)o[d]);
                     const double xd = __dadd_rn(b.x0[d], __dmul_rn(s, b.dx[d]));
                     inside &= xd >= a.region[2 * d] && xd < a.region[2 * d + 1];
                 }
@@ -69,8 +71,14 @@ __global__ void __launch_bounds__(SPEC_THREADS) k_spectrum_partial(Ctx c, SpecAr
                 continue;
         }
         double v[3];
-        for (int d = 0; d < 3; ++d)
-            v[d] = PREC == MHDPIC_PREC_MIXED ? (double)c.p[(int64_t)d * c.np + i] : c.p64[(int64_t)d * c.np + i];
+        if (PREC == MHDPIC_PREC_MIXED) {
+            const float4 vs = c.vel[i];   // the exact value of the two-word four-velocity
+            for (int d = 0; d < 3; ++d)
+                v[d] = vel_f64(vs, d);
+        } else {
+            for (int d = 0; d < 3; ++d)
+                v[d] = c.p64[(int64_t)d * c.np + i];
+        }
         double v2 = __dadd_rn(__dmul_rn(v[0], v[0]), __dmul_rn(v[1], v[1]));
         v2 = __dadd_rn(v2, __dmul_rn(v[2], v[2]));
         double q;

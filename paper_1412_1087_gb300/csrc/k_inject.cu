@@ -310,14 +310,14 @@ __global__ void __launch_bounds__(INJ_THREADS) k_inject_particles(Ctx c, const i
                 ci[d] = i;
                 off[d] = o;
             }
-            c.cell[j] = (int32_t)(((int64_t)ci[2] * b.n[1] + ci[1]) * b.n[0] + ci[0]);
-            for (int d = 0; d < c.ndim; ++d)
-                c.off[(int64_t)d * c.np + j] = off[d];
+            c.pos[j] = make_int4((int32_t)(((int64_t)ci[2] * b.n[1] + ci[1]) * b.n[0] + ci[0]),
+                                 __float_as_int(off[0]), __float_as_int(off[1]), __float_as_int(off[2]));
+            float vf[3];
             for (int d = 0; d < 3; ++d) {
-                const float vf = (float)v[d];
-                c.p[(int64_t)d * c.np + j] = vf;
-                v[d] = (double)vf;   // the sums below are of what is stored
+                vf[d] = (float)v[d];
+                v[d] = (double)vf[d];   // the sums below are of what is stored (no residual)
             }
+            c.vel[j] = make_float4(vf[0], vf[1], vf[2], 0.f);
         } else {
             for (int d = 0; d < c.ndim; ++d)
                 c.x[(int64_t)d * c.np + j] = pos[d];

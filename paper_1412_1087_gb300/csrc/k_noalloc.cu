@@ -71,11 +71,11 @@ struct NoallocBox {
 
 // Cell of a particle (box coordinates), or false when it lies outside the box.
 template <int PREC, int D>
-__device__ __forceinline__ bool particle_cell(const NoallocBox &b, int64_t np, int64_t i, const int32_t *cell,
+__device__ __forceinline__ bool particle_cell(const NoallocBox &b, int64_t np, int64_t i, const int4 *pos,
                                               const double *x, int ci[3], int64_t ncell)
 {
     if (PREC == MHDPIC_PREC_MIXED) {
-        int32_t cl = cell[i];
+        int32_t cl = __ldg(&pos[i].x);
         if (cl < 0 || cl >= ncell)
             return false;
         uint32_t uc = (uint32_t)cl;
@@ -96,12 +96,12 @@ __device__ __forceinline__ bool particle_cell(const NoallocBox &b, int64_t np, i
 
 // particles per cell (cells outside the box are folded in like the stencil)
 template <int PREC, int D>
-__global__ void k_noalloc_count(NoallocBox b, int64_t np, const int32_t *__restrict__ cell,
+__global__ void k_noalloc_count(NoallocBox b, int64_t np, const int4 *__restrict__ pos,
                                 const double *__restrict__ x, ScratchView v, int64_t ncell)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
         int ci[3] = {0, 0, 0};
-        if (!particle_cell<PREC, D>(b, np, i, cell, x, ci, ncell))
+        if (!particle_cell<PREC, D>(b, np, i, pos, x, ci, ncell))
             continue;
         int gx = mhdpic::map_coord(ci[0], b.n[0], b.bc[0]);
         int gy = mhdpic::map_coord(ci[1], b.n[1], b.bc[1]);
@@ -140,10 +140,9 @@ __global__ void k_noalloc_scales(NoallocBox b, ScratchView v)
 
 // n = qm m W / dV, J = qm m u W / dV (App. A.1, eq:nJCR), into int64 fixed point
 template <int PREC, int D>
-__global__ void k_noalloc_deposit(NoallocBox b, int64_t np, const int32_t *__restrict__ cell,
-                                  const float *__restrict__ off, const float *__restrict__ p,
-                                  const double *__restrict__ x, const double *__restrict__ p64, ScratchView sv,
-                                  int64_t ncell)
+__global__ void k_noalloc_deposit(NoallocBox b, int64_t np, const int4 *__restrict__ pos,
+                                  const float4 *__restrict__ vel, const double *__restrict__ x,
+                                  const double *__restrict__ p64, ScratchView sv, int64_t ncell)
 {
     unsigned long long *__restrict__ acc = sv.acc;
     const double sc[4] = {sv.scale[0], sv.scale[1], sv.scale[2], sv.scale[3]};
@@ -152,12 +151,15 @@ __global__ void k_noalloc_deposit(NoallocBox b, int64_t np, const int32_t *__res
         double w[3][3] = {{0, 1, 0}, {0, 1, 0}, {0, 1, 0}};
         double v[3];
         if (PREC == MHDPIC_PREC_MIXED) {
-            if (!particle_cell<PREC, D>(b, np, i, cell, x, ci, ncell))
+            if (!particle_cell<PREC, D>(b, np, i, pos, x, ci, ncell))
                 continue;   // outside the box: contributes nothing
+            const int4 ps = pos[i];
+            const float o[3] = {__int_as_float(ps.y), __int_as_float(ps.z), __int_as_float(ps.w)};
+            const float4 vs = vel[i];
             for (int d = 0; d < D; ++d)
-                mhdpic::tsc_from_offset<double>((double)off[(int64_t)d * np + i], w[d]);
+                mhdpic::tsc_from_offset<double>((double)o[d], w[d]);
             for (int d = 0; d < 3; ++d)
-                v[d] = (double)p[(int64_t)d * np + i];
+                v[d] = mhdpic::vel_f64(vs, d);
         } else {
             if (isnan(x[i]))   // left the box through an open face
                 continue;
@@ -239,7 +241,7 @@ int scratch_on_current_device(cudaStream_t st, unsigned long long **out)
 extern "C" {
 
 int mhdpic_deposit_moments_noalloc(const mhdpic_grid *grid, const mhdpic_params *params, int32_t precision,
-                                   int64_t np, const int32_t *cell, const float *off, const float *p,
+                                   int64_t np, const mhdpic_pos *pos_in, const mhdpic_vel *vel_in,
                                    const double *x, const double *p64, double *out, void *stream)
 {
     if (!grid || !params || !out)
@@ -269,8 +271,12 @@ int mhdpic_deposit_moments_noalloc(const mhdpic_grid *grid, const mhdpic_params 
                             (long long)ncell, MHDPIC_NOALLOC_MAX_CELLS);
     if (np < 0 || np > 0x7fffffffLL)
         return noalloc_fail(MHDPIC_E_CAPACITY, "particle count %lld outside [0, 2^31)", (long long)np);
-    if (np > 0 && (precision == MHDPIC_PREC_MIXED ? (!cell || !off || !p) : (!x || !p64)))
+    if (np > 0 && (precision == MHDPIC_PREC_MIXED ? (!pos_in || !vel_in) : (!x || !p64)))
         return noalloc_fail(MHDPIC_E_ARG, "particle arrays of the chosen precision must be non-NULL");
+    if (precision == MHDPIC_PREC_MIXED && (((uintptr_t)pos_in | (uintptr_t)vel_in) & 15u))
+        return noalloc_fail(MHDPIC_E_ARG, "pos and vel must be 16-byte aligned");
+    const int4 *pos = reinterpret_cast<const int4 *>(pos_in);
+    const float4 *vel = reinterpret_cast<const float4 *>(vel_in);
     if (!(params->C > 0.0) || !std::isfinite(params->qm_cr) || !std::isfinite(params->m_cr))
         return noalloc_fail(MHDPIC_E_ARG, "C must be > 0, qm_cr and m_cr finite");
 
@@ -321,11 +327,11 @@ int mhdpic_deposit_moments_noalloc(const mhdpic_grid *grid, const mhdpic_params 
         }                                                                                 \
     } while (0)
     if (np > 0)
-        MHDPIC_NOALLOC_DISPATCH(k_noalloc_count, b, np, cell, x, sv, ncell);
+        MHDPIC_NOALLOC_DISPATCH(k_noalloc_count, b, np, pos, x, sv, ncell);
     k_noalloc_maxcount<<<cg, 256, 0, st>>>(sv, ncell);
     k_noalloc_scales<<<1, 1, 0, st>>>(b, sv);
     if (np > 0)
-        MHDPIC_NOALLOC_DISPATCH(k_noalloc_deposit, b, np, cell, off, p, x, p64, sv, ncell);
+        MHDPIC_NOALLOC_DISPATCH(k_noalloc_deposit, b, np, pos, vel, x, p64, sv, ncell);
 #undef MHDPIC_NOALLOC_DISPATCH
     const int64_t ob = (4 * ncell + 255) / 256;
     k_noalloc_to_double<<<(int)(ob < 152 * 32 ? ob : 152 * 32), 256, 0, st>>>(sv, ncell, out);

@@ -30,9 +30,14 @@
 //    the particles fall into items (sort cadence included).  A particle whose
 //    quantities exceed the bound the scales were sized for deposits at the
 //    global scale instead (a choice that depends on the particle alone).
-//  * 2-D: each thread copies its next two particles' words into a
-//    three-stage shared-memory ring with cp.async while it pushes the
-//    current one.
+//  * Particles are two 16-byte records (pos = {cell, offsets}, vel = the
+//    two-word four-velocity), one 128-bit load or store each, read through
+//    the sort's permutation by the push that applies it.  The stored
+//    four-velocity takes exactly the deposited dv (two-word sum), so the
+//    exchange with the gas conserves momentum to 2^-35 of |v| per step.
+//  * 2-D: each thread copies its next two particles' records into a
+//    three-stage shared-memory ring with 16-byte cp.async while it pushes
+//    the current one.
 #include "push_common.cuh"
 
 namespace mhdpic {
@@ -297,12 +302,8 @@ __device__ __forceinline__ bool within(const float q[4], const float *qb, int ch
            fabsf(q[3]) <= qb[ch0 + 3];
 }
 
-// Particle words staged per thread: cell, D offsets, 3 momenta.
-template <int D>
-constexpr int ring_planes()
-{
-    return 1 + D + 3;
-}
+// Particle records staged per thread: pos and vel, 16 bytes each.
+constexpr int RING_RECS = 2;
 constexpr int RING_STAGES = 3;
 // Per dimension: 2-D pushes are short, so the kernel hides the particle
 // loads behind a three-stage shared-memory ring (two particles ahead) and
@@ -318,10 +319,10 @@ constexpr int MIN_BLOCKS = D == 3 ? 2 : 3;
 template <int D>
 constexpr bool CONST_IN_SMEM = D == 2;
 
-__device__ __forceinline__ void cp_async4(uint32_t *dst, const void *src)
+__device__ __forceinline__ void cp_async16(int4 *dst, const void *src)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_commit()
@@ -334,54 +335,65 @@ __device__ __forceinline__ void cp_async_wait_prev()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(RING_STAGES - 1) : "memory");
 }
 
-// Start the copy of source particle i into one stage of this thread's ring
-// (one word per plane, planes PUSH_THREADS words apart).
-template <int D>
-__device__ __forceinline__ void stage_particle(const Ctx &c, int64_t i, uint32_t *dst)
+// Start the copy of source particle i's two records into one stage of this
+// thread's ring (records PUSH_THREADS int4 apart).
+__device__ __forceinline__ void stage_particle(const Ctx &c, int64_t i, int4 *dst)
 {
-    const int64_t np = c.np;
-    cp_async4(dst, c.src_cell + i);
-#pragma unroll
-    for (int d = 0; d < D; ++d)
-        cp_async4(dst + (1 + d) * PUSH_THREADS, c.src_off + d * np + i);
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-        cp_async4(dst + (1 + D + d) * PUSH_THREADS, c.src_p + d * np + i);
+    cp_async16(dst, c.src_pos + i);
+    cp_async16(dst + PUSH_THREADS, c.src_vel + i);
 }
 
 struct PIn {
     int32_t cell;
     float o[3], v[3];
+    uint32_t res;   // packed residuals of the two-word four-velocity
 };
 
-template <int D>
-__device__ __forceinline__ PIn load_staged(const uint32_t *in)
+__device__ __forceinline__ PIn unpack(const int4 a, const float4 b)
 {
     PIn r;
-    r.cell = (int32_t)in[0];
-    r.o[0] = r.o[1] = r.o[2] = 0.f;
-#pragma unroll
-    for (int d = 0; d < D; ++d)
-        r.o[d] = __uint_as_float(in[(1 + d) * PUSH_THREADS]);
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-        r.v[d] = __uint_as_float(in[(1 + D + d) * PUSH_THREADS]);
+    r.cell = a.x;
+    r.o[0] = __int_as_float(a.y);
+    r.o[1] = __int_as_float(a.z);
+    r.o[2] = __int_as_float(a.w);
+    r.v[0] = b.x;
+    r.v[1] = b.y;
+    r.v[2] = b.z;
+    r.res = __float_as_uint(b.w);
     return r;
 }
 
-template <int D>
+__device__ __forceinline__ PIn load_staged(const int4 *in)
+{
+    const int4 a = in[0], bi = in[PUSH_THREADS];
+    return unpack(a, make_float4(__int_as_float(bi.x), __int_as_float(bi.y), __int_as_float(bi.z),
+                                 __int_as_float(bi.w)));
+}
+
 __device__ __forceinline__ PIn load_global(const Ctx &c, int64_t i)
 {
-    PIn r;
-    r.cell = c.src_cell[i];
-    r.o[0] = r.o[1] = r.o[2] = 0.f;
-#pragma unroll
-    for (int d = 0; d < D; ++d)
-        r.o[d] = c.src_off[d * c.np + i];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-        r.v[d] = c.src_p[d * c.np + i];
-    return r;
+    return unpack(__ldg(c.src_pos + i), __ldg(c.src_vel + i));
+}
+
+__device__ __forceinline__ void store_particle(const Ctx &c, int64_t j, int32_t cell, const float o[3],
+                                               const float v[3], uint32_t res)
+{
+    c.pos[j] = make_int4(cell, __float_as_int(o[0]), __float_as_int(o[1]), __float_as_int(o[2]));
+    c.vel[j] = make_float4(v[0], v[1], v[2], __uint_as_float(res));
+}
+
+// Byte offset of the particle ring in the push's shared memory: after the
+// deposit tile (NPLANE int planes) and the staged fields (float4 + float2 per
+// slot), rounded up to the 16 bytes a cp.async of 16 bytes needs.
+__host__ __device__ constexpr size_t ring_offset(int slots)
+{
+    return ((sizeof(int) * NPLANE + sizeof(float4) + sizeof(float2)) * (size_t)slots + 15) / 16 * 16;
+}
+
+__device__ __forceinline__ void store_dead(const Ctx &c, int64_t j)
+{
+    c.pos[j] = make_int4(DEAD_CELL, 0, 0, 0);
+    c.vel[j] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Charge and current density deposit of one particle (eq:nJCR) at cell ci,
@@ -431,15 +443,8 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
                                           int64_t j, const PIn &pin, const float4 *sFa, const float2 *sFb,
                                           int *sD, unsigned long long *mout)
 {
-    const int64_t np = c.np;
     if (pin.cell == DEAD_CELL) {   // left the box earlier (kept until the next sort)
-        c.cell[j] = DEAD_CELL;
-#pragma unroll
-        for (int d = 0; d < D; ++d)
-            c.off[d * np + j] = 0.f;
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-            c.p[d * np + j] = 0.f;
+        store_dead(c, j);
         return 0.f;
     }
     int ci[3];
@@ -505,17 +510,17 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
     const float s2 = 2.f / (1.f + b0 * b0 + b1 * b1 + b2 * b2);
     const float r0 = s2 * (t1 * b2 - t2 * b1), r1 = s2 * (t2 * b0 - t0 * b2), r2 = s2 * (t0 * b1 - t1 * b0);
     const float v10 = v00 + r0, v11 = v01 + r1, v12 = v02 + r2;
-    float vn[3] = {v10 + e0, v11 + e1, v12 + e2};
+    const float vk[3] = {v10 + e0, v11 + e1, v12 + e2};   // after the second kick, FP32
 
     // dv = h E + rot without cancellation; the rotation keeps |v|, so dE_k is
     // the change of the two half kicks, E_k(a) - E_k(b) = (a-b).(a+b)/(ga+gb)
-    const float ig2 = rsqrtf(fmaf(vsq3(vn), k.invC2, 1.f));
-    const float gn = 1.f / ign, g1 = 1.f / ig1, g2 = 1.f / ig2;
-    const float dEk = (e0 * (vn[0] + v10) + e1 * (vn[1] + v11) + e2 * (vn[2] + v12)) / (g2 + g1) +
+    const float ig2k = rsqrtf(fmaf(vsq3(vk), k.invC2, 1.f));
+    const float gn = 1.f / ign, g1 = 1.f / ig1, g2 = 1.f / ig2k;
+    const float dEk = (e0 * (vk[0] + v10) + e1 * (vk[1] + v11) + e2 * (vk[2] + v12)) / (g2 + g1) +
                       (e0 * (v00 + v[0]) + e1 * (v01 + v[1]) + e2 * (v02 + v[2])) / (g1 + gn);
+    const float dv[3] = {pinned(2.f * e0 + r0), pinned(2.f * e1 + r1), pinned(2.f * e2 + r2)};
     {
-        const float qc[4] = {pinned(-k.m * (2.f * e0 + r0)), pinned(-k.m * (2.f * e1 + r1)),
-                             pinned(-k.m * (2.f * e2 + r2)), pinned(-k.m * dEk)};
+        const float qc[4] = {pinned(-k.m * dv[0]), pinned(-k.m * dv[1]), pinned(-k.m * dv[2]), pinned(-k.m * dEk)};
         if (within(qc, k.qb, CH_MX)) {
             const float qs[4] = {pinned(qc[0] * k.st[0]), pinned(qc[1] * k.st[1]), pinned(qc[2] * k.st[2]),
                                  pinned(qc[3] * k.st[3])};
@@ -530,21 +535,32 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
         }
     }
 
-    // drift to x^(n+1)
+    // the stored four-velocity takes exactly the deposited dv (two-word sum,
+    // rounded once at 2^-35 of |v|): what the gas is given is what the
+    // particle loses
+    float vn[3] = {v[0], v[1], v[2]};   // the leading words (mirrored by a reflection at the half step)
+    int rq[3] = {res_field(pin.res, 0), res_field(pin.res, 1), res_field(pin.res, 2)};
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+        if (v[d] != pin.v[d])
+            rq[d] = -rq[d];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        two_word_add(vn[d], rq[d], dv[d]);
+    const float ig2 = rsqrtf(fmaf(vsq3(vn), k.invC2, 1.f));
+
+    // drift to x^(n+1); a reflection mirrors both words of the component
 #pragma unroll
     for (int d = 0; d < D; ++d) {
         o[d] = fmaf(k.hdx[d] * ig2, vn[d], o[d]);
+        const float before = vn[d];
         leaving |= renorm_mixed(b, d, ci[d], o[d], vn[d], c.status);
+        if (vn[d] != before)
+            rq[d] = -rq[d];
     }
     leaving |= removed_early(c, j);
     if (leaving) {   // removed: no moments deposit; the next sort drops it
-        c.cell[j] = DEAD_CELL;
-#pragma unroll
-        for (int d = 0; d < D; ++d)
-            c.off[d * np + j] = 0.f;
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-            c.p[d * np + j] = 0.f;
+        store_dead(c, j);
         return 0.f;
     }
 
@@ -553,13 +569,7 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
 
     if (!isfinite(vn[0] + vn[1] + vn[2]))
         set_status(c.status, MHDPIC_ST_NONFINITE);
-    c.cell[j] = (int32_t)(((int64_t)ci[2] * b.n[1] + ci[1]) * b.n[0] + ci[0]);
-#pragma unroll
-    for (int d = 0; d < D; ++d)
-        c.off[d * np + j] = o[d];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-        c.p[d * np + j] = vn[d];
+    store_particle(c, j, (int32_t)(((int64_t)ci[2] * b.n[1] + ci[1]) * b.n[0] + ci[0]), o, vn, res_pack(rq));
     return vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2];
 }
 
@@ -574,9 +584,8 @@ __global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_push_mixed(Ctx 
     int *sD = reinterpret_cast<int *>(smem);
     float4 *sFa = reinterpret_cast<float4 *>(smem + sizeof(int) * NPLANE * S);
     float2 *sFb = reinterpret_cast<float2 *>(smem + (sizeof(int) * NPLANE + sizeof(float4)) * S);
-    uint32_t *ring = reinterpret_cast<uint32_t *>(smem + (sizeof(int) * NPLANE + sizeof(float4) + sizeof(float2)) * S) +
-                     threadIdx.x;
-    constexpr int RS = ring_planes<D>() * PUSH_THREADS;   // words per ring stage
+    int4 *ring = reinterpret_cast<int4 *>(smem + ring_offset(S)) + threadIdx.x;
+    constexpr int RS = RING_RECS * PUSH_THREADS;   // int4 per ring stage
     __shared__ int s_item;
     __shared__ MixedConst s_k;
     unsigned long long *mout = c.momdep[cur_out];
@@ -639,7 +648,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_push_mixed(Ctx 
 #pragma unroll
                 for (int s0 = 0; s0 < NS - 1; ++s0) {
                     if (valid(rb + s0 * rs))
-                        stage_particle<D>(c, src_of(rb + s0 * rs), ring + s0 * RS);
+                        stage_particle(c, src_of(rb + s0 * rs), ring + s0 * RS);
                     cp_async_commit();
                 }
                 int64_t sn = valid(rb + (NS - 1) * rs) ? src_of(rb + (NS - 1) * rs) : 0;
@@ -647,13 +656,13 @@ __global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_push_mixed(Ctx 
                 for (int64_t r = rb; r < re; r += rs) {
                     const int stn = st == 0 ? NS - 1 : st - 1;
                     if (valid(r + (NS - 1) * rs))
-                        stage_particle<D>(c, sn, ring + stn * RS);
+                        stage_particle(c, sn, ring + stn * RS);
                     if (valid(r + NS * rs))
                         sn = src_of(r + NS * rs);
                     cp_async_commit();
                     cp_async_wait_prev();
                     if (lane0 + r < cnt)
-                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + lane0 + r, load_staged<D>(ring + st * RS),
+                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + lane0 + r, load_staged(ring + st * RS),
                                                            sFa, sFb, sD, mout));
                     st = st + 1 == NS ? 0 : st + 1;
                 }
@@ -664,7 +673,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_push_mixed(Ctx 
                         const int64_t src = sn;
                         if (valid(r + rs))
                             sn = src_of(r + rs);
-                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + lane0 + r, load_global<D>(c, src), sFa,
+                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + lane0 + r, load_global(c, src), sFa,
                                                            sFb, sD, mout));
                     }
             }
@@ -746,7 +755,7 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_deposit_mixed(Ctx c, const Wor
                     continue;
                 const int64_t j = lr.base + lane0 + r;
                 const int64_t src = gather ? (int64_t)__ldg(c.perm_src + j) : j;
-                const PIn pin = load_global<D>(c, src);
+                const PIn pin = load_global(c, src);
                 if (pin.cell == DEAD_CELL)
                     continue;
                 int ci[3];
@@ -807,8 +816,8 @@ void launch_d(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur_out
 size_t push_smem_bytes_mixed(const Ctx &c)
 {
     const bool staged = c.ndim == 3 ? STAGED<3> : STAGED<2>;
-    const size_t ring = staged ? sizeof(uint32_t) * RING_STAGES * (size_t)(1 + c.ndim + 3) * PUSH_THREADS : 0;
-    return (sizeof(int) * NPLANE + sizeof(float4) + sizeof(float2)) * (size_t)c.tile_slots + ring;
+    const size_t ring = staged ? sizeof(int4) * RING_STAGES * (size_t)RING_RECS * PUSH_THREADS : 0;
+    return ring_offset(c.tile_slots) + ring;
 }
 
 int push_blocks_per_sm_mixed(const Ctx &c)

@@ -55,7 +55,7 @@ __device__ __forceinline__ int32_t key_in_box(const Ctx &c, const BoxDev &b, int
     int ci[3] = {0, 0, 0};
     bool dead = false;
     if (PREC == MHDPIC_PREC_MIXED) {
-        int32_t cl = c.cell[i];
+        int32_t cl = __ldg(&c.pos[i].x);
         dead = cl == DEAD_CELL;
         if (!dead && (cl < 0 || cl >= b.ncell)) {
             set_status(c.status, MHDPIC_ST_CELL_RANGE);
@@ -561,7 +561,9 @@ __global__ void k_gather_all(int64_t np, const int32_t *__restrict__ perm, Plane
         if (i < 0 || i >= np)   // never taken for a valid permutation
             i = r;
         for (int q = 0; q < pl.n; ++q) {
-            if (pl.esz[q] == 8)
+            if (pl.esz[q] == 16)
+                reinterpret_cast<int4 *>(pl.dst[q])[r] = __ldg(reinterpret_cast<const int4 *>(pl.src[q]) + i);
+            else if (pl.esz[q] == 8)
                 reinterpret_cast<unsigned long long *>(pl.dst[q])[r] =
                     __ldg(reinterpret_cast<const unsigned long long *>(pl.src[q]) + i);
             else
@@ -709,9 +711,8 @@ int launch_gather(const Ctx &c, const int32_t *perm, const PSet &src, const PSet
         }
     };
     if (c.prec == MHDPIC_PREC_MIXED) {
-        add(src.cell, dst.cell, 4, 1);
-        add(src.off, dst.off, 4, c.ndim);
-        add(src.p, dst.p, 4, 3);
+        add(src.pos, dst.pos, 16, 1);
+        add(src.vel, dst.vel, 16, 1);
     } else {
         add(src.x, dst.x, 8, c.ndim);
         add(src.p64, dst.p64, 8, 3);
@@ -756,9 +757,8 @@ __global__ void k_mark_free(Ctx c, const int32_t *__restrict__ offset)
     for (int64_t j = live + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < c.np;
          j += (int64_t)gridDim.x * blockDim.x) {
         if (PREC == MHDPIC_PREC_MIXED) {
-            c.cell[j] = DEAD_CELL;
-            for (int d = 0; d < 3; ++d)
-                c.p[(int64_t)d * c.np + j] = 0.f;
+            c.pos[j] = make_int4(DEAD_CELL, 0, 0, 0);
+            c.vel[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         } else {
             c.x[j] = __longlong_as_double(0x7ff8000000000000ll);
             for (int d = 0; d < 3; ++d)
@@ -772,7 +772,7 @@ __global__ void k_count_live(Ctx c, int prec, unsigned long long *out)
     unsigned long long n = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.np;
          i += (int64_t)gridDim.x * blockDim.x)
-        n += prec == MHDPIC_PREC_MIXED ? (c.cell[i] != DEAD_CELL) : !isnan(c.x[i]);
+        n += prec == MHDPIC_PREC_MIXED ? (c.pos[i].x != DEAD_CELL) : !isnan(c.x[i]);
     for (int o = 16; o > 0; o >>= 1)
         n += __shfl_xor_sync(0xffffffffu, n, o);
     if ((threadIdx.x & 31) == 0 && n)

@@ -134,7 +134,7 @@ struct mhdpic_ctx {
 
     size_t particle_bytes() const
     {
-        return k.prec == MHDPIC_PREC_MIXED ? (size_t)(4 + 4 * k.ndim + 12) : (size_t)(8 * k.ndim + 24);
+        return k.prec == MHDPIC_PREC_MIXED ? (size_t)(sizeof(int4) + sizeof(float4)) : (size_t)(8 * k.ndim + 24);
     }
 };
 
@@ -162,9 +162,8 @@ int copy_particles(mhdpic_ctx *c, bool to_device)
                          : cudaMemcpyAsync(host, dev, bytes, kind, c->stream);
     };
     if (c->k.prec == MHDPIC_PREC_MIXED) {
-        CK(cp(c->k.cell, c->hp.cell, sizeof(int32_t) * np));
-        CK(cp(c->k.off, c->hp.off, sizeof(float) * c->k.ndim * np));
-        CK(cp(c->k.p, c->hp.p, sizeof(float) * 3 * np));
+        CK(cp(c->k.pos, c->hp.pos, sizeof(int4) * np));
+        CK(cp(c->k.vel, c->hp.vel, sizeof(float4) * np));
     } else {
         CK(cp(c->k.x, c->hp.x, sizeof(double) * c->k.ndim * np));
         CK(cp(c->k.p64, c->hp.p64, sizeof(double) * 3 * np));
@@ -197,16 +196,14 @@ void use_set(mhdpic_ctx *c, int set)
     c->cur_set = set;
     const PSet &q = c->sets[set];
     Ctx &k = c->k;
-    k.cell = q.cell;
-    k.off = q.off;
-    k.p = q.p;
+    k.pos = q.pos;
+    k.vel = q.vel;
     k.x = q.x;
     k.p64 = q.p64;
     k.tinj = q.tinj;
     k.perm_src = nullptr;
-    k.src_cell = q.cell;
-    k.src_off = q.off;
-    k.src_p = q.p;
+    k.src_pos = q.pos;
+    k.src_vel = q.vel;
     k.src_x = q.x;
     k.src_p64 = q.p64;
 }
@@ -237,9 +234,8 @@ int sync_to_caller(mhdpic_ctx *c)
     const int64_t np = c->k.np;
     const PSet &a = c->sets[1], &b = c->sets[0];
     if (c->k.prec == MHDPIC_PREC_MIXED) {
-        CK(cudaMemcpyAsync(b.cell, a.cell, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, c->stream));
-        CK(cudaMemcpyAsync(b.off, a.off, sizeof(float) * c->k.ndim * np, cudaMemcpyDeviceToDevice, c->stream));
-        CK(cudaMemcpyAsync(b.p, a.p, sizeof(float) * 3 * np, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(b.pos, a.pos, sizeof(int4) * np, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(b.vel, a.vel, sizeof(float4) * np, cudaMemcpyDeviceToDevice, c->stream));
     } else {
         CK(cudaMemcpyAsync(b.x, a.x, sizeof(double) * c->k.ndim * np, cudaMemcpyDeviceToDevice, c->stream));
         CK(cudaMemcpyAsync(b.p64, a.p64, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, c->stream));
@@ -335,8 +331,10 @@ int validate(int32_t nbox, const mhdpic_grid *grids, const mhdpic_params *params
     if (nc > 0x7fffffffLL)
         return fail(MHDPIC_E_CAPACITY, "%lld cells in total exceed 2^31", (long long)nc);
     if (opt->precision == MHDPIC_PREC_MIXED) {
-        if (parts->np > 0 && (!parts->cell || !parts->off || !parts->p))
-            return fail(MHDPIC_E_ARG, "mixed precision needs particles.cell, .off and .p");
+        if (parts->np > 0 && (!parts->pos || !parts->vel))
+            return fail(MHDPIC_E_ARG, "mixed precision needs particles.pos and .vel");
+        if (((uintptr_t)parts->pos | (uintptr_t)parts->vel) & 15u)
+            return fail(MHDPIC_E_ARG, "particles.pos and .vel must be 16-byte aligned");
     } else if (parts->np > 0 && (!parts->x || !parts->p64)) {
         return fail(MHDPIC_E_ARG, "FP64 needs particles.x and .p64");
     }
@@ -590,16 +588,14 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
     if (c->mem == MHDPIC_MEM_HOST) {
         c->hp = *parts;
         if (k.prec == MHDPIC_PREC_MIXED) {
-            if ((rc = c->alloc(&s0.cell, np)) || (rc = c->alloc(&s0.off, k.ndim * np)) ||
-                (rc = c->alloc(&s0.p, 3 * np)))
+            if ((rc = c->alloc(&s0.pos, np)) || (rc = c->alloc(&s0.vel, np)))
                 return bail(rc);
         } else if ((rc = c->alloc(&s0.x, k.ndim * np)) || (rc = c->alloc(&s0.p64, 3 * np))) {
             return bail(rc);
         }
     } else {
-        s0.cell = parts->cell;
-        s0.off = parts->off;
-        s0.p = parts->p;
+        s0.pos = reinterpret_cast<int4 *>(parts->pos);
+        s0.vel = reinterpret_cast<float4 *>(parts->vel);
         s0.x = parts->x;
         s0.p64 = parts->p64;
     }
@@ -607,9 +603,8 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
     {
         char *t = (char *)c->s.tmp;
         if (k.prec == MHDPIC_PREC_MIXED) {
-            s1.cell = (int32_t *)t;
-            s1.off = (float *)(t + sizeof(int32_t) * np);
-            s1.p = s1.off + (size_t)k.ndim * np;
+            s1.pos = (int4 *)t;
+            s1.vel = (float4 *)(t + sizeof(int4) * np);
         } else {
             s1.x = (double *)t;
             s1.p64 = s1.x + (size_t)k.ndim * np;
@@ -730,16 +725,14 @@ int mhdpic_interp_push(mhdpic_ctx *c, double dt, int32_t nsub)
         const bool gather = c->pending;
         if (gather) {
             const PSet &src = c->sets[c->cur_set], &dst = c->sets[c->cur_set ^ 1];
-            kk.cell = dst.cell;
-            kk.off = dst.off;
-            kk.p = dst.p;
+            kk.pos = dst.pos;
+            kk.vel = dst.vel;
             kk.x = dst.x;
             kk.p64 = dst.p64;
             kk.tinj = dst.tinj;
             kk.perm_src = c->s.perm;
-            kk.src_cell = src.cell;
-            kk.src_off = src.off;
-            kk.src_p = src.p;
+            kk.src_pos = src.pos;
+            kk.src_vel = src.vel;
             kk.src_x = src.x;
             kk.src_p64 = src.p64;
             // the injection times follow the permutation before the push reads them
@@ -1088,6 +1081,16 @@ int mhdpic_get_deposits(mhdpic_ctx *c, int32_t which, double *out)
         return fail(MHDPIC_E_ARG, "which must be 0 or 1 and out non-NULL");
     const unsigned long long *src = which == 0 ? c->k.corr : c->k.momdep[c->cur];
     return check_launch(c, launch_fixed_to_double(c->k, src, which == 0 ? CH_MX : CH_N, out, c->stream));
+}
+
+int mhdpic_get_velocities(mhdpic_ctx *c, double *out)
+{
+    if (!c || !c->valid || !out)
+        return fail(MHDPIC_E_ARG, "invalid context or output pointer");
+    int rc;
+    if ((rc = copy_particles(c, true)) || (rc = sync_to_caller(c)))
+        return rc;
+    return check_launch(c, launch_velocities_to_double(c->k, out, c->stream));
 }
 
 int mhdpic_get_fields(mhdpic_ctx *c, double *out)

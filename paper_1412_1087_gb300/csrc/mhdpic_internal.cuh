@@ -119,19 +119,19 @@ struct Ctx {
     const int64_t *box_part_start; // device [nbox+1]
     const int64_t *box_cell_start; // device [nbox+1]
     // current particle set, device: the caller's buffers (or their mirrors in
-    // host-memory mode) or the library's second set
-    int32_t *cell;
-    float *off;
-    float *p;
+    // host-memory mode) or the library's second set.  Mixed precision keeps
+    // two 16-byte records per particle: pos = {cell, off[3]} (as int4, the
+    // offsets' bits in y, z, w) and vel = {v[3], packed residual} (float4)
+    int4 *pos;
+    float4 *vel;
     double *x;
     double *p64;
     // what a push reads: the current set itself (perm_src null), or right
     // after a sort the previous set through the permutation, sorted position
     // j taking particle perm_src[j]; the push then writes the current set
     const int32_t *perm_src;
-    const int32_t *src_cell;
-    const float *src_off;
-    const float *src_p;
+    const int4 *src_pos;
+    const float4 *src_vel;
     const double *src_x;
     const double *src_p64;
     double *rho, *mom, *egas, *B;
@@ -174,11 +174,10 @@ struct SortScratch {
     int32_t *max_count;    // [1]
 };
 
-// One set of particle arrays (the precision's planes; the others null).
+// One set of particle arrays (the precision's arrays; the others null).
 struct PSet {
-    int32_t *cell;
-    float *off;
-    float *p;
+    int4 *pos;
+    float4 *vel;
     double *x;
     double *p64;
     double *tinj;   // injection times, when tracked
@@ -217,6 +216,8 @@ int launch_totals(const Ctx &c, double *partials, int nchunks, int64_t per_chunk
 int launch_fixed_to_double(const Ctx &c, const unsigned long long *src, int ch0, double *out,
                            cudaStream_t st);
 int launch_fields_to_double(const Ctx &c, double *out, cudaStream_t st);
+// the current four-velocities as double, plane-major [3][np]
+int launch_velocities_to_double(const Ctx &c, double *out, cudaStream_t st);
 
 // Spectrum request (mhdpic_spectrum); edges is a device copy [nbins + 1].
 struct SpecArgs {

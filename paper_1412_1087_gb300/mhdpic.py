@@ -60,8 +60,10 @@ class Options(ctypes.Structure):
 
 
 class Particles(ctypes.Structure):
+    # mixed precision: pos = mhdpic_pos[np] (int32 cell, 3 f32 offsets) and
+    # vel = mhdpic_vel[np] (3 f32 leading words, packed residuals), 16 bytes each
     _fields_ = [("np", ctypes.c_int64), ("box_start", ctypes.POINTER(ctypes.c_int64)),
-                ("cell", ctypes.c_void_p), ("off", ctypes.c_void_p), ("p", ctypes.c_void_p),
+                ("pos", ctypes.c_void_p), ("vel", ctypes.c_void_p),
                 ("x", ctypes.c_void_p), ("p64", ctypes.c_void_p)]
 
 
@@ -95,6 +97,7 @@ SIGNATURES = {
     "mhdpic_sort_cadence": (ctypes.c_int32, [_V]),
     "mhdpic_get_deposits": (ctypes.c_int, [_V, ctypes.c_int32, _V]),
     "mhdpic_get_fields": (ctypes.c_int, [_V, _V]),
+    "mhdpic_get_velocities": (ctypes.c_int, [_V, _V]),
     "mhdpic_num_keys": (ctypes.c_int64, [_V]),
     "mhdpic_get_status": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_uint32)]),
     "mhdpic_clear_status": (ctypes.c_int, [_V]),
@@ -102,7 +105,7 @@ SIGNATURES = {
     "mhdpic_debug_fail_launch": (ctypes.c_int, [_V, ctypes.c_int64]),
     "mhdpic_destroy": (ctypes.c_int, [_V]),
     "mhdpic_deposit_moments_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Params), ctypes.c_int32,
-                                                       ctypes.c_int64, _V, _V, _V, _V, _V, _V, _V]),
+                                                       ctypes.c_int64, _V, _V, _V, _V, _V, _V]),
     "mhdpic_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mhdpic_last_error": (ctypes.c_char_p, []),
 }
@@ -248,6 +251,10 @@ def mhdpic_get_fields(ctx, out_ptr: int) -> None:
     _check(load().mhdpic_get_fields(ctx, out_ptr))
 
 
+def mhdpic_get_velocities(ctx, out_ptr: int) -> None:
+    _check(load().mhdpic_get_velocities(ctx, out_ptr))
+
+
 def mhdpic_num_keys(ctx) -> int:
     return int(load().mhdpic_num_keys(ctx))
 
@@ -274,12 +281,33 @@ def mhdpic_destroy(ctx) -> None:
     _check(load().mhdpic_destroy(ctx))
 
 
-def mhdpic_deposit_moments_noalloc(grid: Grid, params: Params, precision: int, np_: int, cell=0, off=0,
-                                   p=0, x=0, p64=0, out=0, stream=None) -> None:
+def mhdpic_deposit_moments_noalloc(grid: Grid, params: Params, precision: int, np_: int, pos=0, vel=0,
+                                   x=0, p64=0, out=0, stream=None) -> None:
     """Allocation-free charge/current deposit of one box (device pointers as ints)."""
     _check(load().mhdpic_deposit_moments_noalloc(ctypes.byref(grid), ctypes.byref(params), int(precision),
-                                                 int(np_), cell or None, off or None, p or None, x or None,
+                                                 int(np_), pos or None, vel or None, x or None,
                                                  p64 or None, out or None, stream))
+
+
+def pack_records_arrays(cell, off, p):
+    """Mixed-precision particle records from SoA arrays: pos (np, 4) int32 =
+    cell plus the offsets' bits (unused dimensions 0), vel (np, 4) float32 =
+    the four-velocity with a zero residual word."""
+    n = cell.shape[0]
+    pos = np.zeros((n, 4), dtype=np.int32)
+    pos[:, 0] = cell
+    pos.view(np.float32)[:, 1:1 + off.shape[0]] = off.T
+    vel = np.zeros((n, 4), dtype=np.float32)
+    vel[:, :3] = p.T
+    return pos, vel
+
+
+def pack_records(boxes):
+    """pack_records_arrays over the concatenated particles of a batch of boxes."""
+    cat = np.concatenate
+    return pack_records_arrays(cat([b.cell for b in boxes]).astype(np.int32),
+                               cat([b.off for b in boxes], axis=1).astype(np.float32),
+                               cat([b.p for b in boxes], axis=1).astype(np.float32))
 
 
 def status_names(flags: int) -> List[str]:
@@ -329,9 +357,7 @@ class Engine:
         mk_gas = on_device if memory == MHDPIC_MEM_DEVICE else pinned
         cat = np.concatenate
         if precision == MHDPIC_PREC_MIXED:
-            self._cell = mk(cat([b.cell for b in self.boxes]), np.int32)
-            self._off = mk(cat([b.off for b in self.boxes], axis=1), np.float32)
-            self._p = mk(cat([b.p for b in self.boxes], axis=1), np.float32)
+            self._pos, self._vel = (mk(a, a.dtype) for a in pack_records(self.boxes))
             self._x = self._p64 = None
         else:
             from . import workloads as wl
@@ -341,7 +367,7 @@ class Engine:
                 v64 = cat([b.p.astype(np.float64) for b in self.boxes], axis=1)
             self._x = mk(x64, np.float64)
             self._p64 = mk(v64, np.float64)
-            self._cell = self._off = self._p = None
+            self._pos = self._vel = None
         self.rho = mk_gas(cat([b.rho for b in self.boxes]), np.float64)
         self.mom = mk_gas(cat([b.mom for b in self.boxes], axis=1), np.float64)
         self.egas = mk_gas(cat([b.egas for b in self.boxes]), np.float64)
@@ -371,7 +397,7 @@ class Engine:
         def ptr(t):
             return t.data_ptr() if t is not None else None
 
-        parts.cell, parts.off, parts.p = ptr(self._cell), ptr(self._off), ptr(self._p)
+        parts.pos, parts.vel = ptr(self._pos), ptr(self._vel)
         parts.x, parts.p64 = ptr(self._x), ptr(self._p64)
         gas = Gas(ptr(self.rho), ptr(self.mom), ptr(self.egas), ptr(self.B))
         self._parts, self._gas = parts, gas
@@ -400,11 +426,33 @@ class Engine:
             self.sync_particles()
         return t
 
-    cell = property(lambda self: self._synced(self._cell))
-    off = property(lambda self: self._synced(self._off))
-    p = property(lambda self: self._synced(self._p))
+    # mixed precision: views into the 16-byte records (writable in place);
+    # p holds the FP32 leading words of the two-word four-velocity, whose
+    # exact value velocities() returns
+    pos = property(lambda self: self._synced(self._pos))
+    vel = property(lambda self: self._synced(self._vel))
+    cell = property(lambda self: None if self._pos is None else self._synced(self._pos[:, 0]))
+    off = property(lambda self: None if self._pos is None
+                   else self._synced(self._pos.view(self.torch.float32)[:, 1:1 + self.ndim].t()))
+    p = property(lambda self: None if self._vel is None else self._synced(self._vel[:, :3].t()))
     x = property(lambda self: self._synced(self._x))
     p64 = property(lambda self: self._synced(self._p64))
+
+    def set_particles(self, cell, off, p) -> None:
+        """Overwrite the mixed-precision state in the caller's order: cell
+        (np,), off (ndim, np), p (3, np); the residual words become 0."""
+        torch = self.torch
+        self.sync_particles()
+        pos, vel = pack_records_arrays(np.asarray(cell), np.asarray(off), np.asarray(p))
+        self._pos.copy_(torch.from_numpy(pos))
+        self._vel.copy_(torch.from_numpy(vel))
+
+    def velocities(self):
+        """The current four-velocities as float64 (3, np): the exact value of
+        each two-word record (mixed) or a copy of p64."""
+        out = self.torch.empty((3, max(self.np, 1)), dtype=self.torch.float64, device=self.device)
+        mhdpic_get_velocities(self.ctx, out.data_ptr())
+        return out[:, :self.np]
 
     # -- the step ---------------------------------------------------------
     def sort(self, want_perm: bool = False, want_counts: bool = False):

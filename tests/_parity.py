@@ -48,8 +48,17 @@ def positions_of(eng):
 
 
 def momenta_of(eng):
-    t = eng.p64 if eng.p64 is not None else eng.p
-    return t.cpu().numpy().astype(np.float64)
+    """Four-velocities (3, np) as float64: the exact value of the mixed
+    precision's two-word records, or the FP64 state."""
+    return eng.velocities().cpu().numpy()
+
+
+def mixed_rows(eng):
+    """The mixed-precision state as rows (cell, offsets, leading words,
+    residual word), one column per particle, for comparisons bit for bit."""
+    vel = eng.vel.cpu().numpy()
+    return np.vstack([eng.cell.cpu().numpy().astype(np.float64)[None], eng.off.cpu().numpy(),
+                      vel[:, :3].T.astype(np.float64), vel[:, 3].view(np.uint32).astype(np.float64)[None]])
 
 
 def periodic_diff(a, b, L):

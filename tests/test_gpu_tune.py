@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from paper_1412_1087_gb300 import workloads as wl
-from tests._parity import tilt_B
+from tests._parity import mixed_rows, tilt_B
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -19,7 +19,7 @@ from paper_1412_1087_gb300 import tune  # noqa: E402
 
 
 def _state(eng):
-    rows = np.vstack([eng.cell.cpu().numpy().astype(np.float64)[None], eng.off.cpu().numpy(), eng.p.cpu().numpy()])
+    rows = mixed_rows(eng)
     rows = rows[:, np.lexsort(rows[::-1])]
     return (eng.deposits(0).cpu().numpy(), eng.deposits(1).cpu().numpy(), eng.mom.cpu().numpy(),
             eng.egas.cpu().numpy(), rows)

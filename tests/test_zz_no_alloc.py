@@ -40,8 +40,8 @@ def _call(eng, box, prec, out):
     g, p = _structs(box)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     if prec == m.MHDPIC_PREC_MIXED:
-        m.mhdpic_deposit_moments_noalloc(g, p, prec, box.np, cell=eng.cell.data_ptr(), off=eng.off.data_ptr(),
-                                         p=eng.p.data_ptr(), out=out.data_ptr(), stream=stream)
+        m.mhdpic_deposit_moments_noalloc(g, p, prec, box.np, pos=eng.pos.data_ptr(), vel=eng.vel.data_ptr(),
+                                         out=out.data_ptr(), stream=stream)
     else:
         m.mhdpic_deposit_moments_noalloc(g, p, prec, box.np, x=eng.x.data_ptr(), p64=eng.p64.data_ptr(),
                                          out=out.data_ptr(), stream=stream)
