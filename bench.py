@@ -454,6 +454,63 @@ def _error_vs_oracle(args, seed, torch, nsteps=10):
     return out
 
 
+def _build_boxes(name, seed):
+    """The full-size boxes of a named workload (for the extra workloads)."""
+    ns = argparse.Namespace(workload=name, n=128, ppc=32, n2d=1024)
+    return _workload(ns, seed)
+
+
+def _measure_workload(name, boxes, dt, args, torch, m, dev, stream, peak, peak_kind):
+    """One more full-size workload, measured as the headline one is: the
+    library's tuner picks the sort cadence on real steps, then args.steps
+    eager steps (every push bracketed by events: the push kernel's roofline)
+    and args.steps graph-replayed steps (the rate); the worst per-box errors
+    against the oracle come from _error_vs_oracle on a sample of the recipe."""
+    npart = sum(int((b.cell >= 0).sum()) for b in boxes)
+    ncell = sum(b.ncell for b in boxes)
+    ndim = boxes[0].ndim
+    eng = m.Engine(boxes, precision=m.MHDPIC_PREC_MIXED, device=dev, stream=stream)
+    eng.run(dt, 20, 0)
+    k = eng.sort_cadence()
+    torch.cuda.synchronize()
+    _, push_ms, _ = _time_engine(eng, dt, args.steps, args.warmup, k, torch)
+    for _ in range(args.warmup):
+        eng.run(dt, max(k, 1), k)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = eng.launches()
+    ev0.record(stream)
+    eng.run(dt, args.steps, k)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = eng.launches() - l0
+    flags = eng.status()
+    eng.close()
+    del eng
+    torch.cuda.empty_cache()
+    push_avg_s = push_ms / args.steps / 1e3
+    bytes_push = npart * 2 * PARTICLE_BYTES[(ndim, "mixed")] + ncell * (CELL_FIELD_BYTES["mixed"] + CELL_DEPOSIT_BYTES)
+    achieved = bytes_push / push_avg_s / 1e9
+    out = {"workload": _workload_desc(argparse.Namespace(workload=name, n=128, ppc=32, n2d=1024)),
+           "boxes": len(boxes), "particles": npart, "cells": ncell, "dt": dt, "sort_every": k,
+           "value": float(npart) * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+           "steps": args.steps, "gpu_launches_per_step": launches / args.steps,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "kernel": "k_push_mixed<%d,full>" % ndim, "peak_kind": peak_kind,
+                        "bytes_per_launch": bytes_push, "avg_launch_ms": push_avg_s * 1e3},
+           "status_flags": m.status_names(flags)}
+    if args.err_n > 0:
+        err = _error_vs_oracle(argparse.Namespace(workload=name, err_n=args.err_n, sample_n=args.sample_n,
+                                                  ppc=args.ppc), 0, torch)
+        worst = {}
+        for prec in ("mixed", "fp64"):
+            e = err[prec]
+            worst[prec] = {kk: e[kk] for kk in e if kk != "per_box"}
+        out["error_vs_oracle"] = dict(worst, sample=err["sample"])
+    return out
+
+
 def run_native(args):
     import torch
     from paper_1412_1087_gb300 import build as libbuild
@@ -471,6 +528,24 @@ def run_native(args):
     m.load()
     dev = "cuda:%d" % lrank
     boxes, dt = _workload(args, seed=rank)
+    # the other full-size workloads the default run also measures, built on a
+    # host thread while the GPU times the headline box (numpy releases the
+    # GIL in its array operations)
+    extra_names = [w for w in (args.extra_workloads.split(",") if args.extra_workloads else [])
+                   if w and w != args.workload]
+    extra_boxes = {}
+
+    def _build_extra():
+        for w in extra_names:
+            try:
+                extra_boxes[w] = _build_boxes(w, seed=rank)
+            except Exception as e:  # reported in the line, never fatal
+                extra_boxes[w] = e
+
+    import threading
+    extra_thread = threading.Thread(target=_build_extra, daemon=True)
+    if extra_names:
+        extra_thread.start()
     npart = sum(int((b.cell >= 0).sum()) for b in boxes)   # particles, not free slots
     ncell = sum(b.ncell for b in boxes)
     ndim = boxes[0].ndim
@@ -488,16 +563,16 @@ def run_native(args):
 
     # sort cadence: given, or picked by the library's tuner (mhdpic_run with
     # sort_every = 0 times one cycle of each candidate cadence on real steps)
+    # totals of gas + CR momentum and energy before any step (no corrector
+    # is pending here, so this feedback call changes nothing)
+    tot0 = eng.apply_feedback(totals=True).sum(axis=0)
+    steps_done = 0
     tuned = args.sort_every == 0
     if tuned:
         eng.run(dt, 20, 0)
         torch.cuda.synchronize()
         args.sort_every = eng.sort_cadence()
-
-    # totals of gas + CR momentum and energy before the measured steps (no
-    # corrector is pending here, so this feedback call changes nothing)
-    tot0 = eng.apply_feedback(totals=True).sum(axis=0)
-    steps_done = 0
+        steps_done += 20
 
     # eager steps, one call each, so that every push kernel is bracketed by
     # events on the library's stream: the push kernel's roofline
@@ -522,6 +597,11 @@ def run_native(args):
         launches = eng.launches() - l0
     clocks = clk.summary()
     steps_done += args.warmup * max(args.sort_every, 1) + args.steps
+    # the drift is taken over at least args.conservation_steps steps in all:
+    # the rest run here, graph-replayed at the same cadence
+    if steps_done < args.conservation_steps:
+        eng.run(dt, args.conservation_steps - steps_done, args.sort_every)
+        steps_done = args.conservation_steps
     tot1 = eng.apply_feedback(totals=True).sum(axis=0)
     # momentum scale: gross gas momentum plus gross CR momentum
     scaleP = 0.0
@@ -775,6 +855,22 @@ def run_native(args):
         if len(res) > 1:
             e2e_all_host = dict(res[1], mode="particles and gas in pinned host memory")
 
+    extra = None
+    if extra_names:
+        extra_thread.join()
+        extra = {}
+        for w in extra_names:
+            b = extra_boxes.get(w)
+            if isinstance(b, Exception) or b is None:
+                extra[w] = {"unavailable": "%s: %s" % (type(b).__name__, b)}
+                continue
+            try:
+                extra[w] = _measure_workload(w, b[0], b[1], args, torch, m, dev, stream, peak, peak_kind)
+            except Exception as e:  # a secondary figure never costs the line
+                extra[w] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
+            extra_boxes.pop(w, None)
+            torch.cuda.empty_cache()
+
     out = None
     if rank == 0:
         # the oracle's host-core figures are taken at one GPU only
@@ -811,7 +907,7 @@ def run_native(args):
             "fp64_gpu": fp64,
             "error_vs_oracle": err,
             "status_flags": m.status_names(flags),
-            "detail": dict(eng_stats, e2e_all_host=e2e_all_host),
+            "detail": dict(eng_stats, e2e_all_host=e2e_all_host, workloads=extra),
         }
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -892,6 +988,10 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--ref-procs", type=int, default=0,
                     help="--impl reference: oracle processes, one box each (0: one per host core)")
     ap.add_argument("--err-n", type=int, default=24, help="side of the error-check box (0: skip)")
+    ap.add_argument("--conservation-steps", type=int, default=1000,
+                    help="steps the gas + CR conservation drift is taken over (at least)")
+    ap.add_argument("--extra-workloads", default="ensemble_2d,bell_2d",
+                    help="other full-size workloads measured in detail.workloads (comma list, '' for none)")
     return ap
 
 
