@@ -470,6 +470,7 @@ def _measure_workload(name, boxes, dt, args, torch, m, dev, stream, peak, peak_k
     ncell = sum(b.ncell for b in boxes)
     ndim = boxes[0].ndim
     eng = m.Engine(boxes, precision=m.MHDPIC_PREC_MIXED, device=dev, stream=stream)
+    eng.set_sort_lookahead(args.sort_lookahead * dt)
     eng.run(dt, 20, 0)
     k = eng.sort_cadence()
     torch.cuda.synchronize()
@@ -555,11 +556,14 @@ def run_native(args):
     layout = None
     if args.tune_layout:
         from paper_1412_1087_gb300 import tune
-        layout = tune.tune_layout(boxes, steps=8, device=dev)
+        layout = tune.tune_layout(boxes, steps=8, device=dev, lookahead=args.sort_lookahead)
         brick = tuple(layout["brick"])
         torch.cuda.synchronize()
     stream = torch.cuda.Stream(device=dev)
     eng = m.Engine(boxes, precision=m.MHDPIC_PREC_MIXED, brick=brick, device=dev, stream=stream)
+    # sorts key the particles by the cell they reach in this much time (half
+    # a step: the cell where the next push gathers and deposits the corrector)
+    eng.set_sort_lookahead(args.sort_lookahead * dt)
 
     # sort cadence: given, or picked by the library's tuner (mhdpic_run with
     # sort_every = 0 times one cycle of each candidate cadence on real steps)
@@ -816,6 +820,7 @@ def run_native(args):
     torch.cuda.empty_cache()
     if args.fp64_steps > 0:
         e64 = m.Engine(boxes, precision=m.MHDPIC_PREC_FP64, device=dev, stream=stream)
+        e64.set_sort_lookahead(args.sort_lookahead * dt)
         t64, _, _ = _time_engine(e64, dt, args.fp64_steps, 1, args.sort_every, torch)
         v64 = npart * args.fp64_steps / (t64 / 1e3)
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": t64 / args.fp64_steps,
@@ -843,6 +848,7 @@ def run_native(args):
         res = []
         for mem, h2d, d2h in runs:
             eh = m.Engine(boxes, precision=m.MHDPIC_PREC_MIXED, memory=mem, brick=brick, device=dev, stream=stream)
+            eh.set_sort_lookahead(args.sort_lookahead * dt)
             te, _, _ = _time_engine(eh, dt, args.e2e_steps, 1, args.sort_every, torch, per_push=False)
             eh.close()
             del eh
@@ -891,6 +897,7 @@ def run_native(args):
             "dtype_detail": "f32 push, int64 fixed-point deposits, f64 gas and totals",
             "data": "synthetic",
             "config": {"workload": _workload_desc(args), "precision": "mixed", "sort_every": args.sort_every, "sort_every_tuned": tuned,
+                       "sort_lookahead_steps": args.sort_lookahead,
                        "brick": list(brick) if any(brick) else "default", "brick_tuned": bool(args.tune_layout),
                        "l2": "inputs larger than L2 (%.2f GB particle state)"
                              % (npart * RECORD_BYTES[(ndim, prec)] / 1e9),
@@ -970,6 +977,8 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--n2d", type=int, default=1024, help="cells per side of the 2-D Bell box")
     ap.add_argument("--sort-every", type=int, default=0,
                     help="sort cadence in steps (0: picked by the library's tuner)")
+    ap.add_argument("--sort-lookahead", type=float, default=0.5,
+                    help="sorts key particles by their cell this many steps ahead (0: the current cell)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--diagnostics", type=int, default=1, help="time the spectrum and Lambda map once")

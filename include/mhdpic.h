@@ -98,6 +98,8 @@ extern "C" {
 #define MHDPIC_ST_SORT_CAP 8u   /* a cell held more particles than the sort's segment limit */
 #define MHDPIC_ST_CELL_RANGE 16u/* a particle's cell index was outside its box */
 #define MHDPIC_ST_INJECT_CAP 32u/* mhdpic_inject ran out of free particle slots */
+#define MHDPIC_ST_BARRIER 64u   /* a grid-wide barrier of the one-launch step waited beyond its limit:
+                                 * that step's results are not valid */
 
 typedef struct mhdpic_ctx mhdpic_ctx;
 
@@ -235,6 +237,25 @@ int mhdpic_interp_push(mhdpic_ctx *ctx, double dt, int32_t nsub);
  * inside a call.  Returns MHDPIC_E_ARG for every < 0.
  */
 int mhdpic_set_subcycle_sort(mhdpic_ctx *ctx, int32_t every);
+
+/*
+ * mhdpic_set_sort_lookahead - from the next sort on (mhdpic_sort, the sorts of
+ * mhdpic_run and of sub-cycles), key each particle by the cell it reaches
+ * after moving for time t at its current velocity, instead of its current
+ * cell: with t = dt/2 the cell of the half-step position where the next push
+ * gathers E, B and deposits the corrector (App. A.2-A.3), so that the push
+ * finds its particles in the cells it works on.  Per dimension the cell moves
+ * by floor(o_d + (t/dx_d) v_d/gamma) with gamma = sqrt(1 + v^2/C^2), o_d the
+ * offset in the cell (FP64 precision: (x_d - x0_d)/dx_d minus its cell, as
+ * float), v the FP32 four-velocity (the FP64 one rounded to float), every
+ * operation a correctly rounded FP32 one in this order (t/dx_d is rounded
+ * from double); the cell wraps on periodic faces and is clamped into the box
+ * otherwise.  Only the order of the particles and the speed depend on t: the
+ * deposits, the gas and the particle states are the same bit for bit.
+ * 0 (the default) sorts by the current cell.  The paper has no sort.
+ * Errors: MHDPIC_E_STATE, MHDPIC_E_ARG for a non-finite t.
+ */
+int mhdpic_set_sort_lookahead(mhdpic_ctx *ctx, double t);
 
 /*
  * mhdpic_sync_particles - make the caller's particle buffers hold the current

@@ -38,6 +38,7 @@
 //  * 2-D: each thread copies its next two particles' records into a
 //    three-stage shared-memory ring with 16-byte cp.async while it pushes
 //    the current one.
+#include "cells_common.cuh"
 #include "push_common.cuh"
 
 namespace mhdpic {
@@ -573,13 +574,14 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
     return vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2];
 }
 
+// The push over the work items of the last sort, taken from an atomic
+// counter by the calling kernel's persistent blocks (smem: the dynamic shared
+// memory, push_smem_bytes_mixed bytes).
 template <int D, bool FULL>
-__global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_push_mixed(Ctx c, const WorkItem *__restrict__ items,
-                                                                 const int32_t *__restrict__ nitems,
-                                                                 int32_t *__restrict__ work_ctr, int cur_out,
-                                                                 float dt)
+__device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restrict__ items, const int nit,
+                                           int32_t *__restrict__ work_ctr, int cur_out, float dt,
+                                           unsigned char *smem)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
     const int S = c.tile_slots;
     int *sD = reinterpret_cast<int *>(smem);
     float4 *sFa = reinterpret_cast<float4 *>(smem + sizeof(int) * NPLANE * S);
@@ -589,7 +591,6 @@ __global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_push_mixed(Ctx 
     __shared__ int s_item;
     __shared__ MixedConst s_k;
     unsigned long long *mout = c.momdep[cur_out];
-    const int nit = *nitems;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int NW = PUSH_THREADS / 32;
 
@@ -704,6 +705,87 @@ __global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_push_mixed(Ctx 
         }
         __syncthreads();
     }
+}
+
+template <int D, bool FULL>
+__global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_push_mixed(Ctx c, const WorkItem *__restrict__ items,
+                                                                 const int32_t *__restrict__ nitems,
+                                                                 int32_t *__restrict__ work_ctr, int cur_out,
+                                                                 float dt)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    push_items<D, FULL>(c, items, *nitems, work_ctr, cur_out, dt, smem);
+}
+
+// ---------------------------------------------------------------------------
+// The whole step in one launch (mhdpic_run's steps): the corrector scales of
+// every box, the push with both deposits, then the feedback to the gas and
+// the field staging for the next step (what mhdpic_interp_push(dt, 1) and
+// mhdpic_apply_feedback launch as three kernels), separated by grid-wide
+// barriers.  The blocks are co-resident (cooperative launch); a barrier that
+// waits longer than its limit raises MHDPIC_ST_BARRIER and the kernel returns
+// (the step's results are then not valid), so it never hangs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long global_ns()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Sense-counting grid barrier: the last block to arrive resets the count and
+// advances the generation the others wait on.  The fences make every block's
+// writes before the barrier visible to every block after it.
+__device__ __forceinline__ bool grid_sync(GridBarrier *bar, unsigned nblocks, long long limit_ns, uint32_t *status)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *gen = &bar->gen;
+        const unsigned g0 = *gen;   // read before arriving
+        __threadfence();
+        if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const long long t0 = global_ns();
+            while (*gen == g0) {
+                if (global_ns() - t0 > limit_ns) {
+                    set_status(status, MHDPIC_ST_BARRIER);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int D>
+__global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_step_mixed(Ctx c, const WorkItem *__restrict__ items,
+                                                                 const int32_t *__restrict__ nitems,
+                                                                 int32_t *__restrict__ work_ctr, int cur, float dtf,
+                                                                 double dt, GridBarrier *bar, long long limit_ns)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (blockIdx.x == 0) {   // the corrector scales, and the push's work counter
+        for (int bx = threadIdx.x; bx < c.nbox; bx += blockDim.x)
+            scales_box(c, bx, dt);
+        if (threadIdx.x == 0)
+            *work_ctr = 0;
+    }
+    if (!grid_sync(bar, gridDim.x, limit_ns, c.status))
+        return;
+    push_items<D, true>(c, items, *nitems, work_ctr, cur ^ 1, dtf, smem);
+    if (!grid_sync(bar, gridDim.x, limit_ns, c.status))
+        return;
+    prep_cells<MHDPIC_PREC_MIXED>(c, cur ^ 1, 1);
 }
 
 // Standalone charge/current deposit (eq:nJCR) at the particles' positions,
@@ -840,6 +922,45 @@ int launch_deposit_mixed(const Ctx &c, const SortScratch &s, int32_t *work_ctr, 
         k_deposit_mixed<2><<<grid_blocks, PUSH_THREADS, bytes, st>>>(c, s.items, s.nitems, work_ctr, cur);
     }
     return 1;
+}
+
+int step_blocks_per_sm_mixed(const Ctx &c)
+{
+    const size_t bytes = push_smem_bytes_mixed(c);
+    int nb = 0;
+    if (c.ndim == 3) {
+        cudaFuncSetAttribute(k_step_mixed<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, PUSH_SMEM_LIMIT);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_mixed<3>, PUSH_THREADS, bytes);
+    } else {
+        cudaFuncSetAttribute(k_step_mixed<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, PUSH_SMEM_LIMIT);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_mixed<2>, PUSH_THREADS, bytes);
+    }
+    return nb;
+}
+
+int launch_step_mixed(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur, double dt, int grid_blocks,
+                      GridBarrier *bar, long long limit_ns, cudaStream_t st)
+{
+    const size_t bytes = push_smem_bytes_mixed(c);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid_blocks);
+    cfg.blockDim = dim3(PUSH_THREADS);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const float dtf = (float)dt;
+    cudaError_t e;
+    if (c.ndim == 3)
+        e = cudaLaunchKernelEx(&cfg, k_step_mixed<3>, c, (const WorkItem *)s.items, (const int32_t *)s.nitems,
+                               work_ctr, cur, dtf, dt, bar, limit_ns);
+    else
+        e = cudaLaunchKernelEx(&cfg, k_step_mixed<2>, c, (const WorkItem *)s.items, (const int32_t *)s.nitems,
+                               work_ctr, cur, dtf, dt, bar, limit_ns);
+    return e == cudaSuccess ? 1 : -1;
 }
 
 int launch_push_mixed(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur_out, int full, double dt,

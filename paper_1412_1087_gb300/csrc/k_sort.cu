@@ -47,23 +47,58 @@ __device__ __forceinline__ int64_t brick_key(const BoxDev &b, const Ctx &c, int 
     return b.key0 + bid * ((int64_t)c.brick[0] * c.brick[1] * c.brick[2]) + in;
 }
 
+// Whole cells a particle moves along each of the first D dimensions in time
+// t at its current four-velocity v (the sort's look-ahead), from its offsets
+// o in the cell: floor(o_d + (t/dx_d) v_d / gamma), gamma = sqrt(1 + v^2/C^2),
+// in correctly rounded FP32 operations in this order (no contraction), so the
+// key can be recomputed exactly elsewhere.  FP32, not FP64: the GB300's FP64
+// units would make the key pass ten times slower.
+__device__ __forceinline__ void ahead_cells(const BoxDev &b, double t, const float v[3], const float o[3], int D,
+                                            int k[3])
+{
+    const float C = (float)b.C;
+    const float invC2 = __fdiv_rn(1.f, __fmul_rn(C, C));
+    const float v2 = __fadd_rn(__fadd_rn(__fmul_rn(v[0], v[0]), __fmul_rn(v[1], v[1])), __fmul_rn(v[2], v[2]));
+    const float g = __fsqrt_rn(__fadd_rn(1.f, __fmul_rn(v2, invC2)));
+    for (int d = 0; d < D; ++d) {
+        const float ta = (float)(t * b.inv_dx[d]);
+        k[d] = (int)floorf(__fadd_rn(o[d], __fdiv_rn(__fmul_rn(ta, v[d]), g)));
+    }
+}
+
 // Sort key of particle i of box b: brick-major cell order, nkeys for a
-// particle that has left the box.
+// particle that has left the box.  With a look-ahead (c.sort_ahead != 0) the
+// cell is the one the particle reaches in that time at its current velocity
+// (periodic wrap, else clamped into the box): with half a step, the cell of
+// the position where the next push gathers the fields and deposits the
+// corrector.
 template <int PREC>
 __device__ __forceinline__ int32_t key_in_box(const Ctx &c, const BoxDev &b, int64_t i)
 {
     int ci[3] = {0, 0, 0};
     bool dead = false;
+    const bool ahead = c.sort_ahead != 0.0;
     if (PREC == MHDPIC_PREC_MIXED) {
-        int32_t cl = __ldg(&c.pos[i].x);
+        const int4 ps = __ldg(&c.pos[i]);
+        int32_t cl = ps.x;
         dead = cl == DEAD_CELL;
         if (!dead && (cl < 0 || cl >= b.ncell)) {
             set_status(c.status, MHDPIC_ST_CELL_RANGE);
             cl = cl < 0 ? 0 : (int32_t)(b.ncell - 1);
         }
         decode_cell(b, cl, ci);
+        if (ahead && !dead) {
+            const float4 vs = __ldg(&c.vel[i]);
+            const float v[3] = {vs.x, vs.y, vs.z};
+            const float o[3] = {__int_as_float(ps.y), __int_as_float(ps.z), __int_as_float(ps.w)};
+            int k[3] = {0, 0, 0};
+            ahead_cells(b, c.sort_ahead, v, o, c.ndim, k);
+            for (int d = 0; d < c.ndim; ++d)
+                ci[d] += k[d];
+        }
     } else {
         dead = isnan(c.x[i]);
+        float o[3] = {0.f, 0.f, 0.f};
         for (int d = 0; d < c.ndim && !dead; ++d) {
             double s = (c.x[(int64_t)d * c.np + i] - b.x0[d]) / b.dx[d];
             double f = floor(s);
@@ -71,8 +106,20 @@ __device__ __forceinline__ int32_t key_in_box(const Ctx &c, const BoxDev &b, int
             if (!(f >= 0.0 && f < (double)b.n[d]))
                 set_status(c.status, MHDPIC_ST_CELL_RANGE);
             ci[d] = v;
+            o[d] = (float)(s - (double)v);
+        }
+        if (ahead && !dead) {
+            const float v[3] = {(float)c.p64[i], (float)c.p64[c.np + i], (float)c.p64[2 * c.np + i]};
+            int k[3] = {0, 0, 0};
+            ahead_cells(b, c.sort_ahead, v, o, c.ndim, k);
+            for (int d = 0; d < c.ndim; ++d)
+                ci[d] += k[d];
         }
     }
+    if (ahead)
+        for (int d = 0; d < c.ndim; ++d)
+            ci[d] = b.bc[d] == MHDPIC_BC_PERIODIC ? map_coord(ci[d], b.n[d], MHDPIC_BC_PERIODIC)
+                                                  : (ci[d] < 0 ? 0 : (ci[d] >= b.n[d] ? b.n[d] - 1 : ci[d]));
     for (int d = 0; d < 3; ++d)   // defensive: a key outside the box would index out of range
         ci[d] = ci[d] < 0 ? 0 : (ci[d] >= b.n[d] ? b.n[d] - 1 : ci[d]);
     // particles that left the box share one key after all the others

@@ -1054,6 +1054,16 @@ int mhdpic_lambda_map(mhdpic_ctx *c, double *out)
     return check_launch(c, launch_lambda(c->k, c->cur, out, c->stream));
 }
 
+int mhdpic_set_sort_lookahead(mhdpic_ctx *c, double t)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    if (!std::isfinite(t))
+        return fail(MHDPIC_E_ARG, "the look-ahead time must be finite");
+    c->k.sort_ahead = t;
+    return MHDPIC_OK;
+}
+
 int mhdpic_set_subcycle_sort(mhdpic_ctx *c, int32_t every)
 {
     if (!c || !c->valid)

@@ -114,6 +114,7 @@ struct Ctx {
     int32_t ts[3];         // tile strides in slots (x, y, z); padded to spread banks
     int32_t tile_slots;    // slots of the tile (>= tile_vol)
     int32_t halves;        // 1: default 64-cell bricks split into 32-cell halves
+    double sort_ahead;     // sort key: the cell after moving for this time at the current velocity
     int64_t np, nc, nkeys, nbricks_total;
     const BoxDev *boxes;   // device
     const int64_t *box_part_start; // device [nbox+1]
@@ -210,6 +211,18 @@ int launch_push_f64(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int c
 int launch_deposit_mixed(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur, int grid_blocks,
                          cudaStream_t st);
 int launch_scales(const Ctx &c, double dt, cudaStream_t st);
+// The grid-wide barrier of the fused step kernel (zeroed at init and by
+// mhdpic_clear_status).
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+// One whole mixed-precision step in one cooperative launch: scales, push
+// (moments into momdep[cur ^ 1]), feedback and staging from them; -1 when
+// the launch is refused
+int launch_step_mixed(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur, double dt, int grid_blocks,
+                      GridBarrier *bar, long long limit_ns, cudaStream_t st);
+int step_blocks_per_sm_mixed(const Ctx &c);
 // chunked reductions: a box takes ceil((particles + cells) / per_chunk)
 // slices, at least one and at most nchunks
 int launch_totals(const Ctx &c, double *partials, int nchunks, int64_t per_chunk, double *out, cudaStream_t st);

@@ -92,6 +92,7 @@ SIGNATURES = {
     "mhdpic_run": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_int32, ctypes.c_int32]),
     "mhdpic_sync_particles": (ctypes.c_int, [_V]),
     "mhdpic_set_subcycle_sort": (ctypes.c_int, [_V, ctypes.c_int32]),
+    "mhdpic_set_sort_lookahead": (ctypes.c_int, [_V, ctypes.c_double]),
     "mhdpic_spectrum": (ctypes.c_int, [_V, ctypes.c_int32, ctypes.c_int32, _V, _V, ctypes.c_int32, _V, _V]),
     "mhdpic_lambda_map": (ctypes.c_int, [_V, _V]),
     "mhdpic_sort_cadence": (ctypes.c_int32, [_V]),
@@ -217,6 +218,10 @@ def mhdpic_run(ctx, dt: float, nsteps: int, sort_every: int = 0) -> None:
 
 def mhdpic_set_subcycle_sort(ctx, every: int) -> None:
     _check(load().mhdpic_set_subcycle_sort(ctx, int(every)))
+
+
+def mhdpic_set_sort_lookahead(ctx, t: float) -> None:
+    _check(load().mhdpic_set_sort_lookahead(ctx, float(t)))
 
 
 def mhdpic_sync_particles(ctx) -> None:
@@ -535,6 +540,10 @@ class Engine:
 
     def set_subcycle_sort(self, every: int) -> None:
         mhdpic_set_subcycle_sort(self.ctx, every)
+
+    def set_sort_lookahead(self, t: float) -> None:
+        """Sort by the cell each particle reaches in time t (dt/2: the half-step cell)."""
+        mhdpic_set_sort_lookahead(self.ctx, t)
 
     def spectrum(self, kind: int, edges, region=None, n_moment: int = 6):
         """Per-box counts (nbox, nbins) and sums (nbox, 2) of q^(n+1), q^n."""

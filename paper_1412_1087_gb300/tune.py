@@ -23,8 +23,9 @@ CANDIDATES = {
 
 
 def tune_layout(boxes: Sequence, precision: int = m.MHDPIC_PREC_MIXED, candidates: Optional[List] = None,
-                steps: int = 8, device: str = "cuda:0") -> Dict:
-    """Time each candidate brick on copies of ``boxes``; returns
+                steps: int = 8, device: str = "cuda:0", lookahead: float = 0.0) -> Dict:
+    """Time each candidate brick on copies of ``boxes``, sorting with a
+    look-ahead of ``lookahead`` steps (mhdpic_set_sort_lookahead); returns
     {"brick", "sort_every", "ms_per_step", "table": [...]} for the fastest."""
     import torch
 
@@ -42,6 +43,7 @@ def tune_layout(boxes: Sequence, precision: int = m.MHDPIC_PREC_MIXED, candidate
             table.append({"brick": list(brick), "error": str(e)})
             continue
         try:
+            eng.set_sort_lookahead(lookahead * dt)
             eng.run(dt, 3 * 4, 0)                  # the library tunes the sort cadence
             k = eng.sort_cadence()
             cycles = max(1, steps // k)
