@@ -601,6 +601,23 @@ def run_native(args):
         launches = eng.launches() - l0
     clocks = clk.summary()
     steps_done += args.warmup * max(args.sort_every, 1) + args.steps
+    # the same graph-replayed steps with the step split into its separate
+    # launches (scales, push, feedback + staging) against the one-launch
+    # step the timed region used, on this machine in this run
+    fusion = {"one_launch_steps": bool(eng.step_fusion())}
+    if fusion["one_launch_steps"] and args.fusion_ab:
+        ab = {}
+        for fuse in (False, True):
+            eng.set_step_fusion(fuse)
+            eng.run(dt, max(args.sort_every, 1) * 2, args.sort_every)   # capture and warm up
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            eng.run(dt, args.steps, args.sort_every)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ab["one_launch" if fuse else "separate_launches"] = ev0.elapsed_time(ev1) / args.steps
+            steps_done += max(args.sort_every, 1) * 2 + args.steps
+        fusion["ms_per_step"] = ab
     # the drift is taken over at least args.conservation_steps steps in all:
     # the rest run here, graph-replayed at the same cadence
     if steps_done < args.conservation_steps:
@@ -809,7 +826,7 @@ def run_native(args):
                  "eager_ms_per_step": eager_ms / args.steps,
                  "subcycled": subcycled, "diagnostics": diagnostics, "coupled": coupled,
                  "injection": injection, "layout_tuning": layout, "conservation": conservation,
-                 "standalone_deposit": standalone,
+                 "standalone_deposit": standalone, "step_fusion": fusion,
                  "particles": npart, "cells": ncell,
                  "dt": dt}
 
@@ -997,6 +1014,8 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--ref-procs", type=int, default=0,
                     help="--impl reference: oracle processes, one box each (0: one per host core)")
     ap.add_argument("--err-n", type=int, default=24, help="side of the error-check box (0: skip)")
+    ap.add_argument("--fusion-ab", type=int, default=1,
+                    help="also time the step as separate launches against the one-launch step (0: off)")
     ap.add_argument("--conservation-steps", type=int, default=1000,
                     help="steps the gas + CR conservation drift is taken over (at least)")
     ap.add_argument("--extra-workloads", default="ensemble_2d,bell_2d",

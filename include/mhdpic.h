@@ -480,9 +480,41 @@ int mhdpic_gas_correct(mhdpic_ctx *ctx, double dt, int32_t model, double *totals
  * fastest (mhdpic_sort_cadence).
  * Whole cycles are captured once into a CUDA graph and replayed (re-captured
  * when dt or the cadence changes); with the legacy default stream or host
- * buffers the steps run eagerly.  Asynchronous except while tuning.
+ * buffers the steps run eagerly.  Each step is one kernel launch where
+ * mhdpic_set_step_fusion allows it.  Asynchronous except while tuning.
  */
 int mhdpic_run(mhdpic_ctx *ctx, double dt, int32_t nsteps, int32_t sort_every);
+
+/*
+ * mhdpic_set_step_fusion - with enable != 0 (the default) each step of
+ * mhdpic_run is one kernel launch where it can be: the corrector scales, the
+ * push with both deposits, and the feedback with the field staging for the
+ * next step run in one persistent cooperative kernel, its phases separated by
+ * grid-wide barriers (the paper's particle step of App. A.2-A.3 followed by
+ * the corrector's feedback, eq:scheme); a step with a sort adds the sort's
+ * launches.  It applies to mixed precision with device buffers and no open
+ * face or injection times (mhdpic_step_fusion tells whether it does); the
+ * results are the same bit for bit as those of mhdpic_interp_push(dt, 1)
+ * followed by mhdpic_apply_feedback(NULL).  Each barrier waits at most one
+ * second by default; a wait that runs out raises MHDPIC_ST_BARRIER (the step's
+ * results are then not valid) instead of hanging.  A captured cycle is
+ * discarded.  The paper has no counterpart.  Errors: MHDPIC_E_STATE.
+ */
+int mhdpic_set_step_fusion(mhdpic_ctx *ctx, int32_t enable);
+
+/* 1 when mhdpic_run's steps of this context are one-launch steps, 0 when not,
+ * -1 for an invalid context. */
+int32_t mhdpic_step_fusion(const mhdpic_ctx *ctx);
+
+/*
+ * mhdpic_debug_set_barrier_limit - testing interface: the wait limit of the
+ * one-launch step's grid barriers, in nanoseconds (<= 0 restores the default
+ * of one second).  A short limit makes the barrier give up with
+ * MHDPIC_ST_BARRIER where blocks arrive at different times (no kernel is made
+ * to stall; mhdpic_clear_status resets the barrier).  A captured cycle is
+ * discarded.  The paper has no counterpart.  Errors: MHDPIC_E_STATE.
+ */
+int mhdpic_debug_set_barrier_limit(mhdpic_ctx *ctx, int64_t ns);
 
 /* Sort cadence chosen by mhdpic_run's tuner (0 before tuning, -1: bad ctx). */
 int32_t mhdpic_sort_cadence(const mhdpic_ctx *ctx);

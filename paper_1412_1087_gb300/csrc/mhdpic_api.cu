@@ -71,6 +71,12 @@ struct mhdpic_ctx {
     double *spec_edges = nullptr;                // [MHDPIC_SPEC_MAX_BINS + 1]
     int64_t launches = 0;
     int64_t fail_countdown = 0;   // mhdpic_debug_fail_launch: launch checks left before a reported failure
+    // one-launch steps of mhdpic_run (mixed precision): the grid barrier, its
+    // wait limit, the co-resident grid, and whether they are used
+    GridBarrier *bar = nullptr;
+    long long bar_limit_ns = 1000000000ll;
+    int step_grid = 0;
+    bool fuse = true;
     std::vector<BoxDev> boxes;
     std::vector<int64_t> part_start, cell_start, brick_start;
     std::vector<void *> allocs;
@@ -665,6 +671,15 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     c->grid_blocks = bps * (nsm > 0 ? nsm : 1);
+    if (k.prec == MHDPIC_PREC_MIXED) {
+        int coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        c->step_grid = coop ? step_blocks_per_sm_mixed(k) * (nsm > 0 ? nsm : 1) : 0;
+        if ((rc = c->alloc(&c->bar, 1)))
+            return bail(rc);
+        if (cudaMemsetAsync(c->bar, 0, sizeof(GridBarrier), st))
+            return bail(cuda_fail(cudaGetLastError(), "init barrier"));
+    }
 
     // moments at the initial positions, maxima, staged fields
     c->cur = 0;
@@ -1116,12 +1131,62 @@ int mhdpic_get_fields(mhdpic_ctx *c, double *out)
 
 namespace {
 
+// The one-launch step applies where the step is exactly a push and a
+// feedback on device buffers: mixed precision, no open face (whose push is
+// followed by the marking of free slots), no injection times (their clock
+// and permutation are extra launches).
+bool fused_ok(const mhdpic_ctx *c)
+{
+    return c->fuse && c->step_grid > 0 && c->k.prec == MHDPIC_PREC_MIXED && c->mem == MHDPIC_MEM_DEVICE &&
+           !c->has_open && !c->track_tinj && c->k.np > 0;
+}
+
+// mhdpic_interp_push(dt, 1) + mhdpic_apply_feedback(NULL) as one cooperative
+// launch of k_step_mixed, with the same host bookkeeping.
+int fused_step(mhdpic_ctx *c, double dt)
+{
+    int rc;
+    if ((rc = restage_if_stale(c)))
+        return rc;
+    if (!c->next_clear)   // two pushes with no staging in between
+        CK(cudaMemsetAsync(c->k.momdep[c->cur ^ 1], 0, sizeof(unsigned long long) * 4 * c->k.nc, c->stream));
+    Ctx kk = c->k;
+    const bool gather = c->pending;
+    if (gather) {   // read through the permutation, write the other set
+        const PSet &src = c->sets[c->cur_set], &dst = c->sets[c->cur_set ^ 1];
+        kk.pos = dst.pos;
+        kk.vel = dst.vel;
+        kk.perm_src = c->s.perm;
+        kk.src_pos = src.pos;
+        kk.src_vel = src.vel;
+    }
+    const int n = launch_step_mixed(kk, c->s, c->work_ctr, c->cur, dt, c->step_grid, c->bar, c->bar_limit_ns,
+                                    c->stream);
+    if (n < 0)
+        return fail(MHDPIC_E_CUDA, "cooperative launch of the one-launch step: %s",
+                    cudaGetErrorString(cudaGetLastError()));
+    if ((rc = check_launch(c, n)))
+        return rc;
+    if (gather) {
+        use_set(c, c->cur_set ^ 1);
+        c->pending = false;
+    }
+    c->cur ^= 1;
+    c->next_clear = true;
+    c->fields_stale = false;
+    return MHDPIC_OK;
+}
+
 // One full step of mhdpic_run: push, feedback, and the sort at the end of a cycle.
 int run_one_step(mhdpic_ctx *c, double dt, int k)
 {
     int rc;
-    if ((rc = mhdpic_interp_push(c, dt, 1)) || (rc = mhdpic_apply_feedback(c, nullptr)))
+    if (fused_ok(c)) {
+        if ((rc = fused_step(c, dt)))
+            return rc;
+    } else if ((rc = mhdpic_interp_push(c, dt, 1)) || (rc = mhdpic_apply_feedback(c, nullptr))) {
         return rc;
+    }
     if (++c->step_in_cycle >= k) {
         c->step_in_cycle = 0;
         if ((rc = mhdpic_sort(c, nullptr, nullptr)))
@@ -1319,11 +1384,42 @@ int mhdpic_debug_fail_launch(mhdpic_ctx *c, int64_t n)
     return MHDPIC_OK;
 }
 
+int mhdpic_set_step_fusion(mhdpic_ctx *c, int32_t enable)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    c->fuse = enable != 0;
+    if (c->graph) {   // a captured cycle holds the other form of the step
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return MHDPIC_OK;
+}
+
+int32_t mhdpic_step_fusion(const mhdpic_ctx *c)
+{
+    return c && c->valid ? (fused_ok(c) ? 1 : 0) : -1;
+}
+
+int mhdpic_debug_set_barrier_limit(mhdpic_ctx *c, int64_t ns)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    c->bar_limit_ns = ns > 0 ? (long long)ns : 1000000000ll;
+    if (c->graph) {   // the limit is a launch argument of the captured cycle
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return MHDPIC_OK;
+}
+
 int mhdpic_clear_status(mhdpic_ctx *c)
 {
     if (!c || !c->valid)
         return fail(MHDPIC_E_STATE, "invalid context");
     CK(cudaMemsetAsync(c->k.status, 0, sizeof(uint32_t), c->stream));
+    if (c->bar)   // a barrier that timed out may have been left half counted
+        CK(cudaMemsetAsync(c->bar, 0, sizeof(GridBarrier), c->stream));
     return MHDPIC_OK;
 }
 

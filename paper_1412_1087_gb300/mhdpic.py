@@ -37,7 +37,8 @@ MHDPIC_SPEC_MOMENTUM = 1
 MHDPIC_SPEC_MAX_BINS = 2048
 MHDPIC_GAS_SOURCES = 0
 MHDPIC_GAS_LINEAR_X = 1
-STATUS_NAMES = {1: "FAST_MOVER", 2: "NONFINITE", 4: "OVERFLOW", 8: "SORT_CAP", 16: "CELL_RANGE", 32: "INJECT_CAP"}
+STATUS_NAMES = {1: "FAST_MOVER", 2: "NONFINITE", 4: "OVERFLOW", 8: "SORT_CAP", 16: "CELL_RANGE", 32: "INJECT_CAP",
+                64: "BARRIER"}
 
 
 class MhdpicError(RuntimeError):
@@ -96,6 +97,9 @@ SIGNATURES = {
     "mhdpic_spectrum": (ctypes.c_int, [_V, ctypes.c_int32, ctypes.c_int32, _V, _V, ctypes.c_int32, _V, _V]),
     "mhdpic_lambda_map": (ctypes.c_int, [_V, _V]),
     "mhdpic_sort_cadence": (ctypes.c_int32, [_V]),
+    "mhdpic_set_step_fusion": (ctypes.c_int, [_V, ctypes.c_int32]),
+    "mhdpic_step_fusion": (ctypes.c_int32, [_V]),
+    "mhdpic_debug_set_barrier_limit": (ctypes.c_int, [_V, ctypes.c_int64]),
     "mhdpic_get_deposits": (ctypes.c_int, [_V, ctypes.c_int32, _V]),
     "mhdpic_get_fields": (ctypes.c_int, [_V, _V]),
     "mhdpic_get_velocities": (ctypes.c_int, [_V, _V]),
@@ -246,6 +250,18 @@ def mhdpic_lambda_map(ctx, out_ptr: int) -> None:
 
 def mhdpic_sort_cadence(ctx) -> int:
     return int(load().mhdpic_sort_cadence(ctx))
+
+
+def mhdpic_set_step_fusion(ctx, enable: bool) -> None:
+    _check(load().mhdpic_set_step_fusion(ctx, 1 if enable else 0))
+
+
+def mhdpic_step_fusion(ctx) -> int:
+    return int(load().mhdpic_step_fusion(ctx))
+
+
+def mhdpic_debug_set_barrier_limit(ctx, ns: int) -> None:
+    _check(load().mhdpic_debug_set_barrier_limit(ctx, int(ns)))
 
 
 def mhdpic_get_deposits(ctx, which: int, out_ptr: int) -> None:
@@ -531,6 +547,13 @@ class Engine:
 
     def sort_cadence(self) -> int:
         return mhdpic_sort_cadence(self.ctx)
+
+    def set_step_fusion(self, enable: bool) -> None:
+        """One kernel launch per step of run() where the context allows it (default on)."""
+        mhdpic_set_step_fusion(self.ctx, enable)
+
+    def step_fusion(self) -> int:
+        return mhdpic_step_fusion(self.ctx)
 
     # -- read-back ----------------------------------------------------------
     def deposits(self, which: int):

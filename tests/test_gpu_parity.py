@@ -530,7 +530,7 @@ def test_graph_replayed_run_equals_eager_steps(k):
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("fail_at", [1, 3, 7])
+@pytest.mark.parametrize("fail_at", [1, 2, 5])
 def test_failed_graph_capture_leaves_the_context_as_it_was(fail_at):
     """A launch failure injected on the host inside the graph capture of
     mhdpic_run (nothing captured runs): the call reports the error, the
@@ -545,7 +545,7 @@ def test_failed_graph_capture_leaves_the_context_as_it_was(fail_at):
         if mode == "failed":
             m.mhdpic_debug_fail_launch(eng.ctx, fail_at)
             with pytest.raises(m.MhdpicError, match="failure injected"):
-                eng.run(box.dt, 2, 1)   # the capture of a two-step cycle fails
+                eng.run(box.dt, 2, 1)   # the capture of a two-step cycle (at least 6 launches) fails
             m.mhdpic_debug_fail_launch(eng.ctx, 0)
         for s in range(3):
             eng.step(box.dt)
