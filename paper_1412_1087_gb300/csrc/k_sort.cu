@@ -49,21 +49,20 @@ __device__ __forceinline__ int64_t brick_key(const BoxDev &b, const Ctx &c, int 
 
 // Whole cells a particle moves along each of the first D dimensions in time
 // t at its current four-velocity v (the sort's look-ahead), from its offsets
-// o in the cell: floor(o_d + (t/dx_d) v_d / gamma), gamma = sqrt(1 + v^2/C^2),
-// in correctly rounded FP32 operations in this order (no contraction), so the
-// key can be recomputed exactly elsewhere.  FP32, not FP64: the GB300's FP64
-// units would make the key pass ten times slower.
-__device__ __forceinline__ void ahead_cells(const BoxDev &b, double t, const float v[3], const float o[3], int D,
-                                            int k[3])
+// o in the cell: with the box's FP32 constants k = {t/dx, t/dy, t/dz, 1/C^2}
+// (each rounded once from the exact value, on the host),
+//   g = sqrt(1 + v^2 k.w), ig = 1/g, cells_d = floor(o_d + (k_d v_d) ig),
+// v^2 = (vx vx + vy vy) + vz vz, every operation a correctly rounded FP32 one
+// in this order (no contraction), so the key can be recomputed exactly
+// elsewhere.  FP32, not FP64: the GB300's FP64 units would make the key pass
+// several times slower.
+__device__ __forceinline__ void ahead_cells(const float4 k, const float v[3], const float o[3], int D, int cells[3])
 {
-    const float C = (float)b.C;
-    const float invC2 = __fdiv_rn(1.f, __fmul_rn(C, C));
     const float v2 = __fadd_rn(__fadd_rn(__fmul_rn(v[0], v[0]), __fmul_rn(v[1], v[1])), __fmul_rn(v[2], v[2]));
-    const float g = __fsqrt_rn(__fadd_rn(1.f, __fmul_rn(v2, invC2)));
-    for (int d = 0; d < D; ++d) {
-        const float ta = (float)(t * b.inv_dx[d]);
-        k[d] = (int)floorf(__fadd_rn(o[d], __fdiv_rn(__fmul_rn(ta, v[d]), g)));
-    }
+    const float ig = __fdiv_rn(1.f, __fsqrt_rn(__fadd_rn(1.f, __fmul_rn(v2, k.w))));
+    const float ta[3] = {k.x, k.y, k.z};
+    for (int d = 0; d < D; ++d)
+        cells[d] = (int)floorf(__fadd_rn(o[d], __fmul_rn(__fmul_rn(ta[d], v[d]), ig)));
 }
 
 // Sort key of particle i of box b: brick-major cell order, nkeys for a
@@ -73,7 +72,7 @@ __device__ __forceinline__ void ahead_cells(const BoxDev &b, double t, const flo
 // the position where the next push gathers the fields and deposits the
 // corrector.
 template <int PREC>
-__device__ __forceinline__ int32_t key_in_box(const Ctx &c, const BoxDev &b, int64_t i)
+__device__ __forceinline__ int32_t key_in_box(const Ctx &c, const BoxDev &b, int bx, int64_t i)
 {
     int ci[3] = {0, 0, 0};
     bool dead = false;
@@ -92,7 +91,7 @@ __device__ __forceinline__ int32_t key_in_box(const Ctx &c, const BoxDev &b, int
             const float v[3] = {vs.x, vs.y, vs.z};
             const float o[3] = {__int_as_float(ps.y), __int_as_float(ps.z), __int_as_float(ps.w)};
             int k[3] = {0, 0, 0};
-            ahead_cells(b, c.sort_ahead, v, o, c.ndim, k);
+            ahead_cells(__ldg(c.sort_k + bx), v, o, c.ndim, k);
             for (int d = 0; d < c.ndim; ++d)
                 ci[d] += k[d];
         }
@@ -111,7 +110,7 @@ __device__ __forceinline__ int32_t key_in_box(const Ctx &c, const BoxDev &b, int
         if (ahead && !dead) {
             const float v[3] = {(float)c.p64[i], (float)c.p64[c.np + i], (float)c.p64[2 * c.np + i]};
             int k[3] = {0, 0, 0};
-            ahead_cells(b, c.sort_ahead, v, o, c.ndim, k);
+            ahead_cells(__ldg(c.sort_k + bx), v, o, c.ndim, k);
             for (int d = 0; d < c.ndim; ++d)
                 ci[d] += k[d];
         }
@@ -144,8 +143,10 @@ __global__ void k_sort_keys(Ctx c, int32_t *__restrict__ count, int32_t *__restr
 #pragma unroll
         for (int u = 0; u < SORT_ILP; ++u) {
             const int64_t i = i0 + u * stride;
-            key[u] = i < c.np ? key_in_box<PREC>(c, c.boxes[find_box(c.box_part_start, c.nbox, i)], i)
-                              : -1 - lane;
+            int bx = 0;
+            if (i < c.np)
+                bx = find_box(c.box_part_start, c.nbox, i);
+            key[u] = i < c.np ? key_in_box<PREC>(c, c.boxes[bx], bx, i) : -1 - lane;
         }
         // runs of equal keys in consecutive lanes (the input is nearly
         // sorted) take one atomic per run; the rank inside the run is the

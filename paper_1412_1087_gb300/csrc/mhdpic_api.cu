@@ -77,6 +77,9 @@ struct mhdpic_ctx {
     long long bar_limit_ns = 1000000000ll;
     int step_grid = 0;
     bool fuse = true;
+    // look-ahead sort: per box {t/dx, t/dy, t/dz, 1/C^2} in FP32 (device copy in k.sort_k)
+    std::vector<float4> sort_k_host;
+    float4 *sort_k = nullptr;
     std::vector<BoxDev> boxes;
     std::vector<int64_t> part_start, cell_start, brick_start;
     std::vector<void *> allocs;
@@ -583,6 +586,10 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         c->nchunks = (int)std::max<int64_t>(1, std::min<int64_t>(1216, (wmax + c->chunk_work - 1) / c->chunk_work));
         c->spec_chunks = c->nchunks;
     }
+    if ((rc = c->alloc(&c->sort_k, nbox)))
+        return bail(rc);
+    k.sort_k = c->sort_k;
+    c->sort_k_host.assign(nbox, make_float4(0.f, 0.f, 0.f, 0.f));
     if ((rc = c->alloc(&c->partials, (size_t)nbox * c->nchunks * 8)) || (rc = c->alloc(&c->totals_dev, 8 * nbox)) ||
         (rc = c->alloc(&c->spec_counts, (size_t)nbox * MHDPIC_SPEC_MAX_BINS)) ||
         (rc = c->alloc(&c->spec_partials, (size_t)nbox * c->spec_chunks * 2)) ||
@@ -1075,6 +1082,17 @@ int mhdpic_set_sort_lookahead(mhdpic_ctx *c, double t)
         return fail(MHDPIC_E_STATE, "invalid context");
     if (!std::isfinite(t))
         return fail(MHDPIC_E_ARG, "the look-ahead time must be finite");
+    // each constant rounded once to FP32 from its exact double (t/dx) or from
+    // two correctly rounded FP32 operations (1/(C C))
+    for (int b = 0; b < c->nbox; ++b) {
+        const BoxDev &bd = c->boxes[b];
+        const float C = (float)bd.C;
+        const float C2 = C * C;
+        c->sort_k_host[b] = make_float4((float)(t * bd.inv_dx[0]), (float)(t * bd.inv_dx[1]),
+                                        (float)(t * bd.inv_dx[2]), 1.f / C2);
+    }
+    CK(cudaMemcpyAsync(c->sort_k, c->sort_k_host.data(), sizeof(float4) * c->nbox, cudaMemcpyHostToDevice,
+                       c->stream));
     c->k.sort_ahead = t;
     return MHDPIC_OK;
 }

@@ -75,7 +75,8 @@ def test_sort_matches_oracle_bit_exactly(prec, name):
 def _lookahead_cells(box, t, prec, cell=None, off=None, v=None, x=None):
     """The cells the library's look-ahead sort keys particles by, recomputed
     in numpy with the same correctly rounded FP32 operations in the same
-    order: floor(o_d + (t/dx_d) v_d / gamma), gamma = sqrt(1 + v^2/C^2)."""
+    order: floor(o_d + (a_d v_d) ig), ig = 1/sqrt(1 + v^2 w), a_d = t/dx_d
+    rounded to float, w = 1/(C C) in float."""
     n = box.n
     if prec == MIXED:
         c = cell.astype(np.int64)
@@ -95,14 +96,14 @@ def _lookahead_cells(box, t, prec, cell=None, off=None, v=None, x=None):
     C = np.float32(box.C)
     invC2 = np.float32(1) / (C * C)
     v2 = (vf[0] * vf[0] + vf[1] * vf[1]) + vf[2] * vf[2]
-    g = np.sqrt(np.float32(1) + v2 * invC2)
+    ig = np.float32(1) / np.sqrt(np.float32(1) + v2 * invC2)
     out = []
     for d in range(3):
         if d >= box.ndim:
             out.append(ci[d])
             continue
         ta = np.float32(t * (1.0 / box.dx[d]))
-        k = np.floor(o[d] + (ta * vf[d]) / g).astype(np.int64)
+        k = np.floor(o[d] + (ta * vf[d]) * ig).astype(np.int64)
         cd = ci[d] + k
         cd = np.mod(cd, n[d]) if box.bc[d] == 0 else np.clip(cd, 0, n[d] - 1)
         out.append(cd)
