@@ -471,6 +471,7 @@ def _measure_workload(name, boxes, dt, args, torch, m, dev, stream, peak, peak_k
     ndim = boxes[0].ndim
     eng = m.Engine(boxes, precision=m.MHDPIC_PREC_MIXED, device=dev, stream=stream)
     eng.set_sort_lookahead(args.sort_lookahead * dt)
+    eng.set_field_tma(bool(args.field_tma))
     eng.run(dt, 20, 0)
     k = eng.sort_cadence()
     torch.cuda.synchronize()
@@ -564,6 +565,7 @@ def run_native(args):
     # sorts key the particles by the cell they reach in this much time (half
     # a step: the cell where the next push gathers and deposits the corrector)
     eng.set_sort_lookahead(args.sort_lookahead * dt)
+    eng.set_field_tma(bool(args.field_tma))
 
     # sort cadence: given, or picked by the library's tuner (mhdpic_run with
     # sort_every = 0 times one cycle of each candidate cadence on real steps)
@@ -804,6 +806,7 @@ def run_native(args):
                                  "injected": n_tr, "live_before": live0,
                                  "live_after": eng.live_particles()}}
     flags = eng.status()
+    field_tma = bool(eng.field_tma())
 
     # roofline of the push kernel (the dominant kernel)
     peak, peak_kind = _peaks()
@@ -822,7 +825,8 @@ def run_native(args):
     traffic = None
     if args.workload in PUSH_TRAFFIC_BYTES_PER_PARTICLE:
         traffic = PUSH_TRAFFIC_BYTES_PER_PARTICLE[args.workload] * npart
-    eng_stats = {"push_ms_per_step": push_ms / args.steps, "graph_run_ms_per_step": graph_ms,
+    eng_stats = {"field_tma": field_tma,
+                 "push_ms_per_step": push_ms / args.steps, "graph_run_ms_per_step": graph_ms,
                  "eager_ms_per_step": eager_ms / args.steps,
                  "subcycled": subcycled, "diagnostics": diagnostics, "coupled": coupled,
                  "injection": injection, "layout_tuning": layout, "conservation": conservation,
@@ -915,6 +919,7 @@ def run_native(args):
             "data": "synthetic",
             "config": {"workload": _workload_desc(args), "precision": "mixed", "sort_every": args.sort_every, "sort_every_tuned": tuned,
                        "sort_lookahead_steps": args.sort_lookahead,
+                       "field_tiles": "tensor copies" if eng_stats.get("field_tma") else "thread copies",
                        "brick": list(brick) if any(brick) else "default", "brick_tuned": bool(args.tune_layout),
                        "l2": "inputs larger than L2 (%.2f GB particle state)"
                              % (npart * RECORD_BYTES[(ndim, prec)] / 1e9),
@@ -996,6 +1001,8 @@ def build_parser() -> argparse.ArgumentParser:
                     help="sort cadence in steps (0: picked by the library's tuner)")
     ap.add_argument("--sort-lookahead", type=float, default=0.5,
                     help="sorts key particles by their cell this many steps ahead (0: the current cell)")
+    ap.add_argument("--field-tma", type=int, default=1,
+                    help="stage the push's field tiles by tensor copies where possible (0: by the threads)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--diagnostics", type=int, default=1, help="time the spectrum and Lambda map once")

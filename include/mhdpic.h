@@ -100,6 +100,8 @@ extern "C" {
 #define MHDPIC_ST_INJECT_CAP 32u/* mhdpic_inject ran out of free particle slots */
 #define MHDPIC_ST_BARRIER 64u   /* a grid-wide barrier of the one-launch step waited beyond its limit:
                                  * that step's results are not valid */
+#define MHDPIC_ST_COPY_TIMEOUT 128u /* a tensor copy of a push's field tile did not complete within its
+                                     * limit: that push's results are not valid */
 
 typedef struct mhdpic_ctx mhdpic_ctx;
 
@@ -506,6 +508,24 @@ int mhdpic_set_step_fusion(mhdpic_ctx *ctx, int32_t enable);
 /* 1 when mhdpic_run's steps of this context are one-launch steps, 0 when not,
  * -1 for an invalid context. */
 int32_t mhdpic_step_fusion(const mhdpic_ctx *ctx);
+
+/*
+ * mhdpic_set_field_tma - with enable != 0 (the default where possible) a push
+ * stages each work item's field tile, the cell-centred E and B of the tile's
+ * cells (Section 3: the TSC gather reads them), with two tensor copies
+ * (cp.async.bulk.tensor) of the padded staged-field planes, one per plane,
+ * completed on a shared-memory barrier; otherwise its threads copy the tile.
+ * Mixed precision only, and only where the brick's x extent is even (the copy
+ * alignment rule); mhdpic_field_tma tells whether the copies are used.  The
+ * results are the same bit for bit.  A copy that does not complete within one
+ * second raises MHDPIC_ST_COPY_TIMEOUT and ends that push.  A captured cycle
+ * is discarded.  The paper has no counterpart.  Errors: MHDPIC_E_STATE.
+ */
+int mhdpic_set_field_tma(mhdpic_ctx *ctx, int32_t enable);
+
+/* 1 when pushes of this context stage their field tiles by tensor copies, 0
+ * when their threads do, -1 for an invalid context. */
+int32_t mhdpic_field_tma(const mhdpic_ctx *ctx);
 
 /*
  * mhdpic_debug_set_barrier_limit - testing interface: the wait limit of the

@@ -66,10 +66,11 @@ __device__ __forceinline__ void prep_cells(const Ctx &c, int cur, int apply)
             }
         }
         if (PREC == MHDPIC_PREC_MIXED) {
-            float4 a = make_float4((float)E[0], (float)E[1], (float)E[2], (float)Bc[0]);
-            float4 bb = make_float4((float)Bc[1], (float)Bc[2], 0.f, 0.f);
-            reinterpret_cast<float4 *>(c.f32)[2 * g] = a;
-            reinterpret_cast<float4 *>(c.f32)[2 * g + 1] = bb;
+            int ci[3];
+            decode_cell(b, (int32_t)(g - b.cell0), ci);
+            store_fields_mixed(c.fa, c.fb, b, ci[0], ci[1], ci[2],
+                               make_float4((float)E[0], (float)E[1], (float)E[2], (float)Bc[0]),
+                               make_float2((float)Bc[1], (float)Bc[2]));
         } else {
             double2 *f = reinterpret_cast<double2 *>(c.f64) + 3 * g;
             f[0] = make_double2(E[0], E[1]);

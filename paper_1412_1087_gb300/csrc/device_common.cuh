@@ -182,6 +182,58 @@ __device__ __forceinline__ float vsq3(const float v[3])
     return fmaf(v[2], v[2], fmaf(v[1], v[1], __fmul_rn(v[0], v[0])));
 }
 
+// Index in the padded staged-field planes of box coordinates (gx, gy, gz),
+// each in [-FGHOST, n + FGHOST) (z 0 in 2-D).
+__device__ __forceinline__ int64_t fidx(const BoxDev &b, int gx, int gy, int gz)
+{
+    const int gzz = b.ndim == 3 ? gz + FGHOST : 0;
+    return b.fcell0 + ((int64_t)gzz * b.pn[1] + (gy + FGHOST)) * b.pn[0] + (gx + FGHOST);
+}
+
+// Store the staged mixed-precision fields of box-local cell (x, y, z) at its
+// own position and at every ghost that copies it: along each dimension the
+// padded positions u in [-FGHOST, 0) and [n, pn - FGHOST) (up to the brick
+// grid's end plus the halo, so that every push tile is inside the planes)
+// whose stencil cell mapping (map_coord: periodic image, mirror image at a
+// reflecting wall, the last cell beyond an open face) is the cell itself.
+__device__ __forceinline__ bool ghost_of(int u, int x, int n, int bc)
+{
+    return (u < 0 || u >= n) && map_coord(u, n, bc) == x;
+}
+
+// Candidate k of one dimension: the cell itself (k = 0), the lower ghosts
+// -1 .. -FGHOST, then the upper ghosts n .. hi - 1; count 1 + FGHOST + hi - n.
+__device__ __forceinline__ int ghost_candidate(int k, int x, int n)
+{
+    return k == 0 ? x : (k <= FGHOST ? -k : n + (k - 1 - FGHOST));
+}
+
+__device__ __forceinline__ void store_fields_mixed(float4 *fa, float2 *fb, const BoxDev &b, int x, int y, int z,
+                                                   float4 a, float2 bb)
+{
+    const int kx = 1 + FGHOST + (b.pn[0] - FGHOST - b.n[0]);
+    const int ky = 1 + FGHOST + (b.pn[1] - FGHOST - b.n[1]);
+    const int kz = b.ndim == 3 ? 1 + FGHOST + (b.pn[2] - FGHOST - b.n[2]) : 1;
+    for (int iz = 0; iz < kz; ++iz) {
+        const int uz = b.ndim == 3 ? ghost_candidate(iz, z, b.n[2]) : 0;
+        if (iz > 0 && !ghost_of(uz, z, b.n[2], b.bc[2]))
+            continue;
+        for (int iy = 0; iy < ky; ++iy) {
+            const int uy = ghost_candidate(iy, y, b.n[1]);
+            if (iy > 0 && !ghost_of(uy, y, b.n[1], b.bc[1]))
+                continue;
+            for (int ix = 0; ix < kx; ++ix) {
+                const int ux = ghost_candidate(ix, x, b.n[0]);
+                if (ix > 0 && !ghost_of(ux, x, b.n[0], b.bc[0]))
+                    continue;
+                const int64_t f = fidx(b, ux, uy, uz);
+                fa[f] = a;
+                fb[f] = bb;
+            }
+        }
+    }
+}
+
 // Box-local linear cell -> integer coordinates.
 __device__ __forceinline__ void decode_cell(const BoxDev &b, int32_t c, int ci[3])
 {

@@ -166,8 +166,21 @@ __global__ void k_fields_to_double(Ctx c, double *__restrict__ out)
 {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < c.nc;
          g += (int64_t)gridDim.x * blockDim.x) {
-        for (int q = 0; q < 6; ++q)
-            out[q * c.nc + g] = c.prec == MHDPIC_PREC_MIXED ? (double)c.f32[g * 8 + q] : c.f64[g * 6 + q];
+        if (c.prec == MHDPIC_PREC_MIXED) {
+            const int bx = find_box(c.box_cell_start, c.nbox, g);
+            const BoxDev &b = c.boxes[bx];
+            int ci[3];
+            decode_cell(b, (int32_t)(g - b.cell0), ci);
+            const int64_t f = fidx(b, ci[0], ci[1], ci[2]);
+            const float4 a = c.fa[f];
+            const float2 bb = c.fb[f];
+            const float v[6] = {a.x, a.y, a.z, a.w, bb.x, bb.y};
+            for (int q = 0; q < 6; ++q)
+                out[q * c.nc + g] = (double)v[q];
+        } else {
+            for (int q = 0; q < 6; ++q)
+                out[q * c.nc + g] = c.f64[g * 6 + q];
+        }
     }
 }
 

@@ -176,8 +176,11 @@ __global__ void k_gas_predict(Ctx c, int cur, double dt, int model, double *__re
             }
         }
         if (PREC == MHDPIC_PREC_MIXED) {
-            reinterpret_cast<float4 *>(c.f32)[2 * g] = make_float4((float)E[0], (float)E[1], (float)E[2], (float)Bh[0]);
-            reinterpret_cast<float4 *>(c.f32)[2 * g + 1] = make_float4((float)Bh[1], (float)Bh[2], 0.f, 0.f);
+            int ci[3];
+            decode_cell(b, (int32_t)(g - b.cell0), ci);
+            store_fields_mixed(c.fa, c.fb, b, ci[0], ci[1], ci[2],
+                               make_float4((float)E[0], (float)E[1], (float)E[2], (float)Bh[0]),
+                               make_float2((float)Bh[1], (float)Bh[2]));
         } else {
             double2 *f = reinterpret_cast<double2 *>(c.f64) + 3 * g;
             f[0] = make_double2(E[0], E[1]);

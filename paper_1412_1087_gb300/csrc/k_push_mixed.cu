@@ -109,7 +109,7 @@ __device__ __forceinline__ void gather_tile(const Ctx &c, int base, const Wts &w
                                             const float2 *__restrict__ sFb, float E[3], float Bf[3])
 {
     E[0] = E[1] = E[2] = Bf[0] = Bf[1] = Bf[2] = 0.f;
-    const int SY = c.ts[1], SZ = c.ts[2];
+    const int SY = c.fts[1], SZ = c.fts[2];   // the field tile's strides
     // the z layers are kept rolled in 3-D: a third of the code, fewer
     // instruction-cache misses (measured 2% faster); 2-D has one layer
 #pragma unroll 1
@@ -163,17 +163,15 @@ __device__ __noinline__ F6 gather_global(const Ctx &c, const BoxDev &b, int ci0,
 {
     F6 r;
     r.e[0] = r.e[1] = r.e[2] = r.b[0] = r.b[1] = r.b[2] = 0.f;
-    const float4 *__restrict__ gF = reinterpret_cast<const float4 *>(c.f32);
-    const int ci[3] = {ci0, ci1, ci2};
-    int gx[3], gy[3], gz[3];
-    stencil_coords<D>(b, ci, gx, gy, gz);
+    // the stencil's cells, ghosts included, are inside the padded planes
     for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz)
         for (int cy = 0; cy < 3; ++cy) {
             float wyz = D == 3 ? w.y[cy] * w.z[cz] : w.y[cy];
             for (int cx = 0; cx < 3; ++cx) {
                 float ww = w.x[cx] * wyz;
-                int64_t g = b.cell0 + ((int64_t)gz[cz] * b.n[1] + gy[cy]) * b.n[0] + gx[cx];
-                float4 f1 = __ldg(gF + 2 * g), f2 = __ldg(gF + 2 * g + 1);
+                const int64_t f = fidx(b, ci0 + cx - 1, ci1 + cy - 1, D == 3 ? ci2 + cz - 1 : 0);
+                const float4 f1 = __ldg(c.fa + f);
+                const float2 f2 = __ldg(c.fb + f);
                 r.e[0] = fmaf(ww, f1.x, r.e[0]);
                 r.e[1] = fmaf(ww, f1.y, r.e[1]);
                 r.e[2] = fmaf(ww, f1.z, r.e[2]);
@@ -385,12 +383,22 @@ __device__ __forceinline__ void store_particle(const Ctx &c, int64_t j, int32_t 
     c.vel[j] = make_float4(v[0], v[1], v[2], __uint_as_float(res));
 }
 
-// Byte offset of the particle ring in the push's shared memory: after the
-// deposit tile (NPLANE int planes) and the staged fields (float4 + float2 per
-// slot), rounded up to the 16 bytes a cp.async of 16 bytes needs.
-__host__ __device__ constexpr size_t ring_offset(int slots)
+// The push's dynamic shared memory: the deposit tile (NPLANE int planes of
+// `slots`), the field tile (a float4 and a float2 plane of `fslots`, each on a
+// 128-byte boundary for the tensor copies), then the particle ring (2-D).
+struct PushLayout {
+    size_t fa, fb, ring;
+};
+
+__host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) / 128 * 128; }
+
+__host__ __device__ inline PushLayout push_layout(int slots, int fslots)
 {
-    return ((sizeof(int) * NPLANE + sizeof(float4) + sizeof(float2)) * (size_t)slots + 15) / 16 * 16;
+    PushLayout l{};
+    l.fa = align128(sizeof(int) * NPLANE * (size_t)slots);
+    l.fb = align128(l.fa + sizeof(float4) * (size_t)fslots);
+    l.ring = align128(l.fb + sizeof(float2) * (size_t)fslots);
+    return l;
 }
 
 __device__ __forceinline__ void store_dead(const Ctx &c, int64_t j)
@@ -479,10 +487,11 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
     }
     pin_weights(w);
     const int base = (rel[0] - 1) + c.ts[1] * (rel[1] - 1) + (D == 3 ? c.ts[2] * (rel[2] - 1) : 0);
+    const int fbase = (rel[0] - 1) + c.fts[1] * (rel[1] - 1) + (D == 3 ? c.fts[2] * (rel[2] - 1) : 0);
 
     float E[3], Bf[3];
     if (in_tile) {
-        gather_tile<D>(c, base, w, sFa, sFb, E, Bf);
+        gather_tile<D>(c, fbase, w, sFa, sFb, E, Bf);
     } else {
         F6 f = gather_global<D>(c, b, ci[0], ci[1], ci[2], w);
         E[0] = f.e[0];
@@ -576,6 +585,74 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
     return vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2];
 }
 
+// ---------------------------------------------------------------------------
+// Tensor copies of the field tile (TMA): one cp.async.bulk.tensor per plane
+// per work item, completed on a shared-memory mbarrier.  Each wait has a time
+// limit; a copy that does not complete raises MHDPIC_ST_COPY_TIMEOUT.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ long long timer_ns()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// true when the phase completed within limit_ns
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long limit_ns)
+{
+    const long long t0 = timer_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (timer_ns() - t0 > limit_ns)
+            return false;
+    return true;
+}
+
+// The copies read a box of the padded planes starting at the tile's first
+// cell; the innermost coordinate counts floats (4 per cell in plane fa, 2 in
+// fb), so it is a multiple of 16 bytes when the tile starts on an even cell.
+template <int D>
+__device__ __forceinline__ void tma_tile(void *dst, const unsigned char *tmap, int x, int y, int z, uint64_t *bar)
+{
+    if (D == 3)
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                     " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+                     "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+                     : "memory");
+    else
+        asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                     " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+                     "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+                     : "memory");
+}
+
+constexpr long long COPY_LIMIT_NS = 1000000000ll;   // one second
+
 // The push over the work items of the last sort, taken from an atomic
 // counter by the calling kernel's persistent blocks (smem: the dynamic shared
 // memory, push_smem_bytes_mixed bytes).
@@ -585,11 +662,20 @@ __device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restr
                                            unsigned char *smem)
 {
     const int S = c.tile_slots;
+    const PushLayout lay = push_layout(S, c.ftile_slots);
     int *sD = reinterpret_cast<int *>(smem);
-    float4 *sFa = reinterpret_cast<float4 *>(smem + sizeof(int) * NPLANE * S);
-    float2 *sFb = reinterpret_cast<float2 *>(smem + (sizeof(int) * NPLANE + sizeof(float4)) * S);
-    int4 *ring = reinterpret_cast<int4 *>(smem + ring_offset(S)) + threadIdx.x;
+    float4 *sFa = reinterpret_cast<float4 *>(smem + lay.fa);
+    float2 *sFb = reinterpret_cast<float2 *>(smem + lay.fb);
+    int4 *ring = reinterpret_cast<int4 *>(smem + lay.ring) + threadIdx.x;
     constexpr int RS = RING_RECS * PUSH_THREADS;   // int4 per ring stage
+    __shared__ __align__(8) uint64_t s_bar;   // completion of the field tile's tensor copies
+    unsigned phase = 0;
+    const unsigned copy_bytes = (unsigned)((sizeof(float4) + sizeof(float2)) * (size_t)c.ftile_slots);
+    if (c.tma) {
+        if (threadIdx.x == 0)
+            mbar_init(&s_bar);
+        __syncthreads();
+    }
     __shared__ int s_item;
     __shared__ MixedConst s_k;
     unsigned long long *mout = c.momdep[cur_out];
@@ -607,22 +693,45 @@ __device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restr
         const BoxDev &b = c.boxes[it.box];
         const ItemGeom gm = item_geom(c, b, it.brick, D);
 
-        // clear the deposit tile and stage the fields
+        // stage the fields: the tile is one block of the padded planes
+        // (ghosts included), copied by the tensor engine or by the threads
+        if (c.tma) {
+            if (threadIdx.x == 0) {
+                // the previous item's reads of the tile ended at the barrier before
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&s_bar, copy_bytes);
+                const unsigned char *tm = c.tmaps + (size_t)it.box * 256;
+                const int x0 = gm.org[0] + FGHOST, y0 = gm.org[1] + FGHOST, z0 = gm.org[2] + FGHOST;
+                tma_tile<D>(sFa, tm, 4 * x0, y0, z0, &s_bar);
+                tma_tile<D>(sFb, tm + 128, 2 * x0, y0, z0, &s_bar);
+            }
+        } else {
+            for (int t = threadIdx.x; t < c.tile_vol; t += PUSH_THREADS) {
+                const int tx = t % c.tile[0], r = t / c.tile[0];
+                const int ty = r % c.tile[1], tz = r / c.tile[1];
+                // the tile lies inside the padded planes (they cover the brick grid plus the halo)
+                const int64_t f = fidx(b, gm.org[0] + tx, gm.org[1] + ty, gm.org[2] + tz);
+                const int sl = tx + c.fts[1] * ty + c.fts[2] * tz;
+                sFa[sl] = __ldg(c.fa + f);
+                sFb[sl] = __ldg(c.fb + f);
+            }
+        }
+        // clear the deposit tile
         for (int s = threadIdx.x; s < NPLANE * S; s += PUSH_THREADS)
             sD[s] = 0;
-        const float4 *gF = reinterpret_cast<const float4 *>(c.f32);
-        for (int t = threadIdx.x; t < c.tile_vol; t += PUSH_THREADS) {
-            int tx = t % c.tile[0], r = t / c.tile[0];
-            int ty = r % c.tile[1], tz = r / c.tile[1];
-            int64_t g = tile_global(c, b, gm, tx, ty, tz, D);
-            int s = tile_slot(c, tx, ty, tz);
-            float4 f1 = __ldg(gF + 2 * g), f2 = __ldg(gF + 2 * g + 1);
-            sFa[s] = f1;
-            sFb[s] = make_float2(f2.x, f2.y);
-        }
         if (threadIdx.x == 0)
             item_const(b, dt, it.p1 - it.p0, D, s_k);
         __syncthreads();
+        if (c.tma) {
+            const bool ok = mbar_wait(&s_bar, phase, COPY_LIMIT_NS);
+            if (__syncthreads_or(!ok)) {   // give up the launch, after the copies in flight have had their time
+                if (threadIdx.x == 0)
+                    set_status(c.status, MHDPIC_ST_COPY_TIMEOUT);
+                mbar_wait(&s_bar, phase, COPY_LIMIT_NS);
+                return;
+            }
+            phase ^= 1u;
+        }
         // the item constants stay in shared memory where registers are short
         MixedConst kreg;
         if (!CONST_IN_SMEM<D>)
@@ -715,7 +824,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_push_mixed(Ctx 
                                                                  int32_t *__restrict__ work_ctr, int cur_out,
                                                                  float dt)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     push_items<D, FULL>(c, items, *nitems, work_ctr, cur_out, dt, smem);
 }
 
@@ -775,7 +884,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, MIN_BLOCKS<D>) k_step_mixed(Ctx 
                                                                  int32_t *__restrict__ work_ctr, int cur, float dtf,
                                                                  double dt, GridBarrier *bar, long long limit_ns)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     if (blockIdx.x == 0) {   // the corrector scales, and the push's work counter
         for (int bx = threadIdx.x; bx < c.nbox; bx += blockDim.x)
             scales_box(c, bx, dt);
@@ -802,7 +911,7 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_deposit_mixed(Ctx c, const Wor
                                                                const int32_t *__restrict__ nitems,
                                                                int32_t *__restrict__ work_ctr, int cur)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int S = c.tile_slots;
     int *sD = reinterpret_cast<int *>(smem);
     __shared__ int s_item;
@@ -901,7 +1010,7 @@ size_t push_smem_bytes_mixed(const Ctx &c)
 {
     const bool staged = c.ndim == 3 ? STAGED<3> : STAGED<2>;
     const size_t ring = staged ? sizeof(int4) * RING_STAGES * (size_t)RING_RECS * PUSH_THREADS : 0;
-    return ring_offset(c.tile_slots) + ring;
+    return push_layout(c.tile_slots, c.ftile_slots).ring + ring;
 }
 
 int push_blocks_per_sm_mixed(const Ctx &c)

@@ -13,6 +13,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "mhdpic_internal.cuh"
 
 using namespace mhdpic;
@@ -77,6 +80,10 @@ struct mhdpic_ctx {
     long long bar_limit_ns = 1000000000ll;
     int step_grid = 0;
     bool fuse = true;
+    // staged mixed-precision fields: padded planes, their tensor maps
+    int64_t fcells = 0;
+    unsigned char *tmaps = nullptr;   // device, 2 CUtensorMap (128 B) per box
+    bool tma_ok = false;              // the maps could be encoded for this layout
     // look-ahead sort: per box {t/dx, t/dy, t/dz, 1/C^2} in FP32 (device copy in k.sort_k)
     std::vector<float4> sort_k_host;
     float4 *sort_k = nullptr;
@@ -365,6 +372,58 @@ int do_prep(mhdpic_ctx *c, int apply)
     return rc;
 }
 
+// Tensor maps of the field planes, two per box (plane fa: 4 floats per cell,
+// plane fb: 2), each a (floats per row, rows, layers) tensor over the box's
+// padded block whose copy box is the push's field tile: (ts[1] cells, tile y,
+// tile z).  Tiles start on cell org + FGHOST = brick origin, so the copies are
+// used only when the brick's x extent is even (the innermost coordinate of the
+// fb copy is then a multiple of 16 bytes) and the tile fits the copy limits;
+// otherwise, or when the driver entry point is missing, the threads stage the
+// tile.  Returns an error only for allocation or copy failures.
+int setup_tensor_maps(mhdpic_ctx *c)
+{
+    Ctx &k = c->k;
+    k.tma = 0;
+    k.tmaps = nullptr;
+    const int fsy = k.fts[1];
+    if (k.brick[0] % 2 || fsy % 2 || 4 * fsy > 256 || k.tile[1] > 256 || k.tile[2] > 256)
+        return MHDPIC_OK;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return MHDPIC_OK;
+    }
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    std::vector<CUtensorMap> maps(2 * (size_t)c->nbox);
+    const cuuint32_t rank = k.ndim == 3 ? 3 : 2;
+    for (int b = 0; b < c->nbox; ++b) {
+        const BoxDev &bd = c->boxes[b];
+        for (int plane = 0; plane < 2; ++plane) {
+            const int per = plane == 0 ? 4 : 2;   // floats per cell
+            void *base = plane == 0 ? (void *)(k.fa + bd.fcell0) : (void *)(k.fb + bd.fcell0);
+            const cuuint64_t dim[3] = {(cuuint64_t)per * bd.pn[0], (cuuint64_t)bd.pn[1], (cuuint64_t)bd.pn[2]};
+            const cuuint64_t stride[2] = {(cuuint64_t)per * 4 * bd.pn[0], (cuuint64_t)per * 4 * bd.pn[0] * bd.pn[1]};
+            const cuuint32_t box[3] = {(cuuint32_t)(per * fsy), (cuuint32_t)k.tile[1], (cuuint32_t)k.tile[2]};
+            const cuuint32_t estr[3] = {1, 1, 1};
+            CUresult r = encode(&maps[2 * b + plane], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, dim, stride, box,
+                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS)
+                return MHDPIC_OK;   // this layout is not expressible: the threads stage the tiles
+        }
+    }
+    int rc;
+    if ((rc = c->alloc(&c->tmaps, maps.size() * sizeof(CUtensorMap))))
+        return rc;
+    CK(cudaMemcpy(c->tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    k.tmaps = c->tmaps;
+    k.tma = 1;
+    c->tma_ok = true;
+    return MHDPIC_OK;
+}
+
 // Charge/current deposit of the current particles into moments buffer cur.
 // Mixed precision goes through the push's tile over the work list of a sort
 // of the current particles: the list is current when `listed` (right after
@@ -489,6 +548,13 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         k.ts[2] = 24 * k.tile[1];
     }
     k.tile_slots = k.ndim == 3 ? k.ts[2] * k.tile[2] : k.ts[1] * k.tile[1];
+    // the field tile: x stride 1, y stride ts[1] (the bank spread the
+    // gathers need), z dense, as one tensor copy of a (ts[1], tile y, tile z)
+    // box writes it
+    k.fts[0] = 1;
+    k.fts[1] = k.ts[1];
+    k.fts[2] = k.ts[1] * k.tile[1];
+    k.ftile_slots = k.fts[2] * k.tile[2];
     size_t smem = k.prec == MHDPIC_PREC_MIXED ? push_smem_bytes_mixed(k) : push_smem_bytes_f64(k);
     if (smem > 200 * 1024)
         return bail(fail(MHDPIC_E_CAPACITY, "brick %dx%dx%d needs %zu bytes of shared memory", k.brick[0],
@@ -532,6 +598,15 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         key0 += bd.nkeys;
         bd.div_nx = make_fastdiv((uint32_t)g.n[0]);
         bd.div_nxy = make_fastdiv((uint32_t)(g.n[0] * g.n[1]));
+        // padded staged-field planes: FGHOST ghosts below, and above up to
+        // the brick grid's end plus FGHOST, so that every tile of the push
+        // (bricks plus halo, periodic images included) lies inside; x rounded
+        // up to even so that a row of the float2 plane is 16-byte aligned
+        bd.pn[0] = (bd.nb[0] * k.brick[0] + 2 * FGHOST + 1) / 2 * 2;
+        bd.pn[1] = bd.nb[1] * k.brick[1] + 2 * FGHOST;
+        bd.pn[2] = g.ndim == 3 ? bd.nb[2] * k.brick[2] + 2 * FGHOST : 1;
+        bd.fcell0 = c->fcells;
+        c->fcells += (int64_t)bd.pn[0] * bd.pn[1] * bd.pn[2];
         c->boxes.push_back(bd);
     }
     k.nc = c->cell_start[nbox];
@@ -554,12 +629,23 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
     if ((rc = c->alloc(&k.corr, 4 * nc)) || (rc = c->alloc(&k.momdep[0], 4 * nc)) ||
         (rc = c->alloc(&k.momdep[1], 4 * nc)) || (rc = c->alloc(&k.status, 1)))
         return bail(rc);
-    if (k.prec == MHDPIC_PREC_MIXED)
-        rc = c->alloc(&k.f32, 8 * nc);
-    else
+    if (k.prec == MHDPIC_PREC_MIXED) {
+        if (!(rc = c->alloc(&k.fa, c->fcells)))
+            rc = c->alloc(&k.fb, c->fcells);
+    } else {
         rc = c->alloc(&k.f64, 6 * nc);
+    }
     if (rc)
         return bail(rc);
+    if (k.prec == MHDPIC_PREC_MIXED) {
+        // zero the planes once: the columns added for alignment and tile cells
+        // past a ragged box are never written by the staging but are copied
+        if (cudaMemsetAsync(k.fa, 0, sizeof(float4) * c->fcells, c->stream) ||
+            cudaMemsetAsync(k.fb, 0, sizeof(float2) * c->fcells, c->stream))
+            return bail(cuda_fail(cudaGetLastError(), "init field planes"));
+        if ((rc = setup_tensor_maps(c)))
+            return bail(rc);
+    }
     int64_t scan_n = std::max<int64_t>(k.nkeys, k.nbricks_total) / 4096 + 2;
     if ((rc = c->alloc(&c->s.count, k.nkeys + 2)) || (rc = c->alloc(&c->s.offset, k.nkeys + 2)) ||
         (rc = c->alloc(&c->s.pkey, np)) || (rc = c->alloc(&c->s.pslot, np)) || (rc = c->alloc(&c->s.perm, np)) ||
@@ -1417,6 +1503,23 @@ int mhdpic_set_step_fusion(mhdpic_ctx *c, int32_t enable)
 int32_t mhdpic_step_fusion(const mhdpic_ctx *c)
 {
     return c && c->valid ? (fused_ok(c) ? 1 : 0) : -1;
+}
+
+int mhdpic_set_field_tma(mhdpic_ctx *c, int32_t enable)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    c->k.tma = enable && c->tma_ok ? 1 : 0;
+    if (c->graph) {   // a captured cycle holds the other form of the staging
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return MHDPIC_OK;
+}
+
+int32_t mhdpic_field_tma(const mhdpic_ctx *c)
+{
+    return c && c->valid ? c->k.tma : -1;
 }
 
 int mhdpic_debug_set_barrier_limit(mhdpic_ctx *c, int64_t ns)

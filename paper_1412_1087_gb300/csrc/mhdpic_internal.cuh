@@ -23,6 +23,9 @@ enum { CH_MX = 0, CH_MY, CH_MZ, CH_E, CH_N, CH_JX, CH_JY, CH_JZ, NCH };
 // any other particle takes the global-memory path, so the halo only decides
 // speed, never correctness.
 constexpr int HALO = 2;
+// Ghost cells around each box in the staged mixed-precision fields: as many as
+// the tile's halo, so that every tile is one block of the padded array.
+constexpr int FGHOST = HALO;
 constexpr int PUSH_THREADS = 256;
 constexpr int ITEM_MAX_PARTICLES = 4096;
 
@@ -71,6 +74,9 @@ struct BoxDev {
     int64_t key0;    // first sort key of the box
     int64_t nkeys;
     int32_t nb[3];   // bricks per dimension
+    int32_t pn[3];   // staged-field (mixed) array per box: the brick grid nb*brick + 2 FGHOST per dimension
+                     // (x rounded up to even; 1 for z in 2-D), so that every push tile lies inside it
+    int64_t fcell0;  // first cell of the box in the padded staged-field planes
     int32_t nbricks;
     int64_t brick0;  // first global brick number
     FastDiv div_nx, div_nxy;
@@ -113,6 +119,9 @@ struct Ctx {
     int32_t tile_vol;      // cells of the tile
     int32_t ts[3];         // tile strides in slots (x, y, z); padded to spread banks
     int32_t tile_slots;    // slots of the tile (>= tile_vol)
+    int32_t fts[3];        // field tile strides (x 1, y ts[1], z dense): the layout a tensor copy writes
+    int32_t ftile_slots;   // slots of the field tile
+    int32_t tma;           // 1: field tiles staged by tensor copies (tmaps), 0: by the threads
     int32_t halves;        // 1: default 64-cell bricks split into 32-cell halves
     double sort_ahead;     // sort key: the cell after moving for this time at the current velocity
     const float4 *sort_k;  // per box {t/dx, t/dy, t/dz, 1/C^2} in FP32 for that key
@@ -140,7 +149,9 @@ struct Ctx {
     // scratch
     unsigned long long *corr;     // [4][nc]
     unsigned long long *momdep[2];// [4][nc] each
-    float *f32;                   // [nc][8] = Ex,Ey,Ez,Bx,By,Bz,0,0
+    float4 *fa;                   // mixed: padded planes of the staged fields, {Ex, Ey, Ez, Bx}
+    float2 *fb;                   //        and {By, Bz}, per box pn[0] x pn[1] x pn[2] cells from fcell0
+    const unsigned char *tmaps;   // mixed with tma: per box two 128-byte tensor maps (planes fa, fb)
     double *f64;                  // [nc][6]
     uint32_t *status;
     const int32_t *key_off;       // sort offsets: particles of key k are [key_off[k], key_off[k+1])

@@ -38,7 +38,7 @@ MHDPIC_SPEC_MAX_BINS = 2048
 MHDPIC_GAS_SOURCES = 0
 MHDPIC_GAS_LINEAR_X = 1
 STATUS_NAMES = {1: "FAST_MOVER", 2: "NONFINITE", 4: "OVERFLOW", 8: "SORT_CAP", 16: "CELL_RANGE", 32: "INJECT_CAP",
-                64: "BARRIER"}
+                64: "BARRIER", 128: "COPY_TIMEOUT"}
 
 
 class MhdpicError(RuntimeError):
@@ -100,6 +100,8 @@ SIGNATURES = {
     "mhdpic_set_step_fusion": (ctypes.c_int, [_V, ctypes.c_int32]),
     "mhdpic_step_fusion": (ctypes.c_int32, [_V]),
     "mhdpic_debug_set_barrier_limit": (ctypes.c_int, [_V, ctypes.c_int64]),
+    "mhdpic_set_field_tma": (ctypes.c_int, [_V, ctypes.c_int32]),
+    "mhdpic_field_tma": (ctypes.c_int32, [_V]),
     "mhdpic_get_deposits": (ctypes.c_int, [_V, ctypes.c_int32, _V]),
     "mhdpic_get_fields": (ctypes.c_int, [_V, _V]),
     "mhdpic_get_velocities": (ctypes.c_int, [_V, _V]),
@@ -258,6 +260,14 @@ def mhdpic_set_step_fusion(ctx, enable: bool) -> None:
 
 def mhdpic_step_fusion(ctx) -> int:
     return int(load().mhdpic_step_fusion(ctx))
+
+
+def mhdpic_set_field_tma(ctx, enable: bool) -> None:
+    _check(load().mhdpic_set_field_tma(ctx, 1 if enable else 0))
+
+
+def mhdpic_field_tma(ctx) -> int:
+    return int(load().mhdpic_field_tma(ctx))
 
 
 def mhdpic_debug_set_barrier_limit(ctx, ns: int) -> None:
@@ -554,6 +564,13 @@ class Engine:
 
     def step_fusion(self) -> int:
         return mhdpic_step_fusion(self.ctx)
+
+    def set_field_tma(self, enable: bool) -> None:
+        """Stage the pushes' field tiles by tensor copies (default where possible) or by the threads."""
+        mhdpic_set_field_tma(self.ctx, enable)
+
+    def field_tma(self) -> int:
+        return mhdpic_field_tma(self.ctx)
 
     # -- read-back ----------------------------------------------------------
     def deposits(self, which: int):
