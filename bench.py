@@ -584,6 +584,16 @@ def run_native(args):
     # events on the library's stream: the push kernel's roofline
     eager_ms, push_ms, _ = _time_engine(eng, dt, args.steps, args.warmup, args.sort_every, torch)
     steps_done += args.steps + args.warmup
+    # the sort alone (keys, scan, scatter, segment sort, work list), a few calls
+    sev0, sev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eng.sort()
+    torch.cuda.synchronize()
+    sev0.record(stream)
+    for _ in range(3):
+        eng.sort()
+    sev1.record(stream)
+    torch.cuda.synchronize()
+    sort_ms = sev0.elapsed_time(sev1) / 3
 
     # timed region (device time, max over ranks): the production step, the
     # cycle of push + feedback + sort at the tuned cadence captured once in a
@@ -825,7 +835,7 @@ def run_native(args):
     traffic = None
     if args.workload in PUSH_TRAFFIC_BYTES_PER_PARTICLE:
         traffic = PUSH_TRAFFIC_BYTES_PER_PARTICLE[args.workload] * npart
-    eng_stats = {"field_tma": field_tma,
+    eng_stats = {"field_tma": field_tma, "sort_ms": sort_ms,
                  "push_ms_per_step": push_ms / args.steps, "graph_run_ms_per_step": graph_ms,
                  "eager_ms_per_step": eager_ms / args.steps,
                  "subcycled": subcycled, "diagnostics": diagnostics, "coupled": coupled,

@@ -247,14 +247,18 @@ int mhdpic_set_subcycle_sort(mhdpic_ctx *ctx, int32_t every);
  * cell: with t = dt/2 the cell of the half-step position where the next push
  * gathers E, B and deposits the corrector (App. A.2-A.3), so that the push
  * finds its particles in the cells it works on.  Per dimension the cell moves
- * by floor(o_d + (a_d v_d) ig) with ig = 1/sqrt(1 + v^2 w), v^2 =
+ * by -1, 0 or +1 (a half step moves a particle well under one cell): +1 when
+ * v_d > 0 and (a_d v_d)^2 >= ((1 - o_d)(1 - o_d)) g2, -1 when v_d < 0 and
+ * (a_d v_d)^2 > (o_d o_d) g2, with g2 = 1 + v^2 w (gamma^2), v^2 =
  * (vx vx + vy vy) + vz vz, a_d = t/dx_d rounded from double to float and
  * w = 1/(C C) in FP32, o_d the offset in the cell (FP64 precision:
  * (x_d - x0_d)/dx_d minus its cell, as float) and v the FP32 four-velocity
  * (the FP64 one rounded to float), every operation a correctly rounded FP32
- * one in this order; the cell wraps on periodic faces and is clamped into the
- * box otherwise.  The call is ordered on the context's stream.  Only the order of the particles and the speed depend on t: the
- * deposits, the gas and the particle states are the same bit for bit.
+ * one in this order (the faces of o_d + a_d v_d/gamma tested on squares: no
+ * square root, no division); the cell wraps on periodic faces and is clamped
+ * into the box otherwise.  The call is ordered on the context's stream.  Only
+ * the order of the particles and the speed depend on t: the deposits, the gas
+ * and the particle states are the same bit for bit.
  * 0 (the default) sorts by the current cell.  The paper has no sort.
  * Errors: MHDPIC_E_STATE, MHDPIC_E_ARG for a non-finite t.
  */

@@ -47,82 +47,148 @@ __device__ __forceinline__ int64_t brick_key(const BoxDev &b, const Ctx &c, int 
     return b.key0 + bid * ((int64_t)c.brick[0] * c.brick[1] * c.brick[2]) + in;
 }
 
-// Whole cells a particle moves along each of the first D dimensions in time
-// t at its current four-velocity v (the sort's look-ahead), from its offsets
-// o in the cell: with the box's FP32 constants k = {t/dx, t/dy, t/dz, 1/C^2}
-// (each rounded once from the exact value, on the host),
-//   g = sqrt(1 + v^2 k.w), ig = 1/g, cells_d = floor(o_d + (k_d v_d) ig),
+// Cells a particle moves along each of the first D dimensions in time t at
+// its current four-velocity v (the sort's look-ahead), -1, 0 or +1: whether
+// the position o + (t/dx) v/gamma leaves its cell through the lower or the
+// upper face (a half step moves a particle well under one cell).  With the
+// box's FP32 constants k = {t/dx, t/dy, t/dz, 1/C^2} (each rounded once, on
+// the host), g2 = gamma^2 = 1 + v^2 k.w and a_d = k_d, the faces are tested on
+// squares, so that no square root or division is needed:
+//   +1 when v_d > 0 and (a_d v_d)^2 >= ((1 - o_d)(1 - o_d)) g2,
+//   -1 when v_d < 0 and (a_d v_d)^2 >  (o_d o_d) g2,
 // v^2 = (vx vx + vy vy) + vz vz, every operation a correctly rounded FP32 one
 // in this order (no contraction), so the key can be recomputed exactly
-// elsewhere.  FP32, not FP64: the GB300's FP64 units would make the key pass
-// several times slower.
+// elsewhere.
 __device__ __forceinline__ void ahead_cells(const float4 k, const float v[3], const float o[3], int D, int cells[3])
 {
     const float v2 = __fadd_rn(__fadd_rn(__fmul_rn(v[0], v[0]), __fmul_rn(v[1], v[1])), __fmul_rn(v[2], v[2]));
-    const float ig = __fdiv_rn(1.f, __fsqrt_rn(__fadd_rn(1.f, __fmul_rn(v2, k.w))));
+    const float g2 = __fadd_rn(1.f, __fmul_rn(v2, k.w));
     const float ta[3] = {k.x, k.y, k.z};
-    for (int d = 0; d < D; ++d)
-        cells[d] = (int)floorf(__fadd_rn(o[d], __fmul_rn(__fmul_rn(ta[d], v[d]), ig)));
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d >= D)
+            break;
+        const float av = __fmul_rn(ta[d], v[d]);
+        const float l = __fmul_rn(av, av);
+        const float up = __fsub_rn(1.f, o[d]);
+        const float ru = __fmul_rn(__fmul_rn(up, up), g2);
+        const float rl = __fmul_rn(__fmul_rn(o[d], o[d]), g2);
+        cells[d] = (v[d] > 0.f && l >= ru) ? 1 : ((v[d] < 0.f && l > rl) ? -1 : 0);
+    }
 }
 
-// Sort key of particle i of box b: brick-major cell order, nkeys for a
-// particle that has left the box.  With a look-ahead (c.sort_ahead != 0) the
-// cell is the one the particle reaches in that time at its current velocity
-// (periodic wrap, else clamped into the box): with half a step, the cell of
-// the position where the next push gathers the fields and deposits the
-// corrector.
-template <int PREC>
-__device__ __forceinline__ int32_t key_in_box(const Ctx &c, const BoxDev &b, int bx, int64_t i)
+// Clamp or wrap a key cell into the box, and its brick-major key.
+__device__ __forceinline__ int32_t key_of_cell(const Ctx &c, const BoxDev &b, int ci[3], bool ahead)
 {
-    int ci[3] = {0, 0, 0};
-    bool dead = false;
-    const bool ahead = c.sort_ahead != 0.0;
-    if (PREC == MHDPIC_PREC_MIXED) {
-        const int4 ps = __ldg(&c.pos[i]);
-        int32_t cl = ps.x;
-        dead = cl == DEAD_CELL;
-        if (!dead && (cl < 0 || cl >= b.ncell)) {
-            set_status(c.status, MHDPIC_ST_CELL_RANGE);
-            cl = cl < 0 ? 0 : (int32_t)(b.ncell - 1);
-        }
-        decode_cell(b, cl, ci);
-        if (ahead && !dead) {
-            const float4 vs = __ldg(&c.vel[i]);
-            const float v[3] = {vs.x, vs.y, vs.z};
-            const float o[3] = {__int_as_float(ps.y), __int_as_float(ps.z), __int_as_float(ps.w)};
-            int k[3] = {0, 0, 0};
-            ahead_cells(__ldg(c.sort_k + bx), v, o, c.ndim, k);
-            for (int d = 0; d < c.ndim; ++d)
-                ci[d] += k[d];
-        }
-    } else {
-        dead = isnan(c.x[i]);
-        float o[3] = {0.f, 0.f, 0.f};
-        for (int d = 0; d < c.ndim && !dead; ++d) {
-            double s = (c.x[(int64_t)d * c.np + i] - b.x0[d]) / b.dx[d];
-            double f = floor(s);
-            int v = f < 0.0 ? 0 : (f >= (double)b.n[d] ? b.n[d] - 1 : (int)f);
-            if (!(f >= 0.0 && f < (double)b.n[d]))
-                set_status(c.status, MHDPIC_ST_CELL_RANGE);
-            ci[d] = v;
-            o[d] = (float)(s - (double)v);
-        }
-        if (ahead && !dead) {
-            const float v[3] = {(float)c.p64[i], (float)c.p64[c.np + i], (float)c.p64[2 * c.np + i]};
-            int k[3] = {0, 0, 0};
-            ahead_cells(__ldg(c.sort_k + bx), v, o, c.ndim, k);
-            for (int d = 0; d < c.ndim; ++d)
-                ci[d] += k[d];
-        }
-    }
     if (ahead)
         for (int d = 0; d < c.ndim; ++d)
             ci[d] = b.bc[d] == MHDPIC_BC_PERIODIC ? map_coord(ci[d], b.n[d], MHDPIC_BC_PERIODIC)
                                                   : (ci[d] < 0 ? 0 : (ci[d] >= b.n[d] ? b.n[d] - 1 : ci[d]));
     for (int d = 0; d < 3; ++d)   // defensive: a key outside the box would index out of range
         ci[d] = ci[d] < 0 ? 0 : (ci[d] >= b.n[d] ? b.n[d] - 1 : ci[d]);
-    // particles that left the box share one key after all the others
-    return dead ? (int32_t)c.nkeys : (int32_t)brick_key(b, c, ci[0], ci[1], ci[2]);
+    return (int32_t)brick_key(b, c, ci[0], ci[1], ci[2]);
+}
+
+// What the mixed-precision key needs of a box, held in registers while a
+// thread's particles stay in one box (reloaded when the box changes).
+struct KeyBox {
+    int box;
+    int n[3], bc[3], nb[3];
+    int32_t ncell;
+    int64_t key0;
+    FastDiv dnx, dnxy;
+    float4 sk;
+};
+
+__device__ __forceinline__ void load_keybox(const Ctx &c, int bx, KeyBox &kb)
+{
+    const BoxDev &b = c.boxes[bx];
+    kb.box = bx;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        kb.n[d] = b.n[d];
+        kb.bc[d] = b.bc[d];
+        kb.nb[d] = b.nb[d];
+    }
+    kb.ncell = (int32_t)b.ncell;
+    kb.key0 = b.key0;
+    kb.dnx = b.div_nx;
+    kb.dnxy = b.div_nxy;
+    kb.sk = __ldg(c.sort_k + bx);
+}
+
+// Mixed precision: the key of a particle from its two records (loaded by
+// the caller, so that the loads of several particles are in flight at once),
+// as key_of_cell / brick_key compute it.
+__device__ __forceinline__ int32_t key_mixed(const Ctx &c, const KeyBox &kb, const int4 ps, const float4 vs)
+{
+    int32_t cl = ps.x;
+    if (cl == DEAD_CELL)   // particles that left the box share one key after all the others
+        return (int32_t)c.nkeys;
+    if (cl < 0 || cl >= kb.ncell) {
+        set_status(c.status, MHDPIC_ST_CELL_RANGE);
+        cl = cl < 0 ? 0 : kb.ncell - 1;
+    }
+    const uint32_t uc = (uint32_t)cl;
+    const uint32_t kz = fdiv(uc, kb.dnxy);
+    const uint32_t rr = uc - kz * kb.dnxy.d;
+    const uint32_t jy = fdiv(rr, kb.dnx);
+    int ci[3] = {(int)(rr - jy * kb.dnx.d), (int)jy, (int)kz};
+    if (c.sort_ahead != 0.0) {
+        const float v[3] = {vs.x, vs.y, vs.z};
+        const float o[3] = {__int_as_float(ps.y), __int_as_float(ps.z), __int_as_float(ps.w)};
+        int k[3] = {0, 0, 0};
+        ahead_cells(kb.sk, v, o, c.ndim, k);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d >= c.ndim)
+                break;
+            const int g = ci[d] + k[d];
+            ci[d] = kb.bc[d] == MHDPIC_BC_PERIODIC ? (g < 0 ? g + kb.n[d] : (g >= kb.n[d] ? g - kb.n[d] : g))
+                                                   : (g < 0 ? 0 : (g >= kb.n[d] ? kb.n[d] - 1 : g));
+        }
+    }
+    int q[3], r[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (c.brick_sh[d] >= 0) {
+            q[d] = ci[d] >> c.brick_sh[d];
+            r[d] = ci[d] & (c.brick[d] - 1);
+        } else {
+            q[d] = ci[d] / c.brick[d];
+            r[d] = ci[d] - q[d] * c.brick[d];
+        }
+    }
+    const int64_t bid = ((int64_t)q[2] * kb.nb[1] + q[1]) * kb.nb[0] + q[0];
+    const int in = (r[2] * c.brick[1] + r[1]) * c.brick[0] + r[0];
+    return (int32_t)(kb.key0 + bid * ((int64_t)c.brick[0] * c.brick[1] * c.brick[2]) + in);
+}
+
+// FP64 precision: the key of particle i of box b, from its absolute position.
+__device__ __forceinline__ int32_t key_f64(const Ctx &c, const BoxDev &b, int bx, int64_t i)
+{
+    int ci[3] = {0, 0, 0};
+    const bool ahead = c.sort_ahead != 0.0;
+    if (isnan(c.x[i]))   // particles that left the box share one key after all the others
+        return (int32_t)c.nkeys;
+    float o[3] = {0.f, 0.f, 0.f};
+    for (int d = 0; d < c.ndim; ++d) {
+        double s = (c.x[(int64_t)d * c.np + i] - b.x0[d]) / b.dx[d];
+        double f = floor(s);
+        int v = f < 0.0 ? 0 : (f >= (double)b.n[d] ? b.n[d] - 1 : (int)f);
+        if (!(f >= 0.0 && f < (double)b.n[d]))
+            set_status(c.status, MHDPIC_ST_CELL_RANGE);
+        ci[d] = v;
+        o[d] = (float)(s - (double)v);
+    }
+    if (ahead) {
+        const float v[3] = {(float)c.p64[i], (float)c.p64[c.np + i], (float)c.p64[2 * c.np + i]};
+        int k[3] = {0, 0, 0};
+        ahead_cells(__ldg(c.sort_k + bx), v, o, c.ndim, k);
+        for (int d = 0; d < c.ndim; ++d)
+            ci[d] += k[d];
+    }
+    return key_of_cell(c, b, ci, ahead);
 }
 
 // Particles handled per thread and loop pass by the streaming sort kernels:
@@ -135,18 +201,49 @@ __global__ void k_sort_keys(Ctx c, int32_t *__restrict__ count, int32_t *__restr
 {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    KeyBox kb;
+    if (PREC == MHDPIC_PREC_MIXED)
+        load_keybox(c, 0, kb);
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < c.np; i0 += SORT_ILP * stride) {
         // lanes past the end take keys no other lane has, so they form runs
         // of their own and take no atomic
         const unsigned active = __activemask();
         int32_t key[SORT_ILP];
+        if (PREC == MHDPIC_PREC_MIXED) {
+            // every record load of the pass first, then the keys
+            int4 ps[SORT_ILP];
+            float4 vs[SORT_ILP];
+            int bxs[SORT_ILP];
+            const bool ahead = c.sort_ahead != 0.0;
 #pragma unroll
-        for (int u = 0; u < SORT_ILP; ++u) {
-            const int64_t i = i0 + u * stride;
-            int bx = 0;
-            if (i < c.np)
-                bx = find_box(c.box_part_start, c.nbox, i);
-            key[u] = i < c.np ? key_in_box<PREC>(c, c.boxes[bx], bx, i) : -1 - lane;
+            for (int u = 0; u < SORT_ILP; ++u) {
+                const int64_t i = i0 + u * stride;
+                bxs[u] = kb.box;
+                ps[u] = make_int4(DEAD_CELL, 0, 0, 0);
+                vs[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i < c.np) {
+                    if (c.nbox > 1)
+                        bxs[u] = find_box(c.box_part_start, c.nbox, i);
+                    ps[u] = __ldg(c.pos + i);
+                    if (ahead)
+                        vs[u] = __ldg(c.vel + i);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < SORT_ILP; ++u) {
+                if (bxs[u] != kb.box)
+                    load_keybox(c, bxs[u], kb);
+                key[u] = i0 + u * stride < c.np ? key_mixed(c, kb, ps[u], vs[u]) : -1 - lane;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < SORT_ILP; ++u) {
+                const int64_t i = i0 + u * stride;
+                int bx = 0;
+                if (i < c.np)
+                    bx = find_box(c.box_part_start, c.nbox, i);
+                key[u] = i < c.np ? key_f64(c, c.boxes[bx], bx, i) : -1 - lane;
+            }
         }
         // runs of equal keys in consecutive lanes (the input is nearly
         // sorted) take one atomic per run; the rank inside the run is the

@@ -75,8 +75,9 @@ def test_sort_matches_oracle_bit_exactly(prec, name):
 def _lookahead_cells(box, t, prec, cell=None, off=None, v=None, x=None):
     """The cells the library's look-ahead sort keys particles by, recomputed
     in numpy with the same correctly rounded FP32 operations in the same
-    order: floor(o_d + (a_d v_d) ig), ig = 1/sqrt(1 + v^2 w), a_d = t/dx_d
-    rounded to float, w = 1/(C C) in float."""
+    order: per dimension +1 when v > 0 and (a v)^2 >= ((1-o)(1-o)) g2, -1
+    when v < 0 and (a v)^2 > (o o) g2, g2 = 1 + v^2 w, a = t/dx rounded to
+    float, w = 1/(C C) in float."""
     n = box.n
     if prec == MIXED:
         c = cell.astype(np.int64)
@@ -94,16 +95,21 @@ def _lookahead_cells(box, t, prec, cell=None, off=None, v=None, x=None):
         ci.append(np.zeros_like(ci[0]))
         vf = v.astype(np.float32)
     C = np.float32(box.C)
-    invC2 = np.float32(1) / (C * C)
+    w = np.float32(1) / (C * C)
     v2 = (vf[0] * vf[0] + vf[1] * vf[1]) + vf[2] * vf[2]
-    ig = np.float32(1) / np.sqrt(np.float32(1) + v2 * invC2)
+    g2 = np.float32(1) + v2 * w
     out = []
     for d in range(3):
         if d >= box.ndim:
             out.append(ci[d])
             continue
-        ta = np.float32(t * (1.0 / box.dx[d]))
-        k = np.floor(o[d] + (ta * vf[d]) * ig).astype(np.int64)
+        a = np.float32(t * (1.0 / box.dx[d]))
+        av = a * vf[d]
+        lhs = av * av
+        up = np.float32(1) - o[d]
+        ru = (up * up) * g2
+        rl = (o[d] * o[d]) * g2
+        k = np.where((vf[d] > 0) & (lhs >= ru), 1, np.where((vf[d] < 0) & (lhs > rl), -1, 0)).astype(np.int64)
         cd = ci[d] + k
         cd = np.mod(cd, n[d]) if box.bc[d] == 0 else np.clip(cd, 0, n[d] - 1)
         out.append(cd)
@@ -118,7 +124,7 @@ def test_lookahead_sort_matches_oracle_bit_exactly(prec, name):
     sort of those cells, recomputed here."""
     box = _boxes()[name]()
     eng = _engine(box, prec)
-    t = 0.5 * box.dt * 7.0   # several cells for the fast particles, so wraps and clamps occur
+    t = 0.5 * box.dt * 7.0   # a face crossed by many particles, so that wraps and clamps occur
     if prec == MIXED:
         eng.set_particles(box.cell, box.off, box.p)
         cells = _lookahead_cells(box, t, prec, cell=box.cell, off=box.off, v=box.p)
