@@ -212,9 +212,13 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _time_engine(eng, dt, steps, warmup, sort_every, torch, per_push=True):
-    """Run warmup + timed steps; returns (total_ms, push_ms_sum, launches)."""
+def _time_engine(eng, dt, steps, warmup, sort_every, torch, per_push=True, lookahead=None):
+    """Run warmup + timed steps; returns (total_ms, push_ms_sum, launches).
+    With a look-ahead (in steps) the sorts here look sort_every times as far
+    ahead, as mhdpic_run's sorts at that cadence do; it is restored after."""
     st = eng.stream
+    if lookahead is not None:
+        eng.set_sort_lookahead(lookahead * dt * max(sort_every, 1))
     for k in range(warmup):
         eng.interp_push(dt, 1)
         eng.apply_feedback(False)
@@ -238,6 +242,8 @@ def _time_engine(eng, dt, steps, warmup, sort_every, torch, per_push=True):
     torch.cuda.synchronize()
     total = start.elapsed_time(end)
     push = sum(a.elapsed_time(b) for a, b in ev) if per_push else float("nan")
+    if lookahead is not None:
+        eng.set_sort_lookahead(lookahead * dt)
     return total, push, eng.launches() - l0
 
 
@@ -475,7 +481,7 @@ def _measure_workload(name, boxes, dt, args, torch, m, dev, stream, peak, peak_k
     eng.run(dt, 20, 0)
     k = eng.sort_cadence()
     torch.cuda.synchronize()
-    _, push_ms, _ = _time_engine(eng, dt, args.steps, args.warmup, k, torch)
+    _, push_ms, _ = _time_engine(eng, dt, args.steps, args.warmup, k, torch, lookahead=args.sort_lookahead)
     for _ in range(args.warmup):
         eng.run(dt, max(k, 1), k)
     torch.cuda.synchronize()
@@ -582,7 +588,8 @@ def run_native(args):
 
     # eager steps, one call each, so that every push kernel is bracketed by
     # events on the library's stream: the push kernel's roofline
-    eager_ms, push_ms, _ = _time_engine(eng, dt, args.steps, args.warmup, args.sort_every, torch)
+    eager_ms, push_ms, _ = _time_engine(eng, dt, args.steps, args.warmup, args.sort_every, torch,
+                                        lookahead=args.sort_lookahead)
     steps_done += args.steps + args.warmup
     # the sort alone (keys, scan, scatter, segment sort, work list), a few calls
     sev0, sev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -852,7 +859,7 @@ def run_native(args):
     if args.fp64_steps > 0:
         e64 = m.Engine(boxes, precision=m.MHDPIC_PREC_FP64, device=dev, stream=stream)
         e64.set_sort_lookahead(args.sort_lookahead * dt)
-        t64, _, _ = _time_engine(e64, dt, args.fp64_steps, 1, args.sort_every, torch)
+        t64, _, _ = _time_engine(e64, dt, args.fp64_steps, 1, args.sort_every, torch, lookahead=args.sort_lookahead)
         v64 = npart * args.fp64_steps / (t64 / 1e3)
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": t64 / args.fp64_steps,
                 "steps": args.fp64_steps, "speedup_mixed_over_fp64": value / world / v64}
@@ -880,7 +887,8 @@ def run_native(args):
         for mem, h2d, d2h in runs:
             eh = m.Engine(boxes, precision=m.MHDPIC_PREC_MIXED, memory=mem, brick=brick, device=dev, stream=stream)
             eh.set_sort_lookahead(args.sort_lookahead * dt)
-            te, _, _ = _time_engine(eh, dt, args.e2e_steps, 1, args.sort_every, torch, per_push=False)
+            te, _, _ = _time_engine(eh, dt, args.e2e_steps, 1, args.sort_every, torch, per_push=False,
+                                    lookahead=args.sort_lookahead)
             eh.close()
             del eh
             torch.cuda.empty_cache()

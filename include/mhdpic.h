@@ -246,7 +246,9 @@ int mhdpic_set_subcycle_sort(mhdpic_ctx *ctx, int32_t every);
  * after moving for time t at its current velocity, instead of its current
  * cell: with t = dt/2 the cell of the half-step position where the next push
  * gathers E, B and deposits the corrector (App. A.2-A.3), so that the push
- * finds its particles in the cells it works on.  Per dimension the cell moves
+ * finds its particles in the cells it works on.  The sorts of mhdpic_run,
+ * made every k steps, look k t ahead (with t = dt/2 the mean half-step
+ * position of the k pushes of the cycle); mhdpic_sort looks t ahead.  Per dimension the cell moves
  * by -1, 0 or +1 (a half step moves a particle well under one cell): +1 when
  * v_d > 0 and (a_d v_d)^2 >= ((1 - o_d)(1 - o_d)) g2, -1 when v_d < 0 and
  * (a_d v_d)^2 > (o_d o_d) g2, with g2 = 1 + v^2 w (gamma^2), v^2 =

@@ -84,9 +84,12 @@ struct mhdpic_ctx {
     int64_t fcells = 0;
     unsigned char *tmaps = nullptr;   // device, 2 CUtensorMap (128 B) per box
     bool tma_ok = false;              // the maps could be encoded for this layout
-    // look-ahead sort: per box {t/dx, t/dy, t/dz, 1/C^2} in FP32 (device copy in k.sort_k)
+    // look-ahead sort: per box {t/dx, t/dy, t/dz, 1/C^2} in FP32 (device copy
+    // in k.sort_k) for the look-ahead in use, k.sort_ahead; the caller's
+    // look-ahead per sort (mhdpic_sort), scaled by the cadence in mhdpic_run
     std::vector<float4> sort_k_host;
     float4 *sort_k = nullptr;
+    double ahead_user = 0.0;
     std::vector<BoxDev> boxes;
     std::vector<int64_t> part_start, cell_start, brick_start;
     std::vector<void *> allocs;
@@ -422,6 +425,46 @@ int setup_tensor_maps(mhdpic_ctx *c)
     k.tma = 1;
     c->tma_ok = true;
     return MHDPIC_OK;
+}
+
+// Make t the look-ahead of the next sorts: the FP32 key constants of every
+// box, each rounded once to FP32 from its exact double (t/dx) or from two
+// correctly rounded FP32 operations (1/(C C)).  Not during a capture.
+int apply_lookahead(mhdpic_ctx *c, double t)
+{
+    if (t == c->k.sort_ahead)
+        return MHDPIC_OK;
+    for (int b = 0; b < c->nbox; ++b) {
+        const BoxDev &bd = c->boxes[b];
+        const float C = (float)bd.C;
+        const float C2 = C * C;
+        c->sort_k_host[b] = make_float4((float)(t * bd.inv_dx[0]), (float)(t * bd.inv_dx[1]),
+                                        (float)(t * bd.inv_dx[2]), 1.f / C2);
+    }
+    CK(cudaMemcpyAsync(c->sort_k, c->sort_k_host.data(), sizeof(float4) * c->nbox, cudaMemcpyHostToDevice,
+                       c->stream));
+    c->k.sort_ahead = t;
+    return MHDPIC_OK;
+}
+
+// The sort (mhdpic_sort) with whatever look-ahead is in use.
+int do_sort(mhdpic_ctx *c, int64_t *perm_out, int32_t *counts_out)
+{
+    int rc;
+    if ((rc = copy_particles(c, true)))
+        return rc;
+    // a permutation asked for is relative to the order the caller sees
+    if (perm_out && (rc = materialize(c)))
+        return rc;
+    if ((rc = check_launch(c, launch_sort(c->k, c->s, perm_out, counts_out, c->stream))))
+        return rc;
+    c->pending = true;
+    // refresh the densest-cell count used by the corrector scales
+    if ((rc = check_launch(c, launch_max_count(c->k, c->s, c->stream))))
+        return rc;
+    if (c->mem == MHDPIC_MEM_HOST && (rc = materialize(c)))
+        return rc;
+    return copy_particles(c, false);
 }
 
 // Charge/current deposit of the current particles into moments buffer cur.
@@ -794,20 +837,9 @@ int mhdpic_sort(mhdpic_ctx *c, int64_t *perm_out, int32_t *counts_out)
     if (!c || !c->valid)
         return fail(MHDPIC_E_STATE, "invalid context");
     int rc;
-    if ((rc = copy_particles(c, true)))
+    if ((rc = apply_lookahead(c, c->ahead_user)))
         return rc;
-    // a permutation asked for is relative to the order the caller sees
-    if (perm_out && (rc = materialize(c)))
-        return rc;
-    if ((rc = check_launch(c, launch_sort(c->k, c->s, perm_out, counts_out, c->stream))))
-        return rc;
-    c->pending = true;
-    // refresh the densest-cell count used by the corrector scales
-    if ((rc = check_launch(c, launch_max_count(c->k, c->s, c->stream))))
-        return rc;
-    if (c->mem == MHDPIC_MEM_HOST && (rc = materialize(c)))
-        return rc;
-    return copy_particles(c, false);
+    return do_sort(c, perm_out, counts_out);
 }
 
 int mhdpic_interp_push(mhdpic_ctx *c, double dt, int32_t nsub)
@@ -1168,19 +1200,12 @@ int mhdpic_set_sort_lookahead(mhdpic_ctx *c, double t)
         return fail(MHDPIC_E_STATE, "invalid context");
     if (!std::isfinite(t))
         return fail(MHDPIC_E_ARG, "the look-ahead time must be finite");
-    // each constant rounded once to FP32 from its exact double (t/dx) or from
-    // two correctly rounded FP32 operations (1/(C C))
-    for (int b = 0; b < c->nbox; ++b) {
-        const BoxDev &bd = c->boxes[b];
-        const float C = (float)bd.C;
-        const float C2 = C * C;
-        c->sort_k_host[b] = make_float4((float)(t * bd.inv_dx[0]), (float)(t * bd.inv_dx[1]),
-                                        (float)(t * bd.inv_dx[2]), 1.f / C2);
+    c->ahead_user = t;
+    if (c->graph) {   // a captured cycle holds the sorts' look-ahead
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
     }
-    CK(cudaMemcpyAsync(c->sort_k, c->sort_k_host.data(), sizeof(float4) * c->nbox, cudaMemcpyHostToDevice,
-                       c->stream));
-    c->k.sort_ahead = t;
-    return MHDPIC_OK;
+    return apply_lookahead(c, t);
 }
 
 int mhdpic_set_subcycle_sort(mhdpic_ctx *c, int32_t every)
@@ -1293,7 +1318,7 @@ int run_one_step(mhdpic_ctx *c, double dt, int k)
     }
     if (++c->step_in_cycle >= k) {
         c->step_in_cycle = 0;
-        if ((rc = mhdpic_sort(c, nullptr, nullptr)))
+        if ((rc = do_sort(c, nullptr, nullptr)))
             return rc;
     }
     return MHDPIC_OK;
@@ -1329,8 +1354,9 @@ int tune_sort_cadence(mhdpic_ctx *c, double dt, int32_t *steps_left)
         const int reps = (4 + k - 1) / k;
         if (*steps_left < reps * k)
             break;
-        // align to the start of a cycle of length k (sort now)
-        if ((rc = mhdpic_sort(c, nullptr, nullptr)))
+        // align to the start of a cycle of length k (sort now), the sorts
+        // looking k times as far ahead
+        if ((rc = apply_lookahead(c, c->ahead_user * k)) || (rc = do_sort(c, nullptr, nullptr)))
             return rc;
         c->step_in_cycle = 0;
         CK(cudaEventRecord(ev.e[0], c->stream));
@@ -1429,6 +1455,10 @@ int mhdpic_run(mhdpic_ctx *c, double dt, int32_t nsteps, int32_t sort_every)
     const int k = sort_every ? sort_every : c->tuned_k;
     if (c->step_in_cycle >= k)
         c->step_in_cycle = 0;
+    // the sorts of a k-step cycle look k times as far ahead: with a look-ahead
+    // of dt/2, the mean half-step position of the cycle's pushes
+    if ((rc = apply_lookahead(c, c->ahead_user * k)))
+        return rc;
     // finish the current cycle eagerly (and a first step when the next
     // moments buffer has not been cleared by a staging pass yet), up to a
     // sort whose permutation the next push applies: the state every cycle

@@ -537,6 +537,36 @@ def test_graph_replayed_run_equals_eager_steps(k):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("k", [1, 3])
+def test_run_sorts_look_ahead_over_the_whole_cycle(k):
+    """With a look-ahead t set, mhdpic_run's sorts every k steps look k t
+    ahead: its steps equal, bit for bit and in the same particle order, eager
+    steps sorted by mhdpic_sort with a look-ahead of k t."""
+    box = tilt_B(wl.alfvenic_beam_3d(n=12, ppc=6, nmodes=8, seed=46), 46)
+    stream = torch.cuda.Stream()
+    t = 0.5 * box.dt
+    outs = []
+    for mode in ("eager", "graph"):
+        eng = m.Engine([box], precision=MIXED, stream=stream)
+        nsteps = 2 * k * 2 + 1
+        if mode == "eager":
+            eng.set_sort_lookahead(k * t)
+            for s in range(nsteps):
+                eng.step(box.dt)
+                if (s + 1) % k == 0:
+                    eng.sort()
+        else:
+            eng.set_sort_lookahead(t)
+            eng.run(box.dt, nsteps, k)
+        stream.synchronize()
+        outs.append((mixed_rows(eng), eng.mom.cpu().numpy(), eng.deposits(1).cpu().numpy(),
+                     eng.fields().cpu().numpy()))
+        assert eng.status() == 0
+        eng.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("fail_at", [1, 2, 5])
 def test_failed_graph_capture_leaves_the_context_as_it_was(fail_at):
     """A launch failure injected on the host inside the graph capture of
