@@ -15,15 +15,22 @@
 //    128-bit and 64-bit field loads.  (Giving each lane exactly one cell's
 //    particles removes more conflicts but idles a quarter of the lanes, since
 //    cell counts vary; the even split measured 11% faster.)
-//  * Fixed point in the tile: each contribution x (in tile units) is split
-//    exactly into hi = round(x / 2^KLO) and lo = x - hi 2^KLO with one FFMA
-//    against 1.5*2^(23+KLO), one FFMA for the residual and one FADD against
-//    1.5*2^23, and hi, lo are added to two int32 planes.  The tile scale is
-//    sized for the largest item (ITEM_MAX_PARTICLES), so neither plane can
-//    overflow and every item of a box rounds a contribution alike; the flush
+//  * Fixed point in the tile: each contribution x = a w (in tile units, the
+//    product exact inside the FMA) is the integer round(x) split into
+//    hi = round(x / 2^KLO) and lo = round(x - hi 2^KLO), two FFMAs and one
+//    FADD in all: t = fma(a, w, M_H) holds hi in its bit pattern (M_H =
+//    1.5*2^(23+KLO) fixes the exponent), and fma(a, w, (M_H + M) - t) with
+//    M = 1.5*2^23 holds lo (the addend is exact and the residual is rounded
+//    once).  The planes add the two bit patterns as they are, each carrying
+//    a constant offset (the bit pattern of M_H, of M); every deposit also
+//    counts itself once at its stencil corner, and the flush removes the
+//    offsets of the contributions a slot received (mod 2^32) before it
 //    rebuilds hi 2^KLO + lo in int64 and shifts it to the global scale.  The
-//    charge density (all contributions positive, no cancellation) uses the hi
-//    plane alone.
+//    tile scale is sized for the largest item (ITEM_MAX_PARTICLES), so
+//    neither plane can overflow and every item of a box rounds a
+//    contribution alike.  The charge density (all contributions positive, no
+//    cancellation) uses the hi plane alone, as round(x) from one FFMA
+//    against M.
 //  * A particle whose stencil leaves the tile adds the very integers the tile
 //    would have held, shifted, straight to the int64 global accumulators, so
 //    the sums are exact, independent of the order of the additions and of how
@@ -50,7 +57,11 @@ constexpr int MAGIC_BITS = 0x4B400000;
 constexpr int KLO = 19;               // bits of the low word of a split contribution
 constexpr float MAGIC_HI = 6597069766656.0f;  // 1.5 * 2^(23+KLO)
 constexpr int MAGIC_HI_BITS = 0x54C00000;     // bit pattern of MAGIC_HI
+constexpr float MAGIC_HI_LO = 6597082349568.0f;  // MAGIC_HI + MAGIC, exact (bits 2^42 .. 2^22)
 constexpr int NPLANE = 2 * NCH;       // hi planes 0..7, lo planes 8..15
+constexpr int CNT_C = NPLANE;         // contributions of the corrector deposit, by stencil corner
+constexpr int CNT_M = NPLANE + 1;     // the same for the moments deposit
+constexpr int NTILE = NPLANE + 2;     // int planes of the deposit tile
 
 struct MixedConst {
     float hdx[3];    // dt / (2 dx)
@@ -183,20 +194,69 @@ __device__ __noinline__ F6 gather_global(const Ctx &c, const BoxDev &b, int ci0,
     return r;
 }
 
-// x = a * wx split exactly into hi * 2^KLO + lo, both added to the tile
+// round(a * wx) as the words hi + MAGIC_HI_BITS and lo + MAGIC_BITS, with
+// hi = round(a wx / 2^KLO) and lo = round(a wx - hi 2^KLO), |lo| <= 2^(KLO-1):
+// the one place the tile path and the global path compute them
+__device__ __forceinline__ void split_words(float a, float wx, int &hb, int &lb)
+{
+    const float t = fmaf(a, wx, MAGIC_HI);
+    hb = __float_as_int(t);
+    lb = __float_as_int(fmaf(a, wx, MAGIC_HI_LO - t));
+}
+
+// round(a * wx) as one word, plus MAGIC_BITS (|a wx| < 2^22)
+__device__ __forceinline__ int single_word(float a, float wx)
+{
+    return __float_as_int(fmaf(a, wx, MAGIC));
+}
+
+// both words of a split contribution added to the tile as they are
 __device__ __forceinline__ void add_split(int *hi_plane, int *lo_plane, int s, float a, float wx)
 {
-    float t = fmaf(a, wx, MAGIC_HI);
-    int hi = __float_as_int(t) - MAGIC_HI_BITS;
-    float r = fmaf(a, wx, MAGIC_HI - t);   // a wx - hi 2^KLO, |r| <= 2^(KLO-1)
-    int lo = __float_as_int(r + MAGIC) - MAGIC_BITS;
-    atomicAdd(hi_plane + s, hi);
-    atomicAdd(lo_plane + s, lo);
+    int hb, lb;
+    split_words(a, wx, hb, lb);
+    atomicAdd(hi_plane + s, hb);
+    atomicAdd(lo_plane + s, lb);
+}
+
+// Contributions tile cell (tx, ty, tz) received from one deposit: the counts
+// (plane CNT_C or CNT_M) of the stencil corners at most 2 cells below it.
+__device__ __forceinline__ uint32_t slot_count(const Ctx &c, const int *sD, int plane, int tx, int ty, int tz, int D)
+{
+    const int *cnt = sD + plane * c.tile_slots;
+    uint32_t k = 0u;
+    for (int dz = 0; dz < (D == 3 ? 3 : 1); ++dz) {
+        if (tz - dz < 0)
+            break;
+        for (int dy = 0; dy < 3; ++dy) {
+            if (ty - dy < 0)
+                break;
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                if (tx - dx < 0)
+                    break;
+                k += (uint32_t)cnt[(tx - dx) + c.ts[1] * (ty - dy) + c.ts[2] * (tz - dz)];
+            }
+        }
+    }
+    return k;
+}
+
+// channel ch of tile slot s rebuilt as the sum of its rounded contributions
+__device__ __forceinline__ long long slot_value(const int *sD, int S, int s, int ch, uint32_t kc, uint32_t km)
+{
+    const uint32_t k = ch < CH_N ? kc : km;
+    const int hi = (int)((uint32_t)sD[ch * S + s] - k * (uint32_t)(ch == CH_N ? MAGIC_BITS : MAGIC_HI_BITS));
+    if (ch == CH_N)
+        return hi;
+    const int lo = (int)((uint32_t)sD[(NCH + ch) * S + s] - k * (uint32_t)MAGIC_BITS);
+    return (long long)hi * (1ll << KLO) + lo;
 }
 
 // Four channels into the tile; q carries the tile scale.  Every channel is
 // split into hi and lo words except the charge density, whose contributions
-// are all positive and never cancel.
+// are all positive and never cancel.  The words carry their offsets; the
+// deposit counts itself at its stencil corner (base) for the flush.
 template <int D>
 __device__ __forceinline__ void deposit_tile(const Ctx &c, int base, const Wts &w, const float q[4], int ch0,
                                              int *__restrict__ sD)
@@ -221,7 +281,7 @@ __device__ __forceinline__ void deposit_tile(const Ctx &c, int base, const Wts &
             for (int cx = 0; cx < 3; ++cx) {
                 int s = base + cx + SY * cy + SZ * cz;
                 if (first_single)
-                    atomicAdd(h0 + s, __float_as_int(fmaf(a0, w.x[cx], MAGIC)) - MAGIC_BITS);
+                    atomicAdd(h0 + s, single_word(a0, w.x[cx]));
                 else
                     add_split(h0, l0, s, a0, w.x[cx]);
                 add_split(h1, l1, s, a1, w.x[cx]);
@@ -229,6 +289,7 @@ __device__ __forceinline__ void deposit_tile(const Ctx &c, int base, const Wts &
                 add_split(h3, l3, s, a3, w.x[cx]);
             }
         }
+    atomicAdd(sD + (first_single ? CNT_M : CNT_C) * S + base, 1);
 }
 
 // Four channels into the int64 global accumulators as exactly the integers
@@ -256,13 +317,11 @@ __device__ __noinline__ void deposit_global_split(const Ctx &c, const BoxDev &b,
                     const float a = q[k] * wyz;
                     long long v;
                     if (ch0 + k == CH_N) {
-                        v = __float_as_int(fmaf(a, w.x[cx], MAGIC)) - MAGIC_BITS;
+                        v = single_word(a, w.x[cx]) - MAGIC_BITS;
                     } else {
-                        const float t = fmaf(a, w.x[cx], MAGIC_HI);
-                        const int hi = __float_as_int(t) - MAGIC_HI_BITS;
-                        const float r = fmaf(a, w.x[cx], MAGIC_HI - t);
-                        const int lo = __float_as_int(r + MAGIC) - MAGIC_BITS;
-                        v = (long long)hi * (1ll << KLO) + lo;
+                        int hb, lb;
+                        split_words(a, w.x[cx], hb, lb);
+                        v = (long long)(hb - MAGIC_HI_BITS) * (1ll << KLO) + (lb - MAGIC_BITS);
                     }
                     if (v)
                         red_add(g0 + k * nc + g, (long long)((unsigned long long)v << ksh[k]));
@@ -383,7 +442,7 @@ __device__ __forceinline__ void store_particle(const Ctx &c, int64_t j, int32_t 
     c.vel[j] = make_float4(v[0], v[1], v[2], __uint_as_float(res));
 }
 
-// The push's dynamic shared memory: the deposit tile (NPLANE int planes of
+// The push's dynamic shared memory: the deposit tile (NTILE int planes of
 // `slots`), the field tile (a float4 and a float2 plane of `fslots`, each on a
 // 128-byte boundary for the tensor copies), then the particle ring (2-D).
 struct PushLayout {
@@ -395,7 +454,7 @@ __host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) / 128
 __host__ __device__ inline PushLayout push_layout(int slots, int fslots)
 {
     PushLayout l{};
-    l.fa = align128(sizeof(int) * NPLANE * (size_t)slots);
+    l.fa = align128(sizeof(int) * NTILE * (size_t)slots);
     l.fb = align128(l.fa + sizeof(float4) * (size_t)fslots);
     l.ring = align128(l.fb + sizeof(float2) * (size_t)fslots);
     return l;
@@ -716,8 +775,8 @@ __device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restr
                 sFb[sl] = __ldg(c.fb + f);
             }
         }
-        // clear the deposit tile
-        for (int s = threadIdx.x; s < NPLANE * S; s += PUSH_THREADS)
+        // clear the deposit tile and its counts
+        for (int s = threadIdx.x; s < NTILE * S; s += PUSH_THREADS)
             sD[s] = 0;
         if (threadIdx.x == 0)
             item_const(b, dt, it.p1 - it.p0, D, s_k);
@@ -795,19 +854,20 @@ __device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restr
             atomicMax(&c.stats[it.box].vmax, vb);
         __syncthreads();
 
-        // rebuild hi 2^KLO + lo and shift the tile into the global accumulators
+        // remove the offsets, rebuild hi 2^KLO + lo and shift the tile into
+        // the global accumulators
         for (int t = threadIdx.x; t < c.tile_vol; t += PUSH_THREADS) {
             int tx = t % c.tile[0], r = t / c.tile[0];
             int ty = r % c.tile[1], tz = r / c.tile[1];
             int64_t g = tile_global(c, b, gm, tx, ty, tz, D);
             int s = tile_slot(c, tx, ty, tz);
+            const uint32_t kc = slot_count(c, sD, CNT_C, tx, ty, tz, D);
+            const uint32_t km = FULL ? slot_count(c, sD, CNT_M, tx, ty, tz, D) : 0u;
 #pragma unroll
             for (int ch = 0; ch < NCH; ++ch) {
                 if (!FULL && ch >= CH_N)
                     break;
-                long long v = (long long)sD[ch * S + s] * (1ll << KLO) + sD[(NCH + ch) * S + s];
-                if (ch == CH_N)
-                    v = sD[ch * S + s];
+                const long long v = slot_value(sD, S, s, ch, kc, km);
                 if (v) {
                     unsigned long long *dst = ch < CH_N ? c.corr + ch * c.nc + g : mout + (ch - CH_N) * c.nc + g;
                     atomicAdd(dst, (unsigned long long)v << k.ksh[ch]);
@@ -936,6 +996,8 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_deposit_mixed(Ctx c, const Wor
             sD[s] = 0;
         for (int s = threadIdx.x + (NCH + CH_N) * S; s < NPLANE * S; s += PUSH_THREADS)
             sD[s] = 0;
+        for (int s = threadIdx.x; s < S; s += PUSH_THREADS)
+            sD[CNT_M * S + s] = 0;
         if (threadIdx.x == 0)
             item_const(b, 0.f, it.p1 - it.p0, D, s_k);
         __syncthreads();
@@ -963,11 +1025,10 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_deposit_mixed(Ctx c, const Wor
             int ty = r % c.tile[1], tz = r / c.tile[1];
             int64_t g = tile_global(c, b, gm, tx, ty, tz, D);
             int s = tile_slot(c, tx, ty, tz);
+            const uint32_t km = slot_count(c, sD, CNT_M, tx, ty, tz, D);
 #pragma unroll
             for (int ch = CH_N; ch < NCH; ++ch) {
-                long long v = (long long)sD[ch * S + s] * (1ll << KLO) + sD[(NCH + ch) * S + s];
-                if (ch == CH_N)
-                    v = sD[ch * S + s];
+                const long long v = slot_value(sD, S, s, ch, 0u, km);
                 if (v)
                     atomicAdd(mout + (ch - CH_N) * c.nc + g, (unsigned long long)v << k.ksh[ch]);
             }
@@ -1023,7 +1084,7 @@ int push_blocks_per_sm_mixed(const Ctx &c)
 int launch_deposit_mixed(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur, int grid_blocks,
                          cudaStream_t st)
 {
-    const size_t bytes = sizeof(int) * NPLANE * (size_t)c.tile_slots;
+    const size_t bytes = sizeof(int) * NTILE * (size_t)c.tile_slots;
     cudaMemsetAsync(work_ctr, 0, sizeof(int32_t), st);
     if (c.ndim == 3) {
         cudaFuncSetAttribute(k_deposit_mixed<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, PUSH_SMEM_LIMIT);
