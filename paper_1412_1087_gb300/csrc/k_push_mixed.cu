@@ -45,6 +45,7 @@
 //  * 2-D: each thread copies its next two particles' records into a
 //    three-stage shared-memory ring with 16-byte cp.async while it pushes
 //    the current one.
+#include "async_copy.cuh"
 #include "cells_common.cuh"
 #include "push_common.cuh"
 
@@ -649,48 +650,6 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
 // per work item, completed on a shared-memory mbarrier.  Each wait has a time
 // limit; a copy that does not complete raises MHDPIC_ST_COPY_TIMEOUT.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned smem_u32(const void *p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ long long timer_ns()
-{
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(ok)
-                 : "r"(smem_u32(bar)), "r"(parity)
-                 : "memory");
-    return ok != 0;
-}
-
-// true when the phase completed within limit_ns
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long limit_ns)
-{
-    const long long t0 = timer_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (timer_ns() - t0 > limit_ns)
-            return false;
-    return true;
-}
 
 // The copies read a box of the padded planes starting at the tile's first
 // cell; the innermost coordinate counts floats (4 per cell in plane fa, 2 in
@@ -709,8 +668,6 @@ __device__ __forceinline__ void tma_tile(void *dst, const unsigned char *tmap, i
                      "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
                      : "memory");
 }
-
-constexpr long long COPY_LIMIT_NS = 1000000000ll;   // one second
 
 // The push over the work items of the last sort, taken from an atomic
 // counter by the calling kernel's persistent blocks (smem: the dynamic shared
@@ -757,7 +714,7 @@ __device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restr
         if (c.tma) {
             if (threadIdx.x == 0) {
                 // the previous item's reads of the tile ended at the barrier before
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                fence_proxy_async();
                 mbar_expect_tx(&s_bar, copy_bytes);
                 const unsigned char *tm = c.tmaps + (size_t)it.box * 256;
                 const int x0 = gm.org[0] + FGHOST, y0 = gm.org[1] + FGHOST, z0 = gm.org[2] + FGHOST;

@@ -15,6 +15,7 @@
 //      most ITEM_MAX_PARTICLES.
 #include <climits>
 
+#include "async_copy.cuh"
 #include "device_common.cuh"
 
 namespace mhdpic {
@@ -195,6 +196,37 @@ __device__ __forceinline__ int32_t key_f64(const Ctx &c, const BoxDev &b, int bx
 // independent loads (and atomics) in flight hide their latency.
 constexpr int SORT_ILP = 4;
 
+// Runs of equal keys in consecutive lanes (the input is nearly sorted) take
+// one atomic per run, made by the run's first lane; the rank inside the run
+// is the lane offset.  Lanes outside `active` take no part; a negative key
+// takes no atomic.
+struct RunSlot {
+    int start;   // first lane of the run
+    int base;    // first slot of the run (at the first lane)
+};
+
+__device__ __forceinline__ RunSlot run_reserve(int32_t key, int lane, unsigned active, int32_t *count)
+{
+    const int prev = __shfl_up_sync(active, key, 1);
+    const bool head = lane == 0 || !((active >> (lane - 1)) & 1u) || prev != key;
+    const unsigned heads = __ballot_sync(active, head);
+    RunSlot r;
+    r.start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));    // last head at or below lane
+    const unsigned after = heads & ~(0xffffffffu >> (31 - lane));  // heads above lane
+    const int end = after ? __ffs(after) - 1 : 32;
+    const unsigned tail = (end < 32 ? (1u << end) : 0u) - 1u;      // lanes below end
+    const int len = __popc(active & tail & ~((1u << r.start) - 1u));
+    r.base = 0;
+    if (head && key >= 0)
+        r.base = atomicAdd(count + key, len);
+    return r;
+}
+
+__device__ __forceinline__ int32_t run_slot(const RunSlot &r, int lane, unsigned active)
+{
+    return __shfl_sync(active, r.base, r.start) + (lane - r.start);
+}
+
 template <int PREC>
 __global__ void k_sort_keys(Ctx c, int32_t *__restrict__ count, int32_t *__restrict__ pkey,
                             int32_t *__restrict__ pslot)
@@ -245,32 +277,122 @@ __global__ void k_sort_keys(Ctx c, int32_t *__restrict__ count, int32_t *__restr
                 key[u] = i < c.np ? key_f64(c, c.boxes[bx], bx, i) : -1 - lane;
             }
         }
-        // runs of equal keys in consecutive lanes (the input is nearly
-        // sorted) take one atomic per run; the rank inside the run is the
-        // lane offset
-        int start[SORT_ILP], base[SORT_ILP];
+        RunSlot rs[SORT_ILP];
+#pragma unroll
+        for (int u = 0; u < SORT_ILP; ++u)
+            rs[u] = run_reserve(key[u], lane, active, count);
 #pragma unroll
         for (int u = 0; u < SORT_ILP; ++u) {
-            const int prev = __shfl_up_sync(active, key[u], 1);
-            const bool head = lane == 0 || !((active >> (lane - 1)) & 1u) || prev != key[u];
-            const unsigned heads = __ballot_sync(active, head);
-            start[u] = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));   // last head at or below lane
-            const unsigned after = heads & ~(0xffffffffu >> (31 - lane));  // heads above lane
-            const int end = after ? __ffs(after) - 1 : 32;
-            const unsigned tail = (end < 32 ? (1u << end) : 0u) - 1u;      // lanes below end
-            const int len = __popc(active & tail & ~((1u << start[u]) - 1u));
-            base[u] = 0;
-            if (head && key[u] >= 0)
-                base[u] = atomicAdd(count + key[u], len);
-        }
-#pragma unroll
-        for (int u = 0; u < SORT_ILP; ++u) {
-            const int b0 = __shfl_sync(active, base[u], start[u]);
+            const int32_t slot = run_slot(rs[u], lane, active);
             const int64_t i = i0 + u * stride;
             if (i < c.np) {
                 pkey[i] = key[u];
-                pslot[i] = b0 + (lane - start[u]);
+                pslot[i] = slot;
             }
+        }
+    }
+}
+
+// Mixed precision, records staged: the particle records stream through a
+// ring of KEY_STAGES shared-memory stages of KEY_CHUNK particles, each filled
+// by one bulk copy per record array that the block's first thread issues
+// KEY_STAGES chunks ahead, so the loads of later chunks are in flight while
+// the keys and the atomics of this one are done.  (Two stages, 32 KB, let 5
+// blocks share an SM; 3 and 4 stages measured slower at 128^3 x 32.)  A block takes the chunks
+// blockIdx.x, blockIdx.x + gridDim.x, ...; each warp's 32 lanes take 32
+// consecutive particles, as the run detection needs.
+constexpr int KEY_THREADS = 256;
+constexpr int KEY_PER_THREAD = 2;
+constexpr int KEY_CHUNK = KEY_THREADS * KEY_PER_THREAD;
+constexpr int KEY_STAGES = 2;
+constexpr size_t KEY_SMEM = (size_t)KEY_STAGES * KEY_CHUNK * (sizeof(int4) + sizeof(float4));
+
+// Thread 0: the copies of chunk `chunk` into one stage (the velocities only
+// when the key looks ahead).
+__device__ __forceinline__ void issue_records(const Ctx &c, int64_t chunk, int4 *dp, float4 *dv, bool ahead,
+                                              uint64_t *bar)
+{
+    const int64_t p0 = chunk * KEY_CHUNK;
+    const int64_t left = c.np - p0;
+    const unsigned bytes = (unsigned)(left < KEY_CHUNK ? left : KEY_CHUNK) * 16u;
+    mbar_expect_tx(bar, ahead ? 2u * bytes : bytes);
+    bulk_copy(dp, c.pos + p0, bytes, bar);
+    if (ahead)
+        bulk_copy(dv, c.vel + p0, bytes, bar);
+}
+
+__global__ void __launch_bounds__(KEY_THREADS) k_sort_keys_staged(Ctx c, int32_t *__restrict__ count,
+                                                                  int32_t *__restrict__ pkey,
+                                                                  int32_t *__restrict__ pslot)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    int4 *sp = reinterpret_cast<int4 *>(smem);
+    float4 *sv = reinterpret_cast<float4 *>(smem + (size_t)KEY_STAGES * KEY_CHUNK * sizeof(int4));
+    __shared__ __align__(8) uint64_t full[KEY_STAGES];
+    const int lane = threadIdx.x & 31;
+    const bool ahead = c.sort_ahead != 0.0;
+    const int64_t nchunk = (c.np + KEY_CHUNK - 1) / KEY_CHUNK;
+    const int64_t mine = (int64_t)blockIdx.x < nchunk ? (nchunk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < KEY_STAGES; ++st)
+            mbar_init(&full[st]);
+        fence_proxy_async();
+        for (int64_t k = 0; k < KEY_STAGES && k < mine; ++k)
+            issue_records(c, blockIdx.x + k * gridDim.x, sp + k * KEY_CHUNK, sv + k * KEY_CHUNK, ahead, &full[k]);
+    }
+    __syncthreads();
+    KeyBox kb;
+    load_keybox(c, 0, kb);
+    for (int64_t k = 0; k < mine; ++k) {
+        const int st = (int)(k % KEY_STAGES);
+        const bool ok = mbar_wait(&full[st], (unsigned)((k / KEY_STAGES) & 1), COPY_LIMIT_NS);
+        if (__syncthreads_or(!ok)) {
+            // give up the launch, after the copies in flight have had their time
+            if (threadIdx.x == 0) {
+                set_status(c.status, MHDPIC_ST_COPY_TIMEOUT);
+                for (int64_t j = k; j < mine && j < k + KEY_STAGES; ++j)
+                    mbar_wait(&full[j % KEY_STAGES], (unsigned)((j / KEY_STAGES) & 1), COPY_LIMIT_NS);
+            }
+            return;
+        }
+        const int64_t p0 = (blockIdx.x + k * gridDim.x) * (int64_t)KEY_CHUNK;
+        const int n = (int)(c.np - p0 < KEY_CHUNK ? c.np - p0 : KEY_CHUNK);
+        int cbox = 0;   // the chunk's box, or -1 when it spans several
+        if (c.nbox > 1) {
+            const int b0 = find_box(c.box_part_start, c.nbox, p0);
+            cbox = b0 == find_box(c.box_part_start, c.nbox, p0 + n - 1) ? b0 : -1;
+        }
+        int32_t key[KEY_PER_THREAD];
+#pragma unroll
+        for (int u = 0; u < KEY_PER_THREAD; ++u) {
+            const int p = u * KEY_THREADS + threadIdx.x;
+            key[u] = -1 - lane;   // past the end: a run of its own, no atomic
+            if (p < n) {
+                const int bx = cbox >= 0 ? cbox : find_box(c.box_part_start, c.nbox, p0 + p);
+                if (bx != kb.box)
+                    load_keybox(c, bx, kb);
+                const float4 vs = ahead ? sv[st * KEY_CHUNK + p] : make_float4(0.f, 0.f, 0.f, 0.f);
+                key[u] = key_mixed(c, kb, sp[st * KEY_CHUNK + p], vs);
+            }
+        }
+        RunSlot rs[KEY_PER_THREAD];
+#pragma unroll
+        for (int u = 0; u < KEY_PER_THREAD; ++u)
+            rs[u] = run_reserve(key[u], lane, 0xffffffffu, count);
+#pragma unroll
+        for (int u = 0; u < KEY_PER_THREAD; ++u) {
+            const int32_t slot = run_slot(rs[u], lane, 0xffffffffu);
+            const int p = u * KEY_THREADS + threadIdx.x;
+            if (p < n) {
+                pkey[p0 + p] = key[u];
+                pslot[p0 + p] = slot;
+            }
+        }
+        __syncthreads();   // every thread has read the stage
+        if (threadIdx.x == 0 && k + KEY_STAGES < mine) {
+            fence_proxy_async();
+            issue_records(c, blockIdx.x + (k + KEY_STAGES) * gridDim.x, sp + st * KEY_CHUNK, sv + st * KEY_CHUNK,
+                          ahead, &full[st]);
         }
     }
 }
@@ -445,16 +567,18 @@ __device__ __forceinline__ void warp_bitonic(int (&v)[E], int lane)
     }
 }
 
-// Sort of one segment [s, s + n), n <= 32 E, in registers; a segment already
-// in ascending order is left alone.
+// Sort of one segment [s, s + n), n <= 32 E, in registers, read from src
+// (perm + s itself, or a copy of it); a segment already in ascending order is
+// left alone.
 template <int E>
-__device__ __forceinline__ void warp_sort_segment(int32_t *__restrict__ perm, int s, int n, int lane)
+__device__ __forceinline__ void warp_sort_segment(const int32_t *src, int32_t *__restrict__ perm, int s, int n,
+                                                  int lane)
 {
     int v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int i = e * 32 + lane;
-        v[e] = i < n ? perm[s + i] : INT_MAX;
+        v[e] = i < n ? src[i] : INT_MAX;
     }
     bool ok = true;
 #pragma unroll
@@ -574,6 +698,60 @@ __device__ __forceinline__ bool warp_merge_runs(const int32_t *a, int n, int32_t
 // Segments of up to 128 are sorted in registers, up to WARP_SORT_MAX in the
 // warp's shared memory (by their runs when they have at most MERGE_RUNS, else
 // by a bitonic network); longer ones are listed for k_sort_big.
+// One key's segment [s, s + n) read from perm (the warp's buffer a is free).
+__device__ __forceinline__ void sort_one_segment(int64_t k, int s, int n, int32_t *__restrict__ perm, int32_t *a,
+                                                 int *hp, int32_t *__restrict__ big_list,
+                                                 int32_t *__restrict__ big_count, int lane)
+{
+    if (n <= 1)
+        return;
+    if (n <= 32) {
+        warp_sort_segment<1>(perm + s, perm, s, n, lane);
+    } else if (n <= 64) {
+        warp_sort_segment<2>(perm + s, perm, s, n, lane);
+    } else if (n <= 128) {
+        warp_sort_segment<4>(perm + s, perm, s, n, lane);
+    } else if (n <= WARP_SORT_MAX) {
+        int P = 64;
+        while (P < n)
+            P <<= 1;
+        for (int i = lane; i < P; i += 32)
+            a[i] = i < n ? perm[s + i] : INT_MAX;
+        __syncwarp();
+        if (warp_merge_runs(a, n, perm, s, lane, hp))
+            return;
+        for (int kk = 2; kk <= P; kk <<= 1) {
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                for (int i = lane; i < P; i += 32) {
+                    int ixj = i ^ j;
+                    if (ixj > i) {
+                        int x = a[i], y = a[ixj];
+                        bool asc = (i & kk) == 0;
+                        if ((x > y) == asc) {
+                            a[i] = y;
+                            a[ixj] = x;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (int i = lane; i < n; i += 32)
+            perm[s + i] = a[i];
+        __syncwarp();
+    } else if (lane == 0) {
+        int slot = atomicAdd(big_count, 1);
+        big_list[slot] = (int32_t)k;
+    }
+}
+
+// A warp takes SEG_GROUP consecutive keys at a time: their offsets in one
+// load (one per lane), and, when the group's particles fit the warp's buffer,
+// all of them in one coalesced pass, so that the loads of a whole group are in
+// flight together; each segment of up to 128 is then sorted from the buffer.
+// Longer segments, and groups that do not fit, go through sort_one_segment.
+constexpr int SEG_GROUP = 31;
+
 __global__ void __launch_bounds__(256) k_sort_segments(int64_t nkeys, const int32_t *__restrict__ offset,
                                                        int32_t *__restrict__ perm,
                                                        int32_t *__restrict__ big_list,
@@ -584,48 +762,42 @@ __global__ void __launch_bounds__(256) k_sort_segments(int64_t nkeys, const int3
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int32_t *a = buf[wid];
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; k < nkeys; k += nwarps) {
-        int s = offset[k], e = offset[k + 1];
-        int n = e - s;
-        if (n <= 1)
-            continue;
-        if (n <= 32) {
-            warp_sort_segment<1>(perm, s, n, lane);
-        } else if (n <= 64) {
-            warp_sort_segment<2>(perm, s, n, lane);
-        } else if (n <= 128) {
-            warp_sort_segment<4>(perm, s, n, lane);
-        } else if (n <= WARP_SORT_MAX) {
-            int P = 64;
-            while (P < n)
-                P <<= 1;
-            for (int i = lane; i < P; i += 32)
-                a[i] = i < n ? perm[s + i] : INT_MAX;
-            __syncwarp();
-            if (warp_merge_runs(a, n, perm, s, lane, hp[wid]))
-                continue;
-            for (int kk = 2; kk <= P; kk <<= 1) {
-                for (int j = kk >> 1; j > 0; j >>= 1) {
-                    for (int i = lane; i < P; i += 32) {
-                        int ixj = i ^ j;
-                        if (ixj > i) {
-                            int x = a[i], y = a[ixj];
-                            bool asc = (i & kk) == 0;
-                            if ((x > y) == asc) {
-                                a[i] = y;
-                                a[ixj] = x;
-                            }
-                        }
-                    }
-                    __syncwarp();
-                }
+    for (int64_t k0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wid) * SEG_GROUP; k0 < nkeys;
+         k0 += nwarps * SEG_GROUP) {
+        const int nk = (int)(nkeys - k0 < SEG_GROUP ? nkeys - k0 : SEG_GROUP);
+        const int o = lane <= nk ? offset[k0 + lane] : 0;   // offsets of keys k0 .. k0 + nk
+        const int gs = __shfl_sync(0xffffffffu, o, 0), ge = __shfl_sync(0xffffffffu, o, nk);
+        if (ge - gs > WARP_SORT_MAX) {
+            for (int j = 0; j < nk; ++j) {
+                const int s = __shfl_sync(0xffffffffu, o, j), e = __shfl_sync(0xffffffffu, o, j + 1);
+                sort_one_segment(k0 + j, s, e - s, perm, a, hp[wid], big_list, big_count, lane);
             }
-            for (int i = lane; i < n; i += 32)
-                perm[s + i] = a[i];
-            __syncwarp();
-        } else if (lane == 0) {
-            int slot = atomicAdd(big_count, 1);
-            big_list[slot] = (int32_t)k;
+            continue;
+        }
+        for (int i = lane; i < ge - gs; i += 32)
+            a[i] = perm[gs + i];
+        __syncwarp();
+        unsigned longer = 0u;   // keys of the group with segments over 128
+        for (int j = 0; j < nk; ++j) {
+            const int s = __shfl_sync(0xffffffffu, o, j), e = __shfl_sync(0xffffffffu, o, j + 1);
+            const int n = e - s;
+            if (n <= 1)
+                continue;
+            if (n <= 32)
+                warp_sort_segment<1>(a + (s - gs), perm, s, n, lane);
+            else if (n <= 64)
+                warp_sort_segment<2>(a + (s - gs), perm, s, n, lane);
+            else if (n <= 128)
+                warp_sort_segment<4>(a + (s - gs), perm, s, n, lane);
+            else
+                longer |= 1u << j;
+        }
+        __syncwarp();   // the buffer is free again
+        while (longer) {
+            const int j = __ffs(longer) - 1;
+            longer &= longer - 1u;
+            const int s = __shfl_sync(0xffffffffu, o, j), e = __shfl_sync(0xffffffffu, o, j + 1);
+            sort_one_segment(k0 + j, s, e - s, perm, a, hp[wid], big_list, big_count, lane);
         }
     }
 }
@@ -796,6 +968,23 @@ int grid_for(int64_t n, int threads)
     return (int)b;
 }
 
+// Persistent grid of the staged key pass: as many blocks as fit on the
+// device at once, at most one per chunk.
+int key_grid(int64_t np)
+{
+    static int resident = 0;   // blocks of k_sort_keys_staged the device holds at once
+    if (resident == 0) {
+        int dev = 0, nsm = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_sort_keys_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KEY_SMEM);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sort_keys_staged, KEY_THREADS, KEY_SMEM);
+        resident = (per < 1 ? 1 : per) * (nsm < 1 ? 1 : nsm);
+    }
+    const int64_t chunks = (np + KEY_CHUNK - 1) / KEY_CHUNK;
+    return (int)(chunks < resident ? (chunks < 1 ? 1 : chunks) : resident);
+}
+
 }  // namespace
 
 int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *counts_out,
@@ -804,9 +993,10 @@ int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *
     int launches = 0;
     cudaMemsetAsync(s.count, 0, sizeof(int32_t) * (c.nkeys + 2), st);
     if (c.np > 0) {
-        if (c.prec == MHDPIC_PREC_MIXED)
-            k_sort_keys<MHDPIC_PREC_MIXED><<<grid_for(c.np, 256), 256, 0, st>>>(c, s.count, s.pkey, s.pslot);
-        else
+        if (c.prec == MHDPIC_PREC_MIXED) {
+            cudaFuncSetAttribute(k_sort_keys_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KEY_SMEM);
+            k_sort_keys_staged<<<key_grid(c.np), KEY_THREADS, KEY_SMEM, st>>>(c, s.count, s.pkey, s.pslot);
+        } else
             k_sort_keys<MHDPIC_PREC_FP64><<<grid_for(c.np, 256), 256, 0, st>>>(c, s.count, s.pkey, s.pslot);
         ++launches;
     }
@@ -817,7 +1007,7 @@ int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *
         cudaMemsetAsync(s.perm, 0, sizeof(int32_t) * c.np, st);
         k_sort_scatter<<<grid_for(c.np, 256), 256, 0, st>>>(c.np, s.pkey, s.pslot, s.offset, s.perm, c.status);
         cudaMemsetAsync(s.big_count, 0, sizeof(int32_t), st);
-        int64_t nw = (c.nkeys + 7) / 8;
+        const int64_t nw = (c.nkeys + 8 * SEG_GROUP - 1) / (8 * SEG_GROUP);   // blocks of 8 warps
         int gb = (int)(nw < 152 * 16 ? (nw < 1 ? 1 : nw) : 152 * 16);
         k_sort_segments<<<gb, 256, 0, st>>>(c.nkeys, s.offset, s.perm, s.big_list, s.big_count);
         k_sort_big<<<152, 1024, 0, st>>>(s.offset, s.perm, s.big_list, s.big_count, s.pkey, c.status);
