@@ -603,6 +603,94 @@ __device__ __forceinline__ void warp_sort_segment(const int32_t *src, int32_t *_
     }
 }
 
+// Segment [s, s + n), n <= 32 E, read from src, sorted by its runs: the
+// maximal stretches of consecutive particle indices at consecutive slots.
+// They are disjoint index intervals (k_sort_keys gives each run of equal keys
+// in a warp consecutive slots), so every run moves to the number of elements
+// in the runs with smaller first indices.  With more than MERGE_SMALL_RUNS
+// runs the segment is sorted by warp_sort_segment instead; a segment of one
+// run is left alone.
+constexpr int MERGE_SMALL_RUNS = 8;
+
+template <int E>
+__device__ __forceinline__ void warp_merge_small(const int32_t *src, int32_t *__restrict__ perm, int s, int n,
+                                                 int lane)
+{
+    int v[E];
+    unsigned hm[E];   // run heads, element e * 32 + lane in bit lane of hm[e]
+    int nruns = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = e * 32 + lane;
+        v[e] = i < n ? src[i] : 0;
+        int prev = __shfl_up_sync(0xffffffffu, v[e], 1);
+        if (e > 0) {
+            const int last = __shfl_sync(0xffffffffu, v[e > 0 ? e - 1 : 0], 31);
+            if (lane == 0)
+                prev = last;
+        }
+        hm[e] = __ballot_sync(0xffffffffu, i < n && (i == 0 || v[e] != prev + 1));
+        nruns += __popc(hm[e]);
+    }
+    if (nruns == 1)
+        return;
+    if (nruns > MERGE_SMALL_RUNS) {
+        warp_sort_segment<E>(src, perm, s, n, lane);
+        return;
+    }
+    // start and first index of each element's run
+    int st[E], first[E], acc[E];
+    const unsigned le = 0xffffffffu >> (31 - lane);   // lanes at or below this one
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        int w = e;
+        unsigned m = hm[e] & le;
+        while (w > 0 && m == 0) {   // the run began in an earlier word
+            --w;
+            m = hm[w];
+        }
+        const int b = 31 - __clz(m);
+        st[e] = w * 32 + b;
+        int f = 0;
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int x = __shfl_sync(0xffffffffu, v[q], b);
+            if (q == w)
+                f = x;
+        }
+        first[e] = f;
+        acc[e] = 0;
+    }
+    // every run, in order: add its length where its first index is smaller
+    int prev_st = -1, prev_first = 0;
+#pragma unroll
+    for (int w = 0; w < E; ++w) {
+        unsigned m = hm[w];
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1u;
+            const int f = __shfl_sync(0xffffffffu, v[w], b);
+            if (prev_st >= 0) {
+                const int len = w * 32 + b - prev_st;
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    acc[e] += prev_first < first[e] ? len : 0;
+            }
+            prev_st = w * 32 + b;
+            prev_first = f;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        acc[e] += prev_first < first[e] ? n - prev_st : 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = e * 32 + lane;
+        if (i < n)
+            perm[s + acc[e] + (i - st[e])] = v[e];
+    }
+}
+
 // A segment of the scatter is made of runs: each warp of k_sort_keys gives
 // the lanes of a run of equal keys consecutive slots, so a run is an
 // increasing interval of consecutive particle indices, and runs never
@@ -706,9 +794,9 @@ __device__ __forceinline__ void sort_one_segment(int64_t k, int s, int n, int32_
     if (n <= 1)
         return;
     if (n <= 32) {
-        warp_sort_segment<1>(perm + s, perm, s, n, lane);
+        warp_merge_small<1>(perm + s, perm, s, n, lane);
     } else if (n <= 64) {
-        warp_sort_segment<2>(perm + s, perm, s, n, lane);
+        warp_merge_small<2>(perm + s, perm, s, n, lane);
     } else if (n <= 128) {
         warp_sort_segment<4>(perm + s, perm, s, n, lane);
     } else if (n <= WARP_SORT_MAX) {
@@ -784,9 +872,9 @@ __global__ void __launch_bounds__(256) k_sort_segments(int64_t nkeys, const int3
             if (n <= 1)
                 continue;
             if (n <= 32)
-                warp_sort_segment<1>(a + (s - gs), perm, s, n, lane);
+                warp_merge_small<1>(a + (s - gs), perm, s, n, lane);
             else if (n <= 64)
-                warp_sort_segment<2>(a + (s - gs), perm, s, n, lane);
+                warp_merge_small<2>(a + (s - gs), perm, s, n, lane);
             else if (n <= 128)
                 warp_sort_segment<4>(a + (s - gs), perm, s, n, lane);
             else
