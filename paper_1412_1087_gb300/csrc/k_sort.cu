@@ -121,6 +121,7 @@ __device__ __forceinline__ void load_keybox(const Ctx &c, int bx, KeyBox &kb)
 // Mixed precision: the key of a particle from its two records (loaded by
 // the caller, so that the loads of several particles are in flight at once),
 // as key_of_cell / brick_key compute it.
+template <int D>
 __device__ __forceinline__ int32_t key_mixed(const Ctx &c, const KeyBox &kb, const int4 ps, const float4 vs)
 {
     int32_t cl = ps.x;
@@ -139,11 +140,9 @@ __device__ __forceinline__ int32_t key_mixed(const Ctx &c, const KeyBox &kb, con
         const float v[3] = {vs.x, vs.y, vs.z};
         const float o[3] = {__int_as_float(ps.y), __int_as_float(ps.z), __int_as_float(ps.w)};
         int k[3] = {0, 0, 0};
-        ahead_cells(kb.sk, v, o, c.ndim, k);
+        ahead_cells(kb.sk, v, o, D, k);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (d >= c.ndim)
-                break;
+        for (int d = 0; d < D; ++d) {
             const int g = ci[d] + k[d];
             ci[d] = kb.bc[d] == MHDPIC_BC_PERIODIC ? (g < 0 ? g + kb.n[d] : (g >= kb.n[d] ? g - kb.n[d] : g))
                                                    : (g < 0 ? 0 : (g >= kb.n[d] ? kb.n[d] - 1 : g));
@@ -227,55 +226,25 @@ __device__ __forceinline__ int32_t run_slot(const RunSlot &r, int lane, unsigned
     return __shfl_sync(active, r.base, r.start) + (lane - r.start);
 }
 
-template <int PREC>
-__global__ void k_sort_keys(Ctx c, int32_t *__restrict__ count, int32_t *__restrict__ pkey,
-                            int32_t *__restrict__ pslot)
+// FP64 precision: the keys from the absolute positions, SORT_ILP particles
+// per thread and pass.
+__global__ void k_sort_keys_f64(Ctx c, int32_t *__restrict__ count, int32_t *__restrict__ pkey,
+                                int32_t *__restrict__ pslot)
 {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    KeyBox kb;
-    if (PREC == MHDPIC_PREC_MIXED)
-        load_keybox(c, 0, kb);
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < c.np; i0 += SORT_ILP * stride) {
         // lanes past the end take keys no other lane has, so they form runs
         // of their own and take no atomic
         const unsigned active = __activemask();
         int32_t key[SORT_ILP];
-        if (PREC == MHDPIC_PREC_MIXED) {
-            // every record load of the pass first, then the keys
-            int4 ps[SORT_ILP];
-            float4 vs[SORT_ILP];
-            int bxs[SORT_ILP];
-            const bool ahead = c.sort_ahead != 0.0;
 #pragma unroll
-            for (int u = 0; u < SORT_ILP; ++u) {
-                const int64_t i = i0 + u * stride;
-                bxs[u] = kb.box;
-                ps[u] = make_int4(DEAD_CELL, 0, 0, 0);
-                vs[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (i < c.np) {
-                    if (c.nbox > 1)
-                        bxs[u] = find_box(c.box_part_start, c.nbox, i);
-                    ps[u] = __ldg(c.pos + i);
-                    if (ahead)
-                        vs[u] = __ldg(c.vel + i);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < SORT_ILP; ++u) {
-                if (bxs[u] != kb.box)
-                    load_keybox(c, bxs[u], kb);
-                key[u] = i0 + u * stride < c.np ? key_mixed(c, kb, ps[u], vs[u]) : -1 - lane;
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < SORT_ILP; ++u) {
-                const int64_t i = i0 + u * stride;
-                int bx = 0;
-                if (i < c.np)
-                    bx = find_box(c.box_part_start, c.nbox, i);
-                key[u] = i < c.np ? key_f64(c, c.boxes[bx], bx, i) : -1 - lane;
-            }
+        for (int u = 0; u < SORT_ILP; ++u) {
+            const int64_t i = i0 + u * stride;
+            int bx = 0;
+            if (i < c.np)
+                bx = find_box(c.box_part_start, c.nbox, i);
+            key[u] = i < c.np ? key_f64(c, c.boxes[bx], bx, i) : -1 - lane;
         }
         RunSlot rs[SORT_ILP];
 #pragma unroll
@@ -321,6 +290,7 @@ __device__ __forceinline__ void issue_records(const Ctx &c, int64_t chunk, int4 
         bulk_copy(dv, c.vel + p0, bytes, bar);
 }
 
+template <int D>
 __global__ void __launch_bounds__(KEY_THREADS) k_sort_keys_staged(Ctx c, int32_t *__restrict__ count,
                                                                   int32_t *__restrict__ pkey,
                                                                   int32_t *__restrict__ pslot)
@@ -372,7 +342,7 @@ __global__ void __launch_bounds__(KEY_THREADS) k_sort_keys_staged(Ctx c, int32_t
                 if (bx != kb.box)
                     load_keybox(c, bx, kb);
                 const float4 vs = ahead ? sv[st * KEY_CHUNK + p] : make_float4(0.f, 0.f, 0.f, 0.f);
-                key[u] = key_mixed(c, kb, sp[st * KEY_CHUNK + p], vs);
+                key[u] = key_mixed<D>(c, kb, sp[st * KEY_CHUNK + p], vs);
             }
         }
         RunSlot rs[KEY_PER_THREAD];
@@ -603,95 +573,7 @@ __device__ __forceinline__ void warp_sort_segment(const int32_t *src, int32_t *_
     }
 }
 
-// Segment [s, s + n), n <= 32 E, read from src, sorted by its runs: the
-// maximal stretches of consecutive particle indices at consecutive slots.
-// They are disjoint index intervals (k_sort_keys gives each run of equal keys
-// in a warp consecutive slots), so every run moves to the number of elements
-// in the runs with smaller first indices.  With more than MERGE_SMALL_RUNS
-// runs the segment is sorted by warp_sort_segment instead; a segment of one
-// run is left alone.
-constexpr int MERGE_SMALL_RUNS = 8;
-
-template <int E>
-__device__ __forceinline__ void warp_merge_small(const int32_t *src, int32_t *__restrict__ perm, int s, int n,
-                                                 int lane)
-{
-    int v[E];
-    unsigned hm[E];   // run heads, element e * 32 + lane in bit lane of hm[e]
-    int nruns = 0;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = e * 32 + lane;
-        v[e] = i < n ? src[i] : 0;
-        int prev = __shfl_up_sync(0xffffffffu, v[e], 1);
-        if (e > 0) {
-            const int last = __shfl_sync(0xffffffffu, v[e > 0 ? e - 1 : 0], 31);
-            if (lane == 0)
-                prev = last;
-        }
-        hm[e] = __ballot_sync(0xffffffffu, i < n && (i == 0 || v[e] != prev + 1));
-        nruns += __popc(hm[e]);
-    }
-    if (nruns == 1)
-        return;
-    if (nruns > MERGE_SMALL_RUNS) {
-        warp_sort_segment<E>(src, perm, s, n, lane);
-        return;
-    }
-    // start and first index of each element's run
-    int st[E], first[E], acc[E];
-    const unsigned le = 0xffffffffu >> (31 - lane);   // lanes at or below this one
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        int w = e;
-        unsigned m = hm[e] & le;
-        while (w > 0 && m == 0) {   // the run began in an earlier word
-            --w;
-            m = hm[w];
-        }
-        const int b = 31 - __clz(m);
-        st[e] = w * 32 + b;
-        int f = 0;
-#pragma unroll
-        for (int q = 0; q < E; ++q) {
-            const int x = __shfl_sync(0xffffffffu, v[q], b);
-            if (q == w)
-                f = x;
-        }
-        first[e] = f;
-        acc[e] = 0;
-    }
-    // every run, in order: add its length where its first index is smaller
-    int prev_st = -1, prev_first = 0;
-#pragma unroll
-    for (int w = 0; w < E; ++w) {
-        unsigned m = hm[w];
-        while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1u;
-            const int f = __shfl_sync(0xffffffffu, v[w], b);
-            if (prev_st >= 0) {
-                const int len = w * 32 + b - prev_st;
-#pragma unroll
-                for (int e = 0; e < E; ++e)
-                    acc[e] += prev_first < first[e] ? len : 0;
-            }
-            prev_st = w * 32 + b;
-            prev_first = f;
-        }
-    }
-#pragma unroll
-    for (int e = 0; e < E; ++e)
-        acc[e] += prev_first < first[e] ? n - prev_st : 0;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = e * 32 + lane;
-        if (i < n)
-            perm[s + acc[e] + (i - st[e])] = v[e];
-    }
-}
-
-// A segment of the scatter is made of runs: each warp of k_sort_keys gives
+// A segment of the scatter is made of runs: each warp of the key pass gives
 // the lanes of a run of equal keys consecutive slots, so a run is an
 // increasing interval of consecutive particle indices, and runs never
 // overlap.  Sorting such a segment only sorts its runs by their first index.
@@ -785,8 +667,8 @@ __device__ __forceinline__ bool warp_merge_runs(const int32_t *a, int n, int32_t
 
 // Segments of up to 128 are sorted in registers, up to WARP_SORT_MAX in the
 // warp's shared memory (by their runs when they have at most MERGE_RUNS, else
-// by a bitonic network); longer ones are listed for k_sort_big.
-// One key's segment [s, s + n) read from perm (the warp's buffer a is free).
+// by a bitonic network); longer ones are listed for k_sort_big.  This sorts
+// one key's segment [s, s + n), read from perm (the warp's buffer a is free).
 __device__ __forceinline__ void sort_one_segment(int64_t k, int s, int n, int32_t *__restrict__ perm, int32_t *a,
                                                  int *hp, int32_t *__restrict__ big_list,
                                                  int32_t *__restrict__ big_count, int lane)
@@ -794,9 +676,9 @@ __device__ __forceinline__ void sort_one_segment(int64_t k, int s, int n, int32_
     if (n <= 1)
         return;
     if (n <= 32) {
-        warp_merge_small<1>(perm + s, perm, s, n, lane);
+        warp_sort_segment<1>(perm + s, perm, s, n, lane);
     } else if (n <= 64) {
-        warp_merge_small<2>(perm + s, perm, s, n, lane);
+        warp_sort_segment<2>(perm + s, perm, s, n, lane);
     } else if (n <= 128) {
         warp_sort_segment<4>(perm + s, perm, s, n, lane);
     } else if (n <= WARP_SORT_MAX) {
@@ -872,9 +754,9 @@ __global__ void __launch_bounds__(256) k_sort_segments(int64_t nkeys, const int3
             if (n <= 1)
                 continue;
             if (n <= 32)
-                warp_merge_small<1>(a + (s - gs), perm, s, n, lane);
+                warp_sort_segment<1>(a + (s - gs), perm, s, n, lane);
             else if (n <= 64)
-                warp_merge_small<2>(a + (s - gs), perm, s, n, lane);
+                warp_sort_segment<2>(a + (s - gs), perm, s, n, lane);
             else if (n <= 128)
                 warp_sort_segment<4>(a + (s - gs), perm, s, n, lane);
             else
@@ -1065,8 +947,8 @@ int key_grid(int64_t np)
         int dev = 0, nsm = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_sort_keys_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KEY_SMEM);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sort_keys_staged, KEY_THREADS, KEY_SMEM);
+        cudaFuncSetAttribute(k_sort_keys_staged<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KEY_SMEM);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sort_keys_staged<3>, KEY_THREADS, KEY_SMEM);
         resident = (per < 1 ? 1 : per) * (nsm < 1 ? 1 : nsm);
     }
     const int64_t chunks = (np + KEY_CHUNK - 1) / KEY_CHUNK;
@@ -1082,10 +964,17 @@ int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *
     cudaMemsetAsync(s.count, 0, sizeof(int32_t) * (c.nkeys + 2), st);
     if (c.np > 0) {
         if (c.prec == MHDPIC_PREC_MIXED) {
-            cudaFuncSetAttribute(k_sort_keys_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KEY_SMEM);
-            k_sort_keys_staged<<<key_grid(c.np), KEY_THREADS, KEY_SMEM, st>>>(c, s.count, s.pkey, s.pslot);
+            if (c.ndim == 3) {
+                cudaFuncSetAttribute(k_sort_keys_staged<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)KEY_SMEM);
+                k_sort_keys_staged<3><<<key_grid(c.np), KEY_THREADS, KEY_SMEM, st>>>(c, s.count, s.pkey, s.pslot);
+            } else {
+                cudaFuncSetAttribute(k_sort_keys_staged<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)KEY_SMEM);
+                k_sort_keys_staged<2><<<key_grid(c.np), KEY_THREADS, KEY_SMEM, st>>>(c, s.count, s.pkey, s.pslot);
+            }
         } else
-            k_sort_keys<MHDPIC_PREC_FP64><<<grid_for(c.np, 256), 256, 0, st>>>(c, s.count, s.pkey, s.pslot);
+            k_sort_keys_f64<<<grid_for(c.np, 256), 256, 0, st>>>(c, s.count, s.pkey, s.pslot);
         ++launches;
     }
     // key nkeys holds the particles that left the box: offset[nkeys] is the
