@@ -61,12 +61,16 @@ GAS_CORRECT_BYTES = 32 + 56 + 56 + 56 + 32
 # particles through the permutation, as every push does at a sort cadence of
 # one); traffic scales with the particle count (cells scale alike at fixed
 # particles per cell).  Remove an entry whenever its kernel changes, until it
-# is measured again.
-PUSH_TRAFFIC_BYTES_PER_PARTICLE = {}
+# is measured again.  Both from 'ncu --set full' of one launch: the 3-D beam at
+# 64^3 x 32 (590.9 MB for 8,388,608 particles), Bell at 512^2 x 64 (1182.8 MB
+# for 16,777,216 particles); commands in profiles/.
+PUSH_TRAFFIC_BYTES_PER_PARTICLE = {"alfvenic_beam_3d": 590.936064e6 / 8388608,
+                                   "bell_2d": 1182.831872e6 / 16777216}
 # int32 shared-memory atomic adds per particle of the push's two TSC deposits:
 # 8 channels on 3^D cells, one word per contribution for the charge density
-# and two (hi, lo) for the other seven channels
-SMEM_ATOMICS_PER_PARTICLE = {3: 27 * (1 + 7 * 2), 2: 9 * (1 + 7 * 2)}
+# and two (hi, lo) for the other seven channels, and one contribution count
+# per deposit
+SMEM_ATOMICS_PER_PARTICLE = {3: 27 * (1 + 7 * 2) + 2, 2: 9 * (1 + 7 * 2) + 2}
 # SM-cycles per warp-wide 32-bit shared atomic add with its 32 lanes on 32
 # banks, each adding its own value (standalone probe on a GB300)
 SMEM_ATOMIC_CYCLES = 1.1
