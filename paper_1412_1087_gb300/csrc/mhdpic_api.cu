@@ -132,6 +132,16 @@ struct mhdpic_ctx {
     bool fields_stale = false;
     double half_dt = 0.0;
     int half_model = -1;
+    // MEM_HOST_GAS: a feedback right after a push uploads the gas on
+    // copy_stream while the push runs (the push reads only the staged
+    // fields): copy_stream waits for ev_push, recorded before the push, and
+    // the stream waits for ev_h2d before the feedback
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_push = nullptr, ev_h2d = nullptr;
+    bool push_marked = false;       // ev_push marks the work before the last push
+    uint64_t gas_copies = 0;        // gas copies enqueued so far
+    uint64_t gas_copies_push = 0;   // ... when the last push was enqueued
+    int64_t launches_push = 0;      // kernel launches when the last push was enqueued
 
     template <typename T>
     int alloc(T **p, size_t count)
@@ -191,22 +201,49 @@ int copy_particles(mhdpic_ctx *c, bool to_device)
 }
 
 // all: rho, mom, egas, B; otherwise only the arrays the feedback changes
-int copy_gas(mhdpic_ctx *c, bool to_device, bool all)
+int copy_gas(mhdpic_ctx *c, bool to_device, bool all, cudaStream_t st)
 {
     if (c->mem == MHDPIC_MEM_DEVICE)
         return MHDPIC_OK;
+    ++c->gas_copies;
     const int64_t nc = c->k.nc;
     if (to_device) {
         if (all) {
-            CK(cudaMemcpyAsync(c->k.rho, c->hg.rho, sizeof(double) * nc, cudaMemcpyHostToDevice, c->stream));
-            CK(cudaMemcpyAsync(c->k.B, c->hg.B, sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(c->k.rho, c->hg.rho, sizeof(double) * nc, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(c->k.B, c->hg.B, sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, st));
         }
-        CK(cudaMemcpyAsync(c->k.mom, c->hg.mom, sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, c->stream));
-        CK(cudaMemcpyAsync(c->k.egas, c->hg.egas, sizeof(double) * nc, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->k.mom, c->hg.mom, sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c->k.egas, c->hg.egas, sizeof(double) * nc, cudaMemcpyHostToDevice, st));
     } else {
-        CK(cudaMemcpyAsync(c->hg.mom, c->k.mom, sizeof(double) * 3 * nc, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaMemcpyAsync(c->hg.egas, c->k.egas, sizeof(double) * nc, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(c->hg.mom, c->k.mom, sizeof(double) * 3 * nc, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(c->hg.egas, c->k.egas, sizeof(double) * nc, cudaMemcpyDeviceToHost, st));
     }
+    return MHDPIC_OK;
+}
+
+int copy_gas(mhdpic_ctx *c, bool to_device, bool all)
+{
+    return copy_gas(c, to_device, all, c->stream);
+}
+
+// The gas upload of a feedback.  Right after a push (nothing launched and no
+// gas copied since it was enqueued) in MEM_HOST_GAS mode it runs on
+// copy_stream, after the work enqueued before the push and beside the push
+// itself, which reads only the staged fields; the stream then waits for it.
+// Otherwise it is enqueued on the stream.
+int upload_gas_for_feedback(mhdpic_ctx *c)
+{
+    const bool beside = c->mem == MHDPIC_MEM_HOST_GAS && c->copy_stream && c->push_marked &&
+                        c->launches == c->launches_push && c->gas_copies == c->gas_copies_push;
+    c->push_marked = false;
+    if (!beside)
+        return copy_gas(c, true, true);
+    CK(cudaStreamWaitEvent(c->copy_stream, c->ev_push, 0));
+    int rc = copy_gas(c, true, true, c->copy_stream);
+    if (rc)
+        return rc;
+    CK(cudaEventRecord(c->ev_h2d, c->copy_stream));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_h2d, 0));
     return MHDPIC_OK;
 }
 
@@ -531,6 +568,14 @@ int mhdpic_destroy(mhdpic_ctx *c)
         return MHDPIC_OK;
     if (c->stream || c->valid)
         cudaStreamSynchronize(c->stream);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    if (c->ev_push)
+        cudaEventDestroy(c->ev_push);
+    if (c->ev_h2d)
+        cudaEventDestroy(c->ev_h2d);
     if (c->graph)
         cudaGraphExecDestroy(c->graph);
     for (void *p : c->allocs)
@@ -558,6 +603,15 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
     c->stream = (cudaStream_t)stream;
     c->nbox = nbox;
     c->mem = opt->memory;
+    if (c->mem == MHDPIC_MEM_HOST_GAS) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&c->ev_push, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&c->ev_h2d, cudaEventDisableTiming);
+        if (e != cudaSuccess)
+            return bail(cuda_fail(e, "copy stream"));
+    }
     Ctx &k = c->k;
     k.nbox = nbox;
     k.ndim = grids[0].ndim;
@@ -853,6 +907,10 @@ int mhdpic_interp_push(mhdpic_ctx *c, double dt, int32_t nsub)
     int rc;
     if ((rc = copy_particles(c, true)) || (rc = restage_if_stale(c)))
         return rc;
+    if (c->copy_stream) {   // everything before the push (see upload_gas_for_feedback)
+        CK(cudaEventRecord(c->ev_push, c->stream));
+        c->push_marked = false;
+    }
     if ((rc = check_launch(c, launch_scales(c->k, dt, c->stream))))
         return rc;
     if (!c->next_clear)   // two pushes with no staging in between
@@ -904,6 +962,11 @@ int mhdpic_interp_push(mhdpic_ctx *c, double dt, int32_t nsub)
     }
     c->cur ^= 1;
     c->next_clear = false;
+    if (c->copy_stream) {
+        c->push_marked = true;
+        c->launches_push = c->launches;
+        c->gas_copies_push = c->gas_copies;
+    }
     return copy_particles(c, false);
 }
 
@@ -926,7 +989,7 @@ int mhdpic_apply_feedback(mhdpic_ctx *c, double *totals_out)
     if (!c || !c->valid)
         return fail(MHDPIC_E_STATE, "invalid context");
     int rc;
-    if ((rc = copy_gas(c, true, true)))
+    if ((rc = upload_gas_for_feedback(c)))
         return rc;
     if ((rc = do_prep(c, 1)))
         return rc;

@@ -424,6 +424,31 @@ def test_host_buffers_give_identical_results(prec):
             assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("between", ["nothing", "sort"])
+def test_host_gas_upload_beside_the_push_changes_nothing(between):
+    """With the gas in host memory, a feedback that follows a push uploads
+    the gas on a second stream while the push runs; several steps of it (and
+    of the in-order upload, when a sort comes between) give what device
+    buffers give, bit for bit."""
+    box = tilt_B(wl.periodic_thermal_2d(nx=20, ny=16, ppc=6, dv_amp=0.3, seed=14), 14)
+    res = []
+    for mem in (m.MHDPIC_MEM_DEVICE, m.MHDPIC_MEM_HOST_GAS):
+        eng = _engine(box, MIXED, memory=mem)
+        for step in range(5):
+            eng.interp_push(box.dt, 1)
+            if between == "sort" and step % 2 == 0:
+                eng.sort()
+            eng.apply_feedback()
+        eng.run(box.dt, 4, 2)
+        eng.sync_particles()
+        eng.synchronize()
+        res.append((mixed_rows(eng), eng.mom.cpu().numpy(), eng.egas.cpu().numpy()))
+        assert eng.status() == 0
+        eng.close()
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a, b)
+
+
 def test_ensemble_of_boxes_with_an_empty_one():
     boxes = wl.ensemble_2d(nbox=5, seed0=11, max_side=40)
     boxes[2].cell = boxes[2].cell[:0]
