@@ -85,7 +85,10 @@ extern "C" {
 #define MHDPIC_MEM_HOST 1   /* caller buffers are (pinned) host pointers; each call copies */
 #define MHDPIC_MEM_HOST_GAS 2 /* particle buffers on the device, gas buffers (pinned) host pointers:
                                * the particles stay resident and each call copies only the gas
-                               * arrays it reads or writes (a host MHD solver coupled to the push) */
+                               * arrays it reads or writes (a host MHD solver coupled to the push);
+                               * the gas upload of a feedback that directly follows a push runs on
+                               * a second stream of the library's beside that push, still after
+                               * the call is made and after the work queued before the push */
 
 #define MHDPIC_SPEC_ENERGY 0     /* spectrum of E_k = v^2/(gamma+1) per unit mass (eq:parEk) */
 #define MHDPIC_SPEC_MOMENTUM 1   /* spectrum of |v| = p/m (four-velocity magnitude) */
