@@ -546,6 +546,19 @@ int32_t mhdpic_field_tma(const mhdpic_ctx *ctx);
  */
 int mhdpic_debug_set_barrier_limit(mhdpic_ctx *ctx, int64_t ns);
 
+/*
+ * mhdpic_debug_set_copy_limit - testing interface: the wait limit, in
+ * nanoseconds, for the tensor copies of the push's field tiles and of the
+ * sort's key pass to land in shared memory (<= 0 restores the default of one
+ * second).  A block whose wait runs out raises MHDPIC_ST_COPY_TIMEOUT, waits
+ * (up to one second) for its copies still in flight and ends; the results of
+ * that launch are then not valid, and mhdpic_clear_status resets the flag.
+ * With a 1 ns limit the waits that find a copy still in flight give up (no
+ * copy is held back).  A captured cycle is discarded.  The paper has no
+ * counterpart.  Errors: MHDPIC_E_STATE.
+ */
+int mhdpic_debug_set_copy_limit(mhdpic_ctx *ctx, int64_t ns);
+
 /* Sort cadence chosen by mhdpic_run's tuner (0 before tuning, -1: bad ctx). */
 int32_t mhdpic_sort_cadence(const mhdpic_ctx *ctx);
 

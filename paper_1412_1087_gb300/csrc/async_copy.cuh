@@ -68,6 +68,9 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned b
                  : "memory");
 }
 
+// The default wait limit of a copy, and the limit of the wait that drains the
+// copies still in flight before a block that gave up returns (so none lands
+// in shared memory after the block has gone).
 constexpr long long COPY_LIMIT_NS = 1000000000ll;   // one second
 
 }  // namespace mhdpic

@@ -739,7 +739,7 @@ __device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restr
             item_const(b, dt, it.p1 - it.p0, D, s_k);
         __syncthreads();
         if (c.tma) {
-            const bool ok = mbar_wait(&s_bar, phase, COPY_LIMIT_NS);
+            const bool ok = mbar_wait(&s_bar, phase, c.copy_limit_ns);
             if (__syncthreads_or(!ok)) {   // give up the launch, after the copies in flight have had their time
                 if (threadIdx.x == 0)
                     set_status(c.status, MHDPIC_ST_COPY_TIMEOUT);

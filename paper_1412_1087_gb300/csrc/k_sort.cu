@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(KEY_THREADS) k_sort_keys_staged(Ctx c, int32_t
     load_keybox(c, 0, kb);
     for (int64_t k = 0; k < mine; ++k) {
         const int st = (int)(k % KEY_STAGES);
-        const bool ok = mbar_wait(&full[st], (unsigned)((k / KEY_STAGES) & 1), COPY_LIMIT_NS);
+        const bool ok = mbar_wait(&full[st], (unsigned)((k / KEY_STAGES) & 1), c.copy_limit_ns);
         if (__syncthreads_or(!ok)) {
             // give up the launch, after the copies in flight have had their time
             if (threadIdx.x == 0) {
@@ -470,7 +470,9 @@ int scan(const int32_t *in, int64_t n, int32_t *out, int32_t *tmp, cudaStream_t 
     return 3;
 }
 
-__global__ void k_sort_scatter(int64_t np, const int32_t *__restrict__ pkey,
+// A key outside [0, nkeys] (only after a key pass that gave up part of its
+// work) is flagged and its particle skipped.
+__global__ void k_sort_scatter(int64_t np, int64_t nkeys, const int32_t *__restrict__ pkey,
                                const int32_t *__restrict__ pslot, const int32_t *__restrict__ offset,
                                int32_t *__restrict__ perm, uint32_t *status)
 {
@@ -482,6 +484,11 @@ __global__ void k_sort_scatter(int64_t np, const int32_t *__restrict__ pkey,
             const int64_t i = i0 + u * stride;
             key[u] = i < np ? pkey[i] : 0;
             slot[u] = i < np ? pslot[i] : 0;
+            if (key[u] < 0 || key[u] > nkeys) {
+                set_status(status, MHDPIC_ST_SORT_CAP);
+                key[u] = 0;
+                slot[u] = -1 - (int32_t)np;   // lands outside [0, np): not written
+            }
         }
         int32_t off[SORT_ILP];
 #pragma unroll
@@ -982,7 +989,8 @@ int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *
     launches += scan(s.count, c.nkeys + 1, s.offset, s.scan_tmp, st);
     if (c.np > 0) {
         cudaMemsetAsync(s.perm, 0, sizeof(int32_t) * c.np, st);
-        k_sort_scatter<<<grid_for(c.np, 256), 256, 0, st>>>(c.np, s.pkey, s.pslot, s.offset, s.perm, c.status);
+        k_sort_scatter<<<grid_for(c.np, 256), 256, 0, st>>>(c.np, c.nkeys, s.pkey, s.pslot, s.offset, s.perm,
+                                                           c.status);
         cudaMemsetAsync(s.big_count, 0, sizeof(int32_t), st);
         const int64_t nw = (c.nkeys + 8 * SEG_GROUP - 1) / (8 * SEG_GROUP);   // blocks of 8 warps
         int gb = (int)(nw < 152 * 16 ? (nw < 1 ? 1 : nw) : 152 * 16);

@@ -22,6 +22,9 @@ using namespace mhdpic;
 
 namespace {
 
+// default wait limit of the kernels' tensor copies (one second)
+constexpr int64_t COPY_LIMIT_DEFAULT_NS = 1000000000ll;
+
 thread_local std::string g_last_error;
 
 int fail(int code, const char *fmt, ...)
@@ -603,6 +606,7 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
     c->stream = (cudaStream_t)stream;
     c->nbox = nbox;
     c->mem = opt->memory;
+    c->k.copy_limit_ns = COPY_LIMIT_DEFAULT_NS;
     if (c->mem == MHDPIC_MEM_HOST_GAS) {
         cudaError_t e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
         if (e == cudaSuccess)
@@ -829,7 +833,15 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         cudaMemsetAsync(k.corr, 0, sizeof(unsigned long long) * 4 * nc, st) ||
         cudaMemsetAsync(k.momdep[0], 0, sizeof(unsigned long long) * 4 * nc, st) ||
         cudaMemsetAsync(k.momdep[1], 0, sizeof(unsigned long long) * 4 * nc, st) ||
-        cudaMemsetAsync(k.status, 0, sizeof(uint32_t), st) || cudaMemsetAsync(k.stats, 0, sizeof(BoxStats) * nbox, st))
+        cudaMemsetAsync(k.status, 0, sizeof(uint32_t), st) || cudaMemsetAsync(k.stats, 0, sizeof(BoxStats) * nbox, st) ||
+        // the second particle set and the sort's per-particle arrays start as
+        // valid values (cell 0, key 0, slot 0, index 0): a launch that gives
+        // up part of its work (MHDPIC_ST_COPY_TIMEOUT, MHDPIC_ST_BARRIER)
+        // leaves stale but in-range entries behind, never raw memory
+        cudaMemsetAsync(c->s.tmp, 0, (size_t)np * c->particle_bytes(), st) ||
+        cudaMemsetAsync(c->s.pkey, 0, sizeof(int32_t) * np, st) ||
+        cudaMemsetAsync(c->s.pslot, 0, sizeof(int32_t) * np, st) ||
+        cudaMemsetAsync(c->s.perm, 0, sizeof(int32_t) * np, st))
         return bail(cuda_fail(cudaGetLastError(), "init uploads"));
 
     // sort (into the caller's buffers), then size the charge/current scales
@@ -1620,6 +1632,18 @@ int mhdpic_debug_set_barrier_limit(mhdpic_ctx *c, int64_t ns)
     if (!c || !c->valid)
         return fail(MHDPIC_E_STATE, "invalid context");
     c->bar_limit_ns = ns > 0 ? (long long)ns : 1000000000ll;
+    if (c->graph) {   // the limit is a launch argument of the captured cycle
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return MHDPIC_OK;
+}
+
+int mhdpic_debug_set_copy_limit(mhdpic_ctx *c, int64_t ns)
+{
+    if (!c || !c->valid)
+        return fail(MHDPIC_E_STATE, "invalid context");
+    c->k.copy_limit_ns = ns > 0 ? ns : COPY_LIMIT_DEFAULT_NS;
     if (c->graph) {   // the limit is a launch argument of the captured cycle
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;

@@ -125,6 +125,7 @@ struct Ctx {
     int32_t halves;        // 1: default 64-cell bricks split into 32-cell halves
     double sort_ahead;     // sort key: the cell after moving for this time at the current velocity
     const float4 *sort_k;  // per box {t/dx, t/dy, t/dz, 1/C^2} in FP32 for that key
+    int64_t copy_limit_ns; // wait limit for a tensor copy to land (then MHDPIC_ST_COPY_TIMEOUT)
     int64_t np, nc, nkeys, nbricks_total;
     const BoxDev *boxes;   // device
     const int64_t *box_part_start; // device [nbox+1]

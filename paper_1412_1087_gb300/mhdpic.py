@@ -100,6 +100,7 @@ SIGNATURES = {
     "mhdpic_set_step_fusion": (ctypes.c_int, [_V, ctypes.c_int32]),
     "mhdpic_step_fusion": (ctypes.c_int32, [_V]),
     "mhdpic_debug_set_barrier_limit": (ctypes.c_int, [_V, ctypes.c_int64]),
+    "mhdpic_debug_set_copy_limit": (ctypes.c_int, [_V, ctypes.c_int64]),
     "mhdpic_set_field_tma": (ctypes.c_int, [_V, ctypes.c_int32]),
     "mhdpic_field_tma": (ctypes.c_int32, [_V]),
     "mhdpic_get_deposits": (ctypes.c_int, [_V, ctypes.c_int32, _V]),
@@ -272,6 +273,10 @@ def mhdpic_field_tma(ctx) -> int:
 
 def mhdpic_debug_set_barrier_limit(ctx, ns: int) -> None:
     _check(load().mhdpic_debug_set_barrier_limit(ctx, int(ns)))
+
+
+def mhdpic_debug_set_copy_limit(ctx, ns: int) -> None:
+    _check(load().mhdpic_debug_set_copy_limit(ctx, int(ns)))
 
 
 def mhdpic_get_deposits(ctx, which: int, out_ptr: int) -> None:

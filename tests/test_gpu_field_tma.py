@@ -88,3 +88,40 @@ def test_thread_copies_where_the_layout_rules_out_tensor_copies():
     eng = m.Engine([box], precision=m.MHDPIC_PREC_FP64)
     assert eng.field_tma() == 0
     eng.close()
+
+
+def test_copy_wait_limit_raises_a_flag_instead_of_waiting():
+    """With a 1 ns limit, a wait that finds its tensor copy still in flight
+    (the push's field tile, the key pass's particle records) gives up: the
+    launch is flagged MHDPIC_ST_COPY_TIMEOUT and its blocks end after their
+    copies have landed.  With the status cleared and the limit restored the
+    same context steps normally, its particles in range and finite."""
+    box = tilt_B(wl.alfvenic_beam_3d(n=32, ppc=16, nmodes=8, seed=78), 78)
+    stream = torch.cuda.Stream()
+    eng = m.Engine([box], precision=MIXED, stream=stream)
+    assert eng.field_tma() == 1
+    m.mhdpic_debug_set_copy_limit(eng.ctx, 1)
+    flags = 0
+    for _ in range(5):   # each launch has thousands of waits; one that finds a copy in flight suffices
+        eng.sort()
+        stream.synchronize()
+        flags |= eng.status()
+        if flags & 128:
+            break
+        eng.interp_push(box.dt, 1)
+        stream.synchronize()
+        flags |= eng.status()
+        if flags & 128:
+            break
+    assert flags & 128, m.status_names(flags)
+    m.mhdpic_debug_set_copy_limit(eng.ctx, 0)
+    eng.clear_status()
+    assert eng.status() == 0
+    eng.run(box.dt, 4, 2)
+    eng.sync_particles()
+    stream.synchronize()
+    assert eng.status() == 0, m.status_names(eng.status())
+    cell = eng.cell.cpu().numpy()
+    assert cell.min() >= 0 and cell.max() < box.ncell
+    assert np.isfinite(eng.vel.cpu().numpy()).all()
+    eng.close()
