@@ -59,10 +59,16 @@ constexpr int KLO = 19;               // bits of the low word of a split contrib
 constexpr float MAGIC_HI = 6597069766656.0f;  // 1.5 * 2^(23+KLO)
 constexpr int MAGIC_HI_BITS = 0x54C00000;     // bit pattern of MAGIC_HI
 constexpr float MAGIC_HI_LO = 6597082349568.0f;  // MAGIC_HI + MAGIC, exact (bits 2^42 .. 2^22)
-constexpr int NPLANE = 2 * NCH;       // hi planes 0..7, lo planes 8..15
-constexpr int CNT_C = NPLANE;         // contributions of the corrector deposit, by stencil corner
-constexpr int CNT_M = NPLANE + 1;     // the same for the moments deposit
-constexpr int NTILE = NPLANE + 2;     // int planes of the deposit tile
+// A slot of the deposit tile is TILE_WORDS consecutive int words: the hi
+// words of the 8 channels (0..7), their lo words (8..15; the density has
+// none, and its place holds the moments deposit's contribution count) and
+// the corrector deposit's count (16).  An odd number of words keeps slots
+// that differ mod 32 on different banks, and every word of a slot is a
+// constant offset from the slot's address.
+constexpr int TILE_WORDS = 2 * NCH + 1;
+constexpr int W_LO = NCH;               // lo word of channel ch: W_LO + ch
+constexpr int W_CNT_M = NCH + CH_N;     // contributions of the moments deposit, by stencil corner
+constexpr int W_CNT_C = 2 * NCH;        // the same for the corrector deposit
 
 struct MixedConst {
     float hdx[3];    // dt / (2 dx)
@@ -211,20 +217,20 @@ __device__ __forceinline__ int single_word(float a, float wx)
     return __float_as_int(fmaf(a, wx, MAGIC));
 }
 
-// both words of a split contribution added to the tile as they are
-__device__ __forceinline__ void add_split(int *hi_plane, int *lo_plane, int s, float a, float wx)
+// both words of a split contribution added to a tile slot as they are
+__device__ __forceinline__ void add_split(int *hi, int *lo, float a, float wx)
 {
     int hb, lb;
     split_words(a, wx, hb, lb);
-    atomicAdd(hi_plane + s, hb);
-    atomicAdd(lo_plane + s, lb);
+    atomicAdd(hi, hb);
+    atomicAdd(lo, lb);
 }
 
 // Contributions tile cell (tx, ty, tz) received from one deposit: the counts
-// (plane CNT_C or CNT_M) of the stencil corners at most 2 cells below it.
-__device__ __forceinline__ uint32_t slot_count(const Ctx &c, const int *sD, int plane, int tx, int ty, int tz, int D)
+// (word W_CNT_C or W_CNT_M) of the stencil corners at most 2 cells below it.
+__device__ __forceinline__ uint32_t slot_count(const Ctx &c, const int *sD, int word, int tx, int ty, int tz, int D)
 {
-    const int *cnt = sD + plane * c.tile_slots;
+    const int *cnt = sD + word;
     uint32_t k = 0u;
     for (int dz = 0; dz < (D == 3 ? 3 : 1); ++dz) {
         if (tz - dz < 0)
@@ -236,7 +242,7 @@ __device__ __forceinline__ uint32_t slot_count(const Ctx &c, const int *sD, int 
             for (int dx = 0; dx < 3; ++dx) {
                 if (tx - dx < 0)
                     break;
-                k += (uint32_t)cnt[(tx - dx) + c.ts[1] * (ty - dy) + c.ts[2] * (tz - dz)];
+                k += (uint32_t)cnt[((tx - dx) + c.ts[1] * (ty - dy) + c.ts[2] * (tz - dz)) * TILE_WORDS];
             }
         }
     }
@@ -244,13 +250,14 @@ __device__ __forceinline__ uint32_t slot_count(const Ctx &c, const int *sD, int 
 }
 
 // channel ch of tile slot s rebuilt as the sum of its rounded contributions
-__device__ __forceinline__ long long slot_value(const int *sD, int S, int s, int ch, uint32_t kc, uint32_t km)
+__device__ __forceinline__ long long slot_value(const int *sD, int s, int ch, uint32_t kc, uint32_t km)
 {
+    const int *w = sD + s * TILE_WORDS;
     const uint32_t k = ch < CH_N ? kc : km;
-    const int hi = (int)((uint32_t)sD[ch * S + s] - k * (uint32_t)(ch == CH_N ? MAGIC_BITS : MAGIC_HI_BITS));
+    const int hi = (int)((uint32_t)w[ch] - k * (uint32_t)(ch == CH_N ? MAGIC_BITS : MAGIC_HI_BITS));
     if (ch == CH_N)
         return hi;
-    const int lo = (int)((uint32_t)sD[(NCH + ch) * S + s] - k * (uint32_t)MAGIC_BITS);
+    const int lo = (int)((uint32_t)w[W_LO + ch] - k * (uint32_t)MAGIC_BITS);
     return (long long)hi * (1ll << KLO) + lo;
 }
 
@@ -262,15 +269,7 @@ template <int D>
 __device__ __forceinline__ void deposit_tile(const Ctx &c, int base, const Wts &w, const float q[4], int ch0,
                                              int *__restrict__ sD)
 {
-    const int S = c.tile_slots, SY = c.ts[1], SZ = c.ts[2];
-    int *__restrict__ h0 = sD + (ch0 + 0) * S;
-    int *__restrict__ h1 = sD + (ch0 + 1) * S;
-    int *__restrict__ h2 = sD + (ch0 + 2) * S;
-    int *__restrict__ h3 = sD + (ch0 + 3) * S;
-    int *__restrict__ l0 = h0 + NCH * S;
-    int *__restrict__ l1 = h1 + NCH * S;
-    int *__restrict__ l2 = h2 + NCH * S;
-    int *__restrict__ l3 = h3 + NCH * S;
+    const int SY = c.ts[1], SZ = c.ts[2];
     const bool first_single = ch0 == CH_N;
 #pragma unroll 1
     for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz)
@@ -280,17 +279,17 @@ __device__ __forceinline__ void deposit_tile(const Ctx &c, int base, const Wts &
             float a0 = q[0] * wyz, a1 = q[1] * wyz, a2 = q[2] * wyz, a3 = q[3] * wyz;
 #pragma unroll
             for (int cx = 0; cx < 3; ++cx) {
-                int s = base + cx + SY * cy + SZ * cz;
+                int *__restrict__ t = sD + (base + cx + SY * cy + SZ * cz) * TILE_WORDS + ch0;
                 if (first_single)
-                    atomicAdd(h0 + s, single_word(a0, w.x[cx]));
+                    atomicAdd(t, single_word(a0, w.x[cx]));
                 else
-                    add_split(h0, l0, s, a0, w.x[cx]);
-                add_split(h1, l1, s, a1, w.x[cx]);
-                add_split(h2, l2, s, a2, w.x[cx]);
-                add_split(h3, l3, s, a3, w.x[cx]);
+                    add_split(t, t + W_LO, a0, w.x[cx]);
+                add_split(t + 1, t + 1 + W_LO, a1, w.x[cx]);
+                add_split(t + 2, t + 2 + W_LO, a2, w.x[cx]);
+                add_split(t + 3, t + 3 + W_LO, a3, w.x[cx]);
             }
         }
-    atomicAdd(sD + (first_single ? CNT_M : CNT_C) * S + base, 1);
+    atomicAdd(sD + base * TILE_WORDS + (first_single ? W_CNT_M : W_CNT_C), 1);
 }
 
 // Four channels into the int64 global accumulators as exactly the integers
@@ -443,8 +442,8 @@ __device__ __forceinline__ void store_particle(const Ctx &c, int64_t j, int32_t 
     c.vel[j] = make_float4(v[0], v[1], v[2], __uint_as_float(res));
 }
 
-// The push's dynamic shared memory: the deposit tile (NTILE int planes of
-// `slots`), the field tile (a float4 and a float2 plane of `fslots`, each on a
+// The push's dynamic shared memory: the deposit tile (`slots` slots of
+// TILE_WORDS int words), the field tile (a float4 and a float2 plane of `fslots`, each on a
 // 128-byte boundary for the tensor copies), then the particle ring (2-D).
 struct PushLayout {
     size_t fa, fb, ring;
@@ -455,7 +454,7 @@ __host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) / 128
 __host__ __device__ inline PushLayout push_layout(int slots, int fslots)
 {
     PushLayout l{};
-    l.fa = align128(sizeof(int) * NTILE * (size_t)slots);
+    l.fa = align128(sizeof(int) * TILE_WORDS * (size_t)slots);
     l.fb = align128(l.fa + sizeof(float4) * (size_t)fslots);
     l.ring = align128(l.fb + sizeof(float2) * (size_t)fslots);
     return l;
@@ -733,7 +732,7 @@ __device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restr
             }
         }
         // clear the deposit tile and its counts
-        for (int s = threadIdx.x; s < NTILE * S; s += PUSH_THREADS)
+        for (int s = threadIdx.x; s < TILE_WORDS * S; s += PUSH_THREADS)
             sD[s] = 0;
         if (threadIdx.x == 0)
             item_const(b, dt, it.p1 - it.p0, D, s_k);
@@ -818,13 +817,13 @@ __device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restr
             int ty = r % c.tile[1], tz = r / c.tile[1];
             int64_t g = tile_global(c, b, gm, tx, ty, tz, D);
             int s = tile_slot(c, tx, ty, tz);
-            const uint32_t kc = slot_count(c, sD, CNT_C, tx, ty, tz, D);
-            const uint32_t km = FULL ? slot_count(c, sD, CNT_M, tx, ty, tz, D) : 0u;
+            const uint32_t kc = slot_count(c, sD, W_CNT_C, tx, ty, tz, D);
+            const uint32_t km = FULL ? slot_count(c, sD, W_CNT_M, tx, ty, tz, D) : 0u;
 #pragma unroll
             for (int ch = 0; ch < NCH; ++ch) {
                 if (!FULL && ch >= CH_N)
                     break;
-                const long long v = slot_value(sD, S, s, ch, kc, km);
+                const long long v = slot_value(sD, s, ch, kc, km);
                 if (v) {
                     unsigned long long *dst = ch < CH_N ? c.corr + ch * c.nc + g : mout + (ch - CH_N) * c.nc + g;
                     atomicAdd(dst, (unsigned long long)v << k.ksh[ch]);
@@ -949,12 +948,8 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_deposit_mixed(Ctx c, const Wor
         const WorkItem it = items[item];
         const BoxDev &b = c.boxes[it.box];
         const ItemGeom gm = item_geom(c, b, it.brick, D);
-        for (int s = threadIdx.x + CH_N * S; s < NCH * S; s += PUSH_THREADS)
+        for (int s = threadIdx.x; s < TILE_WORDS * S; s += PUSH_THREADS)
             sD[s] = 0;
-        for (int s = threadIdx.x + (NCH + CH_N) * S; s < NPLANE * S; s += PUSH_THREADS)
-            sD[s] = 0;
-        for (int s = threadIdx.x; s < S; s += PUSH_THREADS)
-            sD[CNT_M * S + s] = 0;
         if (threadIdx.x == 0)
             item_const(b, 0.f, it.p1 - it.p0, D, s_k);
         __syncthreads();
@@ -982,10 +977,10 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_deposit_mixed(Ctx c, const Wor
             int ty = r % c.tile[1], tz = r / c.tile[1];
             int64_t g = tile_global(c, b, gm, tx, ty, tz, D);
             int s = tile_slot(c, tx, ty, tz);
-            const uint32_t km = slot_count(c, sD, CNT_M, tx, ty, tz, D);
+            const uint32_t km = slot_count(c, sD, W_CNT_M, tx, ty, tz, D);
 #pragma unroll
             for (int ch = CH_N; ch < NCH; ++ch) {
-                const long long v = slot_value(sD, S, s, ch, 0u, km);
+                const long long v = slot_value(sD, s, ch, 0u, km);
                 if (v)
                     atomicAdd(mout + (ch - CH_N) * c.nc + g, (unsigned long long)v << k.ksh[ch]);
             }
@@ -1041,7 +1036,7 @@ int push_blocks_per_sm_mixed(const Ctx &c)
 int launch_deposit_mixed(const Ctx &c, const SortScratch &s, int32_t *work_ctr, int cur, int grid_blocks,
                          cudaStream_t st)
 {
-    const size_t bytes = sizeof(int) * NTILE * (size_t)c.tile_slots;
+    const size_t bytes = sizeof(int) * TILE_WORDS * (size_t)c.tile_slots;
     cudaMemsetAsync(work_ctr, 0, sizeof(int32_t), st);
     if (c.ndim == 3) {
         cudaFuncSetAttribute(k_deposit_mixed<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, PUSH_SMEM_LIMIT);
