@@ -48,7 +48,20 @@ __device__ __forceinline__ void prep_cells(const Ctx &c, int cur, int apply)
                 set_status(c.status, MHDPIC_ST_OVERFLOW);
         }
         double Bc[3] = {c.B[g], c.B[nc + g], c.B[2 * nc + g]};
-        double v[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
+        // FP64 divisions are slow on this GPU: the mixed path, whose fields
+        // are staged in FP32, divides once by rho (and once by n_g) and
+        // multiplies; the FP64 path keeps the oracle's divisions
+        double v[3];
+        if (PREC == MHDPIC_PREC_MIXED) {
+            const double ir = 1.0 / rho;
+            v[0] = m[0] * ir;
+            v[1] = m[1] * ir;
+            v[2] = m[2] * ir;
+        } else {
+            v[0] = m[0] / rho;
+            v[1] = m[1] / rho;
+            v[2] = m[2] / rho;
+        }
         double E0[3] = {-(v[1] * Bc[2] - v[2] * Bc[1]), -(v[2] * Bc[0] - v[0] * Bc[2]),
                         -(v[0] * Bc[1] - v[1] * Bc[0])};
         double E[3] = {E0[0], E0[1], E0[2]};
@@ -60,28 +73,32 @@ __device__ __forceinline__ void prep_cells(const Ctx &c, int cur, int apply)
             double R = n / (ng + n);
             double JxB[3] = {J[1] * Bc[2] - J[2] * Bc[1], J[2] * Bc[0] - J[0] * Bc[2],
                              J[0] * Bc[1] - J[1] * Bc[0]};
+            const double ing = PREC == MHDPIC_PREC_MIXED ? 1.0 / ng : 0.0;
             for (int d = 0; d < 3; ++d) {
                 double F = (1.0 - R) * (n * E0[d] + JxB[d]);
-                E[d] = E0[d] - F / ng;
+                E[d] = PREC == MHDPIC_PREC_MIXED ? E0[d] - F * ing : E0[d] - F / ng;
             }
         }
+        float em, bm;   // |E| and |B| for the per-box maxima
         if (PREC == MHDPIC_PREC_MIXED) {
             int ci[3];
             decode_cell(b, (int32_t)(g - b.cell0), ci);
-            store_fields_mixed(c.fa, c.fb, b, ci[0], ci[1], ci[2],
-                               make_float4((float)E[0], (float)E[1], (float)E[2], (float)Bc[0]),
-                               make_float2((float)Bc[1], (float)Bc[2]));
+            const float4 fa = make_float4((float)E[0], (float)E[1], (float)E[2], (float)Bc[0]);
+            const float2 fb = make_float2((float)Bc[1], (float)Bc[2]);
+            store_fields_mixed(c.fa, c.fb, b, ci[0], ci[1], ci[2], fa, fb);
+            em = sqrtf(fa.x * fa.x + fa.y * fa.y + fa.z * fa.z);
+            bm = sqrtf(fa.w * fa.w + fb.x * fb.x + fb.y * fb.y);
         } else {
             double2 *f = reinterpret_cast<double2 *>(c.f64) + 3 * g;
             f[0] = make_double2(E[0], E[1]);
             f[1] = make_double2(E[2], Bc[0]);
             f[2] = make_double2(Bc[1], Bc[2]);
+            em = (float)sqrt(E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
+            bm = (float)sqrt(Bc[0] * Bc[0] + Bc[1] * Bc[1] + Bc[2] * Bc[2]);
         }
         for (int q = 0; q < 4; ++q)
             mnext[q * nc + g] = 0ull;
         // per-box maxima of |E| and |B| for the corrector scales
-        float em = (float)sqrt(E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
-        float bm = (float)sqrt(Bc[0] * Bc[0] + Bc[1] * Bc[1] + Bc[2] * Bc[2]);
         unsigned peers = __match_any_sync(__activemask(), bx);
         unsigned eb = __reduce_max_sync(peers, __float_as_uint(em));
         unsigned bb2 = __reduce_max_sync(peers, __float_as_uint(bm));
