@@ -96,7 +96,7 @@ struct KeyBox {
     int box;
     int n[3], bc[3], nb[3];
     int32_t ncell;
-    int64_t key0;
+    int32_t key0;   // keys are int32: the box's first key
     FastDiv dnx, dnxy;
     float4 sk;
 };
@@ -112,7 +112,7 @@ __device__ __forceinline__ void load_keybox(const Ctx &c, int bx, KeyBox &kb)
         kb.nb[d] = b.nb[d];
     }
     kb.ncell = (int32_t)b.ncell;
-    kb.key0 = b.key0;
+    kb.key0 = (int32_t)b.key0;
     kb.dnx = b.div_nx;
     kb.dnxy = b.div_nxy;
     kb.sk = __ldg(c.sort_k + bx);
@@ -121,7 +121,7 @@ __device__ __forceinline__ void load_keybox(const Ctx &c, int bx, KeyBox &kb)
 // Mixed precision: the key of a particle from its two records (loaded by
 // the caller, so that the loads of several particles are in flight at once),
 // as key_of_cell / brick_key compute it.
-template <int D>
+template <int D, bool AHEAD>
 __device__ __forceinline__ int32_t key_mixed(const Ctx &c, const KeyBox &kb, const int4 ps, const float4 vs)
 {
     int32_t cl = ps.x;
@@ -136,7 +136,7 @@ __device__ __forceinline__ int32_t key_mixed(const Ctx &c, const KeyBox &kb, con
     const uint32_t rr = uc - kz * kb.dnxy.d;
     const uint32_t jy = fdiv(rr, kb.dnx);
     int ci[3] = {(int)(rr - jy * kb.dnx.d), (int)jy, (int)kz};
-    if (c.sort_ahead != 0.0) {
+    if (AHEAD) {
         const float v[3] = {vs.x, vs.y, vs.z};
         const float o[3] = {__int_as_float(ps.y), __int_as_float(ps.z), __int_as_float(ps.w)};
         int k[3] = {0, 0, 0};
@@ -148,9 +148,9 @@ __device__ __forceinline__ int32_t key_mixed(const Ctx &c, const KeyBox &kb, con
                                                    : (g < 0 ? 0 : (g >= kb.n[d] ? kb.n[d] - 1 : g));
         }
     }
-    int q[3], r[3];
+    int q[3] = {0, 0, 0}, r[3] = {0, 0, 0};
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
+    for (int d = 0; d < D; ++d) {
         if (c.brick_sh[d] >= 0) {
             q[d] = ci[d] >> c.brick_sh[d];
             r[d] = ci[d] & (c.brick[d] - 1);
@@ -159,9 +159,10 @@ __device__ __forceinline__ int32_t key_mixed(const Ctx &c, const KeyBox &kb, con
             r[d] = ci[d] - q[d] * c.brick[d];
         }
     }
-    const int64_t bid = ((int64_t)q[2] * kb.nb[1] + q[1]) * kb.nb[0] + q[0];
+    // int32 throughout: every key of the context is below nkeys < 2^31
+    const int bid = (q[2] * kb.nb[1] + q[1]) * kb.nb[0] + q[0];
     const int in = (r[2] * c.brick[1] + r[1]) * c.brick[0] + r[0];
-    return (int32_t)(kb.key0 + bid * ((int64_t)c.brick[0] * c.brick[1] * c.brick[2]) + in);
+    return kb.key0 + bid * (c.brick[0] * c.brick[1] * c.brick[2]) + in;
 }
 
 // FP64 precision: the key of particle i of box b, from its absolute position.
@@ -290,7 +291,7 @@ __device__ __forceinline__ void issue_records(const Ctx &c, int64_t chunk, int4 
         bulk_copy(dv, c.vel + p0, bytes, bar);
 }
 
-template <int D>
+template <int D, bool AHEAD>
 __global__ void __launch_bounds__(KEY_THREADS) k_sort_keys_staged(Ctx c, int32_t *__restrict__ count,
                                                                   int32_t *__restrict__ pkey,
                                                                   int32_t *__restrict__ pslot)
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(KEY_THREADS) k_sort_keys_staged(Ctx c, int32_t
     float4 *sv = reinterpret_cast<float4 *>(smem + (size_t)KEY_STAGES * KEY_CHUNK * sizeof(int4));
     __shared__ __align__(8) uint64_t full[KEY_STAGES];
     const int lane = threadIdx.x & 31;
-    const bool ahead = c.sort_ahead != 0.0;
+    constexpr bool ahead = AHEAD;
     const int64_t nchunk = (c.np + KEY_CHUNK - 1) / KEY_CHUNK;
     const int64_t mine = (int64_t)blockIdx.x < nchunk ? (nchunk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     if (threadIdx.x == 0) {
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(KEY_THREADS) k_sort_keys_staged(Ctx c, int32_t
                 if (bx != kb.box)
                     load_keybox(c, bx, kb);
                 const float4 vs = ahead ? sv[st * KEY_CHUNK + p] : make_float4(0.f, 0.f, 0.f, 0.f);
-                key[u] = key_mixed<D>(c, kb, sp[st * KEY_CHUNK + p], vs);
+                key[u] = key_mixed<D, AHEAD>(c, kb, sp[st * KEY_CHUNK + p], vs);
             }
         }
         RunSlot rs[KEY_PER_THREAD];
@@ -954,12 +955,19 @@ int key_grid(int64_t np)
         int dev = 0, nsm = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_sort_keys_staged<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KEY_SMEM);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sort_keys_staged<3>, KEY_THREADS, KEY_SMEM);
+        cudaFuncSetAttribute(k_sort_keys_staged<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KEY_SMEM);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sort_keys_staged<3, true>, KEY_THREADS, KEY_SMEM);
         resident = (per < 1 ? 1 : per) * (nsm < 1 ? 1 : nsm);
     }
     const int64_t chunks = (np + KEY_CHUNK - 1) / KEY_CHUNK;
     return (int)(chunks < resident ? (chunks < 1 ? 1 : chunks) : resident);
+}
+
+template <int D, bool AHEAD>
+void launch_keys(const Ctx &c, const SortScratch &s, cudaStream_t st)
+{
+    cudaFuncSetAttribute(k_sort_keys_staged<D, AHEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KEY_SMEM);
+    k_sort_keys_staged<D, AHEAD><<<key_grid(c.np), KEY_THREADS, KEY_SMEM, st>>>(c, s.count, s.pkey, s.pslot);
 }
 
 }  // namespace
@@ -971,15 +979,15 @@ int launch_sort(const Ctx &c, const SortScratch &s, int64_t *perm_out, int32_t *
     cudaMemsetAsync(s.count, 0, sizeof(int32_t) * (c.nkeys + 2), st);
     if (c.np > 0) {
         if (c.prec == MHDPIC_PREC_MIXED) {
-            if (c.ndim == 3) {
-                cudaFuncSetAttribute(k_sort_keys_staged<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)KEY_SMEM);
-                k_sort_keys_staged<3><<<key_grid(c.np), KEY_THREADS, KEY_SMEM, st>>>(c, s.count, s.pkey, s.pslot);
-            } else {
-                cudaFuncSetAttribute(k_sort_keys_staged<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)KEY_SMEM);
-                k_sort_keys_staged<2><<<key_grid(c.np), KEY_THREADS, KEY_SMEM, st>>>(c, s.count, s.pkey, s.pslot);
-            }
+            const bool ahead = c.sort_ahead != 0.0;
+            if (c.ndim == 3 && ahead)
+                launch_keys<3, true>(c, s, st);
+            else if (c.ndim == 3)
+                launch_keys<3, false>(c, s, st);
+            else if (ahead)
+                launch_keys<2, true>(c, s, st);
+            else
+                launch_keys<2, false>(c, s, st);
         } else
             k_sort_keys_f64<<<grid_for(c.np, 256), 256, 0, st>>>(c, s.count, s.pkey, s.pslot);
         ++launches;
