@@ -757,15 +757,15 @@ __device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restr
         {
             const LaneRange lr = lane_range(it, wid, NW);
             const int64_t base = lr.base, cnt = lr.cnt, lane0 = lane * lr.q, rb = lr.first, re = lr.q,
-                          rs = lr.stride;
-            // source particle of sorted position base + lane0 + r; when the
+                          rs = lr.stride, step = lr.step;
+            // source particle of sorted position base + (lane0 + r) step; when the
             // push applies a sort the permutation entry is loaded one
             // iteration early.  (One code path for both cases, so that the
             // arithmetic is the same instruction for instruction.)
             const bool gather = c.perm_src != nullptr;
             auto valid = [&](int64_t r) { return r < re && lane0 + r < cnt; };
             auto src_of = [&](int64_t r) -> int64_t {
-                const int64_t j = base + lane0 + r;
+                const int64_t j = base + (lane0 + r) * step;
                 return gather ? (int64_t)__ldg(c.perm_src + j) : j;
             };
             if (STAGED<D>) {
@@ -789,7 +789,7 @@ __device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restr
                     cp_async_commit();
                     cp_async_wait_prev();
                     if (lane0 + r < cnt)
-                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + lane0 + r, load_staged(ring + st * RS),
+                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + (lane0 + r) * step, load_staged(ring + st * RS),
                                                            sFa, sFb, sD, mout));
                     st = st + 1 == NS ? 0 : st + 1;
                 }
@@ -800,7 +800,7 @@ __device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restr
                         const int64_t src = sn;
                         if (valid(r + rs))
                             sn = src_of(r + rs);
-                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + lane0 + r, load_global(c, src), sFa,
+                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + (lane0 + r) * step, load_global(c, src), sFa,
                                                            sFb, sD, mout));
                     }
             }
@@ -960,7 +960,7 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_deposit_mixed(Ctx c, const Wor
             for (int64_t r = lr.first; r < lr.q; r += lr.stride) {
                 if (lane0 + r >= lr.cnt)
                     continue;
-                const int64_t j = lr.base + lane0 + r;
+                const int64_t j = lr.base + (lane0 + r) * lr.step;
                 const int64_t src = gather ? (int64_t)__ldg(c.perm_src + j) : j;
                 const PIn pin = load_global(c, src);
                 if (pin.cell == DEAD_CELL)

@@ -886,8 +886,16 @@ __global__ void k_brick_items(Ctx c, const int64_t *__restrict__ brick_start,
         int bx = find_box(brick_start, c.nbox, gb);
         const BoxDev &b = c.boxes[bx];
         int64_t k0 = b.key0 + (gb - b.brick0) * vol;
-        int cnt = offset[k0 + vol] - offset[k0];
-        nitems_of[gb] = (cnt + ITEM_MAX_PARTICLES - 1) / ITEM_MAX_PARTICLES;
+        const int cnt = offset[k0 + vol] - offset[k0];
+        if (cnt <= ITEM_MAX_PARTICLES) {
+            nitems_of[gb] = cnt > 0 ? 1 : 0;
+        } else if (c.halves) {
+            const int na = offset[k0 + vol / 2] - offset[k0];
+            nitems_of[gb] = (na + ITEM_MAX_PARTICLES - 1) / ITEM_MAX_PARTICLES +
+                            (cnt - na + ITEM_MAX_PARTICLES - 1) / ITEM_MAX_PARTICLES;
+        } else {
+            nitems_of[gb] = (cnt + ITEM_MAX_PARTICLES - 1) / ITEM_MAX_PARTICLES;
+        }
     }
 }
 
@@ -903,21 +911,38 @@ __global__ void k_write_items(Ctx c, const int64_t *__restrict__ brick_start,
         int bx = find_box(brick_start, c.nbox, gb);
         const BoxDev &b = c.boxes[bx];
         int64_t k0 = b.key0 + (gb - b.brick0) * vol;
-        int64_t p0 = offset[k0], p1 = offset[k0 + vol];
-        int m = nitems_of[gb];
+        const int64_t p0 = offset[k0], p1 = offset[k0 + vol];
+        const int m = nitems_of[gb];
         if (m == 0)
             continue;
-        int64_t chunk = (p1 - p0 + m - 1) / m;
         int64_t o = item_off[gb];
-        for (int t = 0; t < m; ++t) {
-            WorkItem w;
-            w.box = bx;
-            w.brick = (int32_t)(gb - b.brick0);
-            w.p0 = p0 + t * chunk;
-            w.p1 = min(p1, p0 + (t + 1) * chunk);
-            // a whole 64-cell brick splits at its 32nd cell (the start of the second half)
-            w.pm = (c.halves && m == 1) ? (int64_t)offset[k0 + vol / 2] : -1;
-            items[o + t] = w;
+        WorkItem w;
+        w.box = bx;
+        w.brick = (int32_t)(gb - b.brick0);
+        if (p1 - p0 <= ITEM_MAX_PARTICLES) {
+            // one item; a whole 64-cell brick splits at its 32nd cell (the
+            // start of the second half)
+            w.p0 = p0;
+            w.p1 = p1;
+            w.pm = c.halves ? (int64_t)offset[k0 + vol / 2] : -1;
+            w.step = 1;
+            items[o] = w;
+        } else {
+            // crowded: each part (the two halves, or the whole brick) into
+            // m_p interleaved items, item t taking positions t, t + m_p, ...
+            const int64_t pm = c.halves ? (int64_t)offset[k0 + vol / 2] : p1;
+            const int64_t lo[2] = {p0, pm}, hi[2] = {pm, p1};
+            for (int part = 0; part < 2; ++part) {
+                const int64_t n = hi[part] - lo[part];
+                const int mp = (int)((n + ITEM_MAX_PARTICLES - 1) / ITEM_MAX_PARTICLES);
+                for (int t = 0; t < mp; ++t) {
+                    w.p0 = lo[part] + t;
+                    w.p1 = hi[part];
+                    w.pm = -1;
+                    w.step = mp;
+                    items[o++] = w;
+                }
+            }
         }
         if (gb == nbt - 1)
             *nitems = item_off[nbt];

@@ -755,7 +755,9 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         (rc = c->alloc((char **)&c->s.tmp, (size_t)np * c->particle_bytes())) ||
         (rc = c->alloc(&c->s.brick_items, k.nbricks_total + 1)) ||
         (rc = c->alloc(&c->s.item_off, k.nbricks_total + 1)) ||
-        (rc = c->alloc(&c->s.items, k.nbricks_total + np / ITEM_MAX_PARTICLES + 2)) ||
+        // at most one item per brick, or per half of a crowded brick
+        // ceil(n_half / ITEM_MAX_PARTICLES) <= n_half / ITEM_MAX_PARTICLES + 1
+        (rc = c->alloc(&c->s.items, 2 * k.nbricks_total + np / ITEM_MAX_PARTICLES + 2)) ||
         (rc = c->alloc(&c->s.nitems, 1)) || (rc = c->alloc(&c->s.max_count, 1)) ||
         (rc = c->alloc(&c->work_ctr, 1)))
         return bail(rc);

@@ -101,13 +101,18 @@ struct BoxStats {
     int32_t pad;
 };
 
-// A contiguous run of sorted particles that all belong to one brick.  When the
-// item is a whole 64-cell brick, [p0, pm) and [pm, p1) are its two 32-cell
-// halves (one lane per cell); otherwise pm = -1.
+// A work item: the sorted positions p0, p0 + step, ... below p1, all in one
+// brick.  A brick of at most ITEM_MAX_PARTICLES is one item of step 1; when
+// it is a whole 64-cell brick, [p0, pm) and [pm, p1) are its two 32-cell
+// halves (one lane per cell), otherwise pm = -1.  A crowded brick becomes m
+// interleaved items per half (per brick without halves), item t taking the
+// positions t, t + m, ... of that part (step m, pm = -1), so that every item
+// spans all the part's cells, as the lanes need.
 struct WorkItem {
     int32_t box;
     int32_t brick;   // brick number inside the box
     int64_t p0, pm, p1;
+    int32_t step;
 };
 
 // Everything a kernel needs, passed by value.

@@ -187,9 +187,10 @@ __device__ __forceinline__ void stencil_coords(const BoxDev &b, const int ci[3],
 
 // Split of an item's particles over the block's warps: with halves, warps
 // 0..NW/2-1 take [p0, pm) and the rest [pm, p1); lane l works through the
-// l-th 1/32 of its range, the warps of a group interleaving inside it.
+// l-th 1/32 of its range, the warps of a group interleaving inside it.  The
+// range's k-th particle sits at position base + k * step.
 struct LaneRange {
-    int64_t base, cnt, q;
+    int64_t base, cnt, q, step;
     int first, stride;
 };
 
@@ -203,9 +204,11 @@ __device__ __forceinline__ LaneRange lane_range(const WorkItem &it, int wid, int
         r.cnt = hi ? it.p1 - it.pm : it.pm - it.p0;
         r.first = hi ? wid - half : wid;
         r.stride = half;
+        r.step = 1;
     } else {
         r.base = it.p0;
-        r.cnt = it.p1 - it.p0;
+        r.step = it.step;
+        r.cnt = (it.p1 - it.p0 + it.step - 1) / it.step;
         r.first = wid;
         r.stride = nw;
     }
