@@ -262,6 +262,25 @@ def test_one_step_matches_oracle(prec, name):
 
 
 @pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_crowded_bricks_split_into_interleaved_items(prec):
+    """A brick half holding more than one work item's worth of particles
+    (4096) is pushed as interleaved items (item t of m takes every m-th
+    particle); one push still equals the oracle's."""
+    box = tilt_B(wl.shock_2d(nx=64, ny=16, ppc=40.0, seed=15), 15, amp=0.1)
+    x, y = box.cell % 64, box.cell // 64
+    half = (x // 8) * 4 + (y // 8) * 2 + (y % 8) // 4
+    assert np.bincount(half).max() > 2 * 4096   # at least three items in some half
+    eng = _engine(box, prec)
+    _, _, xs, vs = sorted_oracle_state(box)
+    st = orc.State(box, xs, vs)
+    corr, md = st.push_only(box.dt)
+    eng.interp_push(box.dt, 1)
+    _compare_step(eng, box, st, corr, md, prec)
+    assert eng.status() == 0
+    eng.close()
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
 def test_steps_without_sorting_use_the_global_path(prec):
     """Eight pushes with no sort and no feedback: particles drift out of their
     bricks (up to ~3 cells) and take the global-memory path; the corrector
