@@ -265,11 +265,15 @@ def test_one_step_matches_oracle(prec, name):
 def test_crowded_bricks_split_into_interleaved_items(prec):
     """A brick half holding more than one work item's worth of particles
     (4096) is pushed as interleaved items (item t of m takes every m-th
-    particle); one push still equals the oracle's."""
-    box = tilt_B(wl.shock_2d(nx=64, ny=16, ppc=40.0, seed=15), 15, amp=0.1)
-    x, y = box.cell % 64, box.cell // 64
+    particle); one push still equals the oracle's.  The thermal recipe with
+    12,000 of its particles moved into the 32 cells of one half brick."""
+    box = tilt_B(wl.periodic_thermal_2d(nx=32, ny=16, ppc=40, dv_amp=0.3, seed=15), 15)
+    rng = np.random.default_rng(15)
+    k = rng.choice(box.np, 12000, replace=False)
+    box.cell[k] = (rng.integers(0, 8, k.size) + 32 * rng.integers(0, 4, k.size)).astype(np.int32)
+    x, y = box.cell % 32, box.cell // 32
     half = (x // 8) * 4 + (y // 8) * 2 + (y % 8) // 4
-    assert np.bincount(half).max() > 2 * 4096   # at least three items in some half
+    assert np.bincount(half).max() > 3 * 4096   # at least four items in that half
     eng = _engine(box, prec)
     _, _, xs, vs = sorted_oracle_state(box)
     st = orc.State(box, xs, vs)
