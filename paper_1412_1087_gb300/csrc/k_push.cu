@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push_f64(Ctx c, const WorkItem
         for (int64_t r = lr.first; r < lr.q; r += lr.stride) {
             int64_t loc = lane * lr.q + r;
             if (loc < lr.cnt)
-                vm2 = fmaxf(vm2, push_one_f64<D, FULL>(c, b, gm, k, lr.base + loc * lr.step, sF, sD, mout));
+                vm2 = fmaxf(vm2, push_one_f64<D, FULL>(c, b, gm, k, lr.base + (int32_t)loc * lr.step, sF, sD, mout));
         }
         unsigned vb = __reduce_max_sync(0xffffffffu, __float_as_uint(sqrtf(vm2)));
         if (lane == 0 && vb)

@@ -757,7 +757,8 @@ __device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restr
         {
             const LaneRange lr = lane_range(it, wid, NW);
             const int64_t base = lr.base, cnt = lr.cnt, lane0 = lane * lr.q, rb = lr.first, re = lr.q,
-                          rs = lr.stride, step = lr.step;
+                          rs = lr.stride;
+            const int32_t step = lr.step;
             // source particle of sorted position base + (lane0 + r) step; when the
             // push applies a sort the permutation entry is loaded one
             // iteration early.  (One code path for both cases, so that the
@@ -765,7 +766,7 @@ __device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restr
             const bool gather = c.perm_src != nullptr;
             auto valid = [&](int64_t r) { return r < re && lane0 + r < cnt; };
             auto src_of = [&](int64_t r) -> int64_t {
-                const int64_t j = base + (lane0 + r) * step;
+                const int64_t j = base + (int32_t)(lane0 + r) * step;
                 return gather ? (int64_t)__ldg(c.perm_src + j) : j;
             };
             if (STAGED<D>) {
@@ -789,7 +790,7 @@ __device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restr
                     cp_async_commit();
                     cp_async_wait_prev();
                     if (lane0 + r < cnt)
-                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + (lane0 + r) * step, load_staged(ring + st * RS),
+                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + (int32_t)(lane0 + r) * step, load_staged(ring + st * RS),
                                                            sFa, sFb, sD, mout));
                     st = st + 1 == NS ? 0 : st + 1;
                 }
@@ -800,7 +801,7 @@ __device__ __forceinline__ void push_items(const Ctx &c, const WorkItem *__restr
                         const int64_t src = sn;
                         if (valid(r + rs))
                             sn = src_of(r + rs);
-                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + (lane0 + r) * step, load_global(c, src), sFa,
+                        vm2 = fmaxf(vm2, push_one<D, FULL>(c, b, gm, k, base + (int32_t)(lane0 + r) * step, load_global(c, src), sFa,
                                                            sFb, sD, mout));
                     }
             }
@@ -960,7 +961,7 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_deposit_mixed(Ctx c, const Wor
             for (int64_t r = lr.first; r < lr.q; r += lr.stride) {
                 if (lane0 + r >= lr.cnt)
                     continue;
-                const int64_t j = lr.base + (lane0 + r) * lr.step;
+                const int64_t j = lr.base + (int32_t)(lane0 + r) * lr.step;
                 const int64_t src = gather ? (int64_t)__ldg(c.perm_src + j) : j;
                 const PIn pin = load_global(c, src);
                 if (pin.cell == DEAD_CELL)

@@ -926,6 +926,7 @@ __global__ void k_write_items(Ctx c, const int64_t *__restrict__ brick_start,
             w.p1 = p1;
             w.pm = c.halves ? (int64_t)offset[k0 + vol / 2] : -1;
             w.step = 1;
+            w.count = (int32_t)(p1 - p0);
             items[o] = w;
         } else {
             // crowded: each part (the two halves, or the whole brick) into
@@ -940,6 +941,7 @@ __global__ void k_write_items(Ctx c, const int64_t *__restrict__ brick_start,
                     w.p1 = hi[part];
                     w.pm = -1;
                     w.step = mp;
+                    w.count = (int32_t)((n - t + mp - 1) / mp);
                     items[o++] = w;
                 }
             }

@@ -113,6 +113,7 @@ struct WorkItem {
     int32_t brick;   // brick number inside the box
     int64_t p0, pm, p1;
     int32_t step;
+    int32_t count;   // positions in the item: ceil((p1 - p0) / step) <= ITEM_MAX_PARTICLES
 };
 
 // Everything a kernel needs, passed by value.

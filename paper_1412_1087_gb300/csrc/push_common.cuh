@@ -188,9 +188,11 @@ __device__ __forceinline__ void stencil_coords(const BoxDev &b, const int ci[3],
 // Split of an item's particles over the block's warps: with halves, warps
 // 0..NW/2-1 take [p0, pm) and the rest [pm, p1); lane l works through the
 // l-th 1/32 of its range, the warps of a group interleaving inside it.  The
-// range's k-th particle sits at position base + k * step.
+// range's k-th particle sits at position base + k * step (k * step stays
+// below 2^31: an item holds at most ITEM_MAX_PARTICLES).
 struct LaneRange {
-    int64_t base, cnt, q, step;
+    int64_t base, cnt, q;
+    int32_t step;
     int first, stride;
 };
 
@@ -208,7 +210,7 @@ __device__ __forceinline__ LaneRange lane_range(const WorkItem &it, int wid, int
     } else {
         r.base = it.p0;
         r.step = it.step;
-        r.cnt = (it.p1 - it.p0 + it.step - 1) / it.step;
+        r.cnt = it.count;
         r.first = wid;
         r.stride = nw;
     }
