@@ -251,6 +251,14 @@ def _time_engine(eng, dt, steps, warmup, sort_every, torch, per_push=True, looka
     return total, push, eng.launches() - l0
 
 
+def _whole_cycles(steps, k):
+    """(warm-up, timed) step counts for a side measurement at sort cadence k:
+    one whole cycle of warm-up, so that its last step sorts and the timed
+    steps start where every cycle starts, and whole cycles timed."""
+    k = max(int(k), 1)
+    return k, k * max(1, -(-int(steps) // k))
+
+
 def _sample_box(args, seed, size):
     """A bounded sample of the selected workload's recipe ('cpu' or 'err' size)."""
     from paper_1412_1087_gb300 import workloads as wl
@@ -863,10 +871,11 @@ def run_native(args):
     if args.fp64_steps > 0:
         e64 = m.Engine(boxes, precision=m.MHDPIC_PREC_FP64, device=dev, stream=stream)
         e64.set_sort_lookahead(args.sort_lookahead * dt)
-        t64, _, _ = _time_engine(e64, dt, args.fp64_steps, 1, args.sort_every, torch, lookahead=args.sort_lookahead)
-        v64 = npart * args.fp64_steps / (t64 / 1e3)
-        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": t64 / args.fp64_steps,
-                "steps": args.fp64_steps, "speedup_mixed_over_fp64": value / world / v64}
+        w64, n64 = _whole_cycles(args.fp64_steps, args.sort_every)
+        t64, _, _ = _time_engine(e64, dt, n64, w64, args.sort_every, torch, lookahead=args.sort_lookahead)
+        v64 = npart * n64 / (t64 / 1e3)
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": t64 / n64,
+                "steps": n64, "speedup_mixed_over_fp64": value / world / v64}
         e64.close()
         del e64
         torch.cuda.empty_cache()
@@ -891,15 +900,16 @@ def run_native(args):
         for mem, h2d, d2h in runs:
             eh = m.Engine(boxes, precision=m.MHDPIC_PREC_MIXED, memory=mem, brick=brick, device=dev, stream=stream)
             eh.set_sort_lookahead(args.sort_lookahead * dt)
-            te, _, _ = _time_engine(eh, dt, args.e2e_steps, 1, args.sort_every, torch, per_push=False,
+            we, ne = _whole_cycles(args.e2e_steps, args.sort_every)
+            te, _, _ = _time_engine(eh, dt, ne, we, args.sort_every, torch, per_push=False,
                                     lookahead=args.sort_lookahead)
             eh.close()
             del eh
             torch.cuda.empty_cache()
-            te, e2e_steps = aggregate_ranks(te, float(npart) * args.e2e_steps, dist if world > 1 else None, dev)
+            te, e2e_steps = aggregate_ranks(te, float(npart) * ne, dist if world > 1 else None, dev)
             res.append({"value": e2e_steps / (te / 1e3), "unit": UNIT,
                         "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                        "steps": args.e2e_steps, "ms_per_step": te / args.e2e_steps})
+                        "steps": ne, "ms_per_step": te / ne})
         e2e = dict(res[0], mode="particles resident on the GPU, gas state in pinned host memory")
         if len(res) > 1:
             e2e_all_host = dict(res[1], mode="particles and gas in pinned host memory")
