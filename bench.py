@@ -493,7 +493,8 @@ def _measure_workload(name, boxes, dt, args, torch, m, dev, stream, peak, peak_k
     eng.run(dt, 20, 0)
     k = eng.sort_cadence()
     torch.cuda.synchronize()
-    _, push_ms, _ = _time_engine(eng, dt, args.steps, args.warmup, k, torch, lookahead=args.sort_lookahead)
+    _, push_ms, _ = _time_engine(eng, dt, args.steps, _whole_cycles(args.warmup, k)[1], k, torch,
+                                 lookahead=args.sort_lookahead)
     for _ in range(args.warmup):
         eng.run(dt, max(k, 1), k)
     torch.cuda.synchronize()
@@ -600,9 +601,12 @@ def run_native(args):
 
     # eager steps, one call each, so that every push kernel is bracketed by
     # events on the library's stream: the push kernel's roofline
-    eager_ms, push_ms, _ = _time_engine(eng, dt, args.steps, args.warmup, args.sort_every, torch,
+    # warm-up rounded up to whole sort cycles: the timed pushes keep the
+    # steady-state distances from their sorts
+    eager_warm = _whole_cycles(args.warmup, args.sort_every)[1]
+    eager_ms, push_ms, _ = _time_engine(eng, dt, args.steps, eager_warm, args.sort_every, torch,
                                         lookahead=args.sort_lookahead)
-    steps_done += args.steps + args.warmup
+    steps_done += args.steps + eager_warm
     # the sort alone (keys, scan, scatter, segment sort, work list), a few calls
     sev0, sev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     eng.sort()
