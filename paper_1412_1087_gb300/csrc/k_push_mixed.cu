@@ -523,7 +523,8 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
 
     // drift to x^(n+1/2) with u = v / gamma (a particle at an open face is
     // held just inside it, deposits its corrector and then leaves)
-    const float ign = rsqrtf(fmaf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2], k.invC2, 1.f));
+    const float sn = fmaf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2], k.invC2, 1.f);   // gamma^2
+    const float ign = rsqrtf(sn);
     bool leaving = false;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -573,22 +574,26 @@ __device__ __forceinline__ float push_one(const Ctx &c, const BoxDev &b, const I
     // Boris: v0 = v + (h/2)E; b = (h/2)B/gamma(v0); v1 = v0 + 2(v0 + v0 x b) x b/(1+b^2)
     const float e0 = k.hh * E[0], e1 = k.hh * E[1], e2 = k.hh * E[2];
     const float v00 = v[0] + e0, v01 = v[1] + e1, v02 = v[2] + e2;
-    const float ig1 = rsqrtf(fmaf(v00 * v00 + v01 * v01 + v02 * v02, k.invC2, 1.f));
+    const float s1 = fmaf(v00 * v00 + v01 * v01 + v02 * v02, k.invC2, 1.f);
+    const float ig1 = rsqrtf(s1);
     const float hb = k.hh * ig1;
     const float b0 = hb * Bf[0], b1 = hb * Bf[1], b2 = hb * Bf[2];
     const float t0 = v00 + (v01 * b2 - v02 * b1), t1 = v01 + (v02 * b0 - v00 * b2),
                 t2 = v02 + (v00 * b1 - v01 * b0);
-    const float s2 = 2.f / (1.f + b0 * b0 + b1 * b1 + b2 * b2);
+    // the divisions below have denominators of 1 or more: the fast division
+    // (2 ulp) in place of the IEEE sequence
+    const float s2 = __fdividef(2.f, 1.f + b0 * b0 + b1 * b1 + b2 * b2);
     const float r0 = s2 * (t1 * b2 - t2 * b1), r1 = s2 * (t2 * b0 - t0 * b2), r2 = s2 * (t0 * b1 - t1 * b0);
     const float v10 = v00 + r0, v11 = v01 + r1, v12 = v02 + r2;
     const float vk[3] = {v10 + e0, v11 + e1, v12 + e2};   // after the second kick, FP32
 
     // dv = h E + rot without cancellation; the rotation keeps |v|, so dE_k is
     // the change of the two half kicks, E_k(a) - E_k(b) = (a-b).(a+b)/(ga+gb)
-    const float ig2k = rsqrtf(fmaf(vsq3(vk), k.invC2, 1.f));
-    const float gn = 1.f / ign, g1 = 1.f / ig1, g2 = 1.f / ig2k;
-    const float dEk = (e0 * (vk[0] + v10) + e1 * (vk[1] + v11) + e2 * (vk[2] + v12)) / (g2 + g1) +
-                      (e0 * (v00 + v[0]) + e1 * (v01 + v[1]) + e2 * (v02 + v[2])) / (g1 + gn);
+    const float s2k = fmaf(vsq3(vk), k.invC2, 1.f);
+    const float ig2k = rsqrtf(s2k);
+    const float gn = sn * ign, g1 = s1 * ig1, g2 = s2k * ig2k;   // gamma = gamma^2 / gamma
+    const float dEk = __fdividef(e0 * (vk[0] + v10) + e1 * (vk[1] + v11) + e2 * (vk[2] + v12), g2 + g1) +
+                      __fdividef(e0 * (v00 + v[0]) + e1 * (v01 + v[1]) + e2 * (v02 + v[2]), g1 + gn);
     const float dv[3] = {pinned(2.f * e0 + r0), pinned(2.f * e1 + r1), pinned(2.f * e2 + r2)};
     {
         const float qc[4] = {pinned(-k.m * dv[0]), pinned(-k.m * dv[1]), pinned(-k.m * dv[2]), pinned(-k.m * dEk)};
