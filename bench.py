@@ -62,10 +62,10 @@ GAS_CORRECT_BYTES = 32 + 56 + 56 + 56 + 32
 # one); traffic scales with the particle count (cells scale alike at fixed
 # particles per cell).  Remove an entry whenever its kernel changes, until it
 # is measured again.  Both from 'ncu --set full' of one launch: the 3-D beam at
-# 64^3 x 32 (591.3 MB for 8,388,608 particles), Bell at 512^2 x 64 (1187.5 MB
+# 64^3 x 32 (590.9 MB for 8,388,608 particles), Bell at 512^2 x 64 (1183.5 MB
 # for 16,777,216 particles); commands in profiles/.
-PUSH_TRAFFIC_BYTES_PER_PARTICLE = {"alfvenic_beam_3d": 591.342592e6 / 8388608,
-                                   "bell_2d": 1187.495936e6 / 16777216}
+PUSH_TRAFFIC_BYTES_PER_PARTICLE = {"alfvenic_beam_3d": 590.871296e6 / 8388608,
+                                   "bell_2d": 1183.462144e6 / 16777216}
 # int32 shared-memory atomic adds per particle of the push's two TSC deposits:
 # 8 channels on 3^D cells, one word per contribution for the charge density
 # and two (hi, lo) for the other seven channels, and one contribution count
