@@ -141,6 +141,11 @@ struct mhdpic_ctx {
     // the stream waits for ev_h2d before the feedback
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_push = nullptr, ev_h2d = nullptr;
+    // MEM_DEVICE, a sort every step: the feedback runs on side_stream beside
+    // the sort that follows the push (ev_fork after the push, ev_join after
+    // the feedback)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool push_marked = false;       // ev_push marks the work before the last push
     uint64_t gas_copies = 0;        // gas copies enqueued so far
     uint64_t gas_copies_push = 0;   // ... when the last push was enqueued
@@ -579,6 +584,14 @@ int mhdpic_destroy(mhdpic_ctx *c)
         cudaEventDestroy(c->ev_push);
     if (c->ev_h2d)
         cudaEventDestroy(c->ev_h2d);
+    if (c->side_stream) {
+        cudaStreamSynchronize(c->side_stream);
+        cudaStreamDestroy(c->side_stream);
+    }
+    if (c->ev_fork)
+        cudaEventDestroy(c->ev_fork);
+    if (c->ev_join)
+        cudaEventDestroy(c->ev_join);
     if (c->graph)
         cudaGraphExecDestroy(c->graph);
     for (void *p : c->allocs)
@@ -615,6 +628,15 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
             e = cudaEventCreateWithFlags(&c->ev_h2d, cudaEventDisableTiming);
         if (e != cudaSuccess)
             return bail(cuda_fail(e, "copy stream"));
+    }
+    if (c->mem == MHDPIC_MEM_DEVICE) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess)
+            return bail(cuda_fail(e, "side stream"));
     }
     Ctx &k = c->k;
     k.nbox = nbox;
@@ -1387,6 +1409,30 @@ int fused_step(mhdpic_ctx *c, double dt)
 int run_one_step(mhdpic_ctx *c, double dt, int k)
 {
     int rc;
+    if (k == 1 && c->side_stream) {
+        // every step sorts: the push (with its scales), then the feedback
+        // and staging on the second stream beside the sort; they share no
+        // data (the feedback reads the deposits and writes the gas and the
+        // staged fields, the sort reads the particles and writes its
+        // scratch), and the stream waits for both before the next step
+        if ((rc = mhdpic_interp_push(c, dt, 1)))
+            return rc;
+        CK(cudaEventRecord(c->ev_fork, c->stream));
+        CK(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
+        rc = check_launch(c, launch_prep(c->k, c->cur, 1, c->side_stream));
+        if (rc == MHDPIC_OK) {
+            c->next_clear = true;
+            c->fields_stale = false;
+            c->step_in_cycle = 0;
+            rc = do_sort(c, nullptr, nullptr);
+        }
+        // joined on every way out (a capture needs the side stream back)
+        const cudaError_t e1 = cudaEventRecord(c->ev_join, c->side_stream);
+        const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(c->stream, c->ev_join, 0) : e1;
+        if (rc == MHDPIC_OK && e2 != cudaSuccess)
+            return cuda_fail(e2, "joining the side stream");
+        return rc;
+    }
     if (fused_ok(c)) {
         if ((rc = fused_step(c, dt)))
             return rc;

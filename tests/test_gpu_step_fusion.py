@@ -71,8 +71,39 @@ def test_one_launch_steps_equal_separate_launches(name, k):
     for a, b in zip(*outs):
         assert np.array_equal(a, b)
     assert outs[1][-1] == 0
-    # the corrector-scale and feedback kernels of every step are folded into the push
-    assert launches[0] - launches[1] == 2 * nsteps, launches
+    # the corrector-scale and feedback kernels of every step are folded into
+    # the push; at a sort every step both run the push, then the feedback
+    # beside the sort
+    assert launches[0] - launches[1] == (0 if k == 1 else 2 * nsteps), launches
+
+
+@pytest.mark.parametrize("name", ["beam3d", "thermal2d_hall", "five_boxes"])
+def test_feedback_beside_the_sort_equals_the_calls_in_turn(name):
+    """At a sort every step, mhdpic_run puts each step's feedback on a second
+    stream beside the sort that follows the push (captured in the step graph);
+    the result is the same bits as push, feedback and sort called in turn."""
+    boxes = _case(name)
+    dt = min(b.dt for b in boxes)
+    stream = torch.cuda.Stream()
+    outs = []
+    for graph in (True, False):
+        eng = m.Engine(boxes, precision=MIXED, stream=stream)
+        eng.set_sort_lookahead(0.5 * dt)
+        if graph:
+            eng.run(dt, 7, 1)   # one eager cycle, the capture, replays
+        else:
+            for _ in range(7):
+                eng.interp_push(dt, 1)
+                eng.apply_feedback()
+                eng.sort()
+        stream.synchronize()
+        tot = eng.apply_feedback(totals=True)
+        outs.append((mixed_rows(eng), eng.deposits(1).cpu().numpy(), eng.mom.cpu().numpy(),
+                     eng.egas.cpu().numpy(), eng.fields().cpu().numpy(), tot, eng.status()))
+        eng.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    assert outs[0][-1] == 0
 
 
 def test_one_launch_step_is_one_launch_between_sorts():
@@ -139,7 +170,7 @@ def test_barrier_limit_raises_a_flag_instead_of_waiting():
     eng = m.Engine(boxes, precision=MIXED, stream=stream)
     assert eng.step_fusion() == 1
     m.mhdpic_debug_set_barrier_limit(eng.ctx, 1)
-    eng.run(dt, 1, 1)
+    eng.run(dt, 1, 2)   # a cycle of two steps: the first is the one-launch step
     stream.synchronize()
     flags = eng.status()
     assert flags & 64, m.status_names(flags)
