@@ -637,10 +637,14 @@ def run_native(args):
     clocks = clk.summary()
     steps_done += args.warmup * max(args.sort_every, 1) + args.steps
     # the same graph-replayed steps with the step split into its separate
-    # launches (scales, push, feedback + staging) against the one-launch
-    # step the timed region used, on this machine in this run
-    fusion = {"one_launch_steps": bool(eng.step_fusion())}
-    if fusion["one_launch_steps"] and args.fusion_ab:
+    # launches (scales, push, feedback + staging) in turn on one stream
+    # against the form the timed region used: the one-launch step, or at a
+    # sort every step the feedback on a second stream beside the sort; on
+    # this box in this run
+    fused_form = "feedback_beside_sort" if args.sort_every == 1 else "one_launch"
+    fusion = {"one_launch_steps": bool(eng.step_fusion()) and args.sort_every != 1,
+              "form": fused_form if eng.step_fusion() else "separate_launches"}
+    if eng.step_fusion() and args.fusion_ab:
         ab = {}
         for fuse in (False, True):
             eng.set_step_fusion(fuse)
@@ -650,7 +654,7 @@ def run_native(args):
             eng.run(dt, args.steps, args.sort_every)
             ev1.record(stream)
             torch.cuda.synchronize()
-            ab["one_launch" if fuse else "separate_launches"] = ev0.elapsed_time(ev1) / args.steps
+            ab[fused_form if fuse else "separate_launches"] = ev0.elapsed_time(ev1) / args.steps
             steps_done += max(args.sort_every, 1) * 2 + args.steps
         fusion["ms_per_step"] = ab
     # the drift is taken over at least args.conservation_steps steps in all:

@@ -1409,7 +1409,7 @@ int fused_step(mhdpic_ctx *c, double dt)
 int run_one_step(mhdpic_ctx *c, double dt, int k)
 {
     int rc;
-    if (k == 1 && c->side_stream) {
+    if (k == 1 && c->side_stream && c->fuse) {
         // every step sorts: the push (with its scales), then the feedback
         // and staging on the second stream beside the sort; they share no
         // data (the feedback reads the deposits and writes the gas and the
