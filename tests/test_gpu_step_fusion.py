@@ -77,17 +77,25 @@ def test_one_launch_steps_equal_separate_launches(name, k):
     assert launches[0] - launches[1] == (0 if k == 1 else 2 * nsteps), launches
 
 
+def _particle_rows(eng):
+    if eng.x is None:
+        return mixed_rows(eng)
+    return np.vstack([eng.x.cpu().numpy(), eng.velocities().cpu().numpy()])
+
+
+@pytest.mark.parametrize("prec", [MIXED, m.MHDPIC_PREC_FP64])
 @pytest.mark.parametrize("name", ["beam3d", "thermal2d_hall", "five_boxes"])
-def test_feedback_beside_the_sort_equals_the_calls_in_turn(name):
+def test_feedback_beside_the_sort_equals_the_calls_in_turn(name, prec):
     """At a sort every step, mhdpic_run puts each step's feedback on a second
     stream beside the sort that follows the push (captured in the step graph);
-    the result is the same bits as push, feedback and sort called in turn."""
+    the result is the same bits as push, feedback and sort called in turn, in
+    either precision."""
     boxes = _case(name)
     dt = min(b.dt for b in boxes)
     stream = torch.cuda.Stream()
     outs = []
     for graph in (True, False):
-        eng = m.Engine(boxes, precision=MIXED, stream=stream)
+        eng = m.Engine(boxes, precision=prec, stream=stream)
         eng.set_sort_lookahead(0.5 * dt)
         if graph:
             eng.run(dt, 7, 1)   # one eager cycle, the capture, replays
@@ -98,7 +106,7 @@ def test_feedback_beside_the_sort_equals_the_calls_in_turn(name):
                 eng.sort()
         stream.synchronize()
         tot = eng.apply_feedback(totals=True)
-        outs.append((mixed_rows(eng), eng.deposits(1).cpu().numpy(), eng.mom.cpu().numpy(),
+        outs.append((_particle_rows(eng), eng.deposits(1).cpu().numpy(), eng.mom.cpu().numpy(),
                      eng.egas.cpu().numpy(), eng.fields().cpu().numpy(), tot, eng.status()))
         eng.close()
     for a, b in zip(*outs):
