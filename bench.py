@@ -74,6 +74,17 @@ SMEM_ATOMICS_PER_PARTICLE = {3: 27 * (1 + 7 * 2) + 2, 2: 9 * (1 + 7 * 2) + 2}
 # SM-cycles per warp-wide 32-bit shared atomic add with its 32 lanes on 32
 # banks, each adding its own value (standalone probe on a GB300)
 SMEM_ATOMIC_CYCLES = 1.1
+# Shared-memory wavefronts per particle of the push (its shared loads,
+# stores and atomics, bank conflicts included), from the same captures as
+# the traffic above (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum:
+# 307,599,692 for the 3-D beam at 64^3 x 32, 186,552,819 for Bell at
+# 512^2 x 64); remove an entry whenever its kernel changes.
+PUSH_SHARED_WAVEFRONTS_PER_PARTICLE = {"alfvenic_beam_3d": 307599692 / 8388608,
+                                       "bell_2d": 186552819 / 16777216}
+# wavefronts per SM-cycle that a standalone probe of warp-wide shared atomic
+# adds reaches on this GPU with the deposit tile's own address pattern (the
+# highest rate measured for the pipe)
+SHARED_PIPE_WAVEFRONTS_PER_CYCLE = 0.93
 
 
 def _rank_env():
@@ -205,6 +216,18 @@ def smem_atomic_roofline(ndim, npart, push_avg_s, sm_mhz, nsm):
             "unit": "G warp atomic instructions/s", "frac": achieved / peak,
             "atomics_per_particle": per, "cycles_per_instruction": SMEM_ATOMIC_CYCLES,
             "sm_mhz": sm_mhz, "sms": nsm}
+
+
+def shared_pipe_roofline(wavefronts_per_particle, npart, push_avg_s, sm_mhz, nsm):
+    """The push against the shared-memory pipe it is bound by: its measured
+    wavefronts per particle (conflicts included) per second over the probe's
+    rate on every SM at the given clock."""
+    achieved = wavefronts_per_particle * npart / push_avg_s / 1e9
+    peak = nsm * sm_mhz * 1e6 * SHARED_PIPE_WAVEFRONTS_PER_CYCLE / 1e9
+    return {"bound": "shared-memory pipe", "achieved": achieved, "peak": peak,
+            "unit": "G wavefronts/s", "frac": achieved / peak,
+            "wavefronts_per_particle": wavefronts_per_particle,
+            "wavefronts_per_cycle_peak": SHARED_PIPE_WAVEFRONTS_PER_CYCLE, "sm_mhz": sm_mhz, "sms": nsm}
 
 
 def _peaks():
@@ -857,8 +880,13 @@ def run_native(args):
         if not mhz:
             mhz, mhz_kind = 2070.0, "nominal maximum"
         smem = dict(smem_atomic_roofline(ndim, npart, push_avg_s, float(mhz), nsm), sm_mhz_kind=mhz_kind)
+        pipe = None
+        if args.workload in PUSH_SHARED_WAVEFRONTS_PER_PARTICLE:
+            pipe = dict(shared_pipe_roofline(PUSH_SHARED_WAVEFRONTS_PER_PARTICLE[args.workload], npart, push_avg_s,
+                                             float(mhz), nsm), sm_mhz_kind=mhz_kind)
     except Exception as e:  # a secondary figure never costs the line
         smem = {"unavailable": "%s: %s" % (type(e).__name__, e)}
+        pipe = None
     traffic = None
     if args.workload in PUSH_TRAFFIC_BYTES_PER_PARTICLE:
         traffic = PUSH_TRAFFIC_BYTES_PER_PARTICLE[args.workload] * npart
@@ -969,6 +997,7 @@ def run_native(args):
                          "kernel": "k_push_mixed<%d,full>" % ndim, "peak_kind": peak_kind,
                          "bytes_per_launch": bytes_push, "avg_launch_ms": push_avg_s * 1e3},
             "smem_atomics": smem,
+            "shared_pipe": pipe,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

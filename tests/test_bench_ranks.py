@@ -156,6 +156,20 @@ def test_shared_atomic_roofline_arithmetic():
     assert r2["atomics_per_particle"] == 137 and abs(r2["achieved"] - 137e-9) < 1e-20
 
 
+def test_shared_pipe_roofline_arithmetic():
+    """36.669 wavefronts per particle over 32,000 particles in 1 us is 1173.4
+    G wavefronts/s; the pipe does 0.93 per SM-cycle on 152 SMs at 2000 MHz,
+    282.72 G/s.  The figures per particle are those of the captures."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.shared_pipe_roofline(36.669, 32 * 1000, 1e-6, 2000.0, 152)
+    assert abs(r["achieved"] - 36.669 * 32000 / 1e-6 / 1e9) < 1e-9 * r["achieved"]
+    assert abs(r["peak"] - 152 * 2000e6 * 0.93 / 1e9) < 1e-9 * r["peak"]
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15
+    w = bench.PUSH_SHARED_WAVEFRONTS_PER_PARTICLE
+    assert abs(w["alfvenic_beam_3d"] - 36.669) < 1e-3 and abs(w["bell_2d"] - 11.119) < 1e-3
+
+
 def test_clock_record_parsing(tmp_path):
     """The nvidia-smi rows sampled during the timed region: median SM clock
     under load, the maximum clock, and every throttle reason seen active."""
