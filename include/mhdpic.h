@@ -493,8 +493,9 @@ int mhdpic_gas_correct(mhdpic_ctx *ctx, double dt, int32_t model, double *totals
  * Whole cycles are captured once into a CUDA graph and replayed (re-captured
  * when dt or the cadence changes); with the legacy default stream or host
  * buffers the steps run eagerly.  Each step without a sort is one kernel
- * launch where mhdpic_set_step_fusion allows it; with device buffers and a
- * sort every step, the feedback runs on a second stream beside the sort.
+ * launch where mhdpic_set_step_fusion allows it; with a sort every step and
+ * device buffers or the gas in host memory, the feedback runs on a second
+ * stream beside the sort.
  * Asynchronous except while tuning.
  */
 int mhdpic_run(mhdpic_ctx *ctx, double dt, int32_t nsteps, int32_t sort_every);
@@ -506,8 +507,9 @@ int mhdpic_run(mhdpic_ctx *ctx, double dt, int32_t nsteps, int32_t sort_every);
  * next step run in one persistent cooperative kernel, its phases separated by
  * grid-wide barriers (the paper's particle step of App. A.2-A.3 followed by
  * the corrector's feedback, eq:scheme); a step with a sort adds the sort's
- * launches.  At a sort cadence of 1 with device buffers (either precision)
- * it instead puts each step's feedback and field staging on a second stream
+ * launches.  At a sort cadence of 1 with device buffers or the gas in host
+ * memory (either precision) it instead puts each step's feedback and field
+ * staging (and the gas copies of MHDPIC_MEM_HOST_GAS) on a second stream
  * beside the sort that follows the push, the two joined before the next
  * step; with enable == 0 they run in turn on the context's stream.  The
  * one-launch step applies to mixed precision with device buffers and no open

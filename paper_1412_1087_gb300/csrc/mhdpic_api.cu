@@ -234,24 +234,25 @@ int copy_gas(mhdpic_ctx *c, bool to_device, bool all)
     return copy_gas(c, to_device, all, c->stream);
 }
 
-// The gas upload of a feedback.  Right after a push (nothing launched and no
-// gas copied since it was enqueued) in MEM_HOST_GAS mode it runs on
-// copy_stream, after the work enqueued before the push and beside the push
-// itself, which reads only the staged fields; the stream then waits for it.
-// Otherwise it is enqueued on the stream.
-int upload_gas_for_feedback(mhdpic_ctx *c)
+// The gas upload of a feedback, for the feedback enqueued next on stream
+// `waiter`.  Right after a push (nothing launched and no gas copied since it
+// was enqueued) in MEM_HOST_GAS mode it runs on copy_stream, after the work
+// enqueued before the push and beside the push itself, which reads only the
+// staged fields; `waiter` then waits for it.  Otherwise it is enqueued on
+// `waiter`.
+int upload_gas_for_feedback(mhdpic_ctx *c, cudaStream_t waiter)
 {
     const bool beside = c->mem == MHDPIC_MEM_HOST_GAS && c->copy_stream && c->push_marked &&
                         c->launches == c->launches_push && c->gas_copies == c->gas_copies_push;
     c->push_marked = false;
     if (!beside)
-        return copy_gas(c, true, true);
+        return copy_gas(c, true, true, waiter);
     CK(cudaStreamWaitEvent(c->copy_stream, c->ev_push, 0));
     int rc = copy_gas(c, true, true, c->copy_stream);
     if (rc)
         return rc;
     CK(cudaEventRecord(c->ev_h2d, c->copy_stream));
-    CK(cudaStreamWaitEvent(c->stream, c->ev_h2d, 0));
+    CK(cudaStreamWaitEvent(waiter, c->ev_h2d, 0));
     return MHDPIC_OK;
 }
 
@@ -629,7 +630,7 @@ int mhdpic_init(mhdpic_ctx **out, int32_t nbox, const mhdpic_grid *grids, const 
         if (e != cudaSuccess)
             return bail(cuda_fail(e, "copy stream"));
     }
-    if (c->mem == MHDPIC_MEM_DEVICE) {
+    if (c->mem == MHDPIC_MEM_DEVICE || c->mem == MHDPIC_MEM_HOST_GAS) {
         cudaError_t e = cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking);
         if (e == cudaSuccess)
             e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
@@ -1025,7 +1026,7 @@ int mhdpic_apply_feedback(mhdpic_ctx *c, double *totals_out)
     if (!c || !c->valid)
         return fail(MHDPIC_E_STATE, "invalid context");
     int rc;
-    if ((rc = upload_gas_for_feedback(c)))
+    if ((rc = upload_gas_for_feedback(c, c->stream)))
         return rc;
     if ((rc = do_prep(c, 1)))
         return rc;
@@ -1411,18 +1412,25 @@ int run_one_step(mhdpic_ctx *c, double dt, int k)
     int rc;
     if (k == 1 && c->side_stream && c->fuse) {
         // every step sorts: the push (with its scales), then the feedback
-        // and staging on the second stream beside the sort; they share no
-        // data (the feedback reads the deposits and writes the gas and the
-        // staged fields, the sort reads the particles and writes its
-        // scratch), and the stream waits for both before the next step
+        // and staging on the second stream beside the sort (with the gas in
+        // host memory, also the gas upload's wait and the download of the
+        // result); they share no data (the feedback reads the deposits and
+        // the gas and writes the gas and the staged fields, the sort reads
+        // the particles and writes its scratch), and the stream waits for
+        // both before the next step
         if ((rc = mhdpic_interp_push(c, dt, 1)))
             return rc;
         CK(cudaEventRecord(c->ev_fork, c->stream));
         CK(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
-        rc = check_launch(c, launch_prep(c->k, c->cur, 1, c->side_stream));
+        rc = upload_gas_for_feedback(c, c->side_stream);
+        if (rc == MHDPIC_OK)
+            rc = check_launch(c, launch_prep(c->k, c->cur, 1, c->side_stream));
         if (rc == MHDPIC_OK) {
             c->next_clear = true;
             c->fields_stale = false;
+            rc = copy_gas(c, false, false, c->side_stream);
+        }
+        if (rc == MHDPIC_OK) {
             c->step_in_cycle = 0;
             rc = do_sort(c, nullptr, nullptr);
         }

@@ -83,19 +83,21 @@ def _particle_rows(eng):
     return np.vstack([eng.x.cpu().numpy(), eng.velocities().cpu().numpy()])
 
 
-@pytest.mark.parametrize("prec", [MIXED, m.MHDPIC_PREC_FP64])
+@pytest.mark.parametrize("prec,mem", [(MIXED, m.MHDPIC_MEM_DEVICE), (m.MHDPIC_PREC_FP64, m.MHDPIC_MEM_DEVICE),
+                                      (MIXED, m.MHDPIC_MEM_HOST_GAS)])
 @pytest.mark.parametrize("name", ["beam3d", "thermal2d_hall", "five_boxes"])
-def test_feedback_beside_the_sort_equals_the_calls_in_turn(name, prec):
+def test_feedback_beside_the_sort_equals_the_calls_in_turn(name, prec, mem):
     """At a sort every step, mhdpic_run puts each step's feedback on a second
-    stream beside the sort that follows the push (captured in the step graph);
-    the result is the same bits as push, feedback and sort called in turn, in
-    either precision."""
+    stream beside the sort that follows the push (captured in the step graph;
+    with the gas in host memory also the gas copies, eagerly); the result is
+    the same bits as push, feedback and sort called in turn, in either
+    precision."""
     boxes = _case(name)
     dt = min(b.dt for b in boxes)
     stream = torch.cuda.Stream()
     outs = []
     for graph in (True, False):
-        eng = m.Engine(boxes, precision=prec, stream=stream)
+        eng = m.Engine(boxes, precision=prec, memory=mem, stream=stream)
         eng.set_sort_lookahead(0.5 * dt)
         if graph:
             eng.run(dt, 7, 1)   # one eager cycle, the capture, replays
